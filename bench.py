@@ -1,0 +1,305 @@
+"""Benchmark of the GeoDock pose search on B300: ligands/s and pose-evals/s.
+
+A step is one pass of the whole hot path over one batch: every ligand of the batched
+workload (4,096 ligands of 20-80 atoms, 2-12 rotamers; 64^3 pocket at 0.375 A;
+256 Euler restarts x 64 angles) placed, swept and reduced to its best pose by one
+graph-captured persistent launch of the fused search kernel.
+
+  value : ligands/s with the packed batch resident in HBM (gd_job_launch replays the
+          search; the L2 is flushed between steps, outside the timed events)
+  e2e   : the same metric through gd_dock_batch + gd_fetch_results with host buffers:
+          validation/packing, the host->device copy, the search and the copy of the
+          results back are all inside the timed region
+  roofline : FP32-pipe bound of the search kernel (see the design doc for the op counts)
+  cpu_baseline : the FP64 oracle on the host cores, on a bounded sample
+
+--impl reference times the oracle itself (the paper has no code to run) on the same
+workload and metric.  With torchrun (N > 1) every rank docks its own 4,096 ligands
+(weak scaling, no collective on the data path; one scalar all-reduce for timing).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1901_06229_b300 import synth  # noqa: E402
+
+METRIC = "ligands/s (pose search, 1 B300)"
+FP32_OPS_PER_PAIR = 7        # 3 FSUB, FMUL, 2 FFMA, 1 FMNMX
+FP32_OPS_PER_ATOM_MOVE = 18  # rotation about the bond axis (15) + cell coordinates (3 FFMA)
+FP32_OPS_PER_CANDIDATE = 19  # Rodrigues matrix of the candidate angle
+FP32_LANES_PER_SM = 128
+
+
+def workload_for(name, rank):
+    if name == "batched":
+        return synth.workload_batched(4096, start=4096 * rank)
+    if name == "large":
+        return synth.workload_large(512, start=512 * rank)
+    if name == "single":
+        return synth.workload_single()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(w, flush):
+    p = w.params
+    b = w.batch
+    n = np.diff(b.atom_off)
+    return {"workload": w.name, "ligands": int(b.n_ligands), "atoms": [int(n.min()), int(n.max())],
+            "rotamers": int(len(b.rot_bond)), "grid": list(w.pocket.grid.shape[::-1]),
+            "spacing": w.pocket.spacing, "orientations": p.n_orient, "euler": [p.n_alpha, p.n_beta, p.n_gamma],
+            "angles": p.n_angles, "repetitions": p.repetitions, "bump_dist": p.bump_dist,
+            "l2": flush}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 7]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[4 + k] and "Not" not in r[4 + k]})
+        busy = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": float(np.median(busy or sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(w, seconds=12.0):
+    """Oracle throughput on the host cores over a bounded sample of the workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    done, t0, i = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds and i < w.batch.n_ligands:
+        idx = list(range(i, min(i + cores, w.batch.n_ligands)))
+        oracle.dock_batch(w.batch.subset(idx), w.pocket, w.params, n_threads=cores)
+        done += len(idx)
+        i += len(idx)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "ligands/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {done} ligands of {w.name}, {dt:.1f} s, one std::thread per core"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = workload_for(args.workload, 0)
+    cores = os.cpu_count() or 1
+    import oracle
+    per_step = max(cores, 8)
+    times = []
+    i = 0
+    for s in range(args.warmup + args.steps):
+        idx = [(i + k) % w.batch.n_ligands for k in range(per_step)]
+        i += per_step
+        t0 = time.perf_counter()
+        oracle.dock_batch(w.batch.subset(idx), w.pocket, w.params, n_threads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    dt = float(np.sum(times))
+    v = per_step * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ligands/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w, "n/a (CPU)"),
+        "cpu_baseline": {"value": v, "unit": "ligands/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} ligands per step of {w.name}"},
+        "e2e": {"value": v, "unit": "ligands/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single"])
+    ap.add_argument("--tile", type=int, default=-1, help="-1 autotune, 0 default, >0 tile id")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    assert args.warmup >= 3 or args.steps <= 3, "at least 3 warm-up steps"
+
+    import torch
+    from paper_1901_06229_b300 import geodock as gdk
+
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    w = workload_for(args.workload, rank)
+    stream = torch.cuda.Stream()
+    ctx = gdk.Context(dev)
+    pk = ctx.load_pocket(w.pocket)
+    tile = args.tile
+    if tile == -1:
+        tile, _ = ctx.autotune(pk, w.batch, w.params, max_ligands=512, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    # ---- value: device-resident inputs, one graph replay per step -------------------------
+    job = ctx.dock_batch(pk, w.batch, w.params, stream=stream, tile=tile)
+    first = job.fetch()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            job.launch(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)  # evict the L2 (256 MB > 126 MB) outside the timed events
+                ev[k][0].record(stream)
+                job.launch(stream)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(world)
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = reduce_max(sum(kernel_ms) / 1e3, world)
+    job.download(stream)
+    res = job.fetch()
+    assert np.array_equal(res["best_score"], first["best_score"]), "relaunch changed results"
+    job.free()
+
+    L = w.batch.n_ligands
+    evals = float(res["evals"].sum())
+    pairs = float(res["pair_tests"].sum())
+    moves = float(res["atom_moves"].sum())
+    ops = FP32_OPS_PER_PAIR * pairs + FP32_OPS_PER_ATOM_MOVE * moves + FP32_OPS_PER_CANDIDATE * evals
+    value = L * world * args.steps / dev_s
+    ms_step = 1e3 * dev_s / args.steps
+    clocks = clk.summary()
+
+    # ---- e2e: host buffers through the public API --------------------------------------------
+    e2e_steps = args.e2e_steps or args.steps
+    for _ in range(2):  # warm the context's memory caches
+        j = ctx.dock_batch(pk, w.batch, w.params, stream=stream, tile=tile)
+        j.fetch()
+        j.free()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        j = ctx.dock_batch(pk, w.batch, w.params, stream=stream, tile=tile)
+        out = j.fetch()
+        h2d, d2h = j.bytes_moved()
+        j.free()
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    assert np.array_equal(out["best_score"], first["best_score"])
+    e2e = {"value": L * world * e2e_steps / e2e_s, "unit": "ligands/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+
+    pk.free()
+    ctx.close()
+    if rank != 0:
+        return
+
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    peak_tops = sm_count * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+    per_launch_ops = ops / 1.0
+    achieved = per_launch_ops / (np.mean(kernel_ms) / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators; no public dataset)",
+        "config": workload_config(w, "flushed between steps (256 MB write)") | {"tile": tile},
+        "pose_evals_per_s": evals * world * args.steps / dev_s,
+        "pair_tests_per_s": pairs * world * args.steps / dev_s,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "peak_kind": f"FP32 pipe: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x {mhz:.0f} MHz "
+                                  "(sm_max_mhz of MEASURED_PEAKS.json)",
+                     "ops_per_launch": per_launch_ops},
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/* geodock.h -- C ABI of the B300 GeoDock pose-search library (libgeodock.so).
+ *
+ * The calls follow the paper's problem statement: a target pocket is loaded once
+ * (Listing 1, "load(pocket)"), a library of ligands -- atoms plus rotamers, the bonds
+ * that split a ligand into two fragments rotating about the bond axis (Sec. 1) -- is
+ * docked against it, data crosses the host/device boundary once on the way in and
+ * once on the way out (Sec. 4.1), and only the best pose and score of every ligand
+ * come back (Sec. 4.1, "we only extract the result at the end").
+ *
+ * Method computed for every ligand (Sec. 3.1, Listing 1; Sec. 4.1, Listing 2):
+ *   for each restart o of an Euler-angle grid (generate_starting_pose):
+ *     x <- c_pocket + R_o (x - c_lig)                 rigid placement (align phase)
+ *     repeat `repetitions` times, for each rotamer r in order (optimize_pose):
+ *       rotate the smaller side of bond r about the bond axis by 2 pi k / A,
+ *       k = 0..A-1; a candidate is rejected when a moving and a static atom at
+ *       graph distance >= min_bond_sep come closer than bump_dist (BumpCheck);
+ *       the others are scored as the sum of pocket-grid cells under the atoms
+ *       (scoring function, Sec. 3.2); the best angle is kept (ties: smallest k).
+ *   the best restart (ties: smallest o) is the ligand's pose.
+ * Arithmetic: FP32 on the device.  Scores are exact integers.
+ *
+ * Conventions: every call returns a gd_status; nothing else crosses the ABI (no
+ * exceptions, no exit).  On failure gd_last_error() holds a one-line reason for the
+ * calling thread.  One context per thread, or external locking.  Streams are
+ * cudaStream_t passed as void* (NULL = the legacy default stream).
+ */
+#ifndef GEODOCK_H
+#define GEODOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gd_status;
+#define GD_OK 0
+#define GD_EINVAL 1      /* malformed input or parameter (reason in gd_last_error) */
+#define GD_ENOMEM 2      /* host or device allocation failed */
+#define GD_EBUDGET 3     /* the request would exceed the context's device-memory budget */
+#define GD_ECUDA 4       /* a CUDA runtime call failed */
+#define GD_ETIMEOUT 5    /* a bounded device-side wait ran out (kernel returned early) */
+#define GD_EBUSY 6       /* the object is still in use by queued device work */
+#define GD_ENOTREADY 7   /* non-blocking fetch: results not ready yet */
+
+/* Limits checked by every entry point. */
+#define GD_MAX_ATOMS 256        /* atoms per ligand */
+#define GD_MAX_ROTAMERS 128     /* rotamers per ligand */
+#define GD_MAX_ANGLES 1024      /* angles per rotamer sweep */
+#define GD_MAX_ORIENT 65535     /* restart orientations */
+#define GD_MAX_REPS 16          /* optimize_pose repetitions */
+#define GD_MAX_EXCLUDED 16      /* moving x static pairs closer than min_bond_sep bonds, per rotamer */
+
+/* Flags of gd_search_params.flags */
+#define GD_FLAG_DEBUG 1         /* keep per-orientation scores and picks (orient_score, orient_pick) */
+#define GD_FLAG_DEBUG_BUMPS 2   /* also keep per-candidate bump bits (bump_bits) */
+
+typedef struct gd_ctx gd_ctx;
+typedef struct gd_pocket gd_pocket;
+typedef struct gd_job gd_job;
+
+/* Ligand library in CSR form, host memory, owned by the caller.  The library copies
+ * what it needs before gd_dock_batch returns.
+ *   atom_off[L+1]  first atom of ligand i (atoms of ligand i: atom_off[i] .. atom_off[i+1]-1)
+ *   xyz[3*N]       coordinates in Angstrom, x y z per atom
+ *   bond_off[L+1]  first bond of ligand i
+ *   bonds[2*B]     bond endpoints as ligand-local atom ids; the bonds of a ligand form a tree
+ *   rot_off[L+1]   first rotamer of ligand i
+ *   rot_bond[Rt]   rotamer r of ligand i = its bond rot_bond[rot_off[i]+r] (ligand-local),
+ *                  swept in this order; a rotamer on a terminal bond is rejected. */
+typedef struct {
+  int32_t n_ligands;
+  const int32_t* atom_off;
+  const float* xyz;
+  const int32_t* bond_off;
+  const int32_t* bonds;
+  const int32_t* rot_off;
+  const int32_t* rot_bond;
+} gd_ligand_batch;
+
+/* Search settings.  Restart o = (i*n_beta + j)*n_gamma + k uses the ZYZ Euler angles
+ * (2 pi i/n_alpha, pi (j+1/2)/n_beta, 2 pi k/n_gamma).  tile: 0 = built-in default,
+ * -1 = autotuned (cached per context), > 0 = a tile id from gd_tile_count(); the
+ * tile changes speed only, never results. */
+typedef struct {
+  int32_t n_alpha, n_beta, n_gamma;
+  int32_t n_angles;
+  float bump_dist;
+  int32_t min_bond_sep;
+  int32_t repetitions;
+  int32_t flags;
+  int32_t tile;
+} gd_search_params;
+
+/* Results, caller-allocated host buffers (sizes from the batch it came from):
+ *   best_score[L]          integer score of the best pose
+ *   best_orient[L]         its restart index o
+ *   best_angle[reps*Rt]    its angle index per step, ligand i at rot_off[i]*reps,
+ *                          step = rep*R_i + r; -1 where every candidate was bumped
+ *   best_xyz[3*N]          its final coordinates, atoms in input order
+ *   evals[L]               candidates evaluated (O * reps * R_i * A)
+ *   pair_tests[L]          moving x static pair tests performed (early exit per atom)
+ *   atom_moves[L]          fragment atoms rotated and scored (O * reps * A * sum_r f_r,
+ *                          f_r = atoms of fragment r)
+ * Debug outputs (NULL to skip):
+ *   orient_score[L*O]      final score of every restart            (GD_FLAG_DEBUG)
+ *   orient_pick[O*reps*Rt] picks of every restart, ligand i at rot_off[i]*reps*O,
+ *                          then o*reps*R_i + step                  (GD_FLAG_DEBUG)
+ *   bump_bits[sum_i O*reps*R_i*A]  1 if the candidate was bumped   (GD_FLAG_DEBUG_BUMPS), ligand i at
+ *                          O*reps*A*rot_off[i], then ((o*reps*R_i + step)*A + k) */
+typedef struct {
+  uint32_t* best_score;
+  int32_t* best_orient;
+  int16_t* best_angle;
+  float* best_xyz;
+  uint64_t* evals;
+  uint64_t* pair_tests;
+  uint64_t* atom_moves;
+  uint32_t* orient_score;
+  int16_t* orient_pick;
+  uint8_t* bump_bits;
+} gd_result_batch;
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the device memory
+ * the context may hold (0 = no cap). */
+gd_status gd_create(gd_ctx** ctx, int device, size_t mem_budget_bytes);
+/* Wait for the context's work and free everything it owns. */
+gd_status gd_destroy(gd_ctx* ctx);
+/* Thread-local reason of the last failure on this thread ("" if none). */
+const char* gd_last_error(gd_ctx* ctx);
+
+/* load(pocket), Listing 1: upload a uint8 score grid laid out [nz][ny][nx] (x fastest),
+ * cell (i,j,k) covering origin + h*[i,i+1) x h*[j,j+1) x h*[k,k+1).  Cells outside the
+ * grid score 0.  The grid is copied; the caller keeps ownership of `grid`. */
+gd_status gd_load_pocket(gd_ctx* ctx, const uint8_t* grid, int nx, int ny, int nz, float spacing,
+                         const float origin[3], gd_pocket** out);
+gd_status gd_free_pocket(gd_ctx* ctx, gd_pocket* pocket);
+
+/* Dock a ligand library (the outer loop of Listing 1).  Validates and packs the
+ * batch, copies it to the device on `stream`, launches the search and queues the
+ * copy of the results back; returns without waiting.  The caller may free `batch`
+ * on return.  The job owns its device memory until gd_job_free. */
+gd_status gd_dock_batch(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batch* batch,
+                        const gd_search_params* params, void* stream, gd_job** out);
+/* Copy a job's results into `out`.  blocking = 0 returns GD_ENOTREADY while the device
+ * is still working. */
+gd_status gd_fetch_results(gd_ctx* ctx, gd_job* job, gd_result_batch* out, int blocking);
+/* Run the search of an existing job again on its device-resident inputs (no host
+ * copies; the results stay on the device until gd_job_download). */
+gd_status gd_job_launch(gd_ctx* ctx, gd_job* job, void* stream);
+/* Queue the device-to-host copy of a job's current results (read with gd_fetch_results). */
+gd_status gd_job_download(gd_ctx* ctx, gd_job* job, void* stream);
+/* Bytes one gd_dock_batch of this job moves host->device (packed inputs) and
+ * device->host (results, plus debug arrays when requested). */
+gd_status gd_job_bytes(gd_ctx* ctx, const gd_job* job, uint64_t* h2d_bytes, uint64_t* d2h_bytes);
+/* Wait for the job's queued work and release it. */
+gd_status gd_job_free(gd_ctx* ctx, gd_job* job);
+
+/* Validate a batch and parameters on the host only, without a device: the checks
+ * gd_dock_batch makes before it touches the GPU (tree bonds, atom/rotamer limits,
+ * terminal rotamers, excluded-pair limit, finite coordinates, parameter ranges).
+ * Returns GD_OK or GD_EINVAL with the reason in gd_last_error(NULL). */
+gd_status gd_check_batch(const gd_ligand_batch* batch, const gd_search_params* params);
+
+/* Launch tiles: number of ids (1..count) and the (warps per block, angles per lane)
+ * of one id. */
+int gd_tile_count(void);
+gd_status gd_tile_info(int tile, int* warps_per_block, int* angles_per_lane);
+/* Time every tile on the batch (or its first max_ligands ligands) and return the
+ * fastest; the choice is cached in the context for gd_search_params.tile = -1. */
+gd_status gd_autotune(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batch* batch,
+                      const gd_search_params* params, int max_ligands, void* stream, int* best_tile,
+                      float* best_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEODOCK_H */

@@ -135,6 +135,39 @@ def bumped(xyz, bonds, rb: int, min_sep: int = 3, bump_dist: float = 2.0) -> boo
 
 # ------------------------------------------------------------------ whole search
 
+def dock_pose(lig, pocket, params, o: int, debug: bool = False, eps: float = EPS) -> dict:
+    """One restart ``o`` of one ligand: picks, score (+ eps interval), first fragile step, coords."""
+    n, R = len(lig.xyz), len(lig.rot_bond)
+    reps, A = params.repetitions, params.n_angles
+    x = np.ascontiguousarray(lig.xyz, np.float32)
+    b = np.ascontiguousarray(lig.bonds, np.int32)
+    rb = np.ascontiguousarray(lig.rot_bond, np.int32)
+    g = np.ascontiguousarray(pocket.grid, dtype=np.uint8)
+    nz, ny, nx_ = g.shape
+    org = np.ascontiguousarray(pocket.origin, dtype=np.float64)
+    prm = _Params(params.n_alpha, params.n_beta, params.n_gamma, params.n_angles,
+                  float(params.bump_dist), params.min_bond_sep, params.repetitions)
+    picks = np.zeros(reps * R, np.int16)
+    slhf = np.zeros(4, np.int32)
+    xyz = np.zeros((n, 3))
+    bump = np.zeros(reps * R * A, np.uint8) if debug else None
+    cand = np.zeros(reps * R * A, np.int32) if debug else None
+    nul = lambda ct: C.cast(None, C.POINTER(ct))
+    rc = lib().orc_dock_pose(n, _p(x, C.c_float), len(b), _p(b, C.c_int32), R, _p(rb, C.c_int32),
+                             _p(g, C.c_uint8), nx_, ny, nz, C.c_double(pocket.spacing), _p(org, C.c_double),
+                             C.byref(prm), C.c_double(eps), int(o), _p(picks, C.c_int16),
+                             _p(bump, C.c_uint8) if debug else nul(C.c_uint8),
+                             _p(cand, C.c_int32) if debug else nul(C.c_int32),
+                             _p(slhf, C.c_int32), _p(xyz, C.c_double))
+    if rc:
+        raise ValueError(lib().orc_last_error().decode())
+    out = dict(picks=picks, score=int(slhf[0]), score_lo=int(slhf[1]), score_hi=int(slhf[2]),
+               fragile=int(slhf[3]), xyz=xyz)
+    if debug:
+        out["bump"], out["cand_score"] = bump, cand
+    return out
+
+
 def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, eps: float = EPS) -> dict:
     """Run the search over a CSR ligand batch; returns per-ligand / per-orientation arrays.
 

@@ -255,118 +255,141 @@ struct LigandOut {
   int64_t* evals;              // [1]
 };
 
+// A ligand with its topology, rotamers and centres derived once.
+struct Prepared {
+  int n = 0, R = 0;
+  Topo topo;
+  std::vector<Rotamer> rots;
+  std::vector<V3> x0;
+  V3 c_lig{0, 0, 0}, c_pocket{0, 0, 0};
+};
+
+bool prepare(const float* xyz_in, int n, const int32_t* bonds, int nb, const int32_t* rot_bond, int R,
+             const Pocket& P, const Params& prm, Prepared& L, std::string& err) {
+  L.n = n;
+  L.R = R;
+  if (!build_topology(n, bonds, nb, L.topo, err)) return false;
+  L.rots.assign(R, Rotamer{});
+  for (int r = 0; r < R; ++r)
+    if (!build_rotamer(L.topo, bonds, nb, rot_bond[r], prm.min_bond_sep, L.rots[r], err)) return false;
+  L.x0.resize(n);
+  L.c_lig = V3{0, 0, 0};
+  for (int a = 0; a < n; ++a) {
+    L.x0[a] = V3{(double)xyz_in[3 * a], (double)xyz_in[3 * a + 1], (double)xyz_in[3 * a + 2]};
+    L.c_lig = L.c_lig + L.x0[a];
+  }
+  L.c_lig = (1.0 / n) * L.c_lig;
+  L.c_pocket = P.origin + (0.5 * P.h) * V3{(double)P.nx, (double)P.ny, (double)P.nz};
+  return true;
+}
+
+// One restart o: generate_starting_pose, then `repetitions` passes of optimize_pose.
+// picks[reps*R]; optional bump / cand_score [reps*R*A]; returns the final score, its
+// eps-interval, the first fragile step (-1: none) and the final coordinates x.
+void search_restart(const Prepared& L, const Pocket& P, const Params& prm, double eps, int o, int16_t* picks,
+                    uint8_t* bump, int32_t* cand_score, int* score_out, int* lo_out, int* hi_out,
+                    int* fragile_out, std::vector<V3>& x) {
+  const double pi = 3.14159265358979323846;
+  const int n = L.n, R = L.R, A = prm.n_angles, reps = prm.repetitions;
+  M3 Ro = euler_orientation(o, prm.n_alpha, prm.n_beta, prm.n_gamma);
+  x.resize(n);
+  for (int a = 0; a < n; ++a) x[a] = L.c_pocket + mul(Ro, L.x0[a] - L.c_lig);
+  int fragile_step = -1;
+  std::vector<V3> xm(n);
+  std::vector<int> score(A), lo(A), hi(A), status(A);
+  std::vector<char> bumped(A);
+  for (int rep = 0; rep < reps; ++rep)
+    for (int r = 0; r < R; ++r) {
+      const Rotamer& rot = L.rots[r];
+      const int step = rep * R + r;
+      V3 u = x[rot.q] - x[rot.p];
+      u = (1.0 / norm(u)) * u;
+      int static_score = 0;
+      for (int a = 0; a < n; ++a)
+        if (!rot.moving[a]) static_score += cell_value(P, x[a]);
+      for (int k = 0; k < A; ++k) {
+        double theta = 2.0 * pi * k / A;
+        for (int a = 0; a < n; ++a)
+          xm[a] = rot.moving[a] ? x[rot.p] + rodrigues(u, theta, x[a] - x[rot.p]) : x[a];
+        bool b_exact;
+        status[k] = bump_status(rot, xm, x, prm.bump_dist, eps, &b_exact);
+        bumped[k] = b_exact;
+        int s = static_score, slo = 0, shi = 0;
+        for (int a = 0; a < n; ++a)
+          if (rot.moving[a]) {
+            s += cell_value(P, xm[a]);
+            int l, h;
+            cell_range(P, xm[a], eps, &l, &h);
+            slo += l;
+            shi += h;
+          }
+        score[k] = s;
+        lo[k] = slo;  // moving-atom part only: the static part is common to every k
+        hi[k] = shi;
+        if (bump) bump[(size_t)step * A + k] = (uint8_t)status[k];
+        if (cand_score) cand_score[(size_t)step * A + k] = b_exact ? -1 : s;
+      }
+      int kstar = -1;
+      for (int k = 0; k < A; ++k)
+        if (!bumped[k] && (kstar < 0 || score[k] > score[kstar])) kstar = k;
+      picks[step] = (int16_t)kstar;
+      // Can an eps perturbation change the pick?
+      if (fragile_step < 0) {
+        bool robust;
+        if (kstar < 0) {  // every candidate bumped: robust only if every bump is sure
+          robust = true;
+          for (int k = 0; k < A; ++k)
+            if (status[k] != 1) robust = false;
+        } else {
+          robust = status[kstar] == 0;
+          for (int k = 0; k < A && robust; ++k) {
+            if (k == kstar || status[k] == 1) continue;
+            if (k < kstar && !(hi[k] < lo[kstar])) robust = false;
+            if (k > kstar && !(hi[k] <= lo[kstar])) robust = false;
+          }
+        }
+        if (!robust) fragile_step = step;
+      }
+      if (kstar >= 0) {  // commit the chosen rotation
+        double theta = 2.0 * pi * kstar / A;
+        V3 xp = x[rot.p];
+        for (int a = 0; a < n; ++a)
+          if (rot.moving[a]) x[a] = xp + rodrigues(u, theta, x[a] - xp);
+      }
+    }
+  int s = 0, slo = 0, shi = 0;
+  for (int a = 0; a < n; ++a) {
+    s += cell_value(P, x[a]);
+    int l, h;
+    cell_range(P, x[a], eps, &l, &h);
+    slo += l;
+    shi += h;
+  }
+  *score_out = s;
+  *lo_out = slo;
+  *hi_out = shi;
+  *fragile_out = fragile_step;
+}
+
 int dock_ligand(const float* xyz_in, int n, const int32_t* bonds, int nb, const int32_t* rot_bond,
                 int R, const Pocket& P, const Params& prm, double eps, const LigandOut& out,
                 std::string& err) {
-  Topo topo;
-  if (!build_topology(n, bonds, nb, topo, err)) return 1;
-  std::vector<Rotamer> rots(R);
-  for (int r = 0; r < R; ++r)
-    if (!build_rotamer(topo, bonds, nb, rot_bond[r], prm.min_bond_sep, rots[r], err)) return 1;
-
+  Prepared L;
+  if (!prepare(xyz_in, n, bonds, nb, rot_bond, R, P, prm, L, err)) return 1;
   const int O = prm.n_alpha * prm.n_beta * prm.n_gamma;
   const int A = prm.n_angles;
   const int reps = prm.repetitions;
-  const double pi = 3.14159265358979323846;
-
-  std::vector<V3> x0(n);
-  V3 c_lig{0, 0, 0};
-  for (int a = 0; a < n; ++a) {
-    x0[a] = V3{(double)xyz_in[3 * a], (double)xyz_in[3 * a + 1], (double)xyz_in[3 * a + 2]};
-    c_lig = c_lig + x0[a];
-  }
-  c_lig = (1.0 / n) * c_lig;
-  V3 c_pocket = P.origin + (0.5 * P.h) * V3{(double)P.nx, (double)P.ny, (double)P.nz};
-
   int64_t full_pairs = 0;
-  for (auto& r : rots) full_pairs += (int64_t)r.pairs.size();
+  for (auto& r : L.rots) full_pairs += (int64_t)r.pairs.size();
   *out.pair_tests_full = full_pairs * A * reps * O;
   *out.evals = (int64_t)O * reps * R * A;
 
   std::vector<std::vector<V3>> final_x(O);
-  for (int o = 0; o < O; ++o) {
-    // generate_starting_pose + rigid placement
-    M3 Ro = euler_orientation(o, prm.n_alpha, prm.n_beta, prm.n_gamma);
-    std::vector<V3> x(n);
-    for (int a = 0; a < n; ++a) x[a] = c_pocket + mul(Ro, x0[a] - c_lig);
-    int fragile_step = -1;
-
-    std::vector<V3> xm(n);
-    for (int rep = 0; rep < reps; ++rep)
-      for (int r = 0; r < R; ++r) {
-        const Rotamer& rot = rots[r];
-        const int step = rep * R + r;
-        V3 u = x[rot.q] - x[rot.p];
-        u = (1.0 / norm(u)) * u;
-        std::vector<int> score(A), lo(A), hi(A), status(A);
-        std::vector<char> bumped(A);
-        int static_score = 0;
-        for (int a = 0; a < n; ++a)
-          if (!rot.moving[a]) static_score += cell_value(P, x[a]);
-        for (int k = 0; k < A; ++k) {
-          double theta = 2.0 * pi * k / A;
-          for (int a = 0; a < n; ++a)
-            xm[a] = rot.moving[a] ? x[rot.p] + rodrigues(u, theta, x[a] - x[rot.p]) : x[a];
-          bool b_exact;
-          status[k] = bump_status(rot, xm, x, prm.bump_dist, eps, &b_exact);
-          bumped[k] = b_exact;
-          int s = static_score, slo = 0, shi = 0;
-          for (int a = 0; a < n; ++a)
-            if (rot.moving[a]) {
-              s += cell_value(P, xm[a]);
-              int l, h;
-              cell_range(P, xm[a], eps, &l, &h);
-              slo += l;
-              shi += h;
-            }
-          score[k] = s;
-          lo[k] = slo;  // moving-atom part only: the static part is common to every k
-          hi[k] = shi;
-          if (out.bump) out.bump[((size_t)o * reps * R + step) * A + k] = (uint8_t)status[k];
-          if (out.cand_score) out.cand_score[((size_t)o * reps * R + step) * A + k] = b_exact ? -1 : s;
-        }
-        int kstar = -1;
-        for (int k = 0; k < A; ++k)
-          if (!bumped[k] && (kstar < 0 || score[k] > score[kstar])) kstar = k;
-        out.orient_pick[(size_t)o * reps * R + step] = (int16_t)kstar;
-        // Can an eps perturbation change the pick?
-        if (fragile_step < 0) {
-          bool robust;
-          if (kstar < 0) {  // every candidate bumped: robust only if every bump is sure
-            robust = true;
-            for (int k = 0; k < A; ++k)
-              if (status[k] != 1) robust = false;
-          } else {
-            robust = status[kstar] == 0;
-            for (int k = 0; k < A && robust; ++k) {
-              if (k == kstar || status[k] == 1) continue;
-              if (k < kstar && !(hi[k] < lo[kstar])) robust = false;
-              if (k > kstar && !(hi[k] <= lo[kstar])) robust = false;
-            }
-          }
-          if (!robust) fragile_step = step;
-        }
-        if (kstar >= 0) {  // commit the chosen rotation
-          double theta = 2.0 * pi * kstar / A;
-          V3 xp = x[rot.p];
-          for (int a = 0; a < n; ++a)
-            if (rot.moving[a]) x[a] = xp + rodrigues(u, theta, x[a] - xp);
-        }
-      }
-    int s = 0, slo = 0, shi = 0;
-    for (int a = 0; a < n; ++a) {
-      s += cell_value(P, x[a]);
-      int l, h;
-      cell_range(P, x[a], eps, &l, &h);
-      slo += l;
-      shi += h;
-    }
-    out.orient_score[o] = s;
-    out.orient_score_lo[o] = slo;
-    out.orient_score_hi[o] = shi;
-    out.orient_fragile[o] = fragile_step;
-    final_x[o] = x;
-  }
+  const size_t per_o = (size_t)reps * R;
+  for (int o = 0; o < O; ++o)
+    search_restart(L, P, prm, eps, o, out.orient_pick + o * per_o, out.bump ? out.bump + o * per_o * A : nullptr,
+                   out.cand_score ? out.cand_score + o * per_o * A : nullptr, &out.orient_score[o],
+                   &out.orient_score_lo[o], &out.orient_score_hi[o], &out.orient_fragile[o], final_x[o]);
   int best = 0;
   for (int o = 1; o < O; ++o)
     if (out.orient_score[o] > out.orient_score[best]) best = o;
@@ -494,6 +517,27 @@ struct orc_params {
   double bump_dist;
   int32_t min_bond_sep, repetitions;
 };
+
+// One restart o of one ligand: picks[reps*R], optional bump/cand_score[reps*R*A],
+// score / interval / first fragile step, final coordinates xyz_out[3n].
+int orc_dock_pose(int n, const float* xyz, int nb, const int32_t* bonds, int R, const int32_t* rot_bond,
+                  const uint8_t* grid, int nx, int ny, int nz, double h, const double* origin,
+                  const orc_params* p, double eps, int o, int16_t* picks, uint8_t* bump, int32_t* cand_score,
+                  int32_t* score_lo_hi_fragile, double* xyz_out) {
+  Pocket P{grid, nx, ny, nz, h, V3{origin[0], origin[1], origin[2]}};
+  Params prm{p->n_alpha, p->n_beta, p->n_gamma, p->n_angles, p->bump_dist, p->min_bond_sep, p->repetitions};
+  Prepared L;
+  if (!prepare(xyz, n, bonds, nb, rot_bond, R, P, prm, L, g_err)) return 1;
+  std::vector<V3> x;
+  search_restart(L, P, prm, eps, o, picks, bump, cand_score, &score_lo_hi_fragile[0], &score_lo_hi_fragile[1],
+                 &score_lo_hi_fragile[2], &score_lo_hi_fragile[3], x);
+  for (int a = 0; a < n; ++a) {
+    xyz_out[3 * a] = x[a].x;
+    xyz_out[3 * a + 1] = x[a].y;
+    xyz_out[3 * a + 2] = x[a].z;
+  }
+  return 0;
+}
 
 // Outputs are laid out per ligand i with O = na*nb*ng orientations:
 //   orient_* at [i*O ...], picks at [i*O*reps ... ] per rotamer offsets rot_off,

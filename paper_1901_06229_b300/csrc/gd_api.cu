@@ -1,0 +1,856 @@
+// Host runtime of libgeodock: contexts, pockets, batch validation and packing, job
+// memory, CUDA-graph launch and the launch-tile autotuner.  Implements include/geodock.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "geodock.h"
+#include "gd_internal.h"
+
+using gd::RotDesc;
+using gd::SearchArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+gd_status fail(gd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define GD_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(GD_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- context & memory
+
+struct gd_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t budget = 0;  // 0: unlimited
+  size_t used = 0;    // device bytes currently held (cached blocks included)
+  cudaStream_t capture_stream = nullptr;
+  std::mutex mu;
+  std::multimap<size_t, void*> dev_free;   // cached device blocks by size
+  std::multimap<size_t, void*> host_free;  // cached pinned blocks by size
+  std::map<std::string, int> tuned;        // autotuned tile per workload signature
+};
+
+namespace {
+
+// Blocks are rounded to 1 MiB (or a power of two below) so repeated jobs of the same
+// shape reuse them.
+size_t size_class(size_t b) {
+  if (b <= (1u << 20)) {
+    size_t s = 4096;
+    while (s < b) s <<= 1;
+    return s;
+  }
+  return align_up(b, 1u << 20);
+}
+
+gd_status dev_alloc(gd_ctx* c, size_t bytes, void** out) {
+  const size_t sz = size_class(bytes);
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->dev_free.find(sz);
+    if (it != c->dev_free.end()) {
+      *out = it->second;
+      c->dev_free.erase(it);
+      return GD_OK;
+    }
+  }
+  if (c->budget && c->used + sz > c->budget) {
+    // drop cached blocks before refusing
+    std::lock_guard<std::mutex> g(c->mu);
+    for (auto& kv : c->dev_free) {
+      cudaFree(kv.second);
+      c->used -= kv.first;
+    }
+    c->dev_free.clear();
+    if (c->used + sz > c->budget)
+      return fail(GD_EBUDGET, "device budget %zu B exceeded (held %zu B, need %zu B)", c->budget, c->used, sz);
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sz);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GD_ENOMEM, "cudaMalloc(%zu): %s", sz, cudaGetErrorString(e));
+  }
+  std::lock_guard<std::mutex> g(c->mu);
+  c->used += sz;
+  *out = p;
+  return GD_OK;
+}
+
+void dev_release(gd_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(c->mu);
+  c->dev_free.emplace(size_class(bytes), p);
+}
+
+gd_status host_alloc(gd_ctx* c, size_t bytes, void** out) {
+  const size_t sz = size_class(bytes);
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->host_free.find(sz);
+    if (it != c->host_free.end()) {
+      *out = it->second;
+      c->host_free.erase(it);
+      return GD_OK;
+    }
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMallocHost(&p, sz);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GD_ENOMEM, "cudaMallocHost(%zu): %s", sz, cudaGetErrorString(e));
+  }
+  *out = p;
+  return GD_OK;
+}
+
+void host_release(gd_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(c->mu);
+  c->host_free.emplace(size_class(bytes), p);
+}
+
+}  // namespace
+
+struct gd_pocket {
+  gd::PocketDev dev{};
+  void* buf = nullptr;
+  size_t buf_bytes = 0;
+  int nx = 0, ny = 0, nz = 0;
+};
+
+// ---------------------------------------------------------------- batch packing
+
+namespace {
+
+// Byte layout of a packed batch; the same offsets are used in pinned staging and in
+// device memory so one copy moves the whole input.
+struct InLayout {
+  size_t atom_off, rot_off, xyz, perm, rots, order, total;
+};
+
+InLayout in_layout(int L, long long N, long long Rt) {
+  InLayout l{};
+  size_t o = 0;
+  l.atom_off = o; o = align_up(o + 4 * (size_t)(L + 1), 256);
+  l.rot_off = o;  o = align_up(o + 4 * (size_t)(L + 1), 256);
+  l.xyz = o;      o = align_up(o + 16 * (size_t)N, 256);
+  l.perm = o;     o = align_up(o + (size_t)N, 256);
+  l.rots = o;     o = align_up(o + sizeof(RotDesc) * (size_t)Rt, 256);
+  l.order = o;    o = align_up(o + 4 * (size_t)L, 256);
+  l.total = o;
+  return l;
+}
+
+struct OutLayout {
+  size_t best_score, best_orient, best_angle, best_xyz, evals, pair_tests, atom_moves, err, total;
+};
+
+OutLayout out_layout(int L, long long N, long long Rt, int reps) {
+  OutLayout l{};
+  size_t o = 0;
+  l.best_score = o;  o = align_up(o + 4 * (size_t)L, 256);
+  l.best_orient = o; o = align_up(o + 4 * (size_t)L, 256);
+  l.best_angle = o;  o = align_up(o + 2 * (size_t)Rt * reps, 256);
+  l.best_xyz = o;    o = align_up(o + 12 * (size_t)N, 256);
+  l.evals = o;       o = align_up(o + 8 * (size_t)L, 256);
+  l.pair_tests = o;  o = align_up(o + 8 * (size_t)L, 256);
+  l.atom_moves = o;  o = align_up(o + 8 * (size_t)L, 256);
+  l.err = o;         o = align_up(o + 4, 256);
+  l.total = o;
+  return l;
+}
+
+struct ScratchLayout {
+  size_t pose_score, pose_pick, pose_pairs, done, work, bump, total;
+};
+
+ScratchLayout scratch_layout(int L, int O, long long Rt, int reps, int A, bool debug) {
+  ScratchLayout l{};
+  size_t o = 0;
+  l.pose_score = o; o = align_up(o + 4 * (size_t)L * O, 256);
+  l.pose_pick = o;  o = align_up(o + 2 * (size_t)O * reps * Rt, 256);
+  l.pose_pairs = o; o = align_up(o + 8 * (size_t)L * O, 256);
+  l.done = o;       o = o + 4 * (size_t)L;          // done and work are cleared by one memset
+  o = align_up(o, 8);
+  l.work = o;       o = align_up(o + 8, 256);
+  l.bump = o;       o = align_up(o + (debug ? (size_t)O * reps * A * Rt : 0), 256);
+  l.total = o;
+  return l;
+}
+
+gd_status check_params(const gd_search_params* p) {
+  if (!p) return fail(GD_EINVAL, "params is NULL");
+  if (p->n_alpha < 1 || p->n_beta < 1 || p->n_gamma < 1)
+    return fail(GD_EINVAL, "Euler grid sizes must be >= 1");
+  const long long O = (long long)p->n_alpha * p->n_beta * p->n_gamma;
+  if (O > GD_MAX_ORIENT) return fail(GD_EINVAL, "%lld orientations > %d", O, GD_MAX_ORIENT);
+  if (p->n_angles < 1 || p->n_angles > GD_MAX_ANGLES)
+    return fail(GD_EINVAL, "n_angles %d outside [1, %d]", p->n_angles, GD_MAX_ANGLES);
+  if (!(p->bump_dist > 0.f) || !std::isfinite(p->bump_dist)) return fail(GD_EINVAL, "bump_dist must be > 0");
+  if (p->min_bond_sep < 1 || p->min_bond_sep > 8) return fail(GD_EINVAL, "min_bond_sep outside [1, 8]");
+  if (p->repetitions < 1 || p->repetitions > GD_MAX_REPS)
+    return fail(GD_EINVAL, "repetitions outside [1, %d]", GD_MAX_REPS);
+  if (p->tile < -1 || p->tile > gd::tile_count()) return fail(GD_EINVAL, "tile %d out of range", p->tile);
+  return GD_OK;
+}
+
+// Validate one ligand and write its preorder-packed atoms and rotamer descriptors.
+// cost: an estimate of its search work, used to order the work queue.
+gd_status pack_ligand(int li, int n, const float* xyz, int nb, const int32_t* bonds, int R,
+                      const int32_t* rot_bond, int min_sep, float4* out_xyz, uint8_t* out_perm,
+                      RotDesc* out_rots, double* cost) {
+  if (n < 2 || n > GD_MAX_ATOMS) return fail(GD_EINVAL, "ligand %d: %d atoms outside [2, %d]", li, n, GD_MAX_ATOMS);
+  if (nb != n - 1) return fail(GD_EINVAL, "ligand %d: %d bonds for %d atoms (not a tree)", li, nb, n);
+  if (R < 0 || R > GD_MAX_ROTAMERS) return fail(GD_EINVAL, "ligand %d: %d rotamers > %d", li, R, GD_MAX_ROTAMERS);
+  for (int i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(xyz[i])) return fail(GD_EINVAL, "ligand %d: non-finite coordinate", li);
+  // adjacency (CSR)
+  std::vector<int> deg(n, 0), adj_off(n + 1, 0), adj(2 * nb);
+  for (int b = 0; b < nb; ++b) {
+    int u = bonds[2 * b], v = bonds[2 * b + 1];
+    if (u < 0 || v < 0 || u >= n || v >= n || u == v) return fail(GD_EINVAL, "ligand %d: bad bond %d", li, b);
+    deg[u]++;
+    deg[v]++;
+  }
+  for (int i = 0; i < n; ++i) adj_off[i + 1] = adj_off[i] + deg[i];
+  std::vector<int> fill(adj_off.begin(), adj_off.end() - 1);
+  for (int b = 0; b < nb; ++b) {
+    int u = bonds[2 * b], v = bonds[2 * b + 1];
+    adj[fill[u]++] = v;
+    adj[fill[v]++] = u;
+  }
+  // DFS preorder from atom 0; subtrees become contiguous ranges
+  std::vector<int> parent(n, -2), pre(n, -1), order;
+  order.reserve(n);
+  std::vector<int> stack{0};
+  parent[0] = -1;
+  while (!stack.empty()) {
+    int v = stack.back();
+    stack.pop_back();
+    if (pre[v] >= 0) return fail(GD_EINVAL, "ligand %d: bonds contain a cycle (not a tree)", li);
+    pre[v] = (int)order.size();
+    order.push_back(v);
+    for (int e = adj_off[v + 1] - 1; e >= adj_off[v]; --e) {
+      int w = adj[e];
+      if (w == parent[v]) continue;
+      if (pre[w] >= 0) return fail(GD_EINVAL, "ligand %d: bonds contain a cycle (not a tree)", li);
+      parent[w] = v;
+      stack.push_back(w);
+    }
+  }
+  if ((int)order.size() != n) return fail(GD_EINVAL, "ligand %d: bond graph is not connected", li);
+  std::vector<int> size(n, 1);
+  for (int t = n - 1; t > 0; --t) size[parent[order[t]]] += size[order[t]];
+  for (int t = 0; t < n; ++t) {
+    int v = order[t];
+    out_xyz[t] = make_float4(xyz[3 * v], xyz[3 * v + 1], xyz[3 * v + 2], 0.f);
+    out_perm[t] = (uint8_t)v;
+  }
+  double c = n;
+  std::vector<int> depth(n, -1), queue;
+  for (int r = 0; r < R; ++r) {
+    const int b = rot_bond[r];
+    if (b < 0 || b >= nb) return fail(GD_EINVAL, "ligand %d: rotamer %d names bond %d of %d", li, r, b, nb);
+    int u = bonds[2 * b], v = bonds[2 * b + 1];
+    int child = parent[v] == u ? v : u;
+    int sub = size[child], rest = n - sub;
+    if (sub == 1 || rest == 1) return fail(GD_EINVAL, "ligand %d: rotamer %d is on a terminal bond", li, r);
+    RotDesc d{};
+    d.comp = sub > rest ? 1 : 0;  // equal sides: move the subtree (the side without atom 0)
+    int q = d.comp ? parent[child] : child;
+    int p = d.comp ? child : parent[child];
+    d.p = (uint16_t)pre[p];
+    d.q = (uint16_t)pre[q];
+    d.lo = (uint16_t)pre[child];
+    d.hi = (uint16_t)(pre[child] + sub);
+    auto moving = [&](int atom) {
+      bool in = pre[atom] >= d.lo && pre[atom] < d.hi;
+      return d.comp ? !in : in;
+    };
+    // atoms within min_sep-2 bonds of q (moving side) and of p (static side)
+    std::fill(depth.begin(), depth.end(), -1);
+    std::vector<std::pair<int, int>> near_m, near_s;
+    for (int side = 0; side < 2; ++side) {
+      int root = side ? p : q;
+      queue.assign(1, root);
+      depth[root] = 0;
+      for (size_t h = 0; h < queue.size(); ++h) {
+        int a = queue[h];
+        (side ? near_s : near_m).push_back({a, depth[a]});
+        if (depth[a] >= min_sep - 2) continue;
+        for (int e = adj_off[a]; e < adj_off[a + 1]; ++e) {
+          int w = adj[e];
+          if (depth[w] >= 0 || moving(w) != (side == 0)) continue;
+          depth[w] = depth[a] + 1;
+          queue.push_back(w);
+        }
+      }
+    }
+    std::vector<std::pair<int, int>> ex;
+    for (auto& m : near_m)
+      for (auto& s : near_s)
+        if (m.second + s.second + 1 < min_sep) ex.push_back({pre[m.first], pre[s.first]});
+    if ((int)ex.size() > GD_MAX_EXCLUDED)
+      return fail(GD_EINVAL, "ligand %d: rotamer %d has %zu excluded pairs > %d", li, r, ex.size(), GD_MAX_EXCLUDED);
+    std::sort(ex.begin(), ex.end());
+    d.n_excl = (uint8_t)ex.size();
+    for (size_t e = 0; e < ex.size(); ++e) {
+      d.excl_a[e] = (uint8_t)ex[e].first;
+      d.excl_b[e] = (uint8_t)ex[e].second;
+    }
+    out_rots[r] = d;
+    const int f = d.comp ? rest : sub;
+    c += (double)f * (n - f) + 4.0 * f;
+  }
+  *cost = c * (R > 0 ? 1.0 : 0.1);
+  return GD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- jobs
+
+struct gd_job {
+  gd_ctx* ctx = nullptr;
+  int L = 0, O = 0, reps = 0, A = 0;
+  long long N = 0, Rt = 0;
+  bool debug = false;
+  bool debug_bumps = false;
+  bool grid_in_smem = false;
+  int tile = 1;
+  InLayout in{};
+  OutLayout out{};
+  ScratchLayout scr{};
+  void* d_in = nullptr;
+  void* d_out = nullptr;
+  void* d_scr = nullptr;
+  void* h_in = nullptr;
+  void* h_out = nullptr;
+  void* h_dbg = nullptr;  // pose_score | pose_pick | bump (debug only)
+  size_t dbg_bytes = 0;
+  SearchArgs args{};
+  gd::LaunchCfg cfg{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<int32_t> rot_off;  // host copy for result layout checks
+};
+
+namespace {
+
+gd_status job_release(gd_ctx* c, gd_job* j) {
+  if (j->done) cudaEventSynchronize(j->done);
+  if (j->exec) cudaGraphExecDestroy(j->exec);
+  if (j->graph) cudaGraphDestroy(j->graph);
+  if (j->done) cudaEventDestroy(j->done);
+  dev_release(c, j->d_in, j->in.total);
+  dev_release(c, j->d_out, j->out.total);
+  dev_release(c, j->d_scr, j->scr.total);
+  host_release(c, j->h_in, j->in.total);
+  host_release(c, j->h_out, j->out.total);
+  host_release(c, j->h_dbg, j->dbg_bytes);
+  delete j;
+  return GD_OK;
+}
+
+std::string signature(const gd_pocket* pk, const gd_search_params* p, int nmax, bool smem) {
+  char b[256];
+  snprintf(b, sizeof b, "O%d_A%d_r%d_n%d_g%d_%dx%dx%d", p->n_alpha * p->n_beta * p->n_gamma, p->n_angles,
+           p->repetitions, (nmax + 31) / 32, smem ? 1 : 0, pk->dev.cx, pk->dev.cy, pk->dev.cz);
+  return b;
+}
+
+// Capture [clear counters, search kernel] once; replayed by every launch of the job.
+gd_status build_graph(gd_ctx* c, gd_job* j) {
+  cudaError_t pe = gd::plan_search(j->args, j->tile, j->grid_in_smem, c->num_sms, &j->cfg);
+  if (pe != cudaSuccess) return fail(GD_ECUDA, "search launch shape: %s", cudaGetErrorString(pe));
+  cudaStream_t s = c->capture_stream;
+  GD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s);
+  cudaError_t le = gd::launch_search(j->args, j->cfg, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(s, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(GD_ECUDA, "search launch: %s", cudaGetErrorString(le));
+  }
+  if (ee != cudaSuccess) return fail(GD_ECUDA, "graph capture: %s", cudaGetErrorString(ee));
+  j->graph = g;
+  GD_CUDA(cudaGraphInstantiate(&j->exec, g, 0));
+  return GD_OK;
+}
+
+gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
+                   int tile, gd_job** out) {
+  const int L = b->n_ligands;
+  if (L < 0) return fail(GD_EINVAL, "n_ligands < 0");
+  if (L > 0 && (!b->atom_off || !b->xyz || !b->bond_off || !b->bonds || !b->rot_off || !b->rot_bond))
+    return fail(GD_EINVAL, "batch has a NULL array");
+  if (L > 0 && (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0))
+    return fail(GD_EINVAL, "CSR offsets must start at 0");
+  for (int i = 0; i < L; ++i)
+    if (b->atom_off[i + 1] < b->atom_off[i] || b->bond_off[i + 1] < b->bond_off[i] || b->rot_off[i + 1] < b->rot_off[i])
+      return fail(GD_EINVAL, "CSR offsets decrease at ligand %d", i);
+  const long long N = L ? b->atom_off[L] : 0, Rt = L ? b->rot_off[L] : 0;
+  gd_job* j = new gd_job();
+  j->ctx = c;
+  j->L = L;
+  j->O = p->n_alpha * p->n_beta * p->n_gamma;
+  j->reps = p->repetitions;
+  j->A = p->n_angles;
+  j->N = N;
+  j->Rt = Rt;
+  j->debug = (p->flags & (GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS)) != 0;
+  j->debug_bumps = (p->flags & GD_FLAG_DEBUG_BUMPS) != 0;
+  j->in = in_layout(L, N, Rt);
+  j->out = out_layout(L, N, Rt, j->reps);
+  j->scr = scratch_layout(L, j->O, Rt, j->reps, j->A, j->debug_bumps);
+  gd_status st;
+  if ((st = host_alloc(c, j->in.total, &j->h_in)) || (st = host_alloc(c, j->out.total, &j->h_out))) {
+    job_release(c, j);
+    return st;
+  }
+  char* h = (char*)j->h_in;
+  int32_t* atom_off = (int32_t*)(h + j->in.atom_off);
+  int32_t* rot_off = (int32_t*)(h + j->in.rot_off);
+  float4* xyz = (float4*)(h + j->in.xyz);
+  uint8_t* perm = (uint8_t*)(h + j->in.perm);
+  RotDesc* rots = (RotDesc*)(h + j->in.rots);
+  int32_t* order = (int32_t*)(h + j->in.order);
+  std::vector<double> cost(L);
+  int nmax = 2;
+  for (int i = 0; i < L; ++i) {
+    const int a0 = b->atom_off[i], n = b->atom_off[i + 1] - a0;
+    const int b0 = b->bond_off[i], nb = b->bond_off[i + 1] - b0;
+    const int r0 = b->rot_off[i], R = b->rot_off[i + 1] - r0;
+    st = pack_ligand(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
+                     p->min_bond_sep, xyz + a0, perm + a0, rots + r0, &cost[i]);
+    if (st) {
+      job_release(c, j);
+      return st;
+    }
+    if (R * j->reps > 32767) {
+      job_release(c, j);
+      return fail(GD_EINVAL, "ligand %d: too many steps", i);
+    }
+    nmax = std::max(nmax, n);
+  }
+  for (int i = 0; i <= L; ++i) {
+    atom_off[i] = L ? b->atom_off[i] : 0;
+    rot_off[i] = L ? b->rot_off[i] : 0;
+  }
+  j->rot_off.assign(rot_off, rot_off + L + 1);
+  for (int i = 0; i < L; ++i) order[i] = i;
+  std::stable_sort(order, order + L, [&](int x, int y) { return cost[x] > cost[y]; });
+
+  if ((st = dev_alloc(c, j->in.total, &j->d_in)) || (st = dev_alloc(c, j->out.total, &j->d_out)) ||
+      (st = dev_alloc(c, j->scr.total, &j->d_scr))) {
+    job_release(c, j);
+    return st;
+  }
+  if (j->debug) {
+    j->dbg_bytes = j->scr.total;
+    if ((st = host_alloc(c, j->dbg_bytes, &j->h_dbg))) {
+      job_release(c, j);
+      return st;
+    }
+  }
+  // kernel arguments
+  SearchArgs& a = j->args;
+  a.pk = pk->dev;
+  a.L = L;
+  char* d = (char*)j->d_in;
+  a.atom_off = (const int32_t*)(d + j->in.atom_off);
+  a.rot_off = (const int32_t*)(d + j->in.rot_off);
+  a.xyz = (const float4*)(d + j->in.xyz);
+  a.perm = (const uint8_t*)(d + j->in.perm);
+  a.rots = (const RotDesc*)(d + j->in.rots);
+  a.order = (const int32_t*)(d + j->in.order);
+  a.n_items = (long long)L * j->O;
+  a.na = p->n_alpha;
+  a.nb = p->n_beta;
+  a.ng = p->n_gamma;
+  a.O = j->O;
+  a.A = j->A;
+  a.reps = j->reps;
+  a.thr2 = p->bump_dist * p->bump_dist;
+  char* o = (char*)j->d_out;
+  a.best_score = (uint32_t*)(o + j->out.best_score);
+  a.best_orient = (int32_t*)(o + j->out.best_orient);
+  a.best_angle = (int16_t*)(o + j->out.best_angle);
+  a.best_xyz = (float*)(o + j->out.best_xyz);
+  a.evals = (unsigned long long*)(o + j->out.evals);
+  a.pair_tests = (unsigned long long*)(o + j->out.pair_tests);
+  a.atom_moves = (unsigned long long*)(o + j->out.atom_moves);
+  char* s = (char*)j->d_scr;
+  a.pose_score = (uint32_t*)(s + j->scr.pose_score);
+  a.pose_pick = (int16_t*)(s + j->scr.pose_pick);
+  a.pose_pairs = (unsigned long long*)(s + j->scr.pose_pairs);
+  a.done = (int32_t*)(s + j->scr.done);
+  a.work = (unsigned long long*)(s + j->scr.work);
+  a.err = (int32_t*)(o + j->out.err);
+  a.bump_bits = j->debug_bumps ? (uint8_t*)(s + j->scr.bump) : nullptr;
+  a.nmax = nmax;
+  // tile and grid staging mode
+  j->tile = tile;
+  const size_t smem_cap = 227 * 1024;
+  j->grid_in_smem = pk->dev.bytes_pad <= gd::max_smem_grid_bytes() &&
+                    gd::search_smem_bytes(a, tile, true) <= smem_cap;
+  if (!j->grid_in_smem && gd::search_smem_bytes(a, tile, false) > smem_cap) {
+    job_release(c, j);
+    return fail(GD_EINVAL, "tile %d needs more shared memory than a block has", tile);
+  }
+  GD_CUDA(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
+  if (L > 0 && (st = build_graph(c, j))) {
+    job_release(c, j);
+    return st;
+  }
+  *out = j;
+  return GD_OK;
+}
+
+gd_status enqueue_search(gd_job* j, cudaStream_t s) {
+  if (j->L == 0) return GD_OK;
+  GD_CUDA(cudaGraphLaunch(j->exec, s));
+  GD_CUDA(cudaEventRecord(j->done, s));  // releasing the job waits for this launch
+  return GD_OK;
+}
+
+gd_status enqueue_download(gd_job* j, cudaStream_t s) {
+  GD_CUDA(cudaMemcpyAsync(j->h_out, j->d_out, j->out.total, cudaMemcpyDeviceToHost, s));
+  if (j->debug) GD_CUDA(cudaMemcpyAsync(j->h_dbg, j->d_scr, j->dbg_bytes, cudaMemcpyDeviceToHost, s));
+  GD_CUDA(cudaEventRecord(j->done, s));
+  return GD_OK;
+}
+
+int default_tile(const gd_search_params* p) {
+  // 8 warps per block; two angles per lane once there are at least 64 angles
+  return p->n_angles >= 64 ? 2 : 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* gd_last_error(gd_ctx*) { return g_err.c_str(); }
+
+gd_status gd_create(gd_ctx** out, int device, size_t budget) {
+  if (!out) return fail(GD_EINVAL, "out is NULL");
+  int count = 0;
+  GD_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fail(GD_EINVAL, "device %d of %d", device, count);
+  GD_CUDA(cudaSetDevice(device));
+  gd_ctx* c = new gd_ctx();
+  c->device = device;
+  c->budget = budget;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(GD_ECUDA, "stream: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  g_err.clear();
+  return GD_OK;
+}
+
+gd_status gd_destroy(gd_ctx* c) {
+  if (!c) return GD_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : c->dev_free) cudaFree(kv.second);
+  for (auto& kv : c->host_free) cudaFreeHost(kv.second);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  delete c;
+  return GD_OK;
+}
+
+gd_status gd_load_pocket(gd_ctx* c, const uint8_t* grid, int nx, int ny, int nz, float h, const float origin[3],
+                         gd_pocket** out) {
+  if (!c || !grid || !origin || !out) return fail(GD_EINVAL, "NULL argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1ll << 31))
+    return fail(GD_EINVAL, "grid dims %d x %d x %d", nx, ny, nz);
+  if (!(h > 0.f) || !std::isfinite(h)) return fail(GD_EINVAL, "spacing must be > 0");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(origin[d])) return fail(GD_EINVAL, "origin not finite");
+  cudaSetDevice(c->device);
+  // crop to the bounding box of non-zero cells: every cell outside it scores 0
+  int lo[3] = {nx, ny, nz}, hi[3] = {-1, -1, -1};
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        if (grid[((size_t)k * ny + j) * nx + i]) {
+          lo[0] = std::min(lo[0], i); hi[0] = std::max(hi[0], i);
+          lo[1] = std::min(lo[1], j); hi[1] = std::max(hi[1], j);
+          lo[2] = std::min(lo[2], k); hi[2] = std::max(hi[2], k);
+        }
+  if (hi[0] < 0) lo[0] = lo[1] = lo[2] = hi[0] = hi[1] = hi[2] = 0;  // all zero: one zero cell
+  const int cx = hi[0] - lo[0] + 1, cy = hi[1] - lo[1] + 1, cz = hi[2] - lo[2] + 1;
+  const size_t bytes = (size_t)cx * cy * cz, pad = align_up(bytes, 16);
+  std::vector<uint8_t> crop(pad, 0);
+  for (int k = 0; k < cz; ++k)
+    for (int j = 0; j < cy; ++j)
+      memcpy(&crop[((size_t)k * cy + j) * cx], &grid[((size_t)(k + lo[2]) * ny + (j + lo[1])) * nx + lo[0]], cx);
+  gd_pocket* P = new gd_pocket();
+  gd_status st = dev_alloc(c, pad, &P->buf);
+  if (st) {
+    delete P;
+    return st;
+  }
+  P->buf_bytes = pad;
+  cudaError_t e = cudaMemcpy(P->buf, crop.data(), pad, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    dev_release(c, P->buf, pad);
+    delete P;
+    return fail(GD_ECUDA, "pocket upload: %s", cudaGetErrorString(e));
+  }
+  P->nx = nx; P->ny = ny; P->nz = nz;
+  gd::PocketDev& d = P->dev;
+  d.grid = (const uint8_t*)P->buf;
+  d.cx = cx; d.cy = cy; d.cz = cz;
+  d.bytes_pad = (int)pad;
+  d.inv_h = (float)(1.0 / (double)h);
+  const int n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    d.shift[a] = (float)(0.5 * n[a] - lo[a]);
+    d.centre[a] = (float)((double)origin[a] + 0.5 * (double)h * n[a]);
+  }
+  *out = P;
+  return GD_OK;
+}
+
+gd_status gd_free_pocket(gd_ctx* c, gd_pocket* P) {
+  if (!c || !P) return GD_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();  // a queued job may still read the grid
+  dev_release(c, P->buf, P->buf_bytes);
+  delete P;
+  return GD_OK;
+}
+
+gd_status gd_check_batch(const gd_ligand_batch* b, const gd_search_params* p) {
+  if (!b) return fail(GD_EINVAL, "batch is NULL");
+  gd_status st = check_params(p);
+  if (st) return st;
+  const int L = b->n_ligands;
+  if (L < 0) return fail(GD_EINVAL, "n_ligands < 0");
+  if (L == 0) return GD_OK;
+  if (!b->atom_off || !b->xyz || !b->bond_off || !b->bonds || !b->rot_off || !b->rot_bond)
+    return fail(GD_EINVAL, "batch has a NULL array");
+  if (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0)
+    return fail(GD_EINVAL, "CSR offsets must start at 0");
+  std::vector<float4> xyz;
+  std::vector<uint8_t> perm;
+  std::vector<RotDesc> rots;
+  for (int i = 0; i < L; ++i) {
+    if (b->atom_off[i + 1] < b->atom_off[i] || b->bond_off[i + 1] < b->bond_off[i] || b->rot_off[i + 1] < b->rot_off[i])
+      return fail(GD_EINVAL, "CSR offsets decrease at ligand %d", i);
+    const int a0 = b->atom_off[i], n = b->atom_off[i + 1] - a0;
+    const int b0 = b->bond_off[i], nb = b->bond_off[i + 1] - b0;
+    const int r0 = b->rot_off[i], R = b->rot_off[i + 1] - r0;
+    xyz.resize(std::max(n, 0));
+    perm.resize(std::max(n, 0));
+    rots.resize(std::max(R, 0));
+    double cost;
+    if ((st = pack_ligand(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
+                          p->min_bond_sep, xyz.data(), perm.data(), rots.data(), &cost)))
+      return st;
+  }
+  g_err.clear();
+  return GD_OK;
+}
+
+int gd_tile_count(void) { return gd::tile_count(); }
+
+gd_status gd_tile_info(int tile, int* warps, int* slots) {
+  if (tile < 1 || tile > gd::tile_count()) return fail(GD_EINVAL, "tile %d out of range", tile);
+  gd::Tile t = gd::tile_get(tile);
+  if (warps) *warps = t.warps;
+  if (slots) *slots = t.slots;
+  return GD_OK;
+}
+
+gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
+                      int max_ligands, void* stream, int* best_tile, float* best_ms) {
+  if (!c || !pk || !b || !p) return fail(GD_EINVAL, "NULL argument");
+  gd_status st = check_params(p);
+  if (st) return st;
+  cudaSetDevice(c->device);
+  gd_ligand_batch sub = *b;
+  if (max_ligands > 0 && sub.n_ligands > max_ligands) sub.n_ligands = max_ligands;
+  gd_search_params q = *p;
+  q.flags &= ~GD_FLAG_DEBUG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  GD_CUDA(cudaEventCreate(&e0));
+  GD_CUDA(cudaEventCreate(&e1));
+  int best = 0, nmax = 0;
+  float bms = 1e30f;
+  for (int t = 1; t <= gd::tile_count(); ++t) {
+    gd::Tile tl = gd::tile_get(t);
+    if (tl.slots > 1 && 32 * (tl.slots / 2) >= p->n_angles) continue;  // idle lanes only
+    gd_job* j = nullptr;
+    if (make_job(c, pk, &sub, &q, t, &j)) continue;
+    nmax = j->args.nmax;
+    cudaMemcpyAsync(j->d_in, j->h_in, j->in.total, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync((char*)j->d_out + j->out.err, 0, 4, s);
+    enqueue_search(j, s);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) enqueue_search(j, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    job_release(c, j);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(GD_ECUDA, "autotune tile %d: %s", t, cudaGetErrorString(e));
+    }
+    ms /= 3.f;
+    if (ms < bms) {
+      bms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!best) return fail(GD_EINVAL, "no tile could run this batch");
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->tuned[signature(pk, p, nmax, pk->dev.bytes_pad <= gd::max_smem_grid_bytes())] = best;
+  }
+  if (best_tile) *best_tile = best;
+  if (best_ms) *best_ms = bms;
+  g_err.clear();
+  return GD_OK;
+}
+
+gd_status gd_dock_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
+                        void* stream, gd_job** out) {
+  if (!c || !pk || !b || !out) return fail(GD_EINVAL, "NULL argument");
+  gd_status st = check_params(p);
+  if (st) return st;
+  cudaSetDevice(c->device);
+  int tile = p->tile;
+  if (tile == 0) tile = default_tile(p);
+  if (tile == -1) {
+    int nmax = 2;
+    for (int i = 0; i < b->n_ligands; ++i) nmax = std::max(nmax, b->atom_off[i + 1] - b->atom_off[i]);
+    const std::string sig = signature(pk, p, nmax, pk->dev.bytes_pad <= gd::max_smem_grid_bytes());
+    int found = 0;
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      auto it = c->tuned.find(sig);
+      if (it != c->tuned.end()) found = it->second;
+    }
+    if (!found && (st = gd_autotune(c, pk, b, p, 256, stream, &found, nullptr))) return st;
+    tile = found;
+  }
+  gd_job* j = nullptr;
+  if ((st = make_job(c, pk, b, p, tile, &j))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(j->d_in, j->h_in, j->in.total, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync((char*)j->d_out + j->out.err, 0, 4, s);
+  if (e != cudaSuccess) {
+    job_release(c, j);
+    return fail(GD_ECUDA, "upload: %s", cudaGetErrorString(e));
+  }
+  if ((st = enqueue_search(j, s)) || (st = enqueue_download(j, s))) {
+    job_release(c, j);
+    return st;
+  }
+  *out = j;
+  g_err.clear();
+  return GD_OK;
+}
+
+gd_status gd_job_launch(gd_ctx* c, gd_job* j, void* stream) {
+  if (!c || !j) return fail(GD_EINVAL, "NULL argument");
+  cudaSetDevice(c->device);
+  return enqueue_search(j, (cudaStream_t)stream);
+}
+
+gd_status gd_job_download(gd_ctx* c, gd_job* j, void* stream) {
+  if (!c || !j) return fail(GD_EINVAL, "NULL argument");
+  cudaSetDevice(c->device);
+  return enqueue_download(j, (cudaStream_t)stream);
+}
+
+gd_status gd_fetch_results(gd_ctx* c, gd_job* j, gd_result_batch* r, int blocking) {
+  if (!c || !j || !r) return fail(GD_EINVAL, "NULL argument");
+  cudaSetDevice(c->device);
+  if (blocking) {
+    GD_CUDA(cudaEventSynchronize(j->done));
+  } else {
+    cudaError_t e = cudaEventQuery(j->done);
+    if (e == cudaErrorNotReady) return GD_ENOTREADY;
+    if (e != cudaSuccess) return fail(GD_ECUDA, "job: %s", cudaGetErrorString(e));
+  }
+  if (j->L == 0) return GD_OK;
+  const char* h = (const char*)j->h_out;
+  int32_t err = 0;  // the kernel's error word travels with the results
+  memcpy(&err, h + j->out.err, 4);
+  if (err == gd::ERR_STAGE_TIMEOUT) return fail(GD_ETIMEOUT, "pocket staging wait timed out on the device");
+  const int L = j->L;
+  if (r->best_score) memcpy(r->best_score, h + j->out.best_score, 4 * (size_t)L);
+  if (r->best_orient) memcpy(r->best_orient, h + j->out.best_orient, 4 * (size_t)L);
+  if (r->best_angle) memcpy(r->best_angle, h + j->out.best_angle, 2 * (size_t)j->Rt * j->reps);
+  if (r->best_xyz) memcpy(r->best_xyz, h + j->out.best_xyz, 12 * (size_t)j->N);
+  if (r->evals) memcpy(r->evals, h + j->out.evals, 8 * (size_t)L);
+  if (r->pair_tests) memcpy(r->pair_tests, h + j->out.pair_tests, 8 * (size_t)L);
+  if (r->atom_moves) memcpy(r->atom_moves, h + j->out.atom_moves, 8 * (size_t)L);
+  if (r->orient_score || r->orient_pick || r->bump_bits) {
+    if (!j->debug) return fail(GD_EINVAL, "debug outputs need GD_FLAG_DEBUG at dock time");
+    if (r->bump_bits && !j->debug_bumps) return fail(GD_EINVAL, "bump_bits need GD_FLAG_DEBUG_BUMPS at dock time");
+    const char* dh = (const char*)j->h_dbg;
+    if (r->orient_score) memcpy(r->orient_score, dh + j->scr.pose_score, 4 * (size_t)L * j->O);
+    if (r->orient_pick) memcpy(r->orient_pick, dh + j->scr.pose_pick, 2 * (size_t)j->O * j->reps * j->Rt);
+    if (r->bump_bits) memcpy(r->bump_bits, dh + j->scr.bump, (size_t)j->O * j->reps * j->A * j->Rt);
+  }
+  return GD_OK;
+}
+
+gd_status gd_job_bytes(gd_ctx* c, const gd_job* j, uint64_t* h2d, uint64_t* d2h) {
+  if (!c || !j) return fail(GD_EINVAL, "NULL argument");
+  if (h2d) *h2d = j->L ? (uint64_t)j->in.total : 0;
+  if (d2h) *d2h = (uint64_t)j->out.total + (j->debug ? (uint64_t)j->dbg_bytes : 0);
+  return GD_OK;
+}
+
+gd_status gd_job_free(gd_ctx* c, gd_job* j) {
+  if (!c || !j) return GD_OK;
+  cudaSetDevice(c->device);
+  return job_release(c, j);
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal layout shared by the host runtime (gd_api.cu) and the search kernel
+// (gd_search.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gd {
+
+// One rotamer as the kernel sees it.  Atoms of a ligand are renumbered in DFS
+// preorder from atom 0, so the subtree under either end of a tree bond is one
+// contiguous range [lo, hi); the rotating fragment is that range (comp = 0) or its
+// complement (comp = 1).  p / q are the static / moving ends of the bond (preorder
+// ids).  excl_* lists the moving x static pairs whose graph distance is below
+// min_bond_sep, sorted by the moving atom: in a tree every moving-static path runs
+// through q-p, so these are the pairs with dist(a,q) + 1 + dist(p,b) < min_bond_sep.
+struct alignas(16) RotDesc {
+  uint16_t p, q;
+  uint16_t lo, hi;
+  uint8_t comp;
+  uint8_t n_excl;
+  uint8_t pad[6];
+  uint8_t excl_a[16];
+  uint8_t excl_b[16];
+};
+static_assert(sizeof(RotDesc) == 48, "RotDesc layout");
+
+struct PocketDev {
+  const uint8_t* grid;   // cropped grid [cz][cy][cx]; cells outside the crop are 0
+  int cx, cy, cz;        // crop extents (cells)
+  int bytes_pad;         // cx*cy*cz rounded up to 16 (bulk-copy granule)
+  float inv_h;
+  float shift[3];        // n/2 - crop_lo per axis: cell = floor(x_rel * inv_h + shift)
+  float centre[3];       // pocket centre (world): x_world = x_rel + centre
+};
+
+struct SearchArgs {
+  PocketDev pk;
+  // batch (preorder-packed)
+  int L;
+  const int32_t* atom_off;    // [L+1]
+  const int32_t* rot_off;     // [L+1]
+  const float4* xyz;          // [N] preorder, input coordinates (w unused)
+  const uint8_t* perm;        // [N] preorder id -> input-order local id
+  const RotDesc* rots;        // [Rt]
+  const int32_t* order;       // [L] ligand processing order (largest cost first)
+  long long n_items;          // L * O
+  // search parameters
+  int na, nb, ng, O, A, reps;
+  float thr2;                 // bump_dist^2
+  // outputs
+  uint32_t* best_score;       // [L]
+  int32_t* best_orient;       // [L]
+  int16_t* best_angle;        // [reps * Rt]
+  float* best_xyz;            // [3N]
+  unsigned long long* evals;  // [L]
+  unsigned long long* pair_tests;  // [L]
+  unsigned long long* atom_moves;  // [L]
+  // scratch
+  uint32_t* pose_score;       // [L*O]
+  int16_t* pose_pick;         // [O * reps * Rt]
+  unsigned long long* pose_pairs;  // [L*O]
+  int32_t* done;              // [L]   zeroed before every launch
+  unsigned long long* work;   // [1]   zeroed before every launch
+  int32_t* err;               // [1]   0 = fine, else error code (output block; zeroed at setup)
+  // debug (may be null)
+  uint8_t* bump_bits;         // [O * reps * A * Rt]
+  int nmax;                   // largest ligand of the batch (per-warp buffer size)
+};
+
+enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };
+
+// Launch configuration of one tile.
+struct Tile {
+  int warps;        // warps (poses in flight) per block
+  int slots;        // angles per lane evaluated together
+};
+int tile_count();
+Tile tile_get(int id);  // id in [1, tile_count()]
+
+// Launch shape of the search kernel for one tile (kernel attributes and occupancy are
+// queried here, outside any stream capture).
+struct LaunchCfg {
+  const void* fn = nullptr;
+  unsigned blocks = 0, threads = 0;
+  size_t smem = 0;
+};
+cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int num_sms, LaunchCfg* cfg);
+// Launch the search (kernel only; the work counter and per-ligand counters must be
+// zeroed by the caller first).
+cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t stream);
+size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem);
+int max_smem_grid_bytes();
+
+}  // namespace gd

@@ -1,0 +1,528 @@
+// Fused GeoDock pose-search kernel for sm_103a.
+//
+// One warp owns one pose (ligand, restart orientation) from placement to its final
+// score; the CTA is persistent and its warps pull poses from a global counter.
+//   a1  the pocket grid is staged once per CTA into shared memory with bulk async
+//       copies completing on an mbarrier (when the cropped grid fits), else read
+//       through L1/L2;
+//   a2  the ligand (preorder-packed float4) is read into a per-warp shared buffer;
+//   a3  generate_starting_pose: ZYZ Euler restart about the centroid, moved to the
+//       pocket centre (Listing 1 / Sec. 3.1);
+//   a4  rigid score: sum of grid cells under the atoms (scoring function, Sec. 3.2);
+//   a5-a8 optimize_pose (Sec. 3.1, Sec. 4.1): for each rotamer in order, every lane
+//       evaluates its own angles k = lane + 32 j: Rodrigues rotation of the moving
+//       fragment about the current bond axis, bump test of every moving atom against
+//       every static atom (exclusions of atoms fewer than min_bond_sep bonds apart
+//       handled by parking those static atoms far away while that moving atom is
+//       tested), grid gather; a warp max-reduction over a packed (score, -k) key is
+//       the per-fragment reduction, and the winning rotation is committed;
+//   a9  the rotamer loop repeats `reps` times (num_repetitions, Listing 1);
+//   a10 the last warp to finish a ligand reduces over its restarts (ties: smallest
+//       o), replays the winning pose to recover its coordinates and writes results.
+// All geometry uses explicitly rounded FP32 intrinsics, so the search and the replay
+// produce bitwise-identical coordinates and no launch tile can change a result.
+#include <cstdint>
+
+#include "gd_internal.h"
+
+namespace gd {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr float PARK = 1.0e18f;  // far-away position for excluded static atoms
+
+struct Rot3 {
+  float m[9];
+  float p[3];  // rotation centre: x' = p + M (x - p)
+};
+
+// Rodrigues: M = c I + s [u]x + (1 - c) u u^T for the unit axis u.
+__device__ __forceinline__ Rot3 rodrigues(float ux, float uy, float uz, float c, float s, float4 p) {
+  Rot3 R;
+  const float omc = __fsub_rn(1.0f, c);
+  const float ox = __fmul_rn(omc, ux), oy = __fmul_rn(omc, uy), oz = __fmul_rn(omc, uz);
+  const float sx = __fmul_rn(s, ux), sy = __fmul_rn(s, uy), sz = __fmul_rn(s, uz);
+  R.m[0] = __fmaf_rn(ox, ux, c);
+  R.m[1] = __fsub_rn(__fmul_rn(ox, uy), sz);
+  R.m[2] = __fadd_rn(__fmul_rn(ox, uz), sy);
+  R.m[3] = __fadd_rn(__fmul_rn(oy, ux), sz);
+  R.m[4] = __fmaf_rn(oy, uy, c);
+  R.m[5] = __fsub_rn(__fmul_rn(oy, uz), sx);
+  R.m[6] = __fsub_rn(__fmul_rn(oz, ux), sy);
+  R.m[7] = __fadd_rn(__fmul_rn(oz, uy), sx);
+  R.m[8] = __fmaf_rn(oz, uz, c);
+  R.p[0] = p.x;
+  R.p[1] = p.y;
+  R.p[2] = p.z;
+  return R;
+}
+
+__device__ __forceinline__ void rot_apply(const Rot3& R, float x, float y, float z, float& ox,
+                                          float& oy, float& oz) {
+  const float dx = __fsub_rn(x, R.p[0]), dy = __fsub_rn(y, R.p[1]), dz = __fsub_rn(z, R.p[2]);
+  ox = __fadd_rn(R.p[0], __fmaf_rn(R.m[0], dx, __fmaf_rn(R.m[1], dy, __fmul_rn(R.m[2], dz))));
+  oy = __fadd_rn(R.p[1], __fmaf_rn(R.m[3], dx, __fmaf_rn(R.m[4], dy, __fmul_rn(R.m[5], dz))));
+  oz = __fadd_rn(R.p[2], __fmaf_rn(R.m[6], dx, __fmaf_rn(R.m[7], dy, __fmul_rn(R.m[8], dz))));
+}
+
+// Angle theta_k = 2 pi k / A as (cos, sin).
+__device__ __forceinline__ void angle_cs(int k, int A, float& c, float& s) {
+  sincospif(__fdiv_rn(2.0f * (float)k, (float)A), &s, &c);
+}
+
+// Grid cell under a point (pocket-centred coordinates); 0 outside the cropped box.
+template <bool SG>
+__device__ __forceinline__ int cell(const PocketDev& pk, const uint8_t* sg, float x, float y, float z) {
+  const int ix = __float2int_rd(__fmaf_rn(x, pk.inv_h, pk.shift[0]));
+  const int iy = __float2int_rd(__fmaf_rn(y, pk.inv_h, pk.shift[1]));
+  const int iz = __float2int_rd(__fmaf_rn(z, pk.inv_h, pk.shift[2]));
+  if ((unsigned)ix >= (unsigned)pk.cx || (unsigned)iy >= (unsigned)pk.cy || (unsigned)iz >= (unsigned)pk.cz)
+    return 0;
+  const int idx = (iz * pk.cy + iy) * pk.cx + ix;
+  if (SG) return sg[idx];
+  return __ldg(pk.grid + idx);
+}
+
+__device__ __forceinline__ bool is_moving(const RotDesc& rd, int i) {
+  return rd.comp ? (i < rd.lo || i >= rd.hi) : (i >= rd.lo && i < rd.hi);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  // xor butterfly: every lane adds the same two partial sums in either order, so all
+  // lanes end with the same bits
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(FULL, v, off));
+  return v;
+}
+
+// a3: x <- R_o (x0 - c_lig), coordinates relative to the pocket centre.
+__device__ void place(const SearchArgs& a, float4* X, const float4* x0, int n, int o, int lane) {
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = x0[i];
+    sx = __fadd_rn(sx, v.x);
+    sy = __fadd_rn(sy, v.y);
+    sz = __fadd_rn(sz, v.z);
+  }
+  sx = warp_sum_f(sx);
+  sy = warp_sum_f(sy);
+  sz = warp_sum_f(sz);
+  const float cx = __fdiv_rn(sx, (float)n), cy = __fdiv_rn(sy, (float)n), cz = __fdiv_rn(sz, (float)n);
+  const int ia = o / (a.nb * a.ng), jb = (o / a.ng) % a.nb, kg = o % a.ng;
+  float sa, ca, sb, cb, sg, cg;
+  sincospif(__fdiv_rn(2.0f * (float)ia, (float)a.na), &sa, &ca);
+  sincospif(__fdiv_rn(__fadd_rn((float)jb, 0.5f), (float)a.nb), &sb, &cb);
+  sincospif(__fdiv_rn(2.0f * (float)kg, (float)a.ng), &sg, &cg);
+  // R = Rz(alpha) Ry(beta) Rz(gamma)
+  const float cacb = __fmul_rn(ca, cb), sacb = __fmul_rn(sa, cb);
+  const float r00 = __fsub_rn(__fmul_rn(cacb, cg), __fmul_rn(sa, sg));
+  const float r01 = __fsub_rn(__fmul_rn(-cacb, sg), __fmul_rn(sa, cg));
+  const float r02 = __fmul_rn(ca, sb);
+  const float r10 = __fadd_rn(__fmul_rn(sacb, cg), __fmul_rn(ca, sg));
+  const float r11 = __fadd_rn(__fmul_rn(-sacb, sg), __fmul_rn(ca, cg));
+  const float r12 = __fmul_rn(sa, sb);
+  const float r20 = __fmul_rn(-sb, cg);
+  const float r21 = __fmul_rn(sb, sg);
+  const float r22 = cb;
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = x0[i];
+    const float dx = __fsub_rn(v.x, cx), dy = __fsub_rn(v.y, cy), dz = __fsub_rn(v.z, cz);
+    X[i] = make_float4(__fmaf_rn(r00, dx, __fmaf_rn(r01, dy, __fmul_rn(r02, dz))),
+                       __fmaf_rn(r10, dx, __fmaf_rn(r11, dy, __fmul_rn(r12, dz))),
+                       __fmaf_rn(r20, dx, __fmaf_rn(r21, dy, __fmul_rn(r22, dz))), 0.f);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void load_desc(RotDesc* dst, const RotDesc* src, int lane) {
+  if (lane < 12) reinterpret_cast<uint32_t*>(dst)[lane] = __ldg(reinterpret_cast<const uint32_t*>(src) + lane);
+  __syncwarp();
+}
+
+// Unit bond axis from the static end p to the moving end q (current coordinates).
+__device__ __forceinline__ void bond_axis(const float4* X, const RotDesc& rd, float& ux, float& uy, float& uz) {
+  const float4 xp = X[rd.p], xq = X[rd.q];
+  const float dx = __fsub_rn(xq.x, xp.x), dy = __fsub_rn(xq.y, xp.y), dz = __fsub_rn(xq.z, xp.z);
+  const float inv = __frsqrt_rn(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+  ux = __fmul_rn(dx, inv);
+  uy = __fmul_rn(dy, inv);
+  uz = __fmul_rn(dz, inv);
+}
+
+// Commit the winning rotation k to the fragment (same arithmetic as the candidate).
+__device__ void commit(float4* X, int n, const RotDesc& rd, float ux, float uy, float uz, int k, int A,
+                       int lane) {
+  float c, s;
+  angle_cs(k, A, c, s);
+  const Rot3 R = rodrigues(ux, uy, uz, c, s, X[rd.p]);
+  __syncwarp();
+  for (int i = lane; i < n; i += 32)
+    if (is_moving(rd, i)) {
+      const float4 v = X[i];
+      float x, y, z;
+      rot_apply(R, v.x, v.y, v.z, x, y, z);
+      X[i] = make_float4(x, y, z, 0.f);
+    }
+  __syncwarp();
+}
+
+template <bool SG>
+__device__ __forceinline__ int score_atoms(const PocketDev& pk, const uint8_t* sg, const float4* X, int n,
+                                           int lane) {
+  int s = 0;
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = X[i];
+    s += cell<SG>(pk, sg, v.x, v.y, v.z);
+  }
+  return __reduce_add_sync(FULL, s);
+}
+
+template <bool SG>
+__device__ __forceinline__ int score_static(const PocketDev& pk, const uint8_t* sg, const float4* X, int n,
+                                            const RotDesc& rd, int lane) {
+  int s = 0;
+  for (int i = lane; i < n; i += 32)
+    if (!is_moving(rd, i)) {
+      const float4 v = X[i];
+      s += cell<SG>(pk, sg, v.x, v.y, v.z);
+    }
+  return __reduce_add_sync(FULL, s);
+}
+
+// Smallest squared distance from the S rotated points to static atoms [b0, b1).
+template <int S>
+__device__ __forceinline__ void min_d2_range(const float4* X, int b0, int b1, const float (&xr)[S][3],
+                                             float (&mind)[S]) {
+#pragma unroll 4
+  for (int b = b0; b < b1; ++b) {
+    const float4 xb = X[b];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const float dx = __fsub_rn(xr[j][0], xb.x);
+      const float dy = __fsub_rn(xr[j][1], xb.y);
+      const float dz = __fsub_rn(xr[j][2], xb.z);
+      mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+    }
+  }
+}
+
+// Evaluate every angle of one rotamer step; returns the warp-wide best key
+// ((score + 1) << 16 | (0xFFFF - k)), 0 if every candidate is bumped.
+template <int S, bool SG>
+__device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X, int n, const RotDesc& rd,
+                              float ux, float uy, float uz, int s_static, int lane,
+                              unsigned long long& pairs, uint8_t* dbg) {
+  const float4 xp = X[rd.p];
+  int m0a, m0b, m1a, m1b, s0a, s0b, s1a, s1b;
+  if (rd.comp) {
+    m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
+    s0a = rd.lo; s0b = rd.hi; s1a = 0; s1b = 0;
+  } else {
+    m0a = rd.lo; m0b = rd.hi; m1a = 0; m1b = 0;
+    s0a = 0; s0b = rd.lo; s1a = rd.hi; s1b = n;
+  }
+  const unsigned n_static = (unsigned)((s0b - s0a) + (s1b - s1a));
+  const int passes = (a.A + 32 * S - 1) / (32 * S);
+  unsigned best = 0;
+  for (int pass = 0; pass < passes; ++pass) {
+    Rot3 R[S];
+    int kk[S], sc[S];
+    bool bump[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      kk[j] = lane + 32 * (pass * S + j);
+      float c, s;
+      angle_cs(kk[j] < a.A ? kk[j] : 0, a.A, c, s);
+      R[j] = rodrigues(ux, uy, uz, c, s, xp);
+      sc[j] = s_static;
+      bump[j] = kk[j] >= a.A;  // idle slots count as rejected
+    }
+    int ex = 0;
+    bool stop = false;
+    for (int seg = 0; seg < 2 && !stop; ++seg) {
+      const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
+      for (int ai = ma; ai < mb; ++ai) {
+        const float4 xa = X[ai];
+        // park the static atoms this moving atom must not be tested against
+        int ex_end = ex;
+        while (ex_end < rd.n_excl && rd.excl_a[ex_end] == ai) ++ex_end;
+        float4 saved = make_float4(0.f, 0.f, 0.f, 0.f);
+        int my_b = -1;
+        if (ex_end > ex) {
+          __syncwarp();
+          if (lane < ex_end - ex) {
+            my_b = rd.excl_b[ex + lane];
+            saved = X[my_b];
+            X[my_b] = make_float4(PARK, PARK, PARK, 0.f);
+          }
+          __syncwarp();
+        }
+        float xr[S][3], mind[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          rot_apply(R[j], xa.x, xa.y, xa.z, xr[j][0], xr[j][1], xr[j][2]);
+          sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
+          mind[j] = 3.0e38f;
+        }
+        min_d2_range<S>(X, s0a, s0b, xr, mind);
+        min_d2_range<S>(X, s1a, s1b, xr, mind);
+        bool done = true;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          if (!bump[j]) pairs += n_static;
+          bump[j] = bump[j] || (mind[j] < a.thr2);
+          done = done && bump[j];
+        }
+        if (ex_end > ex) {
+          __syncwarp();
+          if (my_b >= 0) X[my_b] = saved;
+          __syncwarp();
+          ex = ex_end;
+        }
+        if (__all_sync(FULL, done)) {
+          stop = true;
+          break;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+      if (kk[j] < a.A) {
+        const unsigned key = bump[j] ? 0u : (((unsigned)(sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
+        best = key > best ? key : best;
+        if (dbg) dbg[kk[j]] = bump[j] ? 1 : 0;
+      }
+  }
+  return __reduce_max_sync(FULL, best);
+}
+
+// a10: reduce over the ligand's restarts, replay the winner, write the results.
+__device__ void finalize(const SearchArgs& a, float4* X, RotDesc* rds, int li, int lane) {
+  const int O = a.O;
+  unsigned best = 0;
+  unsigned long long pairs = 0;
+  for (int o = lane; o < O; o += 32) {
+    const unsigned s = __ldcg(a.pose_score + (size_t)li * O + o);
+    const unsigned key = ((s + 1u) << 16) | (0xFFFFu - (unsigned)o);
+    best = key > best ? key : best;
+    pairs += __ldcg(a.pose_pairs + (size_t)li * O + o);
+  }
+  best = __reduce_max_sync(FULL, best);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) pairs += __shfl_xor_sync(FULL, pairs, off);
+  const int ob = (int)(0xFFFFu - (best & 0xFFFFu));
+  const unsigned sb = (best >> 16) - 1u;
+  const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
+  const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
+  const size_t pick_base = (size_t)r0 * a.reps * O + (size_t)ob * a.reps * R;
+  unsigned long long fsum = 0;  // sum of fragment sizes over the rotamers
+  for (int r = lane; r < R; r += 32) {
+    const RotDesc* d = a.rots + r0 + r;
+    const int sub = (int)__ldg(&d->hi) - (int)__ldg(&d->lo);
+    fsum += (unsigned long long)(__ldg(&d->comp) ? n - sub : sub);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(FULL, fsum, off);
+  if (lane == 0) {
+    a.best_score[li] = sb;
+    a.best_orient[li] = ob;
+    a.evals[li] = (unsigned long long)O * a.reps * R * a.A;
+    a.pair_tests[li] = pairs;
+    a.atom_moves[li] = (unsigned long long)O * a.reps * a.A * fsum;
+  }
+  for (int s = lane; s < a.reps * R; s += 32)
+    a.best_angle[(size_t)r0 * a.reps + s] = __ldcg(a.pose_pick + pick_base + s);
+  place(a, X, a.xyz + a0, n, ob, lane);
+  for (int rep = 0; rep < a.reps; ++rep)
+    for (int r = 0; r < R; ++r) {
+      const int k = __ldcg(a.pose_pick + pick_base + rep * R + r);
+      if (k < 0) continue;
+      load_desc(rds, a.rots + r0 + r, lane);
+      const RotDesc& rd = *rds;
+      float ux, uy, uz;
+      bond_axis(X, rd, ux, uy, uz);
+      commit(X, n, rd, ux, uy, uz, k, a.A, lane);
+    }
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = X[i];
+    float* dst = a.best_xyz + 3 * ((size_t)a0 + a.perm[a0 + i]);
+    dst[0] = __fadd_rn(v.x, a.pk.centre[0]);
+    dst[1] = __fadd_rn(v.y, a.pk.centre[1]);
+    dst[2] = __fadd_rn(v.z, a.pk.centre[2]);
+  }
+  __syncwarp();
+}
+
+template <int S, bool SG>
+__device__ void search_pose(const SearchArgs& a, const uint8_t* sg, float4* X, RotDesc* rds, int li, int o,
+                            int lane) {
+  const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
+  const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
+  place(a, X, a.xyz + a0, n, o, lane);
+  int cur = score_atoms<SG>(a.pk, sg, X, n, lane);
+  unsigned long long pairs = 0;
+  const size_t pick_base = (size_t)r0 * a.reps * a.O + (size_t)o * a.reps * R;
+  for (int rep = 0; rep < a.reps; ++rep)
+    for (int r = 0; r < R; ++r) {
+      load_desc(rds, a.rots + r0 + r, lane);
+      const RotDesc& rd = *rds;
+      float ux, uy, uz;
+      bond_axis(X, rd, ux, uy, uz);
+      const int s_static = score_static<SG>(a.pk, sg, X, n, rd, lane);
+      uint8_t* dbg = nullptr;
+      if (a.bump_bits)
+        dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
+      const unsigned key = eval_step<S, SG>(a, sg, X, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
+      const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
+      if (k >= 0) {
+        commit(X, n, rd, ux, uy, uz, k, a.A, lane);
+        cur = (int)(key >> 16) - 1;
+      }
+      if (lane == 0) a.pose_pick[pick_base + rep * R + r] = (int16_t)k;
+      __syncwarp();
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) pairs += __shfl_xor_sync(FULL, pairs, off);
+  if (lane == 0) {
+    a.pose_score[(size_t)li * a.O + o] = (uint32_t)cur;
+    a.pose_pairs[(size_t)li * a.O + o] = pairs;
+  }
+  __syncwarp();
+  __threadfence();
+  int prev = 0;
+  if (lane == 0) prev = atomicAdd(a.done + li, 1);
+  prev = __shfl_sync(FULL, prev, 0);
+  if (prev == a.O - 1) {
+    __threadfence();
+    finalize(a, X, rds, li, lane);
+  }
+}
+
+// ---- bulk async copy of the grid into shared memory --------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
+  const int bytes = a.pk.bytes_pad;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+    constexpr int CHUNK = 32768;
+    for (int off = 0; off < bytes; off += CHUNK) {
+      const int len = bytes - off < CHUNK ? bytes - off : CHUNK;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(sg + off)),
+          "l"(a.pk.grid + off), "r"(len), "r"(smem_u32(mbar))
+          : "memory");
+    }
+  }
+  // bounded wait on phase 0 (about two seconds at the maximum clock)
+  const long long t0 = clock64();
+  uint32_t ok = 0;
+  while (!ok) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar))
+        : "memory");
+    if (!ok && clock64() - t0 > 4000000000LL) return false;
+  }
+  return true;
+}
+
+template <int S, bool SG>
+__global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* sg = nullptr;
+  size_t off = 0;
+  if (SG) {
+    sg = smem;
+    off = (size_t)a.pk.bytes_pad;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + off);
+    off += 16;
+    if (!stage_grid(a, sg, mbar)) {
+      if (threadIdx.x == 0) atomicExch(a.err, ERR_STAGE_TIMEOUT);
+      return;
+    }
+  }
+  float4* X = reinterpret_cast<float4*>(smem + off + (size_t)warp * ((size_t)a.nmax * 16 + 64));
+  RotDesc* rds = reinterpret_cast<RotDesc*>(X + a.nmax);
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(a.work, 1ull);
+    t = __shfl_sync(FULL, t, 0);
+    if (t >= (unsigned long long)a.n_items) break;
+    const int li = a.order[t / (unsigned long long)a.O];
+    const int o = (int)(t % (unsigned long long)a.O);
+    search_pose<S, SG>(a, sg, X, rds, li, o, lane);
+  }
+}
+
+template <int S, bool SG>
+cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, LaunchCfg* cfg) {
+  auto k = search_kernel<S, SG>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, warps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = (long long)per_sm * num_sms;
+  const long long need = (a.n_items + warps - 1) / warps;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  cfg->fn = (const void*)k;
+  cfg->blocks = (unsigned)blocks;
+  cfg->threads = (unsigned)(warps * 32);
+  cfg->smem = smem;
+  return cudaSuccess;
+}
+
+constexpr Tile kTiles[] = {{8, 1}, {8, 2}, {8, 4}, {4, 1}, {4, 2}, {4, 4},
+                           {16, 1}, {16, 2}, {16, 4}, {2, 1}, {2, 2}, {2, 4}};
+
+}  // namespace
+
+int tile_count() { return (int)(sizeof(kTiles) / sizeof(kTiles[0])); }
+Tile tile_get(int id) { return kTiles[id - 1]; }
+int max_smem_grid_bytes() { return 200 * 1024; }
+
+size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
+  const Tile t = tile_get(tile);
+  size_t s = (size_t)t.warps * ((size_t)a.nmax * 16 + 64);
+  if (grid_in_smem) s += (size_t)a.pk.bytes_pad + 16;
+  return s;
+}
+
+cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int num_sms, LaunchCfg* cfg) {
+  const Tile t = tile_get(tile);
+  const size_t smem = search_smem_bytes(a, tile, grid_in_smem);
+  if (grid_in_smem) {
+    switch (t.slots) {
+      case 1: return plan_t<1, true>(a, t.warps, smem, num_sms, cfg);
+      case 2: return plan_t<2, true>(a, t.warps, smem, num_sms, cfg);
+      default: return plan_t<4, true>(a, t.warps, smem, num_sms, cfg);
+    }
+  }
+  switch (t.slots) {
+    case 1: return plan_t<1, false>(a, t.warps, smem, num_sms, cfg);
+    case 2: return plan_t<2, false>(a, t.warps, smem, num_sms, cfg);
+    default: return plan_t<4, false>(a, t.warps, smem, num_sms, cfg);
+  }
+}
+
+cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t st) {
+  void* args[] = {const_cast<SearchArgs*>(&a)};
+  return cudaLaunchKernel(cfg.fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+}  // namespace gd

@@ -1,0 +1,285 @@
+"""Python binding of libgeodock (include/geodock.h): argument marshalling only.
+
+Every step of the pose search runs in the CUDA library; this module converts numpy
+arrays to the C structs, passes CUDA stream handles (torch streams or raw handles)
+and turns status codes into exceptions.  If the library has not been built, loading
+fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgeodock.so")
+
+GD_OK, GD_EINVAL, GD_ENOMEM, GD_EBUDGET, GD_ECUDA, GD_ETIMEOUT, GD_EBUSY, GD_ENOTREADY = range(8)
+GD_FLAG_DEBUG = 1
+GD_FLAG_DEBUG_BUMPS = 2
+STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: "GD_ECUDA",
+                5: "GD_ETIMEOUT", 6: "GD_EBUSY", 7: "GD_ENOTREADY"}
+
+# every entry point declared in include/geodock.h
+EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_free_pocket",
+           "gd_dock_batch", "gd_fetch_results", "gd_job_launch", "gd_job_download", "gd_job_bytes", "gd_job_free",
+           "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune"]
+
+
+class GeoDockError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LigandBatchC(C.Structure):
+    _fields_ = [("n_ligands", C.c_int32), ("atom_off", C.POINTER(C.c_int32)), ("xyz", C.POINTER(C.c_float)),
+                ("bond_off", C.POINTER(C.c_int32)), ("bonds", C.POINTER(C.c_int32)),
+                ("rot_off", C.POINTER(C.c_int32)), ("rot_bond", C.POINTER(C.c_int32))]
+
+
+class SearchParamsC(C.Structure):
+    _fields_ = [("n_alpha", C.c_int32), ("n_beta", C.c_int32), ("n_gamma", C.c_int32),
+                ("n_angles", C.c_int32), ("bump_dist", C.c_float), ("min_bond_sep", C.c_int32),
+                ("repetitions", C.c_int32), ("flags", C.c_int32), ("tile", C.c_int32)]
+
+
+class ResultBatchC(C.Structure):
+    _fields_ = [("best_score", C.POINTER(C.c_uint32)), ("best_orient", C.POINTER(C.c_int32)),
+                ("best_angle", C.POINTER(C.c_int16)), ("best_xyz", C.POINTER(C.c_float)),
+                ("evals", C.POINTER(C.c_uint64)), ("pair_tests", C.POINTER(C.c_uint64)),
+                ("atom_moves", C.POINTER(C.c_uint64)), ("orient_score", C.POINTER(C.c_uint32)), ("orient_pick", C.POINTER(C.c_int16)),
+                ("bump_bits", C.POINTER(C.c_uint8))]
+
+
+_lib = None
+
+
+def load():
+    """Load libgeodock.so; raises if it is missing (build it with build.py / build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgeodock.so not found at {LIB_PATH}: build the CUDA library first "
+                           "(python -m paper_1901_06229_b300.build)")
+    L = C.CDLL(LIB_PATH)
+    vp, P = C.c_void_p, C.POINTER
+    L.gd_create.argtypes = [P(vp), C.c_int, C.c_size_t]
+    L.gd_destroy.argtypes = [vp]
+    L.gd_last_error.argtypes = [vp]
+    L.gd_last_error.restype = C.c_char_p
+    L.gd_load_pocket.argtypes = [vp, P(C.c_uint8), C.c_int, C.c_int, C.c_int, C.c_float, P(C.c_float), P(vp)]
+    L.gd_free_pocket.argtypes = [vp, vp]
+    L.gd_dock_batch.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), vp, P(vp)]
+    L.gd_fetch_results.argtypes = [vp, vp, P(ResultBatchC), C.c_int]
+    L.gd_job_launch.argtypes = [vp, vp, vp]
+    L.gd_job_download.argtypes = [vp, vp, vp]
+    L.gd_job_free.argtypes = [vp, vp]
+    L.gd_job_bytes.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint64)]
+    L.gd_check_batch.argtypes = [P(LigandBatchC), P(SearchParamsC)]
+    L.gd_tile_count.argtypes = []
+    L.gd_tile_info.argtypes = [C.c_int, P(C.c_int), P(C.c_int)]
+    L.gd_autotune.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), C.c_int, vp, P(C.c_int), P(C.c_float)]
+    for f in EXPORTS:
+        if f not in ("gd_last_error",):
+            getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def params_c(params, flags=0, tile=0) -> SearchParamsC:
+    return SearchParamsC(params.n_alpha, params.n_beta, params.n_gamma, params.n_angles,
+                         float(params.bump_dist), params.min_bond_sep, params.repetitions, flags, tile)
+
+
+class _BatchArrays:
+    """Keeps the contiguous numpy arrays alive while C holds pointers to them."""
+
+    def __init__(self, batch):
+        self.atom_off = np.ascontiguousarray(batch.atom_off, np.int32)
+        self.xyz = np.ascontiguousarray(batch.xyz, np.float32)
+        self.bond_off = np.ascontiguousarray(batch.bond_off, np.int32)
+        self.bonds = np.ascontiguousarray(batch.bonds, np.int32)
+        self.rot_off = np.ascontiguousarray(batch.rot_off, np.int32)
+        self.rot_bond = np.ascontiguousarray(batch.rot_bond, np.int32)
+        self.c = LigandBatchC(len(self.atom_off) - 1, _ptr(self.atom_off, C.c_int32), _ptr(self.xyz, C.c_float),
+                              _ptr(self.bond_off, C.c_int32), _ptr(self.bonds, C.c_int32),
+                              _ptr(self.rot_off, C.c_int32), _ptr(self.rot_bond, C.c_int32))
+
+
+class Job:
+    def __init__(self, ctx, handle, batch, params, debug, bumps=False):
+        self.ctx, self.handle, self.debug, self.bumps = ctx, handle, debug or bumps, bumps
+        self.L = batch.n_ligands
+        self.N = len(batch.xyz)
+        self.rot_off = np.asarray(batch.rot_off, np.int64)
+        self.params = params
+
+    def fetch(self, blocking=True, out=None):
+        """Results as numpy arrays (see gd_result_batch); None if not ready (non-blocking)."""
+        p = self.params
+        O, reps, A = p.n_alpha * p.n_beta * p.n_gamma, p.repetitions, p.n_angles
+        Rt = int(self.rot_off[-1]) if len(self.rot_off) else 0
+        r = out if out is not None else dict(
+            best_score=np.zeros(self.L, np.uint32), best_orient=np.zeros(self.L, np.int32),
+            best_angle=np.zeros(Rt * reps, np.int16), best_xyz=np.zeros((self.N, 3), np.float32),
+            evals=np.zeros(self.L, np.uint64), pair_tests=np.zeros(self.L, np.uint64),
+            atom_moves=np.zeros(self.L, np.uint64))
+        if self.debug and out is None:
+            r["orient_score"] = np.zeros((self.L, O), np.uint32)
+            r["orient_pick"] = np.zeros(Rt * reps * O, np.int16)
+        if self.bumps and out is None:
+            r["bump_bits"] = np.zeros(Rt * reps * O * A, np.uint8)
+        nul = lambda ct: C.cast(None, C.POINTER(ct))
+        rb = ResultBatchC(_ptr(r["best_score"], C.c_uint32), _ptr(r["best_orient"], C.c_int32),
+                          _ptr(r["best_angle"], C.c_int16), _ptr(r["best_xyz"], C.c_float),
+                          _ptr(r["evals"], C.c_uint64), _ptr(r["pair_tests"], C.c_uint64),
+                          _ptr(r["atom_moves"], C.c_uint64),
+                          _ptr(r["orient_score"], C.c_uint32) if "orient_score" in r else nul(C.c_uint32),
+                          _ptr(r["orient_pick"], C.c_int16) if "orient_pick" in r else nul(C.c_int16),
+                          _ptr(r["bump_bits"], C.c_uint8) if "bump_bits" in r else nul(C.c_uint8))
+        st = load().gd_fetch_results(self.ctx.h, self.handle, C.byref(rb), 1 if blocking else 0)
+        if st == GD_ENOTREADY:
+            return None
+        self.ctx._check(st)
+        return r
+
+    def launch(self, stream=None):
+        """Run the search again on the device-resident inputs (no host copies)."""
+        self.ctx._check(load().gd_job_launch(self.ctx.h, self.handle, _stream_handle(stream)))
+
+    def download(self, stream=None):
+        self.ctx._check(load().gd_job_download(self.ctx.h, self.handle, _stream_handle(stream)))
+
+    def bytes_moved(self):
+        """(host->device, device->host) bytes of one gd_dock_batch of this job."""
+        i, o = C.c_uint64(), C.c_uint64()
+        self.ctx._check(load().gd_job_bytes(self.ctx.h, self.handle, C.byref(i), C.byref(o)))
+        return i.value, o.value
+
+    def free(self):
+        if self.handle:
+            load().gd_job_free(self.ctx.h, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Pocket:
+    def __init__(self, ctx, handle):
+        self.ctx, self.handle = ctx, handle
+
+    def free(self):
+        if self.handle:
+            load().gd_free_pocket(self.ctx.h, self.handle)
+            self.handle = None
+
+
+class Context:
+    """A gd_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        L = load()
+        h = C.c_void_p()
+        st = L.gd_create(C.byref(h), int(device), C.c_size_t(mem_budget_bytes))
+        if st:
+            raise GeoDockError(st, L.gd_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st:
+            raise GeoDockError(st, load().gd_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            load().gd_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load_pocket(self, pocket) -> Pocket:
+        g = np.ascontiguousarray(pocket.grid, np.uint8)
+        nz, ny, nx = g.shape
+        org = np.ascontiguousarray(pocket.origin, np.float32)
+        h = C.c_void_p()
+        self._check(load().gd_load_pocket(self.h, _ptr(g, C.c_uint8), nx, ny, nz, float(pocket.spacing),
+                                          _ptr(org, C.c_float), C.byref(h)))
+        return Pocket(self, h)
+
+    def dock_batch(self, pocket: Pocket, batch, params, stream=None, debug=False, bumps=False, tile=0) -> Job:
+        """gd_dock_batch: debug keeps per-restart scores/picks, bumps also per-candidate bump bits."""
+        arrs = _BatchArrays(batch)
+        flags = (GD_FLAG_DEBUG if debug else 0) | (GD_FLAG_DEBUG_BUMPS if bumps else 0)
+        prm = params_c(params, flags, tile)
+        h = C.c_void_p()
+        self._check(load().gd_dock_batch(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm),
+                                         _stream_handle(stream), C.byref(h)))
+        return Job(self, h, batch, params, debug, bumps)
+
+    def autotune(self, pocket: Pocket, batch, params, max_ligands=256, stream=None):
+        arrs = _BatchArrays(batch)
+        prm = params_c(params)
+        t, ms = C.c_int(), C.c_float()
+        self._check(load().gd_autotune(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm), int(max_ligands),
+                                       _stream_handle(stream), C.byref(t), C.byref(ms)))
+        return t.value, ms.value
+
+
+def check_batch(batch, params) -> None:
+    """gd_check_batch: host-only validation; raises GeoDockError(GD_EINVAL) with the reason."""
+    arrs = _BatchArrays(batch)
+    prm = params_c(params)
+    st = load().gd_check_batch(C.byref(arrs.c), C.byref(prm))
+    if st:
+        raise GeoDockError(st, load().gd_last_error(None).decode())
+
+
+def tile_count() -> int:
+    return load().gd_tile_count()
+
+
+def tile_info(tile: int):
+    w, s = C.c_int(), C.c_int()
+    st = load().gd_tile_info(int(tile), C.byref(w), C.byref(s))
+    if st:
+        raise GeoDockError(st, load().gd_last_error(None).decode())
+    return w.value, s.value
+
+
+def dock(batch, pocket, params, device=0, debug=False, bumps=False, tile=0, stream=None) -> dict:
+    """One-shot convenience: create a context, dock, fetch, clean up."""
+    with Context(device) as ctx:
+        pk = ctx.load_pocket(pocket)
+        job = ctx.dock_batch(pk, batch, params, stream=stream, debug=debug, bumps=bumps, tile=tile)
+        out = job.fetch(blocking=True)
+        job.free()
+        pk.free()
+    return out

@@ -287,13 +287,32 @@ class Workload:
     params: SearchParams
 
 
-def _ligands(config_seed, count, size_fn, start=0):
+def _ligand_range(config_seed, size_fn, lo, hi):
     out = []
-    for i in range(start, start + count):
+    for i in range(lo, hi):
         rng = SplitMix64(ligand_seed(config_seed, i))
         n, r = size_fn(rng)
         out.append(gen_ligand(rng, n, r))
     return out
+
+
+def _ligands(config_seed, count, size_fn, start=0, workers=None):
+    """Ligands start .. start+count-1 of a workload.  Large requests are split over a
+    'spawn' process pool (safe after CUDA has been initialised); every ligand has its
+    own generator stream, so the result does not depend on the split."""
+    import os
+    if workers is None:
+        workers = min(os.cpu_count() or 1, 16)
+    if count < 256 or workers <= 1:
+        return _ligand_range(config_seed, size_fn, start, start + count)
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    chunk = (count + workers * 4 - 1) // (workers * 4)
+    bounds = [(lo, min(lo + chunk, start + count)) for lo in range(start, start + count, chunk)]
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = ex.map(_ligand_range, [config_seed] * len(bounds), [size_fn] * len(bounds),
+                       [b[0] for b in bounds], [b[1] for b in bounds])
+        return [lig for part in parts for lig in part]
 
 
 def workload_single(seed_offset: int = 1) -> Workload:

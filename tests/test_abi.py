@@ -1,0 +1,93 @@
+"""The C ABI library: it loads, exports every entry point of include/geodock.h, and its
+host-side validation rejects malformed batches (no device needed)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1901_06229_b300 import geodock as gdk
+from paper_1901_06229_b300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "geodock.h")).read()
+    return sorted(set(re.findall(r"^(?:gd_status|int|const char\*)\s+(gd_\w+)\(", src, re.M)))
+
+
+def test_library_exports_every_declared_function():
+    lib = gdk.load()
+    declared = header_functions()
+    assert len(declared) >= 13
+    for f in declared:
+        assert hasattr(lib, f), f
+    syms = subprocess.run(["nm", "-D", "--defined-only", gdk.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (gd_\w+)", syms))
+    assert set(declared) <= exported
+    assert set(gdk.EXPORTS) == set(declared)
+
+
+def test_tiles():
+    assert gdk.tile_count() == 12
+    seen = {gdk.tile_info(t) for t in range(1, 13)}
+    assert len(seen) == 12
+    with pytest.raises(gdk.GeoDockError):
+        gdk.tile_info(0)
+
+
+def _lig(bonds, rot, n=None):
+    bonds = np.asarray(bonds, np.int32)
+    n = n or int(bonds.max()) + 1
+    xyz = np.stack([np.arange(n) * 3.0, np.zeros(n), np.zeros(n)], 1).astype(np.float32)
+    return synth.Ligand(xyz=xyz, bonds=bonds.reshape(-1, 2), rot_bond=np.asarray(rot, np.int32))
+
+
+CHAIN = [[0, 1], [1, 2], [2, 3], [3, 4], [4, 5]]
+
+
+def test_check_batch_accepts_generated_workloads():
+    for w in (synth.workload_single(), synth.workload_batched(50)):
+        gdk.check_batch(w.batch, w.params)
+    gdk.check_batch(synth.pack([]), synth.SearchParams())
+
+
+@pytest.mark.parametrize("lig,msg", [
+    (lambda: _lig([[0, 1], [1, 2], [2, 0]], [], n=4), "tree"),           # cycle
+    (lambda: _lig([[0, 1], [2, 3], [1, 0]], [], n=4), "tree"),           # disconnected
+    (lambda: _lig(CHAIN, [0]), "terminal"),                               # terminal rotamer
+    (lambda: _lig(CHAIN, [7]), "bond"),                                   # rotamer bond out of range
+    (lambda: _lig([[0, 7]], [], n=2), "bond"),                            # atom id out of range
+    (lambda: _lig([[0, 0]], [], n=2), "bond"),                            # self bond
+    (lambda: _lig([[i, i + 1] for i in range(256)], []), "atoms"),        # 257 atoms
+])
+def test_check_batch_rejects(lig, msg):
+    with pytest.raises(gdk.GeoDockError) as e:
+        gdk.check_batch(synth.pack([lig()]), synth.SearchParams())
+    assert e.value.status == gdk.GD_EINVAL and msg in str(e.value)
+
+
+def test_check_batch_rejects_nan_and_bad_params():
+    l = _lig(CHAIN, [2])
+    l.xyz[3, 1] = np.nan
+    with pytest.raises(gdk.GeoDockError, match="finite"):
+        gdk.check_batch(synth.pack([l]), synth.SearchParams())
+    ok = synth.pack([_lig(CHAIN, [2])])
+    for bad in (synth.SearchParams(0, 4, 4), synth.SearchParams(n_angles=0), synth.SearchParams(n_angles=2000),
+                synth.SearchParams(bump_dist=-1.0), synth.SearchParams(repetitions=0),
+                synth.SearchParams(min_bond_sep=0), synth.SearchParams(300, 300, 1)):
+        with pytest.raises(gdk.GeoDockError) as e:
+            gdk.check_batch(ok, bad)
+        assert e.value.status == gdk.GD_EINVAL
+
+
+def test_check_batch_excluded_pair_limit():
+    # a star: every atom bonded to atom 1 -> with min_bond_sep 4 the pairs across the
+    # rotamer bond 1-2 that are fewer than 4 bonds apart exceed the per-rotamer limit
+    bonds = [[0, 1]] + [[1, k] for k in range(2, 5)] + [[2, k] for k in range(5, 9)] + [[3, 9]]
+    l = _lig(bonds, [1])
+    gdk.check_batch(synth.pack([l]), synth.SearchParams())
+    with pytest.raises(gdk.GeoDockError, match="excluded"):
+        gdk.check_batch(synth.pack([l]), synth.SearchParams(min_bond_sep=8))

@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Small workloads are compared element by element (every restart's picks and score,
+every candidate's bump flag); the full-size workloads run in the benchmark's launch
+configuration and are compared on sampled ligands and restarts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_06229_b300 import geodock as gdk
+from paper_1901_06229_b300 import synth
+from parity import Stats, check_ligand, check_pose_vs_oracle, compare_debug
+from test_oracle_pins import modular_pocket, textured_pocket
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gdk.Context(0)
+    yield c
+    c.close()
+
+
+def run(ctx, w_pocket, batch, params, debug=True, bumps=True, tile=0):
+    pk = ctx.load_pocket(w_pocket)
+    job = ctx.dock_batch(pk, batch, params, debug=debug, bumps=bumps, tile=tile)
+    out = job.fetch()
+    job.free()
+    pk.free()
+    return out
+
+
+def full_compare(ctx, pocket, batch, params, tile=0, min_exact=1):
+    gpu = run(ctx, pocket, batch, params, tile=tile)
+    orc = oracle.dock_batch(batch, pocket, params, n_threads=8, debug=True)
+    st = compare_debug(gpu, orc, batch, params)
+    print(dict(st))
+    assert st.get("scores_exact", 0) >= min_exact
+    return gpu, orc, st
+
+
+def test_single_ligand_workload(ctx):
+    w = synth.workload_single()
+    _, _, st = full_compare(ctx, w.pocket, w.batch, w.params)
+    assert st["restarts"] == 64
+
+
+def test_single_ligand_textured_pocket(ctx):
+    w = synth.workload_single()
+    gpu, orc, st = full_compare(ctx, textured_pocket(), w.batch, w.params, min_exact=40)
+    assert (orc["orient_pick"] > 0).sum() > 20, "pocket should make the search move fragments"
+
+
+def test_modular_grid_many_boundaries(ctx):
+    P = modular_pocket(40, 40, 40, 0.5, origin=(-10.0, -10.0, -10.0))
+    lig = [synth.gen_ligand(synth.SplitMix64(synth.ligand_seed(99, s)), 18, 3) for s in range(3)]
+    full_compare(ctx, P, synth.pack(lig), synth.SearchParams(2, 3, 2, 32), min_exact=10)
+
+
+def test_batched_subset_elementwise(ctx):
+    w = synth.workload_batched(24)
+    _, _, st = full_compare(ctx, w.pocket, w.batch, w.params, min_exact=1000)
+    assert st["restarts"] == 24 * 256
+
+
+def test_large_ligands_reduced_restarts(ctx):
+    w = synth.workload_large(3)
+    params = synth.SearchParams(2, 2, 1, 128)
+    full_compare(ctx, w.pocket, w.batch, params, min_exact=4)
+
+
+@pytest.mark.parametrize("case", ["ragged_angles", "one_angle", "odd_euler", "reps2", "min_sep4",
+                                  "bump25", "rigid_only", "two_atoms", "max_atoms"])
+def test_edge_cases(ctx, case):
+    pocket = textured_pocket()
+    rng = lambda s: synth.SplitMix64(synth.ligand_seed(4242, s))
+    ligs = [synth.gen_ligand(rng(s), n, r) for s, (n, r) in enumerate([(20, 3), (31, 5), (14, 2)])]
+    params = synth.SearchParams(2, 2, 2, 40)
+    if case == "ragged_angles":
+        params = synth.SearchParams(2, 2, 2, 33)
+    elif case == "one_angle":
+        params = synth.SearchParams(2, 2, 2, 1)
+    elif case == "odd_euler":
+        params = synth.SearchParams(3, 5, 2, 32)
+    elif case == "reps2":
+        params = synth.SearchParams(2, 2, 2, 32, repetitions=2)
+    elif case == "min_sep4":
+        params = synth.SearchParams(2, 2, 2, 32, min_bond_sep=4)
+    elif case == "bump25":
+        params = synth.SearchParams(2, 2, 2, 32, bump_dist=2.5)
+    elif case == "rigid_only":
+        ligs = [synth.gen_ligand(rng(10 + s), 12, 0) for s in range(3)]
+        params = synth.SearchParams(4, 4, 4, 32)
+    elif case == "two_atoms":
+        ligs = [synth.gen_ligand(rng(20), 2, 0), synth.gen_ligand(rng(21), 9, 1)]
+    elif case == "max_atoms":
+        big = synth.workload_large(1).pocket
+        ligs = [synth.gen_ligand(rng(30), 256, 40)]
+        pocket, params = big, synth.SearchParams(1, 2, 1, 64)
+    full_compare(ctx, pocket, synth.pack(ligs), params, min_exact=1)
+
+
+def test_empty_batch(ctx):
+    w = synth.workload_single()
+    out = run(ctx, w.pocket, synth.pack([]), w.params)
+    assert len(out["best_score"]) == 0
+
+
+def test_all_zero_pocket(ctx):
+    w = synth.workload_single()
+    zero = synth.Pocket(grid=np.zeros((8, 9, 10), np.uint8), spacing=0.5, origin=np.zeros(3, np.float32))
+    out = run(ctx, zero, w.batch, w.params)
+    assert out["best_score"][0] == 0 and out["best_orient"][0] == 0
+    assert np.all(out["orient_score"] == 0) and np.all(out["orient_pick"] <= 0)
+
+
+def test_tiles_give_identical_results(ctx):
+    w = synth.workload_batched(32)
+    ref = None
+    for t in range(1, gdk.tile_count() + 1):
+        out = run(ctx, w.pocket, w.batch, w.params, tile=t)
+        if ref is None:
+            ref = out
+            continue
+        for k in ref:
+            if k == "pair_tests":  # counted per tile granularity of the early exit
+                continue
+            np.testing.assert_array_equal(out[k], ref[k], err_msg=f"tile {t}: {k}")
+
+
+def test_relaunch_on_resident_inputs_is_deterministic(ctx):
+    import torch
+    w = synth.workload_batched(16)
+    pk = ctx.load_pocket(w.pocket)
+    s = torch.cuda.Stream()
+    job = ctx.dock_batch(pk, w.batch, w.params, stream=s, debug=True)
+    first = job.fetch()
+    for _ in range(3):
+        job.launch(stream=s)
+    job.download(stream=s)
+    again = job.fetch()
+    for k in first:
+        np.testing.assert_array_equal(first[k], again[k], err_msg=k)
+    job.free()
+    pk.free()
+
+
+def _subset(gpu, batch, params, idx):
+    """Results of a GPU run restricted to ligands idx, laid out as for batch.subset(idx)."""
+    O, reps = params.n_orient, params.repetitions
+    ro, ao = np.asarray(batch.rot_off, np.int64), np.asarray(batch.atom_off, np.int64)
+    out = {k: [] for k in ("best_score", "best_orient", "best_angle", "best_xyz", "evals", "pair_tests",
+                           "atom_moves", "orient_score", "orient_pick")}
+    for i in idx:
+        for k in ("best_score", "best_orient", "evals", "pair_tests", "atom_moves"):
+            out[k].append(gpu[k][i:i + 1])
+        out["orient_score"].append(gpu["orient_score"][i:i + 1])
+        out["best_angle"].append(gpu["best_angle"][ro[i] * reps: ro[i + 1] * reps])
+        out["best_xyz"].append(gpu["best_xyz"][ao[i]: ao[i + 1]])
+        out["orient_pick"].append(gpu["orient_pick"][ro[i] * reps * O: ro[i + 1] * reps * O])
+    return {k: np.concatenate(v) for k, v in out.items()}
+
+
+def test_full_size_batched_sampled(ctx):
+    """4,096 ligands, 256 restarts, 64 angles, autotuned tile (the benchmark's launch)."""
+    w = synth.workload_batched(4096)
+    gpu = run(ctx, w.pocket, w.batch, w.params, debug=True, bumps=False, tile=-1)
+    idx = np.random.default_rng(7).choice(4096, size=24, replace=False)
+    sub = w.batch.subset(idx)
+    orc = oracle.dock_batch(sub, w.pocket, w.params, n_threads=8, debug=False)
+    st = compare_debug(_subset(gpu, w.batch, w.params, idx), orc, sub, w.params, bumps=False)
+    print(dict(st))
+    assert st["scores_exact"] > 0.9 * st["restarts"]
+    # properties that hold for every ligand of the batch
+    assert np.all(gpu["best_score"] == gpu["orient_score"].max(axis=1))
+    assert np.all(gpu["best_orient"] == gpu["orient_score"].argmax(axis=1))
+    R = np.diff(w.batch.rot_off)
+    assert np.all(gpu["evals"] == 256 * 64 * R)
+
+
+def test_full_size_large_sampled(ctx):
+    """512 ligands of 100-250 atoms, 128^3 pocket (global-memory grid path), 128 angles."""
+    w = synth.workload_large(512)
+    gpu = run(ctx, w.pocket, w.batch, w.params, debug=True, bumps=False, tile=-1)
+    st = Stats()
+    rng = np.random.default_rng(11)
+    for i in rng.choice(512, size=3, replace=False):
+        for o in [int(gpu["best_orient"][i]), int(rng.integers(256))]:
+            ref = check_pose_vs_oracle(gpu, w.batch, w.params, w.pocket, int(i), o, st, oracle)
+            if o == int(gpu["best_orient"][i]) and ref["fragile"] < 0:
+                a0, a1 = w.batch.atom_off[i], w.batch.atom_off[i + 1]
+                d = np.abs(gpu["best_xyz"][a0:a1] - ref["xyz"]).max()
+                assert d <= 1e-4, d
+    print(dict(st))
+    assert st["sampled_restarts"] == 6
+    assert np.all(gpu["best_score"] == gpu["orient_score"].max(axis=1))
