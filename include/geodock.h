@@ -50,7 +50,8 @@ typedef int gd_status;
 #define GD_MAX_ANGLES 1024      /* angles per rotamer sweep */
 #define GD_MAX_ORIENT 65535     /* restart orientations */
 #define GD_MAX_REPS 16          /* optimize_pose repetitions */
-#define GD_MAX_EXCLUDED 16      /* moving x static pairs closer than min_bond_sep bonds, per rotamer */
+#define GD_MAX_EXCLUDED 128     /* moving x static pairs closer than min_bond_sep bonds, per rotamer */
+#define GD_MAX_EXCLUDED_ATOM 32 /* ... and per moving atom */
 
 /* Flags of gd_search_params.flags */
 #define GD_FLAG_DEBUG 1         /* keep per-orientation scores and picks (orient_score, orient_pick) */

@@ -152,10 +152,10 @@ namespace {
 // Byte layout of a packed batch; the same offsets are used in pinned staging and in
 // device memory so one copy moves the whole input.
 struct InLayout {
-  size_t atom_off, rot_off, xyz, perm, rots, order, total;
+  size_t atom_off, rot_off, xyz, perm, rots, order, excl, total;
 };
 
-InLayout in_layout(int L, long long N, long long Rt) {
+InLayout in_layout(int L, long long N, long long Rt, long long n_excl) {
   InLayout l{};
   size_t o = 0;
   l.atom_off = o; o = align_up(o + 4 * (size_t)(L + 1), 256);
@@ -164,6 +164,7 @@ InLayout in_layout(int L, long long N, long long Rt) {
   l.perm = o;     o = align_up(o + (size_t)N, 256);
   l.rots = o;     o = align_up(o + sizeof(RotDesc) * (size_t)Rt, 256);
   l.order = o;    o = align_up(o + 4 * (size_t)L, 256);
+  l.excl = o;     o = align_up(o + 2 * (size_t)n_excl, 256);
   l.total = o;
   return l;
 }
@@ -225,7 +226,7 @@ gd_status check_params(const gd_search_params* p) {
 // cost: an estimate of its search work, used to order the work queue.
 gd_status pack_ligand(int li, int n, const float* xyz, int nb, const int32_t* bonds, int R,
                       const int32_t* rot_bond, int min_sep, float4* out_xyz, uint8_t* out_perm,
-                      RotDesc* out_rots, double* cost) {
+                      RotDesc* out_rots, std::vector<uint16_t>& excl, double* cost) {
   if (n < 2 || n > GD_MAX_ATOMS) return fail(GD_EINVAL, "ligand %d: %d atoms outside [2, %d]", li, n, GD_MAX_ATOMS);
   if (nb != n - 1) return fail(GD_EINVAL, "ligand %d: %d bonds for %d atoms (not a tree)", li, nb, n);
   if (R < 0 || R > GD_MAX_ROTAMERS) return fail(GD_EINVAL, "ligand %d: %d rotamers > %d", li, R, GD_MAX_ROTAMERS);
@@ -320,11 +321,15 @@ gd_status pack_ligand(int li, int n, const float* xyz, int nb, const int32_t* bo
     if ((int)ex.size() > GD_MAX_EXCLUDED)
       return fail(GD_EINVAL, "ligand %d: rotamer %d has %zu excluded pairs > %d", li, r, ex.size(), GD_MAX_EXCLUDED);
     std::sort(ex.begin(), ex.end());
-    d.n_excl = (uint8_t)ex.size();
-    for (size_t e = 0; e < ex.size(); ++e) {
-      d.excl_a[e] = (uint8_t)ex[e].first;
-      d.excl_b[e] = (uint8_t)ex[e].second;
+    for (size_t e = 0, run = 0; e < ex.size(); ++e) {
+      run = (e && ex[e].first == ex[e - 1].first) ? run + 1 : 1;
+      if (run > GD_MAX_EXCLUDED_ATOM)
+        return fail(GD_EINVAL, "ligand %d: rotamer %d has more than %d excluded pairs on one atom", li, r,
+                    GD_MAX_EXCLUDED_ATOM);
     }
+    d.n_excl = (uint8_t)ex.size();
+    d.excl_off = (uint32_t)excl.size();
+    for (auto& e : ex) excl.push_back((uint16_t)(e.first | (e.second << 8)));
     out_rots[r] = d;
     const int f = d.comp ? rest : sub;
     c += (double)f * (n - f) + 4.0 * f;
@@ -352,6 +357,7 @@ struct gd_job {
   void* d_out = nullptr;
   void* d_scr = nullptr;
   void* h_in = nullptr;
+  size_t h_in_cap = 0;
   void* h_out = nullptr;
   void* h_dbg = nullptr;  // pose_score | pose_pick | bump (debug only)
   size_t dbg_bytes = 0;
@@ -373,7 +379,7 @@ gd_status job_release(gd_ctx* c, gd_job* j) {
   dev_release(c, j->d_in, j->in.total);
   dev_release(c, j->d_out, j->out.total);
   dev_release(c, j->d_scr, j->scr.total);
-  host_release(c, j->h_in, j->in.total);
+  host_release(c, j->h_in, j->h_in_cap);
   host_release(c, j->h_out, j->out.total);
   host_release(c, j->h_dbg, j->dbg_bytes);
   delete j;
@@ -429,11 +435,19 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   j->Rt = Rt;
   j->debug = (p->flags & (GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS)) != 0;
   j->debug_bumps = (p->flags & GD_FLAG_DEBUG_BUMPS) != 0;
-  j->in = in_layout(L, N, Rt);
+  // validate and pack: atoms / permutation / descriptors go straight into pinned
+  // staging (their sizes are known); exclusions are gathered first and copied after
+  j->in = in_layout(L, N, Rt, 0);
   j->out = out_layout(L, N, Rt, j->reps);
   j->scr = scratch_layout(L, j->O, Rt, j->reps, j->A, j->debug_bumps);
+  const size_t in_cap = j->in.total + align_up(2 * (size_t)Rt * GD_MAX_EXCLUDED, 256);
   gd_status st;
-  if ((st = host_alloc(c, j->in.total, &j->h_in)) || (st = host_alloc(c, j->out.total, &j->h_out))) {
+  if ((st = host_alloc(c, in_cap, &j->h_in))) {
+    job_release(c, j);
+    return st;
+  }
+  j->h_in_cap = in_cap;
+  if ((st = host_alloc(c, j->out.total, &j->h_out))) {
     job_release(c, j);
     return st;
   }
@@ -445,13 +459,14 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   RotDesc* rots = (RotDesc*)(h + j->in.rots);
   int32_t* order = (int32_t*)(h + j->in.order);
   std::vector<double> cost(L);
+  std::vector<uint16_t> excl;
   int nmax = 2;
   for (int i = 0; i < L; ++i) {
     const int a0 = b->atom_off[i], n = b->atom_off[i + 1] - a0;
     const int b0 = b->bond_off[i], nb = b->bond_off[i + 1] - b0;
     const int r0 = b->rot_off[i], R = b->rot_off[i + 1] - r0;
     st = pack_ligand(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
-                     p->min_bond_sep, xyz + a0, perm + a0, rots + r0, &cost[i]);
+                     p->min_bond_sep, xyz + a0, perm + a0, rots + r0, excl, &cost[i]);
     if (st) {
       job_release(c, j);
       return st;
@@ -467,6 +482,8 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
     rot_off[i] = L ? b->rot_off[i] : 0;
   }
   j->rot_off.assign(rot_off, rot_off + L + 1);
+  j->in = in_layout(L, N, Rt, (long long)excl.size());
+  if (!excl.empty()) memcpy(h + j->in.excl, excl.data(), 2 * excl.size());
   for (int i = 0; i < L; ++i) order[i] = i;
   std::stable_sort(order, order + L, [&](int x, int y) { return cost[x] > cost[y]; });
 
@@ -493,6 +510,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.perm = (const uint8_t*)(d + j->in.perm);
   a.rots = (const RotDesc*)(d + j->in.rots);
   a.order = (const int32_t*)(d + j->in.order);
+  a.excl = (const uint16_t*)(d + j->in.excl);
   a.n_items = (long long)L * j->O;
   a.na = p->n_alpha;
   a.nb = p->n_beta;
@@ -671,6 +689,7 @@ gd_status gd_check_batch(const gd_ligand_batch* b, const gd_search_params* p) {
   std::vector<float4> xyz;
   std::vector<uint8_t> perm;
   std::vector<RotDesc> rots;
+  std::vector<uint16_t> excl;
   for (int i = 0; i < L; ++i) {
     if (b->atom_off[i + 1] < b->atom_off[i] || b->bond_off[i + 1] < b->bond_off[i] || b->rot_off[i + 1] < b->rot_off[i])
       return fail(GD_EINVAL, "CSR offsets decrease at ligand %d", i);
@@ -682,7 +701,7 @@ gd_status gd_check_batch(const gd_ligand_batch* b, const gd_search_params* p) {
     rots.resize(std::max(R, 0));
     double cost;
     if ((st = pack_ligand(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
-                          p->min_bond_sep, xyz.data(), perm.data(), rots.data(), &cost)))
+                          p->min_bond_sep, xyz.data(), perm.data(), rots.data(), excl, &cost)))
       return st;
   }
   g_err.clear();

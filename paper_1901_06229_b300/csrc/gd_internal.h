@@ -10,19 +10,19 @@ namespace gd {
 // preorder from atom 0, so the subtree under either end of a tree bond is one
 // contiguous range [lo, hi); the rotating fragment is that range (comp = 0) or its
 // complement (comp = 1).  p / q are the static / moving ends of the bond (preorder
-// ids).  excl_* lists the moving x static pairs whose graph distance is below
-// min_bond_sep, sorted by the moving atom: in a tree every moving-static path runs
-// through q-p, so these are the pairs with dist(a,q) + 1 + dist(p,b) < min_bond_sep.
+// ids).  excl[excl_off .. excl_off + n_excl) lists the moving x static pairs whose
+// graph distance is below min_bond_sep as (a | b << 8), sorted by the moving atom a:
+// in a tree every moving-static path runs through q-p, so these are the pairs with
+// dist(a,q) + 1 + dist(p,b) < min_bond_sep.
 struct alignas(16) RotDesc {
   uint16_t p, q;
   uint16_t lo, hi;
   uint8_t comp;
   uint8_t n_excl;
-  uint8_t pad[6];
-  uint8_t excl_a[16];
-  uint8_t excl_b[16];
+  uint16_t pad;
+  uint32_t excl_off;
 };
-static_assert(sizeof(RotDesc) == 48, "RotDesc layout");
+static_assert(sizeof(RotDesc) == 16, "RotDesc layout");
 
 struct PocketDev {
   const uint8_t* grid;   // cropped grid [cz][cy][cx]; cells outside the crop are 0
@@ -42,6 +42,7 @@ struct SearchArgs {
   const float4* xyz;          // [N] preorder, input coordinates (w unused)
   const uint8_t* perm;        // [N] preorder id -> input-order local id
   const RotDesc* rots;        // [Rt]
+  const uint16_t* excl;       // [sum n_excl] excluded pairs (a | b << 8)
   const int32_t* order;       // [L] ligand processing order (largest cost first)
   long long n_items;          // L * O
   // search parameters

@@ -135,7 +135,7 @@ __device__ void place(const SearchArgs& a, float4* X, const float4* x0, int n, i
 }
 
 __device__ __forceinline__ void load_desc(RotDesc* dst, const RotDesc* src, int lane) {
-  if (lane < 12) reinterpret_cast<uint32_t*>(dst)[lane] = __ldg(reinterpret_cast<const uint32_t*>(src) + lane);
+  if (lane < 4) reinterpret_cast<uint32_t*>(dst)[lane] = __ldg(reinterpret_cast<const uint32_t*>(src) + lane);
   __syncwarp();
 }
 
@@ -237,7 +237,10 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
       sc[j] = s_static;
       bump[j] = kk[j] >= a.A;  // idle slots count as rejected
     }
+    const uint16_t* excl = a.excl + rd.excl_off;
+    const int n_excl = rd.n_excl;
     int ex = 0;
+    int next_a = n_excl ? (int)(__ldg(excl) & 0xFF) : -1;  // moving atom of the next excluded pair
     bool stop = false;
     for (int seg = 0; seg < 2 && !stop; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
@@ -245,13 +248,14 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
         const float4 xa = X[ai];
         // park the static atoms this moving atom must not be tested against
         int ex_end = ex;
-        while (ex_end < rd.n_excl && rd.excl_a[ex_end] == ai) ++ex_end;
         float4 saved = make_float4(0.f, 0.f, 0.f, 0.f);
         int my_b = -1;
-        if (ex_end > ex) {
+        if (ai == next_a) {
+          while (ex_end < n_excl && (int)(__ldg(excl + ex_end) & 0xFF) == ai) ++ex_end;
+          next_a = ex_end < n_excl ? (int)(__ldg(excl + ex_end) & 0xFF) : -1;
           __syncwarp();
           if (lane < ex_end - ex) {
-            my_b = rd.excl_b[ex + lane];
+            my_b = (int)(__ldg(excl + ex + lane) >> 8);
             saved = X[my_b];
             X[my_b] = make_float4(PARK, PARK, PARK, 0.f);
           }
@@ -267,9 +271,10 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
         min_d2_range<S>(X, s0a, s0b, xr, mind);
         min_d2_range<S>(X, s1a, s1b, xr, mind);
         bool done = true;
+        const unsigned tested = n_static - (unsigned)(ex_end - ex);  // parked pairs are not tests
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-          if (!bump[j]) pairs += n_static;
+          if (!bump[j]) pairs += tested;
           bump[j] = bump[j] || (mind[j] < a.thr2);
           done = done && bump[j];
         }

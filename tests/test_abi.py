@@ -89,5 +89,10 @@ def test_check_batch_excluded_pair_limit():
     bonds = [[0, 1]] + [[1, k] for k in range(2, 5)] + [[2, k] for k in range(5, 9)] + [[3, 9]]
     l = _lig(bonds, [1])
     gdk.check_batch(synth.pack([l]), synth.SearchParams())
+    gdk.check_batch(synth.pack([l]), synth.SearchParams(min_bond_sep=5))
+    # a long path with many branches: pairs within 8 bonds across the bond exceed 128
+    bonds = [[i, i + 1] for i in range(20)] + [[i, 21 + i] for i in range(20)] + \
+            [[i, 41 + i] for i in range(20)]
+    l = _lig(bonds, [9])
     with pytest.raises(gdk.GeoDockError, match="excluded"):
         gdk.check_batch(synth.pack([l]), synth.SearchParams(min_bond_sep=8))
