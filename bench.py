@@ -40,11 +40,13 @@ FP32_OPS_PER_CANDIDATE = 19  # Rodrigues matrix of the candidate angle
 FP32_LANES_PER_SM = 128
 
 
-def workload_for(name, rank):
+def workload_for(name, rank, ligands=None):
     if name == "batched":
-        return synth.workload_batched(4096, start=4096 * rank)
+        n = ligands or 4096
+        return synth.workload_batched(n, start=n * rank)
     if name == "large":
-        return synth.workload_large(512, start=512 * rank)
+        n = ligands or 512
+        return synth.workload_large(n, start=n * rank)
     if name == "single":
         return synth.workload_single()
     raise SystemExit(f"unknown workload {name}")
@@ -156,7 +158,7 @@ def barrier(world):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    w = workload_for(args.workload, 0)
+    w = workload_for(args.workload, 0, args.ligands)
     cores = os.cpu_count() or 1
     import oracle
     per_step = max(cores, 8)
@@ -184,13 +186,14 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "large", "single"])
     ap.add_argument("--tile", type=int, default=-1, help="-1 autotune, 0 default, >0 tile id")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--ligands", type=int, default=None, help="smaller batch (profiling runs only)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -203,7 +206,7 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
-    w = workload_for(args.workload, rank)
+    w = workload_for(args.workload, rank, args.ligands)
     stream = torch.cuda.Stream()
     ctx = gdk.Context(dev)
     pk = ctx.load_pocket(w.pocket)
