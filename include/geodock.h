@@ -56,6 +56,8 @@ typedef int gd_status;
 /* Flags of gd_search_params.flags */
 #define GD_FLAG_DEBUG 1         /* keep per-orientation scores and picks (orient_score, orient_pick) */
 #define GD_FLAG_DEBUG_BUMPS 2   /* also keep per-candidate bump bits (bump_bits) */
+#define GD_FLAG_NO_FILTER 4     /* test every moving x static pair at every angle (no reach
+                                   filter); results are identical, only slower */
 
 typedef struct gd_ctx gd_ctx;
 typedef struct gd_pocket gd_pocket;
@@ -104,6 +106,9 @@ typedef struct {
  *   pair_tests[L]          moving x static pair tests performed (early exit per atom)
  *   atom_moves[L]          fragment atoms rotated and scored (O * reps * A * sum_r f_r,
  *                          f_r = atoms of fragment r)
+ *   reach_tests[L]         moving x static pairs checked once per rotamer step by the
+ *                          reach filter (a pair that cannot come within bump_dist at any
+ *                          angle is not tested per angle)
  * Debug outputs (NULL to skip):
  *   orient_score[L*O]      final score of every restart            (GD_FLAG_DEBUG)
  *   orient_pick[O*reps*Rt] picks of every restart, ligand i at rot_off[i]*reps*O,
@@ -118,6 +123,7 @@ typedef struct {
   uint64_t* evals;
   uint64_t* pair_tests;
   uint64_t* atom_moves;
+  uint64_t* reach_tests;
   uint32_t* orient_score;
   int16_t* orient_pick;
   uint8_t* bump_bits;

@@ -170,7 +170,7 @@ InLayout in_layout(int L, long long N, long long Rt, long long n_excl) {
 }
 
 struct OutLayout {
-  size_t best_score, best_orient, best_angle, best_xyz, evals, pair_tests, atom_moves, err, total;
+  size_t best_score, best_orient, best_angle, best_xyz, evals, pair_tests, atom_moves, reach_tests, err, total;
 };
 
 OutLayout out_layout(int L, long long N, long long Rt, int reps) {
@@ -183,13 +183,14 @@ OutLayout out_layout(int L, long long N, long long Rt, int reps) {
   l.evals = o;       o = align_up(o + 8 * (size_t)L, 256);
   l.pair_tests = o;  o = align_up(o + 8 * (size_t)L, 256);
   l.atom_moves = o;  o = align_up(o + 8 * (size_t)L, 256);
+  l.reach_tests = o; o = align_up(o + 8 * (size_t)L, 256);
   l.err = o;         o = align_up(o + 4, 256);
   l.total = o;
   return l;
 }
 
 struct ScratchLayout {
-  size_t pose_score, pose_pick, pose_pairs, done, work, bump, total;
+  size_t pose_score, pose_pick, pose_pairs, pose_reach, done, work, bump, total;
 };
 
 ScratchLayout scratch_layout(int L, int O, long long Rt, int reps, int A, bool debug) {
@@ -198,6 +199,7 @@ ScratchLayout scratch_layout(int L, int O, long long Rt, int reps, int A, bool d
   l.pose_score = o; o = align_up(o + 4 * (size_t)L * O, 256);
   l.pose_pick = o;  o = align_up(o + 2 * (size_t)O * reps * Rt, 256);
   l.pose_pairs = o; o = align_up(o + 8 * (size_t)L * O, 256);
+  l.pose_reach = o; o = align_up(o + 8 * (size_t)L * O, 256);
   l.done = o;       o = o + 4 * (size_t)L;          // done and work are cleared by one memset
   o = align_up(o, 8);
   l.work = o;       o = align_up(o + 8, 256);
@@ -388,8 +390,9 @@ gd_status job_release(gd_ctx* c, gd_job* j) {
 
 std::string signature(const gd_pocket* pk, const gd_search_params* p, int nmax, bool smem) {
   char b[256];
-  snprintf(b, sizeof b, "O%d_A%d_r%d_n%d_g%d_%dx%dx%d", p->n_alpha * p->n_beta * p->n_gamma, p->n_angles,
-           p->repetitions, (nmax + 31) / 32, smem ? 1 : 0, pk->dev.cx, pk->dev.cy, pk->dev.cz);
+  snprintf(b, sizeof b, "O%d_A%d_r%d_n%d_g%d_%dx%dx%d_f%d", p->n_alpha * p->n_beta * p->n_gamma, p->n_angles,
+           p->repetitions, (nmax + 31) / 32, smem ? 1 : 0, pk->dev.cx, pk->dev.cy, pk->dev.cz,
+           (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1);
   return b;
 }
 
@@ -519,6 +522,8 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.A = j->A;
   a.reps = j->reps;
   a.thr2 = p->bump_dist * p->bump_dist;
+  a.reach2 = (p->bump_dist + gd::REACH_MARGIN) * (p->bump_dist + gd::REACH_MARGIN);
+  a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
   char* o = (char*)j->d_out;
   a.best_score = (uint32_t*)(o + j->out.best_score);
   a.best_orient = (int32_t*)(o + j->out.best_orient);
@@ -527,15 +532,19 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.evals = (unsigned long long*)(o + j->out.evals);
   a.pair_tests = (unsigned long long*)(o + j->out.pair_tests);
   a.atom_moves = (unsigned long long*)(o + j->out.atom_moves);
+  a.reach_tests = (unsigned long long*)(o + j->out.reach_tests);
   char* s = (char*)j->d_scr;
   a.pose_score = (uint32_t*)(s + j->scr.pose_score);
   a.pose_pick = (int16_t*)(s + j->scr.pose_pick);
   a.pose_pairs = (unsigned long long*)(s + j->scr.pose_pairs);
+  a.pose_reach = (unsigned long long*)(s + j->scr.pose_reach);
   a.done = (int32_t*)(s + j->scr.done);
   a.work = (unsigned long long*)(s + j->scr.work);
   a.err = (int32_t*)(o + j->out.err);
   a.bump_bits = j->debug_bumps ? (uint8_t*)(s + j->scr.bump) : nullptr;
   a.nmax = nmax;
+  a.near_cap = std::min(4096, std::max(512, (8 * nmax + 15) / 16 * 16));
+  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap);
   // tile and grid staging mode
   j->tile = tile;
   const size_t smem_cap = 227 * 1024;
@@ -727,7 +736,7 @@ gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, 
   gd_ligand_batch sub = *b;
   if (max_ligands > 0 && sub.n_ligands > max_ligands) sub.n_ligands = max_ligands;
   gd_search_params q = *p;
-  q.flags &= ~GD_FLAG_DEBUG;
+  q.flags &= ~(GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS);
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   GD_CUDA(cudaEventCreate(&e0));
@@ -848,6 +857,7 @@ gd_status gd_fetch_results(gd_ctx* c, gd_job* j, gd_result_batch* r, int blockin
   if (r->evals) memcpy(r->evals, h + j->out.evals, 8 * (size_t)L);
   if (r->pair_tests) memcpy(r->pair_tests, h + j->out.pair_tests, 8 * (size_t)L);
   if (r->atom_moves) memcpy(r->atom_moves, h + j->out.atom_moves, 8 * (size_t)L);
+  if (r->reach_tests) memcpy(r->reach_tests, h + j->out.reach_tests, 8 * (size_t)L);
   if (r->orient_score || r->orient_pick || r->bump_bits) {
     if (!j->debug) return fail(GD_EINVAL, "debug outputs need GD_FLAG_DEBUG at dock time");
     if (r->bump_bits && !j->debug_bumps) return fail(GD_EINVAL, "bump_bits need GD_FLAG_DEBUG_BUMPS at dock time");

@@ -48,6 +48,8 @@ struct SearchArgs {
   // search parameters
   int na, nb, ng, O, A, reps;
   float thr2;                 // bump_dist^2
+  float reach2;               // (bump_dist + REACH_MARGIN)^2: pairs farther apart at every angle skip the test
+  int use_filter;             // 1: per-rotamer reach filter; 0: test every moving x static pair
   // outputs
   uint32_t* best_score;       // [L]
   int32_t* best_orient;       // [L]
@@ -66,7 +68,23 @@ struct SearchArgs {
   // debug (may be null)
   uint8_t* bump_bits;         // [O * reps * A * Rt]
   int nmax;                   // largest ligand of the batch (per-warp buffer size)
+  int near_cap;               // capacity of a warp's near-pair list (multiple of 16)
+  int warp_bytes;             // shared memory per warp (see warp_smem_bytes)
+  unsigned long long* reach_tests;  // [L] (output) moving x static pairs checked by the reach filter
+  unsigned long long* pose_reach;   // [L*O] (scratch)
 };
+
+// Margin of the reach filter (A).  FP32 rounding moves a rotated atom by ~1e-5 A at
+// most, so a pair whose closest approach over the whole turn exceeds bump_dist by
+// this margin can never be flagged by the per-angle test.
+constexpr float REACH_MARGIN = 0.01f;
+
+// Per-warp shared memory: X float4[nmax] | HR float2[nmax] | MOFF uint16[nmax+2] |
+// NEAR uint8[near_cap] | RotDesc.
+__host__ __device__ inline int warp_smem_bytes(int nmax, int near_cap) {
+  auto a16 = [](int v) { return (v + 15) / 16 * 16; };
+  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(near_cap) + 16;
+}
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };
 

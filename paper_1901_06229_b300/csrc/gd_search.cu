@@ -301,20 +301,173 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
   return __reduce_max_sync(FULL, best);
 }
 
+struct WarpMem {
+  float4* X;       // current pose, preorder
+  float2* HR;      // (height along the bond axis, distance from it) per atom
+  uint16_t* MOFF;  // near-list offset per moving atom (in sweep order)
+  uint8_t* NEAR;   // static atoms that can come within reach of each moving atom
+  RotDesc* rd;
+};
+
+__device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int near_cap) {
+  auto a16 = [](int v) { return (v + 15) / 16 * 16; };
+  WarpMem w;
+  w.X = reinterpret_cast<float4*>(base);
+  base += a16(16 * nmax);
+  w.HR = reinterpret_cast<float2*>(base);
+  base += a16(8 * nmax);
+  w.MOFF = reinterpret_cast<uint16_t*>(base);
+  base += a16(2 * (nmax + 2));
+  w.NEAR = base;
+  base += a16(near_cap);
+  w.rd = reinterpret_cast<RotDesc*>(base);
+  return w;
+}
+
+// Reach filter of one rotamer step.  A moving atom a sweeps a circle about the bond
+// axis: height h_a along it, radius rho_a.  For a static atom b the distance over the
+// whole turn is at least sqrt((h_a - h_b)^2 + (rho_a - rho_b)^2), so only pairs below
+// bump_dist + margin (and not excluded by graph distance) need per-angle tests.
+// Builds MOFF/NEAR; returns the number of near pairs (> near_cap: list unusable).
+__device__ int build_near(const SearchArgs& a, const WarpMem& w, int n, const RotDesc& rd, float4 xp, float ux,
+                          float uy, float uz, int lane, unsigned long long& reach) {
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = w.X[i];
+    const float rx = __fsub_rn(v.x, xp.x), ry = __fsub_rn(v.y, xp.y), rz = __fsub_rn(v.z, xp.z);
+    const float h = __fmaf_rn(rx, ux, __fmaf_rn(ry, uy, __fmul_rn(rz, uz)));
+    const float r2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmul_rn(rz, rz)));
+    w.HR[i] = make_float2(h, __fsqrt_rn(fmaxf(__fmaf_rn(-h, h, r2), 0.0f)));
+  }
+  __syncwarp();
+  int m0a, m0b, m1a, m1b, s0a, s0b, s1a, s1b;
+  if (rd.comp) {
+    m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
+    s0a = rd.lo; s0b = rd.hi; s1a = 0; s1b = 0;
+  } else {
+    m0a = rd.lo; m0b = rd.hi; m1a = 0; m1b = 0;
+    s0a = 0; s0b = rd.lo; s1a = rd.hi; s1b = n;
+  }
+  const int n_static = (s0b - s0a) + (s1b - s1a);
+  const uint16_t* excl = a.excl + rd.excl_off;
+  const int n_excl = rd.n_excl;
+  int ex = 0, cnt = 0, ia = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int seg = 0; seg < 2; ++seg) {
+    const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
+    for (int ai = ma; ai < mb; ++ai, ++ia) {
+      if (lane == 0) w.MOFF[ia] = (uint16_t)(cnt < 65535 ? cnt : 65535);
+      const float2 ha = w.HR[ai];
+      int ex_end = ex;
+      while (ex_end < n_excl && (int)(__ldg(excl + ex_end) & 0xFF) == ai) ++ex_end;
+      for (int t = 0; t < n_static; t += 32) {
+        const int k = t + lane;
+        bool near = false;
+        int b = 0;
+        if (k < n_static) {
+          b = k < s0b - s0a ? s0a + k : s1a + (k - (s0b - s0a));
+          const float2 hb = w.HR[b];
+          const float dh = __fsub_rn(ha.x, hb.x), dr = __fsub_rn(ha.y, hb.y);
+          near = __fmaf_rn(dh, dh, __fmul_rn(dr, dr)) < a.reach2;
+          for (int e = ex; e < ex_end && near; ++e)
+            if ((int)(__ldg(excl + e) >> 8) == b) near = false;
+        }
+        const unsigned m = __ballot_sync(FULL, near);
+        const int pos = cnt + __popc(m & lt);
+        if (near && pos < a.near_cap) w.NEAR[pos] = (uint8_t)b;
+        cnt += __popc(m);
+      }
+      ex = ex_end;
+    }
+  }
+  if (lane == 0) w.MOFF[ia] = (uint16_t)(cnt < 65535 ? cnt : 65535);
+  reach += (unsigned long long)ia * (unsigned long long)n_static;
+  __syncwarp();
+  return cnt;
+}
+
+// Every angle of one rotamer step, bump tests restricted to the near list.
+template <int S, bool SG>
+__device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
+                                   const RotDesc& rd, float4 xp, float ux, float uy, float uz, int s_static,
+                                   int lane, unsigned long long& pairs, uint8_t* dbg) {
+  const float4* X = w.X;
+  int m0a, m0b, m1a, m1b;
+  if (rd.comp) {
+    m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
+  } else {
+    m0a = rd.lo; m0b = rd.hi; m1a = 0; m1b = 0;
+  }
+  const int passes = (a.A + 32 * S - 1) / (32 * S);
+  const unsigned n_near = w.MOFF[(m0b - m0a) + (m1b - m1a)];
+  unsigned best = 0;
+  for (int pass = 0; pass < passes; ++pass) {
+    Rot3 R[S];
+    int kk[S], sc[S];
+    float mind[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      kk[j] = lane + 32 * (pass * S + j);
+      float c, s;
+      angle_cs(kk[j] < a.A ? kk[j] : 0, a.A, c, s);
+      R[j] = rodrigues(ux, uy, uz, c, s, xp);
+      sc[j] = s_static;
+      mind[j] = 3.0e38f;
+      if (kk[j] < a.A) pairs += n_near;
+    }
+    int ia = 0;
+    for (int seg = 0; seg < 2; ++seg) {
+      const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
+      for (int ai = ma; ai < mb; ++ai, ++ia) {
+        const float4 xa = X[ai];
+        float xr[S][3];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          rot_apply(R[j], xa.x, xa.y, xa.z, xr[j][0], xr[j][1], xr[j][2]);
+          sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
+        }
+        const int e1 = w.MOFF[ia + 1];
+        for (int e = w.MOFF[ia]; e < e1; ++e) {
+          const float4 xb = X[w.NEAR[e]];
+#pragma unroll
+          for (int j = 0; j < S; ++j) {
+            const float dx = __fsub_rn(xr[j][0], xb.x);
+            const float dy = __fsub_rn(xr[j][1], xb.y);
+            const float dz = __fsub_rn(xr[j][2], xb.z);
+            mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+      if (kk[j] < a.A) {
+        const bool bump = mind[j] < a.thr2;
+        const unsigned key = bump ? 0u : (((unsigned)(sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
+        best = key > best ? key : best;
+        if (dbg) dbg[kk[j]] = bump ? 1 : 0;
+      }
+  }
+  return __reduce_max_sync(FULL, best);
+}
+
 // a10: reduce over the ligand's restarts, replay the winner, write the results.
 __device__ void finalize(const SearchArgs& a, float4* X, RotDesc* rds, int li, int lane) {
   const int O = a.O;
   unsigned best = 0;
-  unsigned long long pairs = 0;
+  unsigned long long pairs = 0, reach = 0;
   for (int o = lane; o < O; o += 32) {
     const unsigned s = __ldcg(a.pose_score + (size_t)li * O + o);
     const unsigned key = ((s + 1u) << 16) | (0xFFFFu - (unsigned)o);
     best = key > best ? key : best;
     pairs += __ldcg(a.pose_pairs + (size_t)li * O + o);
+    reach += __ldcg(a.pose_reach + (size_t)li * O + o);
   }
   best = __reduce_max_sync(FULL, best);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) pairs += __shfl_xor_sync(FULL, pairs, off);
+  for (int off = 16; off > 0; off >>= 1) {
+    pairs += __shfl_xor_sync(FULL, pairs, off);
+    reach += __shfl_xor_sync(FULL, reach, off);
+  }
   const int ob = (int)(0xFFFFu - (best & 0xFFFFu));
   const unsigned sb = (best >> 16) - 1u;
   const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
@@ -333,6 +486,7 @@ __device__ void finalize(const SearchArgs& a, float4* X, RotDesc* rds, int li, i
     a.best_orient[li] = ob;
     a.evals[li] = (unsigned long long)O * a.reps * R * a.A;
     a.pair_tests[li] = pairs;
+    a.reach_tests[li] = reach;
     a.atom_moves[li] = (unsigned long long)O * a.reps * a.A * fsum;
   }
   for (int s = lane; s < a.reps * R; s += 32)
@@ -359,13 +513,14 @@ __device__ void finalize(const SearchArgs& a, float4* X, RotDesc* rds, int li, i
 }
 
 template <int S, bool SG>
-__device__ void search_pose(const SearchArgs& a, const uint8_t* sg, float4* X, RotDesc* rds, int li, int o,
-                            int lane) {
+__device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int lane) {
+  float4* X = w.X;
+  RotDesc* rds = w.rd;
   const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
   const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
   place(a, X, a.xyz + a0, n, o, lane);
   int cur = score_atoms<SG>(a.pk, sg, X, n, lane);
-  unsigned long long pairs = 0;
+  unsigned long long pairs = 0, reach = 0;
   const size_t pick_base = (size_t)r0 * a.reps * a.O + (size_t)o * a.reps * R;
   for (int rep = 0; rep < a.reps; ++rep)
     for (int r = 0; r < R; ++r) {
@@ -377,7 +532,12 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, float4* X, R
       uint8_t* dbg = nullptr;
       if (a.bump_bits)
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
-      const unsigned key = eval_step<S, SG>(a, sg, X, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
+      unsigned key;
+      const float4 xp = X[rd.p];
+      if (a.use_filter && build_near(a, w, n, rd, xp, ux, uy, uz, lane, reach) <= a.near_cap)
+        key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, lane, pairs, dbg);
+      else
+        key = eval_step<S, SG>(a, sg, X, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
         commit(X, n, rd, ux, uy, uz, k, a.A, lane);
@@ -391,6 +551,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, float4* X, R
   if (lane == 0) {
     a.pose_score[(size_t)li * a.O + o] = (uint32_t)cur;
     a.pose_pairs[(size_t)li * a.O + o] = pairs;
+    a.pose_reach[(size_t)li * a.O + o] = reach;
   }
   __syncwarp();
   __threadfence();
@@ -459,8 +620,7 @@ __global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ Sea
       return;
     }
   }
-  float4* X = reinterpret_cast<float4*>(smem + off + (size_t)warp * ((size_t)a.nmax * 16 + 64));
-  RotDesc* rds = reinterpret_cast<RotDesc*>(X + a.nmax);
+  const WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.near_cap);
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(a.work, 1ull);
@@ -468,7 +628,7 @@ __global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ Sea
     if (t >= (unsigned long long)a.n_items) break;
     const int li = a.order[t / (unsigned long long)a.O];
     const int o = (int)(t % (unsigned long long)a.O);
-    search_pose<S, SG>(a, sg, X, rds, li, o, lane);
+    search_pose<S, SG>(a, sg, w, li, o, lane);
   }
 }
 
@@ -503,7 +663,7 @@ int max_smem_grid_bytes() { return 200 * 1024; }
 
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
   const Tile t = tile_get(tile);
-  size_t s = (size_t)t.warps * ((size_t)a.nmax * 16 + 64);
+  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.near_cap);
   if (grid_in_smem) s += (size_t)a.pk.bytes_pad + 16;
   return s;
 }

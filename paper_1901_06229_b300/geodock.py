@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgeodock.so")
 GD_OK, GD_EINVAL, GD_ENOMEM, GD_EBUDGET, GD_ECUDA, GD_ETIMEOUT, GD_EBUSY, GD_ENOTREADY = range(8)
 GD_FLAG_DEBUG = 1
 GD_FLAG_DEBUG_BUMPS = 2
+GD_FLAG_NO_FILTER = 4
 STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: "GD_ECUDA",
                 5: "GD_ETIMEOUT", 6: "GD_EBUSY", 7: "GD_ENOTREADY"}
 
@@ -49,7 +50,8 @@ class ResultBatchC(C.Structure):
     _fields_ = [("best_score", C.POINTER(C.c_uint32)), ("best_orient", C.POINTER(C.c_int32)),
                 ("best_angle", C.POINTER(C.c_int16)), ("best_xyz", C.POINTER(C.c_float)),
                 ("evals", C.POINTER(C.c_uint64)), ("pair_tests", C.POINTER(C.c_uint64)),
-                ("atom_moves", C.POINTER(C.c_uint64)), ("orient_score", C.POINTER(C.c_uint32)), ("orient_pick", C.POINTER(C.c_int16)),
+                ("atom_moves", C.POINTER(C.c_uint64)), ("reach_tests", C.POINTER(C.c_uint64)),
+                ("orient_score", C.POINTER(C.c_uint32)), ("orient_pick", C.POINTER(C.c_int16)),
                 ("bump_bits", C.POINTER(C.c_uint8))]
 
 
@@ -144,7 +146,7 @@ class Job:
             best_score=np.zeros(self.L, np.uint32), best_orient=np.zeros(self.L, np.int32),
             best_angle=np.zeros(Rt * reps, np.int16), best_xyz=np.zeros((self.N, 3), np.float32),
             evals=np.zeros(self.L, np.uint64), pair_tests=np.zeros(self.L, np.uint64),
-            atom_moves=np.zeros(self.L, np.uint64))
+            atom_moves=np.zeros(self.L, np.uint64), reach_tests=np.zeros(self.L, np.uint64))
         if self.debug and out is None:
             r["orient_score"] = np.zeros((self.L, O), np.uint32)
             r["orient_pick"] = np.zeros(Rt * reps * O, np.int16)
@@ -154,7 +156,7 @@ class Job:
         rb = ResultBatchC(_ptr(r["best_score"], C.c_uint32), _ptr(r["best_orient"], C.c_int32),
                           _ptr(r["best_angle"], C.c_int16), _ptr(r["best_xyz"], C.c_float),
                           _ptr(r["evals"], C.c_uint64), _ptr(r["pair_tests"], C.c_uint64),
-                          _ptr(r["atom_moves"], C.c_uint64),
+                          _ptr(r["atom_moves"], C.c_uint64), _ptr(r["reach_tests"], C.c_uint64),
                           _ptr(r["orient_score"], C.c_uint32) if "orient_score" in r else nul(C.c_uint32),
                           _ptr(r["orient_pick"], C.c_int16) if "orient_pick" in r else nul(C.c_int16),
                           _ptr(r["bump_bits"], C.c_uint8) if "bump_bits" in r else nul(C.c_uint8))
@@ -234,19 +236,22 @@ class Context:
                                           _ptr(org, C.c_float), C.byref(h)))
         return Pocket(self, h)
 
-    def dock_batch(self, pocket: Pocket, batch, params, stream=None, debug=False, bumps=False, tile=0) -> Job:
-        """gd_dock_batch: debug keeps per-restart scores/picks, bumps also per-candidate bump bits."""
+    def dock_batch(self, pocket: Pocket, batch, params, stream=None, debug=False, bumps=False, tile=0,
+                   no_filter=False) -> Job:
+        """gd_dock_batch: debug keeps per-restart scores/picks, bumps also per-candidate bump bits,
+        no_filter tests every pair at every angle (same results, slower)."""
         arrs = _BatchArrays(batch)
-        flags = (GD_FLAG_DEBUG if debug else 0) | (GD_FLAG_DEBUG_BUMPS if bumps else 0)
+        flags = ((GD_FLAG_DEBUG if debug else 0) | (GD_FLAG_DEBUG_BUMPS if bumps else 0)
+                 | (GD_FLAG_NO_FILTER if no_filter else 0))
         prm = params_c(params, flags, tile)
         h = C.c_void_p()
         self._check(load().gd_dock_batch(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm),
                                          _stream_handle(stream), C.byref(h)))
         return Job(self, h, batch, params, debug, bumps)
 
-    def autotune(self, pocket: Pocket, batch, params, max_ligands=256, stream=None):
+    def autotune(self, pocket: Pocket, batch, params, max_ligands=256, stream=None, no_filter=False):
         arrs = _BatchArrays(batch)
-        prm = params_c(params)
+        prm = params_c(params, GD_FLAG_NO_FILTER if no_filter else 0)
         t, ms = C.c_int(), C.c_float()
         self._check(load().gd_autotune(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm), int(max_ligands),
                                        _stream_handle(stream), C.byref(t), C.byref(ms)))

@@ -23,17 +23,17 @@ def ctx():
     c.close()
 
 
-def run(ctx, w_pocket, batch, params, debug=True, bumps=True, tile=0):
+def run(ctx, w_pocket, batch, params, debug=True, bumps=True, tile=0, no_filter=False):
     pk = ctx.load_pocket(w_pocket)
-    job = ctx.dock_batch(pk, batch, params, debug=debug, bumps=bumps, tile=tile)
+    job = ctx.dock_batch(pk, batch, params, debug=debug, bumps=bumps, tile=tile, no_filter=no_filter)
     out = job.fetch()
     job.free()
     pk.free()
     return out
 
 
-def full_compare(ctx, pocket, batch, params, tile=0, min_exact=1):
-    gpu = run(ctx, pocket, batch, params, tile=tile)
+def full_compare(ctx, pocket, batch, params, tile=0, min_exact=1, no_filter=False):
+    gpu = run(ctx, pocket, batch, params, tile=tile, no_filter=no_filter)
     orc = oracle.dock_batch(batch, pocket, params, n_threads=8, debug=True)
     st = compare_debug(gpu, orc, batch, params)
     print(dict(st))
@@ -102,6 +102,36 @@ def test_edge_cases(ctx, case):
     full_compare(ctx, pocket, synth.pack(ligs), params, min_exact=1)
 
 
+def test_unfiltered_sweep_matches_oracle(ctx):
+    w = synth.workload_batched(12)
+    full_compare(ctx, w.pocket, w.batch, w.params, min_exact=1000, no_filter=True)
+
+
+@pytest.mark.parametrize("which", ["batched", "large", "min_sep4", "bump25"])
+def test_reach_filter_is_exact(ctx, which):
+    """The per-rotamer reach filter only skips pair tests that cannot fire: every output
+    but the work counters is bitwise identical to testing every pair at every angle."""
+    if which == "batched":
+        w = synth.workload_batched(48)
+        pocket, batch, params = w.pocket, w.batch, w.params
+    else:
+        w = synth.workload_large(4)
+        pocket, batch = w.pocket, w.batch
+        params = synth.SearchParams(2, 2, 2, 128)
+        if which == "min_sep4":
+            params = synth.SearchParams(2, 2, 2, 64, min_bond_sep=4)
+        elif which == "bump25":
+            params = synth.SearchParams(2, 2, 2, 64, bump_dist=2.5)
+    a = run(ctx, pocket, batch, params, no_filter=False)
+    b = run(ctx, pocket, batch, params, no_filter=True)
+    for k in a:
+        if k in ("pair_tests", "reach_tests"):
+            continue
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert a["pair_tests"].sum() < b["pair_tests"].sum()
+    assert b["reach_tests"].sum() == 0 and a["reach_tests"].sum() > 0
+
+
 def test_empty_batch(ctx):
     w = synth.workload_single()
     out = run(ctx, w.pocket, synth.pack([]), w.params)
@@ -125,7 +155,7 @@ def test_tiles_give_identical_results(ctx):
             ref = out
             continue
         for k in ref:
-            if k == "pair_tests":  # counted per tile granularity of the early exit
+            if k in ("pair_tests", "reach_tests"):  # work counters depend on the early exit
                 continue
             np.testing.assert_array_equal(out[k], ref[k], err_msg=f"tile {t}: {k}")
 
