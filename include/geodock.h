@@ -180,6 +180,38 @@ gd_status gd_autotune(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batc
                       const gd_search_params* params, int max_ligands, void* stream, int* best_tile,
                       float* best_ms);
 
+/* ---- Docking without allocation --------------------------------------------------
+ * The paper has no counterpart: this serves callers that cannot allocate device memory
+ * when they dock -- a process whose device memory is already fully reserved by
+ * another framework's caching allocator, a service that forbids allocation after
+ * start-up so its memory footprint stays fixed, or code that must avoid cudaMalloc /
+ * cudaFree because they synchronise the whole device.
+ *
+ * gd_dock_batch_noalloc docks like gd_dock_batch + gd_fetch_results (same search
+ * kernel, same results) but calls no cudaMalloc, cudaFree, cudaMallocHost or other
+ * allocating routine and needs no context.  Its working memory -- the cropped pocket
+ * grid, the packed ligands, the results and the kernel's scratch (per-restart scores,
+ * picks and counters) -- is one file-scope __device__ array of GD_NOALLOC_MAX_BYTES
+ * (64 MiB) that every GPU which loads the library holds until the process exits, plus
+ * a host staging array of the same size.  Inputs: the pocket grid and the batch in
+ * host memory (layouts as for gd_load_pocket / gd_ligand_batch); outputs: the caller's
+ * host buffers of `out` (debug arrays must be NULL; GD_FLAG_DEBUG* are rejected).
+ * The call is synchronous on `stream` (results are in `out` on return).
+ * Limits: a batch whose grid, inputs, results and scratch need more than
+ * GD_NOALLOC_MAX_BYTES is rejected with GD_EINVAL (about 20*L*O + 2*O*reps*Rt +
+ * 300*Rt + 48*N + 64*L bytes plus the cropped grid); all other limits as gd_dock_batch.
+ * Set-up: the first call on a device (the current device) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * Concurrency: every call shares the one array and its contents persist between calls
+ * (the kernel clears what must start at zero), so calls that overlap on the GPU -- from
+ * two threads, or on two streams -- race and must be serialised by the caller.
+ * err_msg (optional, err_len bytes) receives a one-line reason on failure. */
+#define GD_NOALLOC_MAX_BYTES (64u << 20)
+gd_status gd_dock_batch_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacing,
+                                const float origin[3], const gd_ligand_batch* batch,
+                                const gd_search_params* params, gd_result_batch* out, void* stream,
+                                char* err_msg, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

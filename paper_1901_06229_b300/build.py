@@ -5,7 +5,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("gd_api.cu", "gd_search.cu")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("gd_api.cu", "gd_search.cu", "gd_noalloc.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "gd_internal.h"), os.path.join(ROOT, "include", "geodock.h")]
 LIB = os.path.join(HERE, "libgeodock.so")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: 
 # every entry point declared in include/geodock.h
 EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_free_pocket",
            "gd_dock_batch", "gd_fetch_results", "gd_job_launch", "gd_job_download", "gd_job_bytes", "gd_job_free",
-           "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune"]
+           "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc"]
 
 
 class GeoDockError(RuntimeError):
@@ -265,6 +265,46 @@ def check_batch(batch, params) -> None:
     st = load().gd_check_batch(C.byref(arrs.c), C.byref(prm))
     if st:
         raise GeoDockError(st, load().gd_last_error(None).decode())
+
+
+def dock_noalloc(batch, pocket, params, stream=None, tile=0) -> dict:
+    """gd_dock_batch_noalloc: dock without any allocation at call time (synchronous).
+
+    For callers that cannot allocate device memory when they dock (device memory
+    already reserved by another allocator, allocation forbidden after start-up, or
+    cudaMalloc/cudaFree's device-wide synchronisation unacceptable): the library's
+    fixed 64 MiB device array holds the grid, packed ligands, results and scratch.
+    Calls share that array, so overlapping calls race.
+    """
+    L = load()
+    if not hasattr(L, "_noalloc_ready"):
+        L.gd_dock_batch_noalloc.argtypes = [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, C.c_float,
+                                            C.POINTER(C.c_float), C.POINTER(LigandBatchC), C.POINTER(SearchParamsC),
+                                            C.POINTER(ResultBatchC), C.c_void_p, C.c_char_p, C.c_size_t]
+        L.gd_dock_batch_noalloc.restype = C.c_int
+        L._noalloc_ready = True
+    arrs = _BatchArrays(batch)
+    prm = params_c(params, 0, tile)
+    g = np.ascontiguousarray(pocket.grid, np.uint8)
+    nz, ny, nx = g.shape
+    org = np.ascontiguousarray(pocket.origin, np.float32)
+    n_lig, n_atoms, Rt = batch.n_ligands, len(batch.xyz), int(batch.rot_off[-1]) if len(batch.rot_off) else 0
+    r = dict(best_score=np.zeros(n_lig, np.uint32), best_orient=np.zeros(n_lig, np.int32),
+             best_angle=np.zeros(Rt * params.repetitions, np.int16), best_xyz=np.zeros((n_atoms, 3), np.float32),
+             evals=np.zeros(n_lig, np.uint64), pair_tests=np.zeros(n_lig, np.uint64),
+             atom_moves=np.zeros(n_lig, np.uint64), reach_tests=np.zeros(n_lig, np.uint64))
+    nul = lambda ct: C.cast(None, C.POINTER(ct))
+    rb = ResultBatchC(_ptr(r["best_score"], C.c_uint32), _ptr(r["best_orient"], C.c_int32),
+                      _ptr(r["best_angle"], C.c_int16), _ptr(r["best_xyz"], C.c_float),
+                      _ptr(r["evals"], C.c_uint64), _ptr(r["pair_tests"], C.c_uint64),
+                      _ptr(r["atom_moves"], C.c_uint64), _ptr(r["reach_tests"], C.c_uint64),
+                      nul(C.c_uint32), nul(C.c_int16), nul(C.c_uint8))
+    msg = C.create_string_buffer(512)
+    st = L.gd_dock_batch_noalloc(_ptr(g, C.c_uint8), nx, ny, nz, float(pocket.spacing), _ptr(org, C.c_float),
+                                 C.byref(arrs.c), C.byref(prm), C.byref(rb), _stream_handle(stream), msg, 512)
+    if st:
+        raise GeoDockError(st, msg.value.decode())
+    return r
 
 
 def tile_count() -> int:
