@@ -18,6 +18,8 @@
 using gd::RotDesc;
 using gd::SearchArgs;
 
+static_assert(gd::EXCL_SMEM == GD_MAX_EXCLUDED, "per-warp exclusion buffer must hold a rotamer's list");
+
 namespace {
 
 thread_local std::string g_err;

@@ -79,11 +79,15 @@ struct SearchArgs {
 // this margin can never be flagged by the per-angle test.
 constexpr float REACH_MARGIN = 0.01f;
 
+// Capacity of a warp's copy of the current rotamer's excluded pairs (the per-rotamer
+// limit GD_MAX_EXCLUDED of the public header).
+constexpr int EXCL_SMEM = 128;
+
 // Per-warp shared memory: X float4[nmax] | HR float2[nmax] | MOFF uint16[nmax+2] |
-// NEAR uint8[near_cap] | RotDesc.
+// NEAR uint8[near_cap] | EX uint16[EXCL_SMEM] | RotDesc.
 __host__ __device__ inline int warp_smem_bytes(int nmax, int near_cap) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
-  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(near_cap) + 16;
+  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(near_cap) + 2 * EXCL_SMEM + 16;
 }
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };

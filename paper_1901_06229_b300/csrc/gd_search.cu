@@ -65,9 +65,11 @@ __device__ __forceinline__ void rot_apply(const Rot3& R, float x, float y, float
   oz = __fadd_rn(R.p[2], __fmaf_rn(R.m[6], dx, __fmaf_rn(R.m[7], dy, __fmul_rn(R.m[8], dz))));
 }
 
-// Angle theta_k = 2 pi k / A as (cos, sin).
-__device__ __forceinline__ void angle_cs(int k, int A, float& c, float& s) {
+// Angle theta_k = 2 pi k / A as (cos, sin), computed once per block into a table.
+__device__ __forceinline__ float2 angle_entry(int k, int A) {
+  float c, s;
   sincospif(__fdiv_rn(2.0f * (float)k, (float)A), &s, &c);
+  return make_float2(c, s);
 }
 
 // Grid cell under a point (pocket-centred coordinates); 0 outside the cropped box.
@@ -81,10 +83,6 @@ __device__ __forceinline__ int cell(const PocketDev& pk, const uint8_t* sg, floa
   const int idx = (iz * pk.cy + iy) * pk.cx + ix;
   if (SG) return sg[idx];
   return __ldg(pk.grid + idx);
-}
-
-__device__ __forceinline__ bool is_moving(const RotDesc& rd, int i) {
-  return rd.comp ? (i < rd.lo || i >= rd.hi) : (i >= rd.lo && i < rd.hi);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -149,20 +147,27 @@ __device__ __forceinline__ void bond_axis(const float4* X, const RotDesc& rd, fl
   uz = __fmul_rn(dz, inv);
 }
 
-// Commit the winning rotation k to the fragment (same arithmetic as the candidate).
-__device__ void commit(float4* X, int n, const RotDesc& rd, float ux, float uy, float uz, int k, int A,
-                       int lane) {
-  float c, s;
-  angle_cs(k, A, c, s);
-  const Rot3 R = rodrigues(ux, uy, uz, c, s, X[rd.p]);
+// i-th atom of the rotating fragment (preorder id), i in [0, f).
+__device__ __forceinline__ int frag_atom(const RotDesc& rd, int i) {
+  return rd.comp ? (i < rd.lo ? i : rd.hi + (i - rd.lo)) : rd.lo + i;
+}
+
+__device__ __forceinline__ int frag_size(const RotDesc& rd, int n) {
+  return rd.comp ? n - (rd.hi - rd.lo) : rd.hi - rd.lo;
+}
+
+// Commit the winning rotation to the fragment (same arithmetic as the candidate).
+__device__ void commit(float4* X, int n, const RotDesc& rd, float ux, float uy, float uz, float2 cs, int lane) {
+  const Rot3 R = rodrigues(ux, uy, uz, cs.x, cs.y, X[rd.p]);
   __syncwarp();
-  for (int i = lane; i < n; i += 32)
-    if (is_moving(rd, i)) {
-      const float4 v = X[i];
-      float x, y, z;
-      rot_apply(R, v.x, v.y, v.z, x, y, z);
-      X[i] = make_float4(x, y, z, 0.f);
-    }
+  const int f = frag_size(rd, n);
+  for (int i = lane; i < f; i += 32) {
+    const int t = frag_atom(rd, i);
+    const float4 v = X[t];
+    float x, y, z;
+    rot_apply(R, v.x, v.y, v.z, x, y, z);
+    X[t] = make_float4(x, y, z, 0.f);
+  }
   __syncwarp();
 }
 
@@ -177,15 +182,17 @@ __device__ __forceinline__ int score_atoms(const PocketDev& pk, const uint8_t* s
   return __reduce_add_sync(FULL, s);
 }
 
+// Cells under the fragment's current atoms.  The static part of every candidate's
+// score is the running score minus this (integer arithmetic, exact).
 template <bool SG>
-__device__ __forceinline__ int score_static(const PocketDev& pk, const uint8_t* sg, const float4* X, int n,
-                                            const RotDesc& rd, int lane) {
+__device__ __forceinline__ int score_fragment(const PocketDev& pk, const uint8_t* sg, const float4* X, int n,
+                                              const RotDesc& rd, int lane) {
   int s = 0;
-  for (int i = lane; i < n; i += 32)
-    if (!is_moving(rd, i)) {
-      const float4 v = X[i];
-      s += cell<SG>(pk, sg, v.x, v.y, v.z);
-    }
+  const int f = frag_size(rd, n);
+  for (int i = lane; i < f; i += 32) {
+    const float4 v = X[frag_atom(rd, i)];
+    s += cell<SG>(pk, sg, v.x, v.y, v.z);
+  }
   return __reduce_add_sync(FULL, s);
 }
 
@@ -209,9 +216,9 @@ __device__ __forceinline__ void min_d2_range(const float4* X, int b0, int b1, co
 // Evaluate every angle of one rotamer step; returns the warp-wide best key
 // ((score + 1) << 16 | (0xFFFF - k)), 0 if every candidate is bumped.
 template <int S, bool SG>
-__device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X, int n, const RotDesc& rd,
-                              float ux, float uy, float uz, int s_static, int lane,
-                              unsigned long long& pairs, uint8_t* dbg) {
+__device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X, const float2* CS,
+                              const uint16_t* excl, int n, const RotDesc& rd, float ux, float uy, float uz,
+                              int s_static, int lane, unsigned long long& pairs, uint8_t* dbg) {
   const float4 xp = X[rd.p];
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a, s1b;
   if (rd.comp) {
@@ -231,16 +238,14 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
-      float c, s;
-      angle_cs(kk[j] < a.A ? kk[j] : 0, a.A, c, s);
-      R[j] = rodrigues(ux, uy, uz, c, s, xp);
+      const float2 cs = CS[kk[j] < a.A ? kk[j] : 0];
+      R[j] = rodrigues(ux, uy, uz, cs.x, cs.y, xp);
       sc[j] = s_static;
       bump[j] = kk[j] >= a.A;  // idle slots count as rejected
     }
-    const uint16_t* excl = a.excl + rd.excl_off;
     const int n_excl = rd.n_excl;
     int ex = 0;
-    int next_a = n_excl ? (int)(__ldg(excl) & 0xFF) : -1;  // moving atom of the next excluded pair
+    int next_a = n_excl ? (int)(excl[0] & 0xFF) : -1;  // moving atom of the next excluded pair
     bool stop = false;
     for (int seg = 0; seg < 2 && !stop; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
@@ -251,11 +256,11 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
         float4 saved = make_float4(0.f, 0.f, 0.f, 0.f);
         int my_b = -1;
         if (ai == next_a) {
-          while (ex_end < n_excl && (int)(__ldg(excl + ex_end) & 0xFF) == ai) ++ex_end;
-          next_a = ex_end < n_excl ? (int)(__ldg(excl + ex_end) & 0xFF) : -1;
+          while (ex_end < n_excl && (int)(excl[ex_end] & 0xFF) == ai) ++ex_end;
+          next_a = ex_end < n_excl ? (int)(excl[ex_end] & 0xFF) : -1;
           __syncwarp();
           if (lane < ex_end - ex) {
-            my_b = (int)(__ldg(excl + ex + lane) >> 8);
+            my_b = (int)(excl[ex + lane] >> 8);
             saved = X[my_b];
             X[my_b] = make_float4(PARK, PARK, PARK, 0.f);
           }
@@ -306,7 +311,9 @@ struct WarpMem {
   float2* HR;      // (height along the bond axis, distance from it) per atom
   uint16_t* MOFF;  // near-list offset per moving atom (in sweep order)
   uint8_t* NEAR;   // static atoms that can come within reach of each moving atom
+  uint16_t* EX;    // the current rotamer's excluded pairs
   RotDesc* rd;
+  const float2* CS;  // (cos, sin) of every angle, shared by the block
 };
 
 __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int near_cap) {
@@ -320,7 +327,10 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int n
   base += a16(2 * (nmax + 2));
   w.NEAR = base;
   base += a16(near_cap);
+  w.EX = reinterpret_cast<uint16_t*>(base);
+  base += 2 * EXCL_SMEM;
   w.rd = reinterpret_cast<RotDesc*>(base);
+  w.CS = nullptr;
   return w;
 }
 
@@ -348,7 +358,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, int n, const Ro
     s0a = 0; s0b = rd.lo; s1a = rd.hi; s1b = n;
   }
   const int n_static = (s0b - s0a) + (s1b - s1a);
-  const uint16_t* excl = a.excl + rd.excl_off;
+  const uint16_t* excl = w.EX;
   const int n_excl = rd.n_excl;
   int ex = 0, cnt = 0, ia = 0;
   const unsigned lt = (1u << lane) - 1u;
@@ -358,7 +368,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, int n, const Ro
       if (lane == 0) w.MOFF[ia] = (uint16_t)(cnt < 65535 ? cnt : 65535);
       const float2 ha = w.HR[ai];
       int ex_end = ex;
-      while (ex_end < n_excl && (int)(__ldg(excl + ex_end) & 0xFF) == ai) ++ex_end;
+      while (ex_end < n_excl && (int)(excl[ex_end] & 0xFF) == ai) ++ex_end;
       for (int t = 0; t < n_static; t += 32) {
         const int k = t + lane;
         bool near = false;
@@ -369,7 +379,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, int n, const Ro
           const float dh = __fsub_rn(ha.x, hb.x), dr = __fsub_rn(ha.y, hb.y);
           near = __fmaf_rn(dh, dh, __fmul_rn(dr, dr)) < a.reach2;
           for (int e = ex; e < ex_end && near; ++e)
-            if ((int)(__ldg(excl + e) >> 8) == b) near = false;
+            if ((int)(excl[e] >> 8) == b) near = false;
         }
         const unsigned m = __ballot_sync(FULL, near);
         const int pos = cnt + __popc(m & lt);
@@ -407,9 +417,8 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
-      float c, s;
-      angle_cs(kk[j] < a.A ? kk[j] : 0, a.A, c, s);
-      R[j] = rodrigues(ux, uy, uz, c, s, xp);
+      const float2 cs = w.CS[kk[j] < a.A ? kk[j] : 0];
+      R[j] = rodrigues(ux, uy, uz, cs.x, cs.y, xp);
       sc[j] = s_static;
       mind[j] = 3.0e38f;
       if (kk[j] < a.A) pairs += n_near;
@@ -451,7 +460,9 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 }
 
 // a10: reduce over the ligand's restarts, replay the winner, write the results.
-__device__ void finalize(const SearchArgs& a, float4* X, RotDesc* rds, int li, int lane) {
+__device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane) {
+  float4* X = w.X;
+  RotDesc* rds = w.rd;
   const int O = a.O;
   unsigned best = 0;
   unsigned long long pairs = 0, reach = 0;
@@ -500,7 +511,7 @@ __device__ void finalize(const SearchArgs& a, float4* X, RotDesc* rds, int li, i
       const RotDesc& rd = *rds;
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
-      commit(X, n, rd, ux, uy, uz, k, a.A, lane);
+      commit(X, n, rd, ux, uy, uz, w.CS[k], lane);
     }
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
@@ -526,9 +537,11 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
     for (int r = 0; r < R; ++r) {
       load_desc(rds, a.rots + r0 + r, lane);
       const RotDesc& rd = *rds;
+      for (int e = lane; e < rd.n_excl; e += 32) w.EX[e] = __ldg(a.excl + rd.excl_off + e);
+      __syncwarp();
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
-      const int s_static = score_static<SG>(a.pk, sg, X, n, rd, lane);
+      const int s_static = cur - score_fragment<SG>(a.pk, sg, X, n, rd, lane);
       uint8_t* dbg = nullptr;
       if (a.bump_bits)
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
@@ -537,10 +550,10 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       if (a.use_filter && build_near(a, w, n, rd, xp, ux, uy, uz, lane, reach) <= a.near_cap)
         key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, lane, pairs, dbg);
       else
-        key = eval_step<S, SG>(a, sg, X, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
+        key = eval_step<S, SG>(a, sg, X, w.CS, w.EX, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
-        commit(X, n, rd, ux, uy, uz, k, a.A, lane);
+        commit(X, n, rd, ux, uy, uz, w.CS[k], lane);
         cur = (int)(key >> 16) - 1;
       }
       if (lane == 0) a.pose_pick[pick_base + rep * R + r] = (int16_t)k;
@@ -560,7 +573,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   prev = __shfl_sync(FULL, prev, 0);
   if (prev == a.O - 1) {
     __threadfence();
-    finalize(a, X, rds, li, lane);
+    finalize(a, w, li, lane);
   }
 }
 
@@ -620,7 +633,13 @@ __global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ Sea
       return;
     }
   }
-  const WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.near_cap);
+  // (cos, sin) of every angle, once per block
+  float2* cs = reinterpret_cast<float2*>(smem + off);
+  for (int k = threadIdx.x; k < a.A; k += blockDim.x) cs[k] = angle_entry(k, a.A);
+  off += ((size_t)a.A * 8 + 15) / 16 * 16;
+  __syncthreads();
+  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.near_cap);
+  w.CS = cs;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(a.work, 1ull);
@@ -663,7 +682,7 @@ int max_smem_grid_bytes() { return 200 * 1024; }
 
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
   const Tile t = tile_get(tile);
-  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.near_cap);
+  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.near_cap) + ((size_t)a.A * 8 + 15) / 16 * 16;
   if (grid_in_smem) s += (size_t)a.pk.bytes_pad + 16;
   return s;
 }
