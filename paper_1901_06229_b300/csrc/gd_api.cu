@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "geodock.h"
@@ -463,32 +464,70 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   uint8_t* perm = (uint8_t*)(h + j->in.perm);
   RotDesc* rots = (RotDesc*)(h + j->in.rots);
   int32_t* order = (int32_t*)(h + j->in.order);
+  // ligands are packed by up to 16 host threads over contiguous ranges; each keeps its
+  // own exclusion list, concatenated afterwards in ligand order
   std::vector<double> cost(L);
-  std::vector<uint16_t> excl;
+  const int T = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), L / 64}));
+  struct Part {
+    int l0 = 0, l1 = 0, nmax = 2, bad = -1;
+    gd_status st = GD_OK;
+    std::string err;
+    std::vector<uint16_t> excl;
+  };
+  std::vector<Part> parts(T);
+  auto work = [&](Part& pt) {
+    for (int i = pt.l0; i < pt.l1; ++i) {
+      const int a0 = b->atom_off[i], n = b->atom_off[i + 1] - a0;
+      const int b0 = b->bond_off[i], nb = b->bond_off[i + 1] - b0;
+      const int r0 = b->rot_off[i], R = b->rot_off[i + 1] - r0;
+      gd_status s2 = pack_ligand(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
+                                 p->min_bond_sep, xyz + a0, perm + a0, rots + r0, pt.excl, &cost[i]);
+      if (!s2 && R * j->reps > 32767) s2 = fail(GD_EINVAL, "ligand %d: too many steps", i);
+      if (s2) {
+        pt.st = s2;
+        pt.bad = i;
+        pt.err = g_err;  // the message lives in this thread's g_err
+        return;
+      }
+      pt.nmax = std::max(pt.nmax, n);
+    }
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < T; ++t) {
+      parts[t].l0 = (int)((long long)L * t / T);
+      parts[t].l1 = (int)((long long)L * (t + 1) / T);
+      if (t) pool.emplace_back(work, std::ref(parts[t]));
+    }
+    work(parts[0]);
+    for (auto& th : pool) th.join();
+  }
   int nmax = 2;
-  for (int i = 0; i < L; ++i) {
-    const int a0 = b->atom_off[i], n = b->atom_off[i + 1] - a0;
-    const int b0 = b->bond_off[i], nb = b->bond_off[i + 1] - b0;
-    const int r0 = b->rot_off[i], R = b->rot_off[i + 1] - r0;
-    st = pack_ligand(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
-                     p->min_bond_sep, xyz + a0, perm + a0, rots + r0, excl, &cost[i]);
-    if (st) {
+  size_t n_excl = 0;
+  for (auto& pt : parts) {
+    if (pt.st) {
       job_release(c, j);
-      return st;
+      g_err = pt.err;
+      return pt.st;
     }
-    if (R * j->reps > 32767) {
-      job_release(c, j);
-      return fail(GD_EINVAL, "ligand %d: too many steps", i);
+    nmax = std::max(nmax, pt.nmax);
+    n_excl += pt.excl.size();
+  }
+  j->in = in_layout(L, N, Rt, (long long)n_excl);
+  {
+    size_t base = 0;
+    for (auto& pt : parts) {
+      if (base)
+        for (long long r = b->rot_off[pt.l0]; r < b->rot_off[pt.l1]; ++r) rots[r].excl_off += (uint32_t)base;
+      if (!pt.excl.empty()) memcpy(h + j->in.excl + 2 * base, pt.excl.data(), 2 * pt.excl.size());
+      base += pt.excl.size();
     }
-    nmax = std::max(nmax, n);
   }
   for (int i = 0; i <= L; ++i) {
     atom_off[i] = L ? b->atom_off[i] : 0;
     rot_off[i] = L ? b->rot_off[i] : 0;
   }
   j->rot_off.assign(rot_off, rot_off + L + 1);
-  j->in = in_layout(L, N, Rt, (long long)excl.size());
-  if (!excl.empty()) memcpy(h + j->in.excl, excl.data(), 2 * excl.size());
   for (int i = 0; i < L; ++i) order[i] = i;
   std::stable_sort(order, order + L, [&](int x, int y) { return cost[x] > cost[y]; });
 
