@@ -1,0 +1,32 @@
+// Internal interface of the tensor-core MLP kernels (gd_mlp.cu).  Not part of the ABI.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace gd {
+
+// D = A * B^T (BF16 inputs, FP32 accumulation in TMEM), then per element
+// x = D + bias[n]; x = relu(x) if relu; C (FP32) and/or Cb (BF16) receive x;
+// with dotw, dot_out[m] = sum_n bf16(x[m][n]) * dotw[n] + dot_bias (requires N <= 256).
+// A is M x K (transA: stored K x M), B is N x K (transB: stored K x N); K and N are
+// multiples of 16.
+struct GemmArgs {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int lda, ldb, ldc;
+  int M, N, K;
+  bool transA, transB;
+  const float* bias;
+  bool relu;
+  float* C;
+  __nv_bfloat16* Cb;
+  const float* dotw;
+  float dot_bias;
+  float* dot_out;
+  int* err;  // set to 1 if a bounded wait ran out (may be null)
+};
+
+size_t gemm_smem_bytes();
+cudaError_t gemm_launch(const GemmArgs& g, cudaStream_t stream);
+
+}  // namespace gd

@@ -1,0 +1,57 @@
+"""Tensor-core (tcgen05) GEMM of the learned proposer against an FP64 numpy product of
+the same BF16-rounded operands."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _ref(A, B, transA, transB):
+    a = A.float().cpu().numpy().astype(np.float64)
+    b = B.float().cpu().numpy().astype(np.float64)
+    a = a.T if transA else a
+    b = b.T if transB else b
+    return a @ b.T
+
+
+@pytest.mark.parametrize("M,N,K,tA,tB", [(128, 256, 48, 0, 0), (128, 16, 16, 0, 0), (256, 256, 256, 0, 0),
+                                         (300, 48, 64, 0, 0), (200, 256, 80, 1, 0), (256, 48, 384, 1, 1),
+                                         (384, 512, 32, 0, 1), (130, 32, 4096, 1, 1)])
+def test_gemm_matches_fp64(M, N, K, tA, tB):
+    import torch
+    from paper_1901_06229_b300 import mlp
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn((K, M) if tA else (M, K), generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn((K, N) if tB else (N, K), generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mlp.gemm(A, B, M, N, K, transA=tA, transB=tB, C_out=C, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = _ref(A, B, tA, tB)
+    got = C.cpu().numpy()
+    # FP32 accumulation of K products of O(1) BF16 values; a layout error is O(1)
+    bound = 1e-4 * np.sqrt(K)
+    assert np.isfinite(got).all()
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=bound)
+
+
+def test_gemm_epilogue_bias_relu_bf16_and_dot():
+    import torch
+    from paper_1901_06229_b300 import mlp
+    g = torch.Generator(device="cpu").manual_seed(5)
+    M, N, K = 256, 256, 48
+    A = torch.randn((M, K), generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn((N, K), generator=g).to(torch.bfloat16).cuda()
+    bias = torch.randn(N, generator=g).cuda()
+    w = torch.randn(N, generator=g).cuda()
+    Cb = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros(M, device="cuda")
+    mlp.gemm(A, B, M, N, K, Cb_out=Cb, bias=bias, relu=True, dotw=w, dot_bias=0.25, dot_out=y)
+    torch.cuda.synchronize()
+    x = np.maximum(_ref(A, B, 0, 0) + bias.cpu().numpy()[None, :], 0.0)
+    xb = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).float().numpy()
+    got = Cb.float().cpu().numpy()
+    # the kernel rounds its FP32 value to BF16: at most one BF16 ulp from rounding the FP64 value
+    np.testing.assert_allclose(got, xb, rtol=2 ** -7, atol=1e-6)
+    np.testing.assert_allclose(y.cpu().numpy(), got.astype(np.float64) @ w.cpu().numpy() + 0.25, rtol=1e-4, atol=1e-3)
