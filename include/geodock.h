@@ -150,6 +150,11 @@ gd_status gd_free_pocket(gd_ctx* ctx, gd_pocket* pocket);
  * on return.  The job owns its device memory until gd_job_free. */
 gd_status gd_dock_batch(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batch* batch,
                         const gd_search_params* params, void* stream, gd_job** out);
+/* The first half of gd_dock_batch: validate, pack and copy the batch to the device on
+ * `stream`, without searching.  Search it later with gd_job_launch (every restart) or
+ * gd_job_launch_subset (chosen restarts), then gd_job_download + gd_fetch_results. */
+gd_status gd_prepare_batch(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batch* batch,
+                           const gd_search_params* params, void* stream, gd_job** out);
 /* Copy a job's results into `out`.  blocking = 0 returns GD_ENOTREADY while the device
  * is still working. */
 gd_status gd_fetch_results(gd_ctx* ctx, gd_job* job, gd_result_batch* out, int blocking);

@@ -29,6 +29,19 @@ gd_status gd_mlp_gemm(const void* A, int lda, int transA, const void* B, int ldb
                       void* Cb, int ldc, int M, int N, int K, const float* bias, int relu,
                       const float* dotw, float dot_bias, float* dot_out, int* dev_err, void* stream);
 
+/* Features of every (ligand, restart) of a prepared job: 48 numbers per row, row
+ * li * O + o (input ligand order), written as BF16 (x_bf16, the network's input) and/or
+ * FP32 (x_f32); either may be NULL.  Row layout:
+ *   0..3   unit quaternion (w, x, y, z) of the restart rotation Rz(a) Ry(b) Rz(g), w >= 0
+ *   4, 5   atoms / 250, rotamers / 60
+ *   6      radius of gyration of the input coordinates / 10 A
+ *   7..22  fraction of atoms at distance [0.75 b, 0.75 (b+1)) A from the centroid
+ *   23..47 pocket value / 255 under 25 atoms of the placed restart pose, chosen by
+ *          farthest-point sampling from the atom farthest from the centroid (ties to
+ *          the smaller preorder id), cyclic for ligands of fewer than 25 atoms.
+ * Runs on `stream` after the job's upload (use the stream the job was prepared on). */
+gd_status gd_job_features(gd_ctx* ctx, gd_job* job, void* x_bf16, float* x_f32, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

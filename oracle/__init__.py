@@ -133,6 +133,28 @@ def bumped(xyz, bonds, rb: int, min_sep: int = 3, bump_dist: float = 2.0) -> boo
     return bool(r)
 
 
+def features(xyz, n_rot: int, o: int, params, pocket, eps: float = EPS) -> dict:
+    """The proposer's 48 features of one (ligand, restart) in FP64, with near-tie flags."""
+    x = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+    g = np.ascontiguousarray(pocket.grid, dtype=np.uint8)
+    nz, ny, nx_ = g.shape
+    org = np.ascontiguousarray(pocket.origin, dtype=np.float64)
+    feat = np.zeros(48)
+    fps = np.zeros(25, np.int32)
+    gap, edge = C.c_double(), C.c_double()
+    frag = np.zeros(25, np.uint8)
+    L = lib()
+    L.orc_features.argtypes = [C.POINTER(C.c_float), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                               C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double),
+                               C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), C.POINTER(C.c_uint8)]
+    if L.orc_features(_p(x, C.c_float), len(x), int(n_rot), int(o), params.n_alpha, params.n_beta, params.n_gamma,
+                      _p(g, C.c_uint8), nx_, ny, nz, float(pocket.spacing), _p(org, C.c_double), float(eps),
+                      _p(feat, C.c_double), _p(fps, C.c_int32), C.byref(gap), C.byref(edge), _p(frag, C.c_uint8)):
+        raise ValueError("bad ligand")
+    return dict(feat=feat, fps=fps, fps_gap=gap.value, hist_edge=edge.value, sample_fragile=frag.astype(bool))
+
+
 # ------------------------------------------------------------------ whole search
 
 def dock_pose(lig, pocket, params, o: int, debug: bool = False, eps: float = EPS) -> dict:

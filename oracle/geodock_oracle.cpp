@@ -510,6 +510,105 @@ int orc_bumped(int n, const int32_t* bonds, int nb, int rb, int min_sep, double 
   return 0;
 }
 
+// ---- features of the learned orientation proposer (FP64) -------------------------
+//
+// 48 numbers per (ligand, restart o): the restart quaternion (w >= 0), n/250, R/60,
+// radius of gyration / 10, 16-bin histogram of centroid distances over [0, 12) A as
+// fractions, and grid value / 255 under 25 farthest-point-sampled atoms of the placed
+// restart pose.  Farthest-point sampling starts from the atom farthest from the
+// centroid; at every step the candidates within a relative 1e-4 of the farthest count
+// as tied and the smallest input index wins (the generator's fixed bond geometry makes
+// exact ties common).  Also reports how close each decision came to flipping: the
+// smallest relative distance of a candidate to that tie threshold, the
+// smallest distance of an atom to a histogram bin edge, and a per-sample flag set when
+// an eps move of the sampled atom could read another cell value.
+
+static void qmul(const double a[4], const double b[4], double o[4]) {
+  o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+int orc_features(const float* xyz, int n, int R, int o, int na, int nb, int ng, const uint8_t* grid, int nx, int ny,
+                 int nz, double h, const double* origin, double eps, double* feat, int32_t* fps_out, double* fps_gap,
+                 double* hist_edge, uint8_t* sample_fragile) {
+  const double pi = 3.14159265358979323846;
+  if (n < 1) return 1;
+  Pocket P{grid, nx, ny, nz, h, V3{origin[0], origin[1], origin[2]}};
+  std::vector<V3> x(n);
+  V3 c{0, 0, 0};
+  for (int a = 0; a < n; ++a) {
+    x[a] = V3{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]};
+    c = c + x[a];
+  }
+  c = (1.0 / n) * c;
+  // restart quaternion: qz(alpha) * qy(beta) * qz(gamma), axis-angle halves
+  const int i = o / (nb * ng), j = (o / ng) % nb, k = o % ng;
+  const double al = 2.0 * pi * i / na, be = pi * (j + 0.5) / nb, ga = 2.0 * pi * k / ng;
+  const double qa[4] = {std::cos(al / 2), 0, 0, std::sin(al / 2)};
+  const double qb[4] = {std::cos(be / 2), 0, std::sin(be / 2), 0};
+  const double qg[4] = {std::cos(ga / 2), 0, 0, std::sin(ga / 2)};
+  double t[4], q[4];
+  qmul(qa, qb, t);
+  qmul(t, qg, q);
+  if (q[0] < 0)
+    for (double& v : q) v = -v;
+  for (int e = 0; e < 4; ++e) feat[e] = q[e];
+  feat[4] = n / 250.0;
+  feat[5] = R / 60.0;
+  double r2 = 0, edge = 1e30;
+  for (int e = 0; e < 16; ++e) feat[7 + e] = 0;
+  for (int a = 0; a < n; ++a) {
+    const double d = norm(x[a] - c);
+    r2 += d * d;
+    const int b = (int)std::floor(d / 0.75);
+    if (b < 16) feat[7 + b] += 1.0 / n;
+    edge = std::min(edge, std::fabs(d - 0.75 * std::round(d / 0.75)));
+  }
+  feat[6] = std::sqrt(r2 / n) / 10.0;
+  *hist_edge = edge;
+  // farthest-point sampling
+  const int nsel = n < 25 ? n : 25;
+  std::vector<double> mind(n);
+  std::vector<char> used(n, 0);
+  std::vector<int> fps;
+  double gap = 1e30;
+  for (int a = 0; a < n; ++a) mind[a] = norm(x[a] - c);
+  for (int s = 0; s < nsel; ++s) {
+    // candidates within a relative 1e-4 of the farthest count as tied; smallest index wins
+    double dmax = -1;
+    for (int a = 0; a < n; ++a)
+      if (!used[a]) dmax = std::max(dmax, mind[a]);
+    const double thr = (1.0 - 1e-4) * dmax;
+    int best = -1;
+    for (int a = 0; a < n; ++a) {
+      if (used[a]) continue;
+      if (best < 0 && mind[a] >= thr) best = a;
+      if (dmax > 0) gap = std::min(gap, std::fabs(mind[a] - thr) / dmax);
+    }
+    used[best] = 1;
+    fps.push_back(best);
+    for (int a = 0; a < n; ++a) {
+      const double d = norm(x[a] - x[best]);
+      mind[a] = s == 0 ? d : std::min(mind[a], d);
+    }
+  }
+  *fps_gap = gap;
+  const M3 Ro = euler_orientation(o, na, nb, ng);
+  const V3 cp = P.origin + (0.5 * P.h) * V3{(double)P.nx, (double)P.ny, (double)P.nz};
+  for (int sidx = 0; sidx < 25; ++sidx) {
+    const int a = fps[sidx % nsel];
+    fps_out[sidx] = a;
+    const V3 y = cp + mul(Ro, x[a] - c);
+    feat[23 + sidx] = cell_value(P, y) / 255.0;
+    int lo, hi;
+    cell_range(P, y, eps, &lo, &hi);
+    sample_fragile[sidx] = lo != hi;
+  }
+  return 0;
+}
+
 // ---- the whole search over a CSR batch --------------------------------------------
 
 struct orc_params {

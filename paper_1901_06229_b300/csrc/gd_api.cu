@@ -824,8 +824,11 @@ gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, 
   return GD_OK;
 }
 
-gd_status gd_dock_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
-                        void* stream, gd_job** out) {
+namespace {
+
+// Validate, pack and upload a batch on `stream`; the search is not launched.
+gd_status prepare(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p, void* stream,
+                  gd_job** out) {
   if (!c || !pk || !b || !out) return fail(GD_EINVAL, "NULL argument");
   gd_status st = check_params(p);
   if (st) return st;
@@ -850,16 +853,47 @@ gd_status gd_dock_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(j->d_in, j->h_in, j->in.total, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)j->d_out + j->out.err, 0, 4, s);
+  if (e == cudaSuccess) e = cudaEventRecord(j->done, s);
   if (e != cudaSuccess) {
     job_release(c, j);
     return fail(GD_ECUDA, "upload: %s", cudaGetErrorString(e));
   }
+  *out = j;
+  return GD_OK;
+}
+
+}  // namespace
+
+gd_status gd_prepare_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
+                           void* stream, gd_job** out) {
+  gd_status st = prepare(c, pk, b, p, stream, out);
+  if (!st) g_err.clear();
+  return st;
+}
+
+gd_status gd_dock_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
+                        void* stream, gd_job** out) {
+  gd_job* j = nullptr;
+  gd_status st = prepare(c, pk, b, p, stream, &j);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
   if ((st = enqueue_search(j, s)) || (st = enqueue_download(j, s))) {
     job_release(c, j);
     return st;
   }
   *out = j;
   g_err.clear();
+  return GD_OK;
+}
+
+gd_status gd_job_features(gd_ctx* c, gd_job* j, void* x_bf16, float* x_f32, void* stream) {
+  if (!c || !j) return fail(GD_EINVAL, "NULL argument");
+  if (!x_bf16 && !x_f32) return fail(GD_EINVAL, "no output");
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = gd::launch_features(j->args, (__nv_bfloat16*)x_bf16, x_f32, c->num_sms, s);
+  if (e == cudaSuccess) e = cudaEventRecord(j->done, s);
+  if (e != cudaSuccess) return fail(GD_ECUDA, "features: %s", cudaGetErrorString(e));
   return GD_OK;
 }
 

@@ -2,6 +2,7 @@
 // (gd_search.cu).  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace gd {
@@ -108,6 +109,9 @@ struct LaunchCfg {
   size_t smem = 0;
 };
 cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int num_sms, LaunchCfg* cfg);
+// The proposer's 48 features of every (ligand, restart) of a packed batch, rows
+// li * O + o, as BF16 (Xb) and/or FP32 (Xf).
+cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, int num_sms, cudaStream_t stream);
 // Launch the search (kernel only; the work counter and per-ligand counters must be
 // zeroed by the caller first).
 cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t stream);

@@ -21,6 +21,8 @@
 //       o), replays the winning pose to recover its coordinates and writes results.
 // All geometry uses explicitly rounded FP32 intrinsics, so the search and the replay
 // produce bitwise-identical coordinates and no launch tile can change a result.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "gd_internal.h"
@@ -651,6 +653,166 @@ __global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ Sea
   }
 }
 
+// ---- features of the learned orientation proposer -----------------------------------
+//
+// For every (ligand, restart) 48 numbers: the restart's unit quaternion (w >= 0); atoms /
+// 250 and rotamers / 60; radius of gyration / 10 A; the fraction of atoms in each of 16
+// bins of width 0.75 A of distance to the centroid over [0, 12) A; and the pocket value /
+// 255 under 25 atoms of the placed restart pose, chosen by farthest-point sampling
+// (first the atom farthest from the centroid, then repeatedly the atom farthest from
+// those chosen, ties to the smaller preorder id; cyclic when the ligand has < 25 atoms).
+// One warp per ligand: the restart-independent part once, then a row per restart.
+constexpr int NFEAT = 48, NFPS = 25, NHIST = 16;
+
+__global__ void __launch_bounds__(256) feature_kernel(const __grid_constant__ SearchArgs a, __nv_bfloat16* Xb,
+                                                       float* Xf) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  __shared__ int fps_s[8][NFPS];
+  int* fps = fps_s[threadIdx.x >> 5];
+  for (int li = gw; li < a.L; li += nw) {
+    const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
+    const int R = a.rot_off[li + 1] - a.rot_off[li];
+    const float4* x0 = a.xyz + a0;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const float4 v = x0[i];
+      sx = __fadd_rn(sx, v.x);
+      sy = __fadd_rn(sy, v.y);
+      sz = __fadd_rn(sz, v.z);
+    }
+    sx = warp_sum_f(sx);
+    sy = warp_sum_f(sy);
+    sz = warp_sum_f(sz);
+    const float cx = __fdiv_rn(sx, (float)n), cy = __fdiv_rn(sy, (float)n), cz = __fdiv_rn(sz, (float)n);
+    // per-lane atoms (at most 8) with their squared distance to the centroid
+    float mind[8];
+    int hist = 0;  // this lane's count for bin == lane (lanes 0..15)
+    float r2sum = 0.f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = lane + 32 * t;
+      mind[t] = -1.f;
+      if (i < n) {
+        const float4 v = x0[i];
+        const float dx = v.x - cx, dy = v.y - cy, dz = v.z - cz;
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        mind[t] = d2;
+        r2sum += d2;
+      }
+    }
+    r2sum = warp_sum_f(r2sum);
+    for (int t = 0; t < 8; ++t)
+      for (int src = 0; src < 32; ++src) {
+        const float d2 = __shfl_sync(FULL, mind[t], src);
+        if (d2 >= 0.f) {
+          const float d = sqrtf(d2);
+          const int b = (int)floorf(d / 0.75f);
+          if (b == lane && b < NHIST) ++hist;
+        }
+      }
+    // farthest-point sampling
+    const int nsel = n < NFPS ? n : NFPS;
+    for (int k = 0; k < nsel; ++k) {
+      // candidates within a relative 1e-4 of the farthest (in distance) count as tied;
+      // the smallest input-order atom id among them wins
+      float dmax2 = -1.f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) dmax2 = fmaxf(dmax2, mind[t]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) dmax2 = fmaxf(dmax2, __shfl_xor_sync(FULL, dmax2, off));
+      const float thr2 = dmax2 * ((1.0f - 1e-4f) * (1.0f - 1e-4f));
+      unsigned best = 0xFFFFFFFFu;  // (input id << 8) | preorder id
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n && mind[t] >= 0.f && mind[t] >= thr2) {
+          const unsigned key = ((unsigned)a.perm[a0 + i] << 8) | (unsigned)i;
+          best = key < best ? key : best;
+        }
+      }
+      best = __reduce_min_sync(FULL, best);
+      const int sel = (int)(best & 0xFFu);  // preorder id (< 256)
+      if (lane == 0) fps[k] = sel;
+      const float4 vs = x0[sel];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = lane + 32 * t;
+        if (i == sel) mind[t] = -1.f;
+        else if (i < n && mind[t] >= 0.f) {
+          const float4 v = x0[i];
+          const float dx = v.x - vs.x, dy = v.y - vs.y, dz = v.z - vs.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          mind[t] = k == 0 ? d2 : fminf(mind[t], d2);
+        }
+      }
+    }
+    __syncwarp();
+    // restart-independent features: lanes hold feature e = lane and e = lane + 32
+    float inv[2];
+    for (int h = 0; h < 2; ++h) {
+      const int e = lane + 32 * h;
+      float v = 0.f;
+      if (e == 4) v = (float)n / 250.f;
+      else if (e == 5) v = (float)R / 60.f;
+      else if (e == 6) v = sqrtf(r2sum / (float)n) / 10.f;
+      inv[h] = v;
+    }
+    const float hfrac = (float)hist / (float)n;  // lanes 0..15: bins
+    const float h7 = __shfl_sync(FULL, hfrac, (lane - 7) & 31);  // feature e = 7 + b holds bin b
+    const int samp0 = lane - 23, samp1 = lane + 32 - 23;          // grid sample index per slot
+    const int at0 = samp0 >= 0 ? fps[samp0 % nsel] : 0, at1 = (lane + 32 < NFEAT) ? fps[samp1 % nsel] : 0;
+    const float4 p0 = x0[at0], p1 = x0[at1];
+    for (int o = 0; o < a.O; ++o) {
+      const int ia = o / (a.nb * a.ng), jb = (o / a.ng) % a.nb, kg = o % a.ng;
+      float sa, ca, sb, cb, sg, cg;
+      sincospif(__fdiv_rn(2.0f * (float)ia, (float)a.na), &sa, &ca);
+      sincospif(__fdiv_rn(__fadd_rn((float)jb, 0.5f), (float)a.nb), &sb, &cb);
+      sincospif(__fdiv_rn(2.0f * (float)kg, (float)a.ng), &sg, &cg);
+      const float cacb = ca * cb, sacb = sa * cb;
+      const float r[9] = {cacb * cg - sa * sg, -cacb * sg - sa * cg, ca * sb, sacb * cg + ca * sg,
+                          -sacb * sg + ca * cg, sa * sb, -sb * cg, sb * sg, cb};
+      // half-angle quaternion of Rz(alpha) Ry(beta) Rz(gamma):
+      // (cos b cos((a+g)), sin b sin(g-a), sin b cos(g-a), cos b sin(a+g)), half angles
+      float hb_s, hb_c, hp_s, hp_c, hm_s, hm_c;
+      sincospif(__fdiv_rn((float)jb + 0.5f, 2.0f * (float)a.nb), &hb_s, &hb_c);
+      // (alpha + gamma) / 2 and (gamma - alpha) / 2 in units of pi
+      const float apg = (float)ia / (float)a.na + (float)kg / (float)a.ng;
+      const float gma = (float)kg / (float)a.ng - (float)ia / (float)a.na;
+      sincospif(apg, &hp_s, &hp_c);
+      sincospif(gma, &hm_s, &hm_c);
+      float q[4] = {hb_c * hp_c, hb_s * hm_s, hb_s * hm_c, hb_c * hp_s};
+      if (q[0] < 0.f)
+        for (int t = 0; t < 4; ++t) q[t] = -q[t];
+      float out[2];
+      for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h;
+        float v = inv[h];
+        if (e < 4) v = q[e];
+        else if (e >= 7 && e < 23) v = h7;
+        else if (e >= 23 && e < NFEAT) {
+          const float4 p = h ? p1 : p0;
+          const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
+          const float X = r[0] * dx + r[1] * dy + r[2] * dz;
+          const float Y = r[3] * dx + r[4] * dy + r[5] * dz;
+          const float Z = r[6] * dx + r[7] * dy + r[8] * dz;
+          v = (float)cell<false>(a.pk, nullptr, X, Y, Z) / 255.f;
+        }
+        out[h] = v;
+      }
+      const size_t row = ((size_t)li * a.O + o) * NFEAT;
+      for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h;
+        if (e < NFEAT) {
+          if (Xb) Xb[row + e] = __float2bfloat16(out[h]);
+          if (Xf) Xf[row + e] = out[h];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <int S, bool SG>
 cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, LaunchCfg* cfg) {
   auto k = search_kernel<S, SG>;
@@ -702,6 +864,14 @@ cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int nu
     case 2: return plan_t<2, false>(a, t.warps, smem, num_sms, cfg);
     default: return plan_t<4, false>(a, t.warps, smem, num_sms, cfg);
   }
+}
+
+cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, int num_sms, cudaStream_t st) {
+  if (a.L == 0) return cudaSuccess;
+  int blocks = (a.L + 7) / 8;
+  if (blocks > num_sms * 8) blocks = num_sms * 8;
+  feature_kernel<<<blocks, 256, 0, st>>>(a, Xb, Xf);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t st) {

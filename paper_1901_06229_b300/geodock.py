@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: 
 # every entry point declared in include/geodock.h
 EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_free_pocket",
            "gd_dock_batch", "gd_fetch_results", "gd_job_launch", "gd_job_download", "gd_job_bytes", "gd_job_free",
-           "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc"]
+           "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc",
+           "gd_prepare_batch"]
 
 
 class GeoDockError(RuntimeError):
@@ -81,6 +82,9 @@ def load():
     L.gd_job_free.argtypes = [vp, vp]
     L.gd_job_bytes.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint64)]
     L.gd_check_batch.argtypes = [P(LigandBatchC), P(SearchParamsC)]
+    L.gd_prepare_batch.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), vp, P(vp)]
+    L.gd_job_features.argtypes = [vp, vp, vp, vp, vp]
+    L.gd_job_features.restype = C.c_int
     L.gd_tile_count.argtypes = []
     L.gd_tile_info.argtypes = [C.c_int, P(C.c_int), P(C.c_int)]
     L.gd_autotune.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), C.c_int, vp, P(C.c_int), P(C.c_float)]
@@ -166,6 +170,11 @@ class Job:
         self.ctx._check(st)
         return r
 
+    def features(self, x_bf16=None, x_f32=None, stream=None):
+        """gd_job_features into torch CUDA tensors [L*O, 48] (BF16 and/or FP32)."""
+        p = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+        self.ctx._check(load().gd_job_features(self.ctx.h, self.handle, p(x_bf16), p(x_f32), _stream_handle(stream)))
+
     def launch(self, stream=None):
         """Run the search again on the device-resident inputs (no host copies)."""
         self.ctx._check(load().gd_job_launch(self.ctx.h, self.handle, _stream_handle(stream)))
@@ -248,6 +257,15 @@ class Context:
         self._check(load().gd_dock_batch(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm),
                                          _stream_handle(stream), C.byref(h)))
         return Job(self, h, batch, params, debug, bumps)
+
+    def prepare_batch(self, pocket: Pocket, batch, params, stream=None, debug=False, tile=0) -> Job:
+        """gd_prepare_batch: validate, pack and upload without searching."""
+        arrs = _BatchArrays(batch)
+        prm = params_c(params, GD_FLAG_DEBUG if debug else 0, tile)
+        h = C.c_void_p()
+        self._check(load().gd_prepare_batch(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm),
+                                            _stream_handle(stream), C.byref(h)))
+        return Job(self, h, batch, params, debug)
 
     def autotune(self, pocket: Pocket, batch, params, max_ligands=256, stream=None, no_filter=False):
         arrs = _BatchArrays(batch)

@@ -1,0 +1,67 @@
+"""The learned proposer on the GPU: features against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_06229_b300 import geodock as gdk
+from paper_1901_06229_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gdk.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_features(ctx, w):
+    import torch
+    pk = ctx.load_pocket(w.pocket)
+    job = ctx.prepare_batch(pk, w.batch, w.params)
+    L, O = w.batch.n_ligands, w.params.n_orient
+    xf = torch.zeros((L * O, 48), device="cuda")
+    xb = torch.zeros((L * O, 48), dtype=torch.bfloat16, device="cuda")
+    job.features(x_bf16=xb, x_f32=xf)
+    torch.cuda.synchronize()
+    job.free()
+    pk.free()
+    return xf.cpu().numpy(), xb.float().cpu().numpy()
+
+
+@pytest.mark.parametrize("which", ["batched", "single", "large"])
+def test_features_match_oracle(ctx, which):
+    w = {"batched": lambda: synth.workload_batched(12), "single": synth.workload_single,
+         "large": lambda: synth.workload_large(2)}[which]()
+    xf, xb = gpu_features(ctx, w)
+    O = w.params.n_orient
+    rng = np.random.default_rng(3)
+    compared = {"samples": 0, "skipped": 0}
+    for i in range(w.batch.n_ligands):
+        lig = w.batch.ligand(i)
+        for o in sorted(set(rng.integers(0, O, size=6).tolist()) | {0, O - 1}):
+            ref = oracle.features(lig.xyz, len(lig.rot_bond), o, w.params, w.pocket)
+            g = xf[i * O + o]
+            q, qr = g[:4].astype(np.float64), ref["feat"][:4]
+            if abs(qr[0]) < 1e-6:  # q and -q are the same rotation
+                q = q if np.dot(q, qr) >= 0 else -q
+            np.testing.assert_allclose(q, qr, atol=2e-6)
+            np.testing.assert_allclose(g[4:7], ref["feat"][4:7], rtol=2e-6, atol=1e-7)
+            if ref["hist_edge"] > 1e-5:
+                np.testing.assert_allclose(g[7:23], ref["feat"][7:23], atol=1e-7)
+            if ref["fps_gap"] > 1e-5:
+                ok = ~ref["sample_fragile"]
+                np.testing.assert_array_equal(g[23:][ok], ref["feat"][23:][ok].astype(np.float32))
+                compared["samples"] += int(ok.sum())
+            else:
+                compared["skipped"] += 1
+    print(compared)
+    assert compared["samples"] > 100
+    # the BF16 copy is the FP32 features rounded to nearest
+    np.testing.assert_array_equal(xb, _bf16(xf))
+
+
+def _bf16(x):
+    import torch
+    return torch.tensor(x).to(torch.bfloat16).float().numpy()
