@@ -29,6 +29,35 @@ gd_status gd_mlp_gemm(const void* A, int lda, int transA, const void* B, int ldb
                       void* Cb, int ldc, int M, int N, int K, const float* bias, int relu,
                       const float* dotw, float dot_bias, float* dot_out, int* dev_err, void* stream);
 
+/* ---- the network ------------------------------------------------------------------
+ * Parameters, FP32 masters in this order: W1[256][48] | b1[256] | W2[256][256] | b2[256]
+ * | w3[256] | b3 (gd_mlp_param_count() floats).  The forward pass multiplies BF16
+ * roundings of the weights and stores activations as BF16:
+ *   H1 = bf16(relu(X W1^T + b1)), H2 = bf16(relu(H1 W2^T + b2)), y = H2 . bf16(w3) + b3.
+ * Training minimises the mean squared error with Adam (beta 0.9 / 0.999, eps 1e-8);
+ * gradients follow the same rounding points (products of BF16 operands, FP32 sums). */
+typedef struct gd_mlp gd_mlp;
+int gd_mlp_param_count(void);
+/* Allocate a model on `device` (He-uniform initialisation from `seed`) able to train on
+ * batches of up to max_batch rows (a multiple of 16). */
+gd_status gd_mlp_create(int device, uint64_t seed, int max_batch, gd_mlp** out);
+gd_status gd_mlp_destroy(gd_mlp* model);
+/* Parameters to / from host FP32 arrays (set also resets the Adam state). */
+gd_status gd_mlp_set_params(gd_mlp* model, const float* host);
+gd_status gd_mlp_get_params(gd_mlp* model, float* host);
+/* y[M] = network(X[M x 48] BF16), device pointers, asynchronous on `stream`. */
+gd_status gd_mlp_predict(gd_mlp* model, const void* x_bf16, long long M, float* y, void* stream);
+/* Gradients (device FP32 array in the parameter layout) and loss (device float) of the
+ * MSE over B rows (a multiple of 16, <= max_batch): rows idx[0..B) of X / t, or the
+ * first B rows when idx is NULL.  No update. */
+gd_status gd_mlp_gradients(gd_mlp* model, const void* x_bf16, const float* t, const int32_t* idx, int B,
+                           float* grad, float* loss, void* stream);
+/* One Adam step on that loss with learning rate lr; loss (device float, may be NULL). */
+gd_status gd_mlp_train_step(gd_mlp* model, const void* x_bf16, const float* t, const int32_t* idx, int B,
+                            float lr, float* loss, void* stream);
+/* 1 if a bounded device wait of the model's kernels ran out since creation. */
+gd_status gd_mlp_error(gd_mlp* model, int* host_err);
+
 /* Features of every (ligand, restart) of a prepared job: 48 numbers per row, row
  * li * O + o (input ligand order), written as BF16 (x_bf16, the network's input) and/or
  * FP32 (x_f32); either may be NULL.  Row layout:

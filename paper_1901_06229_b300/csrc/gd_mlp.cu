@@ -16,7 +16,10 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "gd_mlp.h"
 #include "geodock_mlp.h"
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
         }
       }
     }
-    if (g.dotw && row < g.M) g.dot_out[row] = dot + g.dot_bias;
+    if (g.dotw && row < g.M) g.dot_out[row] = dot + g.dot_bias + (g.dot_bias_dev ? *g.dot_bias_dev : 0.f);
   }
   tc_fence_before();
   __syncthreads();
@@ -247,3 +250,383 @@ extern "C" gd_status gd_mlp_gemm(const void* A, int lda, int transA, const void*
   g.err = dev_err;
   return gd::gemm_launch(g, (cudaStream_t)stream) == cudaSuccess ? GD_OK : GD_ECUDA;
 }
+
+// ============================================================================ the model
+//
+// Parameters (FP32 masters, public layout): W1[256][48] | b1[256] | W2[256][256] | b2[256]
+// | w3[256] | b3.  The forward pass uses their BF16 roundings; activations are stored as
+// BF16 (the next product's operand), accumulation is FP32 throughout:
+//   H1 = bf16(relu(X W1^T + b1)), H2 = bf16(relu(H1 W2^T + b2)), y = H2 . w3 + b3.
+// Loss: mean squared error.  Backward (B rows):
+//   dy = 2 (y - t) / B;  dw3 = H2^T dy;  db3 = sum dy
+//   G2 = dy w3^T * [H2 > 0] (FP32; BF16 copy for the products);  db2 = column sums of G2
+//   dW2 = bf16(G2)^T H1;  dH1 = bf16(G2) W2;  G1 = dH1 * [H1 > 0];  db1 = column sums
+//   dW1 = bf16(G1)^T X;  then Adam on the FP32 masters.
+namespace gd {
+namespace {
+
+constexpr int F_IN = 48, HID = 256;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * F_IN, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID * HID,
+              OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID, NPARAM = OFF_B3 + 1;
+constexpr int COLSUM_ROWS = 256;  // rows per block of the column-sum kernels
+constexpr int PREDICT_CHUNK = 1 << 18;
+
+__global__ void k_gather(const __nv_bfloat16* X, const float* t, const int32_t* idx, int B, __nv_bfloat16* Xg,
+                         float* tg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * F_IN) return;
+  const int r = i / F_IN, c = i % F_IN;
+  const int src = idx ? idx[r] : r;
+  Xg[i] = X[(size_t)src * F_IN + c];
+  if (c == 0) tg[r] = t[src];
+}
+
+__global__ void k_loss(const float* y, const float* t, int B, float* dy, float* loss) {
+  __shared__ float red[256];
+  float acc = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B; i += gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    dy[i] = 2.f * d / (float)B;
+    acc += d * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) atomicAdd(loss, red[0] / (float)B);
+}
+
+// Per block of COLSUM_ROWS rows, one thread per column j (blockDim = HID):
+//   mode 0: v = dy[m] * w3[j] * [H[m][j] > 0]  -> Gb[m][j] = bf16(v), partial[blk][j] += v,
+//           partial2[blk][j] += dy[m] * H[m][j]   (dw3), partial2[blk][HID] += dy (db3)
+//   mode 1: v = D[m][j] * [H[m][j] > 0]        -> Gb[m][j] = bf16(v), partial[blk][j] += v
+__global__ void k_grad_rows(int mode, const float* dy, const float* w3, const float* D, const __nv_bfloat16* H,
+                            int B, __nv_bfloat16* Gb, float* partial, float* partial2) {
+  const int j = threadIdx.x, r0 = blockIdx.x * COLSUM_ROWS;
+  float acc = 0.f, acc2 = 0.f, acc3 = 0.f;
+  for (int m = r0; m < r0 + COLSUM_ROWS && m < B; ++m) {
+    const float h = __bfloat162float(H[(size_t)m * HID + j]);
+    const float mask = h > 0.f ? 1.f : 0.f;
+    float v;
+    if (mode == 0) {
+      v = dy[m] * w3[j] * mask;
+      acc2 += dy[m] * h;
+      acc3 += dy[m];
+    } else {
+      v = D[(size_t)m * HID + j] * mask;
+    }
+    Gb[(size_t)m * HID + j] = __float2bfloat16(v);
+    acc += v;
+  }
+  partial[blockIdx.x * (HID + 1) + j] = acc;
+  if (mode == 0) {
+    partial2[blockIdx.x * (HID + 1) + j] = acc2;
+    if (j == 0) partial2[blockIdx.x * (HID + 1) + HID] = acc3;
+  }
+}
+
+// out[j] = sum over blocks of partial[blk][j] (fixed order), j < n
+__global__ void k_sum_partials(const float* partial, int nblk, int n, float* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float s = 0.f;
+  for (int b = 0; b < nblk; ++b) s += partial[b * (HID + 1) + j];
+  out[j] = s;
+}
+
+__global__ void k_adam(float* P, float* Mo, float* Vo, const float* G, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float m = b1 * Mo[i] + (1.f - b1) * g;
+  const float v = b2 * Vo[i] + (1.f - b2) * g * g;
+  Mo[i] = m;
+  Vo[i] = v;
+  P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+__global__ void k_refresh(const float* P, __nv_bfloat16* W1b, __nv_bfloat16* W2b, float* w3r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < HID * F_IN) W1b[i] = __float2bfloat16(P[OFF_W1 + i]);
+  if (i < HID * HID) W2b[i] = __float2bfloat16(P[OFF_W2 + i]);
+  if (i < HID) w3r[i] = __bfloat162float(__float2bfloat16(P[OFF_W3 + i]));
+}
+
+}  // namespace
+}  // namespace gd
+
+struct gd_mlp {
+  int device = 0, max_batch = 0, step = 0;
+  float *P = nullptr, *Mo = nullptr, *Vo = nullptr, *G = nullptr, *w3r = nullptr;
+  __nv_bfloat16 *W1b = nullptr, *W2b = nullptr;
+  __nv_bfloat16 *Xg = nullptr, *H1 = nullptr, *H2 = nullptr, *G2b = nullptr, *G1b = nullptr;
+  float *tg = nullptr, *y = nullptr, *dy = nullptr, *dH1 = nullptr, *partial = nullptr, *partial2 = nullptr,
+        *loss = nullptr;
+  int* err = nullptr;
+  __nv_bfloat16* H1p = nullptr;  // prediction chunk activations
+};
+
+namespace {
+
+using gd::HID;
+using gd::F_IN;
+
+gd_status mlp_forward(gd_mlp* m, const __nv_bfloat16* X, int M, __nv_bfloat16* H1, __nv_bfloat16* H2, float* y,
+                      cudaStream_t s) {
+  gd::GemmArgs g{};
+  g.A = X;
+  g.B = m->W1b;
+  g.lda = F_IN;
+  g.ldb = F_IN;
+  g.ldc = HID;
+  g.M = M;
+  g.N = HID;
+  g.K = F_IN;
+  g.bias = m->P + gd::OFF_B1;
+  g.relu = true;
+  g.Cb = H1;
+  g.err = m->err;
+  if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  g = gd::GemmArgs{};
+  g.A = H1;
+  g.B = m->W2b;
+  g.lda = HID;
+  g.ldb = HID;
+  g.ldc = HID;
+  g.M = M;
+  g.N = HID;
+  g.K = HID;
+  g.bias = m->P + gd::OFF_B2;
+  g.relu = true;
+  g.Cb = H2;
+  g.dotw = m->w3r;
+  g.dot_bias_dev = m->P + gd::OFF_B3;
+  g.dot_out = y;
+  g.err = m->err;
+  return gd::gemm_launch(g, s) == cudaSuccess ? GD_OK : GD_ECUDA;
+}
+
+// Forward + backward of the batch MSE into m->G (and the loss into m->loss).
+gd_status mlp_backward(gd_mlp* m, const void* X, const float* t, const int32_t* idx, int B, cudaStream_t s) {
+  if (B < 16 || B % 16 || B > m->max_batch) return GD_EINVAL;
+  gd::k_gather<<<(B * F_IN + 255) / 256, 256, 0, s>>>((const __nv_bfloat16*)X, t, idx, B, m->Xg, m->tg);
+  gd_status st = mlp_forward(m, m->Xg, B, m->H1, m->H2, m->y, s);
+  if (st) return st;
+  cudaMemsetAsync(m->loss, 0, sizeof(float), s);
+  gd::k_loss<<<32, 256, 0, s>>>(m->y, m->tg, B, m->dy, m->loss);
+  const int nblk = (B + gd::COLSUM_ROWS - 1) / gd::COLSUM_ROWS;
+  gd::k_grad_rows<<<nblk, HID, 0, s>>>(0, m->dy, m->w3r, nullptr, m->H2, B, m->G2b, m->partial, m->partial2);
+  gd::k_sum_partials<<<1, HID, 0, s>>>(m->partial, nblk, HID, m->G + gd::OFF_B2);
+  gd::k_sum_partials<<<2, HID, 0, s>>>(m->partial2, nblk, HID + 1, m->G + gd::OFF_W3);  // dw3 | db3
+  // dW2 = G2^T H1
+  gd::GemmArgs g{};
+  g.A = m->G2b;
+  g.transA = true;
+  g.lda = HID;
+  g.B = m->H1;
+  g.transB = true;
+  g.ldb = HID;
+  g.M = HID;
+  g.N = HID;
+  g.K = B;
+  g.C = m->G + gd::OFF_W2;
+  g.ldc = HID;
+  g.err = m->err;
+  if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  // dH1 = G2 W2
+  g = gd::GemmArgs{};
+  g.A = m->G2b;
+  g.lda = HID;
+  g.B = m->W2b;
+  g.transB = true;
+  g.ldb = HID;
+  g.M = B;
+  g.N = HID;
+  g.K = HID;
+  g.C = m->dH1;
+  g.ldc = HID;
+  g.err = m->err;
+  if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  gd::k_grad_rows<<<nblk, HID, 0, s>>>(1, nullptr, nullptr, m->dH1, m->H1, B, m->G1b, m->partial, nullptr);
+  gd::k_sum_partials<<<1, HID, 0, s>>>(m->partial, nblk, HID, m->G + gd::OFF_B1);
+  // dW1 = G1^T X
+  g = gd::GemmArgs{};
+  g.A = m->G1b;
+  g.transA = true;
+  g.lda = HID;
+  g.B = m->Xg;
+  g.transB = true;
+  g.ldb = F_IN;
+  g.M = HID;
+  g.N = F_IN;
+  g.K = B;
+  g.C = m->G + gd::OFF_W1;
+  g.ldc = F_IN;
+  g.err = m->err;
+  if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ECUDA;
+}
+
+void mlp_refresh(gd_mlp* m, cudaStream_t s) {
+  gd::k_refresh<<<(HID * HID + 255) / 256, 256, 0, s>>>(m->P, m->W1b, m->W2b, m->w3r);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gd_mlp_param_count(void) { return gd::NPARAM; }
+
+gd_status gd_mlp_create(int device, uint64_t seed, int max_batch, gd_mlp** out) {
+  if (!out || max_batch < 16 || max_batch % 16) return GD_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return GD_ECUDA;
+  gd_mlp* m = new gd_mlp();
+  m->device = device;
+  m->max_batch = max_batch;
+  const size_t B = (size_t)max_batch, nblk = (B + gd::COLSUM_ROWS - 1) / gd::COLSUM_ROWS;
+  bool ok = cudaMalloc(&m->P, 4 * gd::NPARAM) == cudaSuccess && cudaMalloc(&m->Mo, 4 * gd::NPARAM) == cudaSuccess &&
+            cudaMalloc(&m->Vo, 4 * gd::NPARAM) == cudaSuccess && cudaMalloc(&m->G, 4 * gd::NPARAM) == cudaSuccess &&
+            cudaMalloc(&m->w3r, 4 * HID) == cudaSuccess && cudaMalloc(&m->W1b, 2 * HID * F_IN) == cudaSuccess &&
+            cudaMalloc(&m->W2b, 2 * HID * HID) == cudaSuccess && cudaMalloc(&m->Xg, 2 * B * F_IN) == cudaSuccess &&
+            cudaMalloc(&m->H1, 2 * B * HID) == cudaSuccess && cudaMalloc(&m->H2, 2 * B * HID) == cudaSuccess &&
+            cudaMalloc(&m->G2b, 2 * B * HID) == cudaSuccess && cudaMalloc(&m->G1b, 2 * B * HID) == cudaSuccess &&
+            cudaMalloc(&m->tg, 4 * B) == cudaSuccess && cudaMalloc(&m->y, 4 * B) == cudaSuccess &&
+            cudaMalloc(&m->dy, 4 * B) == cudaSuccess && cudaMalloc(&m->dH1, 4 * B * HID) == cudaSuccess &&
+            cudaMalloc(&m->partial, 4 * nblk * (HID + 1)) == cudaSuccess &&
+            cudaMalloc(&m->partial2, 4 * nblk * (HID + 1)) == cudaSuccess &&
+            cudaMalloc(&m->loss, 4) == cudaSuccess && cudaMalloc(&m->err, 4) == cudaSuccess &&
+            cudaMalloc(&m->H1p, 2 * (size_t)gd::PREDICT_CHUNK * HID) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gd_mlp_destroy(m);
+    return GD_ENOMEM;
+  }
+  // He-uniform initialisation from a SplitMix64 stream; biases 0, output bias 0.5
+  std::vector<float> h(gd::NPARAM, 0.f);
+  uint64_t st = seed;
+  auto u01 = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  const double a1 = std::sqrt(6.0 / F_IN), a2 = std::sqrt(6.0 / HID), a3 = std::sqrt(3.0 / HID);
+  for (int i = 0; i < HID * F_IN; ++i) h[gd::OFF_W1 + i] = (float)((2 * u01() - 1) * a1);
+  for (int i = 0; i < HID * HID; ++i) h[gd::OFF_W2 + i] = (float)((2 * u01() - 1) * a2);
+  for (int i = 0; i < HID; ++i) h[gd::OFF_W3 + i] = (float)((2 * u01() - 1) * a3);
+  h[gd::OFF_B3] = 0.5f;
+  return gd_mlp_set_params(m, h.data()) ? GD_ECUDA : ((*out = m), GD_OK);
+}
+
+gd_status gd_mlp_destroy(gd_mlp* m) {
+  if (!m) return GD_OK;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  for (void* p : {(void*)m->P, (void*)m->Mo, (void*)m->Vo, (void*)m->G, (void*)m->w3r, (void*)m->W1b,
+                  (void*)m->W2b, (void*)m->Xg, (void*)m->H1, (void*)m->H2, (void*)m->G2b, (void*)m->G1b,
+                  (void*)m->tg, (void*)m->y, (void*)m->dy, (void*)m->dH1, (void*)m->partial, (void*)m->partial2,
+                  (void*)m->loss, (void*)m->err, (void*)m->H1p})
+    if (p) cudaFree(p);
+  delete m;
+  return GD_OK;
+}
+
+gd_status gd_mlp_set_params(gd_mlp* m, const float* host) {
+  if (!m || !host) return GD_EINVAL;
+  cudaSetDevice(m->device);
+  if (cudaMemcpy(m->P, host, 4 * gd::NPARAM, cudaMemcpyHostToDevice) != cudaSuccess) return GD_ECUDA;
+  cudaMemset(m->Mo, 0, 4 * gd::NPARAM);
+  cudaMemset(m->Vo, 0, 4 * gd::NPARAM);
+  cudaMemset(m->err, 0, 4);
+  m->step = 0;
+  mlp_refresh(m, 0);
+  return cudaDeviceSynchronize() == cudaSuccess ? GD_OK : GD_ECUDA;
+}
+
+gd_status gd_mlp_get_params(gd_mlp* m, float* host) {
+  if (!m || !host) return GD_EINVAL;
+  cudaSetDevice(m->device);
+  return cudaMemcpy(host, m->P, 4 * gd::NPARAM, cudaMemcpyDeviceToHost) == cudaSuccess ? GD_OK : GD_ECUDA;
+}
+
+gd_status gd_mlp_predict(gd_mlp* m, const void* X, long long M, float* y, void* stream) {
+  if (!m || !X || !y || M < 0) return GD_EINVAL;
+  cudaSetDevice(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (long long r0 = 0; r0 < M; r0 += gd::PREDICT_CHUNK) {
+    const int rows = (int)std::min<long long>(gd::PREDICT_CHUNK, M - r0);
+    gd::GemmArgs g{};
+    g.A = (const __nv_bfloat16*)X + r0 * F_IN;
+    g.B = m->W1b;
+    g.lda = F_IN;
+    g.ldb = F_IN;
+    g.ldc = HID;
+    g.M = rows;
+    g.N = HID;
+    g.K = F_IN;
+    g.bias = m->P + gd::OFF_B1;
+    g.relu = true;
+    g.Cb = m->H1p;
+    g.err = m->err;
+    if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+    g = gd::GemmArgs{};
+    g.A = m->H1p;
+    g.B = m->W2b;
+    g.lda = HID;
+    g.ldb = HID;
+    g.ldc = HID;
+    g.M = rows;
+    g.N = HID;
+    g.K = HID;
+    g.bias = m->P + gd::OFF_B2;
+    g.relu = true;
+    g.dotw = m->w3r;
+    g.dot_bias_dev = m->P + gd::OFF_B3;
+    g.dot_out = y + r0;
+    g.err = m->err;
+    if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  }
+  return GD_OK;
+}
+
+gd_status gd_mlp_gradients(gd_mlp* m, const void* X, const float* t, const int32_t* idx, int B, float* grad,
+                           float* loss, void* stream) {
+  if (!m || !X || !t) return GD_EINVAL;
+  cudaSetDevice(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  gd_status st = mlp_backward(m, X, t, idx, B, s);
+  if (st) return st;
+  if (grad && cudaMemcpyAsync(grad, m->G, 4 * gd::NPARAM, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return GD_ECUDA;
+  if (loss && cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GD_ECUDA;
+  return GD_OK;
+}
+
+gd_status gd_mlp_train_step(gd_mlp* m, const void* X, const float* t, const int32_t* idx, int B, float lr,
+                            float* loss, void* stream) {
+  if (!m || !X || !t) return GD_EINVAL;
+  cudaSetDevice(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  gd_status st = mlp_backward(m, X, t, idx, B, s);
+  if (st) return st;
+  m->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)m->step), c2 = 1.f - std::pow(b2, (float)m->step);
+  gd::k_adam<<<(gd::NPARAM + 255) / 256, 256, 0, s>>>(m->P, m->Mo, m->Vo, m->G, gd::NPARAM, lr, b1, b2, 1e-8f, c1, c2);
+  mlp_refresh(m, s);
+  if (loss && cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GD_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ECUDA;
+}
+
+gd_status gd_mlp_error(gd_mlp* m, int* host_err) {
+  if (!m || !host_err) return GD_EINVAL;
+  cudaSetDevice(m->device);
+  return cudaMemcpy(host_err, m->err, 4, cudaMemcpyDeviceToHost) == cudaSuccess ? GD_OK : GD_ECUDA;
+}
+
+}  // extern "C"

@@ -22,6 +22,7 @@ struct GemmArgs {
   __nv_bfloat16* Cb;
   const float* dotw;
   float dot_bias;
+  const float* dot_bias_dev;  // added to dot_bias when non-null (device scalar)
   float* dot_out;
   int* err;  // set to 1 if a bounded wait ran out (may be null)
 };

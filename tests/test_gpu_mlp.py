@@ -55,3 +55,72 @@ def test_gemm_epilogue_bias_relu_bf16_and_dot():
     # the kernel rounds its FP32 value to BF16: at most one BF16 ulp from rounding the FP64 value
     np.testing.assert_allclose(got, xb, rtol=2 ** -7, atol=1e-6)
     np.testing.assert_allclose(y.cpu().numpy(), got.astype(np.float64) @ w.cpu().numpy() + 0.25, rtol=1e-4, atol=1e-3)
+
+
+def _net_case(seed, B):
+    rng = np.random.default_rng(seed)
+    from oracle import mlp as om
+    P = (rng.normal(scale=0.15, size=om.NPARAM)).astype(np.float32)
+    X = rng.uniform(0, 1, size=(B, 48)).astype(np.float32)
+    t = rng.uniform(0, 1, size=B).astype(np.float32)
+    return P, X, t
+
+
+def test_network_forward_and_gradients_match_oracle():
+    import torch
+    from oracle import mlp as om
+    from paper_1901_06229_b300 import mlp
+    B = 512
+    P, X, t = _net_case(7, B)
+    net = mlp.MLP(0, seed=1, max_batch=1024)
+    net.set_params(P)
+    Xb = torch.tensor(X).to(torch.bfloat16).cuda()
+    tt = torch.tensor(t).cuda()
+    y = torch.zeros(B, device="cuda")
+    net.predict(Xb, y)
+    grad = torch.zeros(net.nparam, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    net.gradients(Xb, tt, grad, loss)
+    torch.cuda.synchronize()
+    assert net.error() == 0
+    Xr = Xb.float().cpu().numpy()
+    f = om.forward(P, Xr, rounding=True)
+    np.testing.assert_allclose(y.cpu().numpy(), f["y"], rtol=1e-3, atol=2e-3)
+    ref_loss, ref = om.gradients(P, Xr, t, rounding=True)
+    assert abs(loss.item() - ref_loss) <= 1e-3 * ref_loss + 1e-6
+    g = grad.cpu().numpy()
+    o = 0
+    for name, shape in om.SIZES:
+        n = int(np.prod(shape))
+        a, b = g[o:o + n], ref[o:o + n]
+        scale = np.abs(b).max() + 1e-12
+        # BF16 rounding points agree except where FP32 and FP64 sums straddle a BF16
+        # rounding boundary (a few elements, one BF16 ulp): compare on the tensor's scale
+        assert np.abs(a - b).max() <= 2e-2 * scale, (name, np.abs(a - b).max(), scale)
+        assert np.corrcoef(a, b)[0, 1] > 0.9999 if n > 1 else True
+        o += n
+    net.close()
+
+
+def test_training_reduces_loss():
+    import torch
+    from paper_1901_06229_b300 import mlp
+    rng = np.random.default_rng(9)
+    N = 8192
+    X = rng.uniform(0, 1, size=(N, 48)).astype(np.float32)
+    t = (0.5 + 0.3 * np.sin(3 * X[:, 0]) * X[:, 5] + 0.2 * X[:, 30] ** 2).astype(np.float32)
+    Xb = torch.tensor(X).to(torch.bfloat16).cuda()
+    tt = torch.tensor(t).cuda()
+    net = mlp.MLP(0, seed=3, max_batch=1024)
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for epoch in range(8):
+        perm = torch.randperm(N, generator=torch.Generator().manual_seed(epoch)).to(torch.int32).cuda()
+        for b in range(N // 1024):
+            net.train_step(Xb, tt, 1e-3, loss=loss, idx=perm[b * 1024:(b + 1) * 1024], B=1024)
+            losses.append(loss.item())
+    assert net.error() == 0
+    first, last = np.mean(losses[:4]), np.mean(losses[-4:])
+    print(first, last)
+    assert last < 0.05 * first
+    net.close()
