@@ -71,6 +71,18 @@ gd_status gd_mlp_error(gd_mlp* model, int* host_err);
  * Runs on `stream` after the job's upload (use the stream the job was prepared on). */
 gd_status gd_job_features(gd_ctx* ctx, gd_job* job, void* x_bf16, float* x_f32, void* stream);
 
+/* Pruned search of a prepared job: pred[L x O] (device, e.g. gd_mlp_predict on the
+ * job's features) ranks the restarts of every ligand; the k best (ties to the smaller
+ * restart id) get the full search of Sec. 3.1, except that a ligand falls back to every
+ * restart when the spread s = pred(1st) - pred(k-th) is below `margin` (rule 0) or
+ * above it (rule 1).  The best pose is then taken over the searched restarts only;
+ * evals[] counts them.  Needs O <= 256.  Queue gd_job_download + gd_fetch_results. */
+gd_status gd_job_launch_proposed(gd_ctx* ctx, gd_job* job, const float* pred, int k, float margin, int rule,
+                                 void* stream);
+/* Restarts searched per ligand (k or O) and the prediction spreads of the last proposed
+ * launch (host arrays of L; either may be NULL; waits for the job). */
+gd_status gd_job_selection(gd_ctx* ctx, gd_job* job, int32_t* counts, float* spreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -370,6 +370,13 @@ struct gd_job {
   gd::LaunchCfg cfg{};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // restart selection of the learned proposer (allocated on first use)
+  void* d_sel = nullptr;
+  size_t sel_bytes = 0;
+  int32_t *sel_cnt = nullptr, *sel_off = nullptr, *sel_n = nullptr;
+  uint16_t* sel_topk = nullptr;
+  float* sel_spread = nullptr;
+  uint32_t* sel_items = nullptr;
   cudaEvent_t done = nullptr;
   std::vector<int32_t> rot_off;  // host copy for result layout checks
 };
@@ -384,6 +391,7 @@ gd_status job_release(gd_ctx* c, gd_job* j) {
   dev_release(c, j->d_in, j->in.total);
   dev_release(c, j->d_out, j->out.total);
   dev_release(c, j->d_scr, j->scr.total);
+  dev_release(c, j->d_sel, j->sel_bytes);
   host_release(c, j->h_in, j->h_in_cap);
   host_release(c, j->h_out, j->out.total);
   host_release(c, j->h_dbg, j->dbg_bytes);
@@ -894,6 +902,61 @@ gd_status gd_job_features(gd_ctx* c, gd_job* j, void* x_bf16, float* x_f32, void
   cudaError_t e = gd::launch_features(j->args, (__nv_bfloat16*)x_bf16, x_f32, c->num_sms, s);
   if (e == cudaSuccess) e = cudaEventRecord(j->done, s);
   if (e != cudaSuccess) return fail(GD_ECUDA, "features: %s", cudaGetErrorString(e));
+  return GD_OK;
+}
+
+gd_status gd_job_launch_proposed(gd_ctx* c, gd_job* j, const float* pred, int k, float margin, int rule,
+                                 void* stream) {
+  if (!c || !j || !pred) return fail(GD_EINVAL, "NULL argument");
+  if (j->O > 256) return fail(GD_EINVAL, "restart selection supports at most 256 restarts (have %d)", j->O);
+  if (k < 1 || k > j->O) return fail(GD_EINVAL, "k = %d outside [1, %d]", k, j->O);
+  if (j->L == 0) return GD_OK;
+  cudaSetDevice(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t L = (size_t)j->L, O = (size_t)j->O;
+  if (!j->d_sel) {
+    size_t o = 0;
+    const size_t o_cnt = o;    o = align_up(o + 4 * L, 256);
+    const size_t o_off = o;    o = align_up(o + 4 * L, 256);
+    const size_t o_n = o;      o = align_up(o + 4, 256);
+    const size_t o_topk = o;   o = align_up(o + 2 * L * O, 256);
+    const size_t o_spr = o;    o = align_up(o + 4 * L, 256);
+    const size_t o_items = o;  o = align_up(o + 4 * L * O, 256);
+    gd_status st = dev_alloc(c, o, &j->d_sel);
+    if (st) return st;
+    j->sel_bytes = o;
+    char* b = (char*)j->d_sel;
+    j->sel_cnt = (int32_t*)(b + o_cnt);
+    j->sel_off = (int32_t*)(b + o_off);
+    j->sel_n = (int32_t*)(b + o_n);
+    j->sel_topk = (uint16_t*)(b + o_topk);
+    j->sel_spread = (float*)(b + o_spr);
+    j->sel_items = (uint32_t*)(b + o_items);
+  }
+  SearchArgs a = j->args;
+  a.items = j->sel_items;
+  a.item_cnt = j->sel_cnt;
+  a.n_items_dev = j->sel_n;
+  gd::LaunchCfg cfg;
+  cudaError_t e = gd::plan_search(a, j->tile, j->grid_in_smem, c->num_sms, &cfg);
+  if (e == cudaSuccess)
+    e = gd::launch_selection(a, pred, k, margin, rule, j->sel_cnt, j->sel_topk, j->sel_spread, j->sel_off, j->sel_items,
+                             j->sel_n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.pose_score, 0xFF, 4 * L * O, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s);
+  if (e == cudaSuccess) e = gd::launch_search(a, cfg, s);
+  if (e == cudaSuccess) e = cudaEventRecord(j->done, s);
+  if (e != cudaSuccess) return fail(GD_ECUDA, "proposed search: %s", cudaGetErrorString(e));
+  return GD_OK;
+}
+
+gd_status gd_job_selection(gd_ctx* c, gd_job* j, int32_t* counts, float* spreads) {
+  if (!c || !j) return fail(GD_EINVAL, "NULL argument");
+  if (!j->d_sel) return fail(GD_EINVAL, "no proposed search was launched on this job");
+  cudaSetDevice(c->device);
+  GD_CUDA(cudaEventSynchronize(j->done));
+  if (counts) GD_CUDA(cudaMemcpy(counts, j->sel_cnt, 4 * (size_t)j->L, cudaMemcpyDeviceToHost));
+  if (spreads) GD_CUDA(cudaMemcpy(spreads, j->sel_spread, 4 * (size_t)j->L, cudaMemcpyDeviceToHost));
   return GD_OK;
 }
 

@@ -46,6 +46,9 @@ struct SearchArgs {
   const uint16_t* excl;       // [sum n_excl] excluded pairs (a | b << 8)
   const int32_t* order;       // [L] ligand processing order (largest cost first)
   long long n_items;          // L * O
+  const uint32_t* items;      // optional explicit (ligand, restart) list, rows li * O + o
+  const int32_t* item_cnt;    // with items: restarts searched per ligand (>= 1)
+  const int32_t* n_items_dev; // with items: list length (device scalar)
   // search parameters
   int na, nb, ng, O, A, reps;
   float thr2;                 // bump_dist^2
@@ -93,6 +96,9 @@ __host__ __device__ inline int warp_smem_bytes(int nmax, int near_cap) {
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };
 
+// pose_score of a restart that a subset launch leaves out (buffers are filled with it)
+constexpr uint32_t NOT_SEARCHED = 0xFFFFFFFFu;
+
 // Launch configuration of one tile.
 struct Tile {
   int warps;        // warps (poses in flight) per block
@@ -112,6 +118,12 @@ cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int nu
 // The proposer's 48 features of every (ligand, restart) of a packed batch, rows
 // li * O + o, as BF16 (Xb) and/or FP32 (Xf).
 cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, int num_sms, cudaStream_t stream);
+// Restart selection from predicted scores [L x O]: per ligand the top k (or all O when
+// the top-k spread is below (rule 0) / above (rule 1) margin), written as an item list
+// in queue order.
+cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, float margin, int rule, int32_t* cnt,
+                             uint16_t* topk, float* spread, int32_t* off, uint32_t* items, int32_t* n_items,
+                             cudaStream_t stream);
 // Launch the search (kernel only; the work counter and per-ligand counters must be
 // zeroed by the caller first).
 cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t stream);

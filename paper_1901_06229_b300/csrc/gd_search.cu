@@ -470,6 +470,7 @@ __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane
   unsigned long long pairs = 0, reach = 0;
   for (int o = lane; o < O; o += 32) {
     const unsigned s = __ldcg(a.pose_score + (size_t)li * O + o);
+    if (s == NOT_SEARCHED) continue;  // restarts left out of a chosen subset
     const unsigned key = ((s + 1u) << 16) | (0xFFFFu - (unsigned)o);
     best = key > best ? key : best;
     pairs += __ldcg(a.pose_pairs + (size_t)li * O + o);
@@ -494,13 +495,14 @@ __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(FULL, fsum, off);
+  const unsigned long long nres = a.item_cnt ? (unsigned long long)a.item_cnt[li] : (unsigned long long)O;
   if (lane == 0) {
     a.best_score[li] = sb;
     a.best_orient[li] = ob;
-    a.evals[li] = (unsigned long long)O * a.reps * R * a.A;
+    a.evals[li] = nres * a.reps * R * a.A;
     a.pair_tests[li] = pairs;
     a.reach_tests[li] = reach;
-    a.atom_moves[li] = (unsigned long long)O * a.reps * a.A * fsum;
+    a.atom_moves[li] = nres * a.reps * a.A * fsum;
   }
   for (int s = lane; s < a.reps * R; s += 32)
     a.best_angle[(size_t)r0 * a.reps + s] = __ldcg(a.pose_pick + pick_base + s);
@@ -573,7 +575,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   int prev = 0;
   if (lane == 0) prev = atomicAdd(a.done + li, 1);
   prev = __shfl_sync(FULL, prev, 0);
-  if (prev == a.O - 1) {
+  if (prev == (a.item_cnt ? a.item_cnt[li] : a.O) - 1) {
     __threadfence();
     finalize(a, w, li, lane);
   }
@@ -642,13 +644,22 @@ __global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ Sea
   __syncthreads();
   WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.near_cap);
   w.CS = cs;
+  // items: every (ligand, restart) in queue order, or an explicit list of rows li*O + o
+  const unsigned long long n_items = a.items ? (unsigned long long)*a.n_items_dev : (unsigned long long)a.n_items;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(a.work, 1ull);
     t = __shfl_sync(FULL, t, 0);
-    if (t >= (unsigned long long)a.n_items) break;
-    const int li = a.order[t / (unsigned long long)a.O];
-    const int o = (int)(t % (unsigned long long)a.O);
+    if (t >= n_items) break;
+    int li, o;
+    if (a.items) {
+      const unsigned row = __ldg(a.items + t);
+      li = (int)(row / (unsigned)a.O);
+      o = (int)(row % (unsigned)a.O);
+    } else {
+      li = a.order[t / (unsigned long long)a.O];
+      o = (int)(t % (unsigned long long)a.O);
+    }
     search_pose<S, SG>(a, sg, w, li, o, lane);
   }
 }
@@ -813,6 +824,92 @@ __global__ void __launch_bounds__(256) feature_kernel(const __grid_constant__ Se
   }
 }
 
+// ---- restart selection for the learned proposer ----------------------------------
+//
+// Per ligand (one warp): the k restarts of highest predicted score (ties to the smaller
+// restart id) and the spread pred(1st) - pred(k-th).  The ligand falls back to every
+// restart when the spread is below `margin` (rule 0: the network cannot separate its
+// top choices) or above it (rule 1: the network expects only a few restarts to be good,
+// which is where a wrong top-k loses the best pose).
+__global__ void select_kernel(const float* pred, int L, int O, int k, float margin, int rule, int32_t* cnt,
+                              uint16_t* topk, float* spread) {
+  const int lane = threadIdx.x & 31;
+  const int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (li >= L) return;
+  const float* p = pred + (size_t)li * O;
+  // orderable keys: larger prediction first, then smaller restart id
+  float first = 0.f, last = 0.f;
+  unsigned taken[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // bit per (lane, slot): restarts o = lane + 32 s
+  for (int r = 0; r < k; ++r) {
+    unsigned long long best = 0;
+    for (int sidx = 0; sidx * 32 + lane < O && sidx < 8; ++sidx) {
+      if (taken[sidx]) continue;
+      const int o = sidx * 32 + lane;
+      const unsigned u = __float_as_uint(p[o]);
+      const unsigned ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+      const unsigned long long key = ((unsigned long long)ord << 32) | (0xFFFFFFFFu - (unsigned)o);
+      best = key > best ? key : best;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long q = __shfl_xor_sync(FULL, best, off);
+      best = q > best ? q : best;
+    }
+    const int o = (int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFu));
+    if ((o & 31) == lane) taken[o >> 5] = 1;
+    if (lane == 0) topk[(size_t)li * k + r] = (uint16_t)o;
+    const float v = p[o];
+    if (r == 0) first = v;
+    last = v;
+  }
+  if (lane == 0) {
+    const float sp = first - last;
+    spread[li] = sp;
+    cnt[li] = (rule ? sp > margin : sp < margin) ? O : k;
+  }
+}
+
+// Exclusive scan of the counts in queue order (one block): off[p] for position p.
+__global__ void scan_kernel(const int32_t* order, const int32_t* cnt, int L, int32_t* off, int32_t* total) {
+  __shared__ int32_t part[1024];
+  const int per = (L + blockDim.x - 1) / blockDim.x;
+  const int p0 = threadIdx.x * per, p1 = min(L, p0 + per);
+  int32_t s = 0;
+  for (int p = p0; p < p1; ++p) s += cnt[order[p]];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t run = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int32_t v = part[t];
+      part[t] = run;
+      run += v;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  s = part[threadIdx.x];
+  for (int p = p0; p < p1; ++p) {
+    off[p] = s;
+    s += cnt[order[p]];
+  }
+}
+
+// Items (rows li * O + o) of every ligand at its queue offset.
+__global__ void items_kernel(const int32_t* order, const int32_t* cnt, const int32_t* off, const uint16_t* topk, int L,
+                             int O, int k, uint32_t* items) {
+  const int lane = threadIdx.x & 31;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= L) return;
+  const int li = order[p];
+  const int c = cnt[li];
+  uint32_t* dst = items + off[p];
+  for (int s = lane; s < c; s += 32) {
+    const int o = c == k ? (int)topk[(size_t)li * k + s] : s;
+    dst[s] = (uint32_t)li * (uint32_t)O + (uint32_t)o;
+  }
+}
+
 template <int S, bool SG>
 cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, LaunchCfg* cfg) {
   auto k = search_kernel<S, SG>;
@@ -864,6 +961,17 @@ cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int nu
     case 2: return plan_t<2, false>(a, t.warps, smem, num_sms, cfg);
     default: return plan_t<4, false>(a, t.warps, smem, num_sms, cfg);
   }
+}
+
+cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, float margin, int rule, int32_t* cnt,
+                             uint16_t* topk, float* spread, int32_t* off, uint32_t* items, int32_t* n_items,
+                             cudaStream_t st) {
+  if (a.L == 0) return cudaSuccess;
+  const int blocks = (a.L * 32 + 255) / 256;
+  select_kernel<<<blocks, 256, 0, st>>>(pred, a.L, a.O, k, margin, rule, cnt, topk, spread);
+  scan_kernel<<<1, 1024, 0, st>>>(a.order, cnt, a.L, off, n_items);
+  items_kernel<<<blocks, 256, 0, st>>>(a.order, cnt, off, topk, a.L, a.O, k, items);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, int num_sms, cudaStream_t st) {

@@ -85,6 +85,10 @@ def load():
     L.gd_prepare_batch.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), vp, P(vp)]
     L.gd_job_features.argtypes = [vp, vp, vp, vp, vp]
     L.gd_job_features.restype = C.c_int
+    L.gd_job_launch_proposed.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.c_int, vp]
+    L.gd_job_launch_proposed.restype = C.c_int
+    L.gd_job_selection.argtypes = [vp, vp, vp, vp]
+    L.gd_job_selection.restype = C.c_int
     L.gd_tile_count.argtypes = []
     L.gd_tile_info.argtypes = [C.c_int, P(C.c_int), P(C.c_int)]
     L.gd_autotune.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), C.c_int, vp, P(C.c_int), P(C.c_float)]
@@ -174,6 +178,21 @@ class Job:
         """gd_job_features into torch CUDA tensors [L*O, 48] (BF16 and/or FP32)."""
         p = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
         self.ctx._check(load().gd_job_features(self.ctx.h, self.handle, p(x_bf16), p(x_f32), _stream_handle(stream)))
+
+    def launch_proposed(self, pred, k, margin, rule=1, stream=None):
+        """gd_job_launch_proposed: search the k best-predicted restarts per ligand, all of
+        them where the top-k spread is below (rule 0) / above (rule 1) margin; pred is a
+        CUDA float tensor [L*O]."""
+        self.ctx._check(load().gd_job_launch_proposed(self.ctx.h, self.handle, C.c_void_p(pred.data_ptr()), int(k),
+                                                      float(margin), int(rule), _stream_handle(stream)))
+
+    def selection(self):
+        """(restarts searched per ligand, prediction spread per ligand) of the last proposed launch."""
+        cnt = np.zeros(self.L, np.int32)
+        spr = np.zeros(self.L, np.float32)
+        self.ctx._check(load().gd_job_selection(self.ctx.h, self.handle, C.c_void_p(cnt.ctypes.data),
+                                                C.c_void_p(spr.ctypes.data)))
+        return cnt, spr
 
     def launch(self, stream=None):
         """Run the search again on the device-resident inputs (no host copies)."""

@@ -362,3 +362,23 @@ def workload_large(n_ligands: int = 512, start: int = 0) -> Workload:
     pocket = gen_pocket(SplitMix64(seed ^ 0x5EED), 128, 0.375, 20, 0.30)
     ligs = _ligands(seed, n_ligands, c3_sizes, start)
     return Workload(f"large-{n_ligands}lig-128grid", pocket, pack(ligs), SearchParams(8, 8, 4, 128))
+
+
+def workload_proposer_train(n_ligands: int = 3907) -> Workload:
+    """Training tuples of the learned proposer: fresh 24-atom, 4-rotamer ligands docked
+    exhaustively (256 restarts, 64 angles) on the 64^3 pocket: 3,907 x 256 ~ 1M rows."""
+    ligs = _ligands(BASE_SEED + 4, n_ligands, c1_style_sizes)
+    return Workload(f"proposer-train-{n_ligands}lig", pocket_64(), pack(ligs), SearchParams(8, 8, 4, 64))
+
+
+def workload_proposer_eval(n_ligands: int = 16384, start: int = 0) -> Workload:
+    """Held-out ligands of the same kind (other seeds) for recall / regret / throughput."""
+    ligs = _ligands(BASE_SEED + 40, n_ligands, c1_style_sizes, start)
+    return Workload(f"proposer-eval-{n_ligands}lig", pocket_64(), pack(ligs), SearchParams(8, 8, 4, 64))
+
+
+def workload_stream(n_ligands: int = 100000, start: int = 0, seed_offset: int = 5) -> Workload:
+    """Streaming-screen ligands: atoms lognormal (median 40, sigma 0.5) clamped to
+    15..250, rotamers round(atoms / 6); 64^3 pocket; 256 restarts, 64 angles."""
+    ligs = _ligands(BASE_SEED + seed_offset, n_ligands, lognormal_sizes, start)
+    return Workload(f"stream-{n_ligands}lig", pocket_64(), pack(ligs), SearchParams(8, 8, 4, 64))

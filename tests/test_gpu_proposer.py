@@ -65,3 +65,50 @@ def test_features_match_oracle(ctx, which):
 def _bf16(x):
     import torch
     return torch.tensor(x).to(torch.bfloat16).float().numpy()
+
+
+def _topk_host(pred, k):
+    """Top-k restarts per row, ties to the smaller restart id."""
+    L, O = pred.shape
+    out = []
+    for i in range(L):
+        order = np.lexsort((np.arange(O), -pred[i].astype(np.float64)))
+        out.append(order[:k])
+    return np.array(out)
+
+
+def test_subset_search_is_the_best_of_the_chosen_restarts(ctx):
+    import torch
+    w = synth.workload_batched(24)
+    L, O, k = w.batch.n_ligands, w.params.n_orient, 16
+    pk = ctx.load_pocket(w.pocket)
+    job = ctx.prepare_batch(pk, w.batch, w.params, debug=True)
+    job.launch()
+    job.download()
+    ex = job.fetch()
+    pred = np.random.default_rng(2).normal(size=(L, O)).astype(np.float32)
+    pred[:, 5] = pred[:, 9] = 10.0  # a planted tie: restart 5 ranks before 9
+    job.launch_proposed(torch.tensor(pred.ravel()).cuda(), k, 1e30, rule=1)
+    job.download()
+    pr = job.fetch()
+    cnt, spread = job.selection()
+    assert np.all(cnt == k)
+    top = _topk_host(pred, k)
+    R = np.diff(w.batch.rot_off)
+    for i in range(L):
+        sc = ex["orient_score"][i, top[i]].astype(np.int64)
+        best = sc.max()
+        assert pr["best_score"][i] == best
+        assert pr["best_orient"][i] == top[i][sc == best].min()
+        np.testing.assert_array_equal(pr["orient_score"][i, top[i]], ex["orient_score"][i, top[i]])
+        assert pr["evals"][i] == k * R[i] * w.params.n_angles
+        np.testing.assert_allclose(spread[i], np.sort(pred[i])[::-1][0] - np.sort(pred[i])[::-1][k - 1], rtol=1e-6)
+    # rule 0 with an infinite margin: every ligand falls back to the full search
+    job.launch_proposed(torch.tensor(pred.ravel()).cuda(), k, 1e30, rule=0)
+    job.download()
+    full = job.fetch()
+    assert np.all(job.selection()[0] == O)
+    for key in ("best_score", "best_orient", "best_angle", "best_xyz", "evals"):
+        np.testing.assert_array_equal(full[key], ex[key], err_msg=key)
+    job.free()
+    pk.free()
