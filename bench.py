@@ -183,13 +183,119 @@ def run_reference(args, world, rank):
         "e2e": {"value": v, "unit": "ligands/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+MLP_FLOPS_PER_ROW = 2 * (48 * 256 + 256 * 256 + 256)
+
+
+def run_learned(args, world, rank, local):
+    """Learned-pruned search vs the plain exhaustive search on the same held-out ligands.
+
+    Training: 12,000 streaming-screen ligands (lognormal sizes) x 256 restarts, targets
+    from the plain search; margin tuned for 99 % best-pose recall on 4,000 more; timed on
+    16,384 held-out ligands.  A learned step = features + network + selection + pruned
+    search; a plain step = the exhaustive search.  Both device-timed with CUDA events.
+    """
+    import torch
+    from paper_1901_06229_b300 import geodock as gdk, mlp, proposer
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    n_eval = args.ligands or 16384
+    wt = synth.workload_stream(12000, seed_offset=50)
+    wv = synth.workload_stream(4000, seed_offset=51)
+    we = synth.workload_stream(n_eval, seed_offset=52 + 10 * rank)
+    ctx = gdk.Context(dev)
+    pk = ctx.load_pocket(we.pocket)
+    X, t, _ = proposer.dataset(ctx, pk, wt)
+    ts, mu, sd = proposer.standardise(t)
+    net = mlp.MLP(dev, seed=1, max_batch=4096)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = proposer.train(net, X, ts)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    k = 16
+    margin, _ = proposer.tune_margin(ctx, net, pk, wv, k=k, rule=1)
+    L, O = we.batch.n_ligands, we.params.n_orient
+    stream = torch.cuda.current_stream()
+    job = ctx.prepare_batch(pk, we.batch, we.params, stream=stream, tile=args.tile)
+    Xe = torch.empty((L * O, 48), dtype=torch.bfloat16, device="cuda")
+    ye = torch.empty(L * O, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def plain():
+        job.launch(stream)
+
+    def learned():
+        job.features(x_bf16=Xe, stream=stream)
+        net.predict(Xe, ye)
+        job.launch_proposed(ye, k, margin, 1, stream)
+
+    times = {}
+    for name, fn in (("plain", plain), ("learned", learned)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = []
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        times[name] = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, world)
+        job.download(stream)
+        times[name + "_res"] = job.fetch()
+    cnt, _ = job.selection()
+    # the network alone (tensor-core kernels), for its roofline
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        net.predict(Xe, ye)
+    b.record(stream)
+    torch.cuda.synchronize()
+    mlp_s = a.elapsed_time(b) / 1e3 / args.steps
+    ex, pr = times["plain_res"], times["learned_res"]
+    recall = float(np.mean(pr["best_score"] == ex["best_score"]))
+    be, bp = ex["best_score"].astype(np.int64), pr["best_score"].astype(np.int64)
+    regret = float(np.mean((be - bp) / np.maximum(be, 1)))
+    job.free()
+    pk.free()
+    ctx.close()
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    tflops = MLP_FLOPS_PER_ROW * L * O / mlp_s / 1e12
+    peak = peaks.get("bf16_tflops", 1787.5)
+    value = L * world * args.steps / times["learned"]
+    plain_v = L * world * args.steps / times["plain"]
+    print(json.dumps({
+        "metric": "ligands/s (learned-pruned pose search, 1 B300)", "value": value, "unit": "ligands/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * times["learned"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 search / bf16 network", "data": "synthetic (seeded generators)",
+        "config": workload_config(we, "flushed between steps (256 MB write)") | {
+            "k": k, "margin_rule": "fall back when pred(1st) - pred(16th) > margin", "margin": margin,
+            "train": {"ligands": 12000, "rows": int(X.shape[0]), "epochs": len(hist), "seconds": train_s,
+                      "final_loss_std_units": hist[-1]}},
+        "plain_value": plain_v, "speedup_vs_plain": value / plain_v,
+        "best_pose_recall": recall, "score_regret": regret, "fallback_fraction": float(np.mean(cnt > k)),
+        "restarts_searched_per_ligand": float(cnt.mean()),
+        "gpu_launches": args.steps * 6,
+        "roofline": {"bound": "tensor", "kernel": "gemm_kernel (network forward, 2 launches)",
+                     "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak, "traffic": None,
+                     "peak_kind": "bf16_tflops of MEASURED_PEAKS.json (burst)"},
+        "mlp_rows_per_s": L * O / mlp_s,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned"])
     ap.add_argument("--tile", type=int, default=-1, help="-1 autotune, 0 default, >0 tile id")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -200,6 +306,9 @@ def main():
         run_reference(args, world, rank)
         return
     assert args.warmup >= 3 or args.steps <= 3, "at least 3 warm-up steps"
+    if args.workload == "learned":
+        run_learned(args, world, rank, local)
+        return
 
     import torch
     from paper_1901_06229_b300 import geodock as gdk
