@@ -247,14 +247,18 @@ def run_learned(args, world, rank, local):
         job.download(stream)
         times[name + "_res"] = job.fetch()
     cnt, _ = job.selection()
-    # the network alone (tensor-core kernels), for its roofline
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(args.steps):
-        net.predict(Xe, ye)
-    b.record(stream)
-    torch.cuda.synchronize()
-    mlp_s = a.elapsed_time(b) / 1e3 / args.steps
+    # each stage of a learned step alone
+    def stage_time(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / args.steps
+    mlp_s = stage_time(lambda: net.predict(Xe, ye))
+    feat_s = stage_time(lambda: job.features(x_bf16=Xe, stream=stream))
+    search_s = stage_time(lambda: job.launch_proposed(ye, k, margin, 1, stream))
     ex, pr = times["plain_res"], times["learned_res"]
     recall = float(np.mean(pr["best_score"] == ex["best_score"]))
     be, bp = ex["best_score"].astype(np.int64), pr["best_score"].astype(np.int64)
@@ -282,10 +286,11 @@ def run_learned(args, world, rank, local):
         "best_pose_recall": recall, "score_regret": regret, "fallback_fraction": float(np.mean(cnt > k)),
         "restarts_searched_per_ligand": float(cnt.mean()),
         "gpu_launches": args.steps * 6,
-        "roofline": {"bound": "tensor", "kernel": "gemm_kernel (network forward, 2 launches)",
+        "roofline": {"bound": "tensor", "kernel": "mlp_infer_kernel (fused two-layer forward, 1 launch)",
                      "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak, "traffic": None,
                      "peak_kind": "bf16_tflops of MEASURED_PEAKS.json (burst)"},
         "mlp_rows_per_s": L * O / mlp_s,
+        "stage_ms": {"features": 1e3 * feat_s, "network": 1e3 * mlp_s, "select_and_search": 1e3 * search_s},
     }))
 
 

@@ -200,11 +200,137 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
+// Fused inference: y = relu(relu(X W1^T + b1) W2^T + b2) . w3 + b3 for 128-row tiles.
+// One persistent CTA per SM keeps W1 (24 KB) and W2 (128 KB) in shared memory in the
+// tensor core's layout; per tile the X rows are staged into the H1 buffer, layer 1 runs
+// as 3 MMAs (K = 48) into TMEM, the epilogue writes bias+ReLU BF16 activations back into
+// the same buffer as layer 2's A operand, layer 2 runs as 16 MMAs (K = 256) into the same
+// TMEM columns, and the second epilogue reduces bias+ReLU activations against w3.  Eight
+// warps: warp w reads TMEM lanes 32 (w % 4) and columns 128 (w / 4) .. + 128.
+constexpr int INF_THREADS = 256;
+constexpr size_t INF_W1 = 256 * 48 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2;
+
+__global__ void __launch_bounds__(INF_THREADS, 1)
+    mlp_infer_kernel(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
+                     const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* w1s = smem;
+  uint8_t* w2s = smem + INF_W1;
+  uint8_t* h1s = smem + INF_W1 + INF_W2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  __shared__ float red[2][128];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  stage(w1s, W1b, 48, 256, 48, 0, 256, 0, 48, false);
+  stage(w2s, W2b, 256, 256, 256, 0, 256, 0, 256, false);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = make_idesc(128, 256);
+  const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
+  uint32_t phase = 0;
+  bool ok = true;
+  const int ntiles = (M + 127) / 128;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int r0 = tile * 128;
+    stage(h1s, X, 48, M, 48, r0, 128, 0, 48, false);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      for (int kk = 0; kk < 3; ++kk)
+        mma_bf16(tmem, make_desc(smem_addr(h1s) + kk * 256, 128, 768), make_desc(smem_addr(w1s) + kk * 256, 128, 768),
+                 idesc, kk > 0);
+      mma_commit(mbar);
+    }
+    ok = mbar_wait(mbar, phase);
+    phase ^= 1;
+    tc_fence_after();
+    if (!ok) break;
+    // layer-1 epilogue: bias, ReLU, BF16 into the core-matrix layout of layer 2's A
+    const int row = quad * 32 + lane;
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      float v[32];
+      tmem_ld32(taddr + (uint32_t)c0, v);
+      const int col0 = half * 128 + c0;
+#pragma unroll
+      for (int c8 = 0; c8 < 4; ++c8) {
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(fmaxf(v[c8 * 8 + e] + b1[col0 + c8 * 8 + e], 0.f));
+        const int kc = (col0 >> 3) + c8;
+        *reinterpret_cast<uint4*>(h1s + (size_t)(row >> 3) * 4096 + kc * 128 + (row & 7) * 16) =
+            *reinterpret_cast<uint4*>(h);
+      }
+    }
+    tc_fence_before();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      for (int kk = 0; kk < 16; ++kk)
+        mma_bf16(tmem, make_desc(smem_addr(h1s) + kk * 256, 128, 4096),
+                 make_desc(smem_addr(w2s) + kk * 256, 128, 4096), idesc, kk > 0);
+      mma_commit(mbar);
+    }
+    ok = mbar_wait(mbar, phase);
+    phase ^= 1;
+    tc_fence_after();
+    if (!ok) break;
+    // layer-2 epilogue: bias, ReLU, BF16, dot with w3 (two column halves, then added)
+    float dot = 0.f;
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      float v[32];
+      tmem_ld32(taddr + (uint32_t)c0, v);
+      const int col0 = half * 128 + c0;
+#pragma unroll
+      for (int e = 0; e < 32; ++e)
+        dot = fmaf(__bfloat162float(__float2bfloat16(fmaxf(v[e] + b2[col0 + e], 0.f))), w3r[col0 + e], dot);
+    }
+    red[half][row] = dot;
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 128 && r0 + (int)threadIdx.x < M)
+      y[r0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x] + *b3;
+  }
+  if (!ok && threadIdx.x == 0 && err) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
 }  // namespace
 
 // Operand staging (48 KB) plus 32 KB of headroom: at most two CTAs share an SM, so the
 // two 256-column TMEM allocations always fit the SM's 512 columns.
 size_t gemm_smem_bytes() { return 128 * KC * 2 + 256 * KC * 2 + 16 + 32 * 1024; }
+
+cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
+                         const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
+                         int num_sms, cudaStream_t st) {
+  static bool attr = false;
+  const size_t smem = INF_W1 + INF_W2 + INF_H1 + 16;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (M <= 0) return cudaSuccess;
+  const int tiles = (M + 127) / 128;
+  mlp_infer_kernel<<<tiles < num_sms ? tiles : num_sms, INF_THREADS, smem, st>>>(X, M, W1b, W2b, b1, b2, w3r, b3, y,
+                                                                                 err);
+  return cudaGetLastError();
+}
 
 cudaError_t gemm_launch(const GemmArgs& g, cudaStream_t st) {
   static bool attr = false;
@@ -555,43 +681,14 @@ gd_status gd_mlp_get_params(gd_mlp* m, float* host) {
 }
 
 gd_status gd_mlp_predict(gd_mlp* m, const void* X, long long M, float* y, void* stream) {
-  if (!m || !X || !y || M < 0) return GD_EINVAL;
+  if (!m || !X || !y || M < 0 || M > 0x7FFFFFFFll) return GD_EINVAL;
   cudaSetDevice(m->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  for (long long r0 = 0; r0 < M; r0 += gd::PREDICT_CHUNK) {
-    const int rows = (int)std::min<long long>(gd::PREDICT_CHUNK, M - r0);
-    gd::GemmArgs g{};
-    g.A = (const __nv_bfloat16*)X + r0 * F_IN;
-    g.B = m->W1b;
-    g.lda = F_IN;
-    g.ldb = F_IN;
-    g.ldc = HID;
-    g.M = rows;
-    g.N = HID;
-    g.K = F_IN;
-    g.bias = m->P + gd::OFF_B1;
-    g.relu = true;
-    g.Cb = m->H1p;
-    g.err = m->err;
-    if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
-    g = gd::GemmArgs{};
-    g.A = m->H1p;
-    g.B = m->W2b;
-    g.lda = HID;
-    g.ldb = HID;
-    g.ldc = HID;
-    g.M = rows;
-    g.N = HID;
-    g.K = HID;
-    g.bias = m->P + gd::OFF_B2;
-    g.relu = true;
-    g.dotw = m->w3r;
-    g.dot_bias_dev = m->P + gd::OFF_B3;
-    g.dot_out = y + r0;
-    g.err = m->err;
-    if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
-  }
-  return GD_OK;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  return gd::infer_launch((const __nv_bfloat16*)X, (int)M, m->W1b, m->W2b, m->P + gd::OFF_B1, m->P + gd::OFF_B2,
+                          m->w3r, m->P + gd::OFF_B3, y, m->err, sms, (cudaStream_t)stream) == cudaSuccess
+             ? GD_OK
+             : GD_ECUDA;
 }
 
 gd_status gd_mlp_gradients(gd_mlp* m, const void* X, const float* t, const int32_t* idx, int B, float* grad,

@@ -28,6 +28,10 @@ struct GemmArgs {
 };
 
 size_t gemm_smem_bytes();
+// Fused two-layer forward of the proposer network (persistent, one CTA per SM).
+cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
+                         const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
+                         int num_sms, cudaStream_t stream);
 cudaError_t gemm_launch(const GemmArgs& g, cudaStream_t stream);
 
 }  // namespace gd

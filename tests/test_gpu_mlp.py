@@ -124,3 +124,29 @@ def test_training_reduces_loss():
     print(first, last)
     assert last < 0.05 * first
     net.close()
+
+
+@pytest.mark.parametrize("M", [1, 127, 1000, 70000])
+def test_fused_predict_matches_oracle(M):
+    import torch
+    from oracle import mlp as om
+    from paper_1901_06229_b300 import mlp
+    P, X, _ = _net_case(11, M)
+    net = mlp.MLP(0, seed=1, max_batch=1024)
+    net.set_params(P)
+    Xb = torch.tensor(X).to(torch.bfloat16).cuda()
+    y = torch.full((M + 5,), float("nan"), device="cuda")
+    net.predict(Xb, y[:M])
+    torch.cuda.synchronize()
+    assert net.error() == 0
+    got = y.cpu().numpy()
+    assert np.isnan(got[M:]).all(), "wrote past the last row"
+    f = om.forward(P, Xb.float().cpu().numpy(), rounding=True)
+    err = np.abs(got[:M] - f["y"])
+    # a hidden activation whose FP32 and FP64 sums round to neighbouring BF16 values moves
+    # y by one BF16 ulp (2^-8 relative) of that unit's contribution: bound per row by the
+    # row's total |H2 w3| mass; typical rows agree to FP32 summation error
+    mass = np.abs(f["H2"]) @ np.abs(f["w3"])
+    assert np.all(err <= 2.0 ** -7 * mass + 1e-3), err.max()
+    assert np.median(err) <= 1e-4
+    net.close()
