@@ -102,3 +102,23 @@ def tune_margin(ctx, net, pk, w, k=16, target=0.99, rule=1, margins=None):
         if r["recall"] >= target:
             return float(m), r
     return float(margins[-1]), r
+
+
+def fit(ctx, pk, n_train=12000, n_val=4000, k=16, target=0.99, seed=1):
+    """Train on streaming-screen ligands and tune the fallback margin for `target` recall
+    on a held-out split.  Returns (network, margin, training info)."""
+    import torch
+    from . import synth
+    wt = synth.workload_stream(n_train, seed_offset=50)
+    wv = synth.workload_stream(n_val, seed_offset=51)
+    X, t, _ = dataset(ctx, pk, wt)
+    ts, mu, sd = standardise(t)
+    net = _mlp.MLP(torch.cuda.current_device(), seed=seed, max_batch=4096)
+    t0 = time.perf_counter()
+    hist = train(net, X, ts)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    margin, r = tune_margin(ctx, net, pk, wv, k=k, target=target, rule=1)
+    del X, t, ts
+    return net, margin, dict(rows=n_train * wt.params.n_orient, epochs=len(hist), seconds=secs,
+                             final_loss=hist[-1], val_recall=r["recall"], val_fallback=r["fallback"])

@@ -1,0 +1,158 @@
+"""Streaming screen: continuous batching of arriving ligands onto the resident pocket.
+
+Ligands arrive over time (a Poisson process in the benchmark).  Whenever an in-flight
+slot is free and the context's device-memory budget admits it, every ligand that has
+arrived and is still waiting is packed into one batch (up to max_batch) and submitted on
+its own CUDA stream: features -> proposer network -> restart selection with fallback ->
+pruned search -> copy back.  Several batches are in flight at once, so packing and
+copies of one overlap the kernels of others, and a ligand arriving while others run
+waits only for the next free slot, not for a fixed batch to fill.  Completions are
+polled without blocking; each ligand's latency is its completion time minus its
+arrival time.  Every computation runs in libgeodock's kernels; this module schedules.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import geodock as gdk
+from . import synth
+
+
+@dataclass
+class _Batch:
+    ids: np.ndarray
+    job: object
+    X: object
+    y: object
+    stream: object
+    submitted: float
+
+
+@dataclass
+class ScreenResult:
+    best_score: np.ndarray
+    best_orient: np.ndarray
+    arrival: np.ndarray
+    done: np.ndarray
+    batches: int = 0
+    budget_waits: int = 0
+    batch_sizes: list = field(default_factory=list)
+    restarts: np.ndarray = None
+
+    @property
+    def latency(self):
+        return self.done - self.arrival
+
+    def summary(self):
+        lat = self.latency
+        span = float(self.done.max() - self.arrival.min())
+        return dict(ligands=int(len(lat)), ligands_per_s=len(lat) / span, p50_ms=1e3 * float(np.percentile(lat, 50)),
+                    p99_ms=1e3 * float(np.percentile(lat, 99)), mean_batch=float(np.mean(self.batch_sizes)),
+                    batches=self.batches, budget_waits=self.budget_waits,
+                    restarts_per_ligand=float(np.mean(self.restarts)))
+
+
+class Screen:
+    """Continuous-batching screen of one pocket with a trained proposer.
+
+    Admission: a batch is admitted when a stream slot is free and gd_prepare_batch fits
+    the context's device-memory budget; otherwise it waits for an in-flight batch to
+    finish, and if nothing is in flight the batch size is halved."""
+
+    def __init__(self, ctx, pocket, params, net, k=16, margin=1e30, rule=1, max_batch=512, max_inflight=4,
+                 debug=False):
+        import torch
+        self.ctx, self.pk, self.params, self.net = ctx, pocket, params, net
+        self.k, self.margin, self.rule = k, margin, rule
+        self.max_batch, self.debug = max_batch, debug
+        self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
+
+    def _submit(self, batch, ids, stream):
+        import torch
+        job = self.ctx.prepare_batch(self.pk, batch, self.params, stream=stream, debug=self.debug)
+        rows = batch.n_ligands * self.params.n_orient
+        with torch.cuda.stream(stream):
+            X = torch.empty((rows, 48), dtype=torch.bfloat16, device="cuda")
+            y = torch.empty(rows, device="cuda")
+            job.features(x_bf16=X, stream=stream)
+            self.net.predict(X, y)
+            job.launch_proposed(y, self.k, self.margin, self.rule, stream)
+            job.download(stream)
+        return job, X, y
+
+    def run(self, workload, arrival_times, clock=time.perf_counter):
+        """Serve every ligand of `workload`; ligand i becomes available at arrival_times[i]
+        seconds after the start.  Returns per-ligand results and timings."""
+        N = workload.batch.n_ligands
+        order = np.argsort(arrival_times, kind="stable")
+        res = ScreenResult(best_score=np.zeros(N, np.uint32), best_orient=np.zeros(N, np.int32),
+                           arrival=np.asarray(arrival_times, np.float64).copy(), done=np.zeros(N),
+                           restarts=np.zeros(N, np.int32))
+        pending, inflight = deque(), []
+        free = list(range(len(self.streams)))
+        cap = self.max_batch  # shrinks if a batch cannot fit the budget even alone
+        nxt, finished = 0, 0
+        t0 = clock()
+        while finished < N:
+            now = clock() - t0
+            while nxt < N and arrival_times[order[nxt]] <= now:
+                pending.append(order[nxt])
+                nxt += 1
+            progressed = False
+            for b in list(inflight):
+                out = b.job.fetch(blocking=False)
+                if out is None:
+                    continue
+                t_done = clock() - t0
+                cnt, _ = b.job.selection()
+                res.best_score[b.ids] = out["best_score"]
+                res.best_orient[b.ids] = out["best_orient"]
+                res.restarts[b.ids] = cnt
+                res.done[b.ids] = t_done
+                b.job.free()
+                free.append(self.streams.index(b.stream))
+                inflight.remove(b)
+                finished += len(b.ids)
+                progressed = True
+            if pending and free:
+                take = [pending.popleft() for _ in range(min(cap, len(pending)))]
+                ids = np.array(take, np.int64)
+                stream = self.streams[free[-1]]
+                try:
+                    job, X, y = self._submit(workload.batch.subset(ids), ids, stream)
+                except gdk.GeoDockError as e:
+                    if e.status != gdk.GD_EBUDGET:
+                        raise
+                    pending.extendleft(reversed(take))
+                    res.budget_waits += 1
+                    if not inflight:  # nothing will free memory: admit a smaller batch
+                        if len(take) == 1:
+                            raise
+                        cap = max(1, len(take) // 2)
+                    time.sleep(1e-4)  # else wait for a batch to finish and return its memory
+                    continue
+                free.pop()
+                inflight.append(_Batch(ids, job, X, y, stream, clock() - t0))
+                res.batches += 1
+                res.batch_sizes.append(len(ids))
+                progressed = True
+            if not progressed:
+                wait = 2e-4
+                if nxt < N and not inflight:
+                    wait = max(0.0, min(wait, arrival_times[order[nxt]] - (clock() - t0)))
+                time.sleep(wait)
+        return res
+
+
+def poisson_arrivals(n, rate, seed=0):
+    """Arrival times (s) of n events of a Poisson process with `rate` per second."""
+    rng = synth.SplitMix64(synth.ligand_seed(seed, 0))
+    t, out = 0.0, np.empty(n)
+    for i in range(n):
+        t += -np.log(1.0 - rng.uniform()) / rate
+        out[i] = t
+    return out

@@ -1,0 +1,82 @@
+"""Streaming screen: continuous batching gives every ligand the result it gets alone,
+and admission by device-memory budget delays work without changing results."""
+import numpy as np
+import pytest
+
+from paper_1901_06229_b300 import geodock as gdk
+from paper_1901_06229_b300 import mlp, serve, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(ctx, pk, w, net, i, k, margin):
+    import torch
+    b = w.batch.subset([i])
+    job = ctx.prepare_batch(pk, b, w.params)
+    X = torch.empty((w.params.n_orient, 48), dtype=torch.bfloat16, device="cuda")
+    y = torch.empty(w.params.n_orient, device="cuda")
+    job.features(x_bf16=X)
+    net.predict(X, y)
+    job.launch_proposed(y, k, margin, 1)
+    job.download()
+    out = job.fetch()
+    job.free()
+    return int(out["best_score"][0]), int(out["best_orient"][0])
+
+
+def _median_spread(ctx, pk, w, net, k):
+    import torch
+    job = ctx.prepare_batch(pk, w.batch, w.params)
+    L, O = w.batch.n_ligands, w.params.n_orient
+    X = torch.empty((L * O, 48), dtype=torch.bfloat16, device="cuda")
+    y = torch.empty(L * O, device="cuda")
+    job.features(x_bf16=X)
+    net.predict(X, y)
+    job.launch_proposed(y, k, 1e30, 1)
+    _, spread = job.selection()
+    job.free()
+    return float(np.median(spread))
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    ctx = gdk.Context(0)
+    w = synth.workload_stream(400, seed_offset=77)
+    pk = ctx.load_pocket(w.pocket)
+    net = mlp.MLP(0, seed=5, max_batch=1024)  # untrained: consistency does not need a good model
+    margin = _median_spread(ctx, pk, w, net, 16)  # about half of the ligands fall back
+    yield ctx, pk, w, net, margin
+    net.close()
+    pk.free()
+    ctx.close()
+
+
+def test_results_are_the_same_alone_and_in_the_mix(setup):
+    ctx, pk, w, net, margin = setup
+    arr = serve.poisson_arrivals(w.batch.n_ligands, 20000.0, seed=3)
+    scr = serve.Screen(ctx, pk, w.params, net, k=16, margin=margin, max_batch=64, max_inflight=3)
+    res = scr.run(w, arr)
+    s = res.summary()
+    print(s)
+    assert res.batches > 3 and max(res.batch_sizes) > 1
+    assert 0 < np.mean(res.restarts == 256) < 1  # both pruned and fallback ligands
+    assert np.all(res.latency > 0)
+    for i in np.random.default_rng(0).choice(w.batch.n_ligands, 40, replace=False):
+        assert _alone(ctx, pk, w, net, int(i), 16, margin) == (int(res.best_score[i]), int(res.best_orient[i]))
+
+
+def test_memory_budget_admission(setup):
+    ctx0, pk0, w, net, margin = setup
+    arr = np.zeros(w.batch.n_ligands)  # everything arrives at once
+    free_run = serve.Screen(ctx0, pk0, w.params, net, k=16, margin=margin, max_batch=100, max_inflight=4).run(w, arr)
+    # a budget that holds the pocket and about one batch: the others wait for memory
+    tight = gdk.Context(0, mem_budget_bytes=3 << 20)
+    pk = tight.load_pocket(w.pocket)
+    res = serve.Screen(tight, pk, w.params, net, k=16, margin=margin, max_batch=100, max_inflight=4).run(w, arr)
+    print(res.summary())
+    assert res.budget_waits > 0
+    np.testing.assert_array_equal(res.best_score, free_run.best_score)
+    np.testing.assert_array_equal(res.best_orient, free_run.best_orient)
+    pk.free()
+    tight.close()
