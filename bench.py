@@ -199,9 +199,14 @@ def run_learned(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
     n_eval = args.ligands or 16384
-    wt = synth.workload_stream(12000, seed_offset=50)
-    wv = synth.workload_stream(4000, seed_offset=51)
-    we = synth.workload_stream(n_eval, seed_offset=52 + 10 * rank)
+    if args.workload == "learned24":  # the proposer's own spec: 24-atom, 4-rotamer ligands
+        wt = synth.workload_proposer_train(3907)
+        wv = synth.workload_proposer_eval(4000, start=100000)
+        we = synth.workload_proposer_eval(n_eval, start=200000 * (rank + 1))
+    else:
+        wt = synth.workload_stream(12000, seed_offset=50)
+        wv = synth.workload_stream(4000, seed_offset=51)
+        we = synth.workload_stream(n_eval, seed_offset=52 + 10 * rank)
     ctx = gdk.Context(dev)
     pk = ctx.load_pocket(we.pocket)
     X, t, _ = proposer.dataset(ctx, pk, wt)
@@ -280,7 +285,7 @@ def run_learned(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32 search / bf16 network", "data": "synthetic (seeded generators)",
         "config": workload_config(we, "flushed between steps (256 MB write)") | {
             "k": k, "margin_rule": "fall back when pred(1st) - pred(16th) > margin", "margin": margin,
-            "train": {"ligands": 12000, "rows": int(X.shape[0]), "epochs": len(hist), "seconds": train_s,
+            "train": {"ligands": wt.batch.n_ligands, "rows": int(X.shape[0]), "epochs": len(hist), "seconds": train_s,
                       "final_loss_std_units": hist[-1]}},
         "plain_value": plain_v, "speedup_vs_plain": value / plain_v,
         "best_pose_recall": recall, "score_regret": regret, "fallback_fraction": float(np.mean(cnt > k)),
@@ -335,7 +340,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned", "stream"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned", "learned24", "stream"])
     ap.add_argument("--rate", type=float, default=100000.0, help="stream: Poisson arrival rate (ligands/s)")
     ap.add_argument("--max-batch", type=int, default=2048, help="stream: largest admitted batch")
     ap.add_argument("--tile", type=int, default=-1, help="-1 autotune, 0 default, >0 tile id")
@@ -348,7 +353,7 @@ def main():
         run_reference(args, world, rank)
         return
     assert args.warmup >= 3 or args.steps <= 3, "at least 3 warm-up steps"
-    if args.workload == "learned":
+    if args.workload in ("learned", "learned24"):
         run_learned(args, world, rank, local)
         return
     if args.workload == "stream":
