@@ -299,6 +299,50 @@ def run_learned(args, world, rank, local):
     }))
 
 
+def run_mlp(args, world, rank, local):
+    """The proposer network's fused tensor-core forward alone: L x 256 rows of 48 BF16
+    features (random weights and inputs), rows/s and TFLOP/s against the BF16 peak."""
+    import torch
+    from paper_1901_06229_b300 import mlp
+    torch.cuda.set_device(local)
+    rows = (args.ligands or 16384) * 256
+    net = mlp.MLP(torch.cuda.current_device(), seed=1, max_batch=1024)
+    g = torch.Generator(device="cuda").manual_seed(rank)
+    X = torch.rand((rows, 48), device="cuda", generator=g).to(torch.bfloat16)
+    y = torch.empty(rows, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        net.predict(X, y)
+    torch.cuda.synchronize()
+    barrier(world)
+    st = torch.cuda.current_stream()
+    ev = []
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        net.predict(X, y)
+        b.record(st)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    t = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, world)
+    assert net.error() == 0 and bool(torch.isfinite(y).all())
+    net.close()
+    if rank != 0:
+        return
+    tflops = MLP_FLOPS_PER_ROW * rows * world * args.steps / t / 1e12
+    peak = measured_peaks().get("bf16_tflops", 1787.5)
+    print(json.dumps({
+        "metric": "rows/s (proposer network forward, 1 B300)", "value": rows * world * args.steps / t,
+        "unit": "rows/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (fp32 accumulate)", "data": "synthetic (random weights and features)",
+        "config": {"workload": f"mlp-48-256-256-1-{rows}rows", "rows": rows, "l2": "flushed between steps"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                     "traffic": None, "peak_kind": "bf16_tflops of MEASURED_PEAKS.json (burst)"}}))
+
+
 def run_stream(args, world, rank, local):
     """Streaming screen: Poisson arrivals onto the resident pocket with continuous batching,
     learned pruning with fallback, an 8 GB device-memory budget; ligands/s and p50/p99."""
@@ -340,7 +384,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned", "learned24", "stream"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned", "learned24", "stream", "mlp"])
     ap.add_argument("--rate", type=float, default=100000.0, help="stream: Poisson arrival rate (ligands/s)")
     ap.add_argument("--max-batch", type=int, default=2048, help="stream: largest admitted batch")
     ap.add_argument("--tile", type=int, default=-1, help="-1 autotune, 0 default, >0 tile id")
@@ -358,6 +402,9 @@ def main():
         return
     if args.workload == "stream":
         run_stream(args, world, rank, local)
+        return
+    if args.workload == "mlp":
+        run_mlp(args, world, rank, local)
         return
 
     import torch
