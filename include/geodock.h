@@ -85,7 +85,12 @@ typedef struct {
 /* Search settings.  Restart o = (i*n_beta + j)*n_gamma + k uses the ZYZ Euler angles
  * (2 pi i/n_alpha, pi (j+1/2)/n_beta, 2 pi k/n_gamma).  tile: 0 = built-in default,
  * -1 = autotuned (cached per context), > 0 = a tile id from gd_tile_count(); the
- * tile changes speed only, never results. */
+ * tile changes speed only, never results.
+ * rigid_span s > 0 adds the rigid alignment sweep of align_ligand (Sec. 3.1, 4.1) after
+ * each restart's placement: the (2s+1)^3 rotations about the pocket centre by rotation
+ * vectors rigid_step * (i-s, j-s, k-s), i, j, k in [0, 2s] (identity first, then the
+ * others in (i, j, k) order), are scored rigidly and the best (ties: the earlier one)
+ * is kept before optimize_pose.  s <= 3; 0 = off. */
 typedef struct {
   int32_t n_alpha, n_beta, n_gamma;
   int32_t n_angles;
@@ -94,6 +99,8 @@ typedef struct {
   int32_t repetitions;
   int32_t flags;
   int32_t tile;
+  int32_t rigid_span;
+  float rigid_step;
 } gd_search_params;
 
 /* Results, caller-allocated host buffers (sizes from the batch it came from):
@@ -106,6 +113,7 @@ typedef struct {
  *   pair_tests[L]          moving x static pair tests performed (early exit per atom)
  *   atom_moves[L]          fragment atoms rotated and scored (O * reps * A * sum_r f_r,
  *                          f_r = atoms of fragment r)
+ *   best_rigid[L]          rigid-sweep candidate kept for the best restart (0 without sweep)
  *   reach_tests[L]         moving x static pairs checked once per rotamer step by the
  *                          reach filter (a pair that cannot come within bump_dist at any
  *                          angle is not tested per angle)
@@ -113,6 +121,7 @@ typedef struct {
  *   orient_score[L*O]      final score of every restart            (GD_FLAG_DEBUG)
  *   orient_pick[O*reps*Rt] picks of every restart, ligand i at rot_off[i]*reps*O,
  *                          then o*reps*R_i + step                  (GD_FLAG_DEBUG)
+ *   orient_rigid[L*O]      rigid-sweep candidate kept by every restart (GD_FLAG_DEBUG)
  *   bump_bits[sum_i O*reps*R_i*A]  1 if the candidate was bumped   (GD_FLAG_DEBUG_BUMPS), ligand i at
  *                          O*reps*A*rot_off[i], then ((o*reps*R_i + step)*A + k) */
 typedef struct {
@@ -127,6 +136,8 @@ typedef struct {
   uint32_t* orient_score;
   int16_t* orient_pick;
   uint8_t* bump_bits;
+  int16_t* best_rigid;
+  int16_t* orient_rigid;
 } gd_result_batch;
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes caps the device memory

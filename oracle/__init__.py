@@ -65,10 +65,26 @@ def _p(a, ct):
 class _Params(C.Structure):
     _fields_ = [("n_alpha", C.c_int32), ("n_beta", C.c_int32), ("n_gamma", C.c_int32),
                 ("n_angles", C.c_int32), ("bump_dist", C.c_double),
-                ("min_bond_sep", C.c_int32), ("repetitions", C.c_int32)]
+                ("min_bond_sep", C.c_int32), ("repetitions", C.c_int32),
+                ("rigid_span", C.c_int32), ("rigid_step", C.c_double)]
+
+
+def _prm(params):
+    return _Params(params.n_alpha, params.n_beta, params.n_gamma, params.n_angles, float(params.bump_dist),
+                   params.min_bond_sep, params.repetitions, int(getattr(params, "rigid_span", 0)),
+                   float(getattr(params, "rigid_step", 0.0)))
 
 
 # ------------------------------------------------------------------ single operations
+
+def rigid_candidate(m: int, span: int, step: float) -> np.ndarray:
+    """Rotation matrix of candidate m of the rigid alignment sweep."""
+    R = np.zeros(9)
+    L = lib()
+    L.orc_rigid_candidate.argtypes = [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double)]
+    L.orc_rigid_candidate(int(m), int(span), float(step), _p(R, C.c_double))
+    return R.reshape(3, 3)
+
 
 def euler(o: int, na: int, nb: int, ng: int) -> np.ndarray:
     R = np.zeros(9)
@@ -167,10 +183,9 @@ def dock_pose(lig, pocket, params, o: int, debug: bool = False, eps: float = EPS
     g = np.ascontiguousarray(pocket.grid, dtype=np.uint8)
     nz, ny, nx_ = g.shape
     org = np.ascontiguousarray(pocket.origin, dtype=np.float64)
-    prm = _Params(params.n_alpha, params.n_beta, params.n_gamma, params.n_angles,
-                  float(params.bump_dist), params.min_bond_sep, params.repetitions)
+    prm = _prm(params)
     picks = np.zeros(reps * R, np.int16)
-    slhf = np.zeros(4, np.int32)
+    slhf = np.zeros(5, np.int32)
     xyz = np.zeros((n, 3))
     bump = np.zeros(reps * R * A, np.uint8) if debug else None
     cand = np.zeros(reps * R * A, np.int32) if debug else None
@@ -184,7 +199,7 @@ def dock_pose(lig, pocket, params, o: int, debug: bool = False, eps: float = EPS
     if rc:
         raise ValueError(lib().orc_last_error().decode())
     out = dict(picks=picks, score=int(slhf[0]), score_lo=int(slhf[1]), score_hi=int(slhf[2]),
-               fragile=int(slhf[3]), xyz=xyz)
+               fragile=int(slhf[3]), rigid=int(slhf[4]), xyz=xyz)
     if debug:
         out["bump"], out["cand_score"] = bump, cand
     return out
@@ -212,12 +227,12 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
         orient_fragile=np.zeros((L, O), np.int32), best_xyz=np.zeros((len(batch.xyz), 3)),
         best_orient=np.zeros(L, np.int32), best_score=np.zeros(L, np.int32),
         best_robust=np.zeros(L, np.int32), pair_tests_full=np.zeros(L, np.int64),
-        evals=np.zeros(L, np.int64), status=np.zeros(L, np.int32), cand_off=cand_off)
+        evals=np.zeros(L, np.int64), status=np.zeros(L, np.int32), cand_off=cand_off,
+        orient_rigid=np.zeros((L, O), np.int16))
     if debug:
         out["bump"] = np.zeros(int(cand_off[-1]), np.uint8)
         out["cand_score"] = np.zeros(int(cand_off[-1]), np.int32)
-    prm = _Params(params.n_alpha, params.n_beta, params.n_gamma, params.n_angles,
-                  float(params.bump_dist), params.min_bond_sep, params.repetitions)
+    prm = _prm(params)
     g = np.ascontiguousarray(pocket.grid, dtype=np.uint8)
     nz, ny, nx = g.shape
     org = np.ascontiguousarray(pocket.origin, dtype=np.float64)
@@ -239,7 +254,8 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
         _p(out["cand_score"], C.c_int32) if debug else nul(C.c_int32),
         _p(cand_off, C.c_int64), _p(out["best_xyz"], C.c_double), _p(out["best_orient"], C.c_int32),
         _p(out["best_score"], C.c_int32), _p(out["best_robust"], C.c_int32),
-        _p(out["pair_tests_full"], C.c_int64), _p(out["evals"], C.c_int64), _p(out["status"], C.c_int32))
+        _p(out["pair_tests_full"], C.c_int64), _p(out["evals"], C.c_int64), _p(out["status"], C.c_int32),
+        _p(out["orient_rigid"], C.c_int16))
     if rc:
         raise ValueError("oracle rejected a ligand: " + lib().orc_last_error().decode())
     return out

@@ -149,7 +149,36 @@ struct Params {
   double bump_dist;
   int min_bond_sep;
   int repetitions;
+  int rigid_span;     // rigid alignment sweep (align_ligand): (2s+1)^3 rotations, 0 = off
+  double rigid_step;  // radians
 };
+
+// Rigid candidate m of the sweep: m = 0 is the identity, the others are the rotation
+// vectors step * (i - s, j - s, k - s), i, j, k in [0, 2s], in (i, j, k) order without
+// the zero vector; as a rotation about that vector's direction by its length.
+M3 rigid_candidate(int m, int s, double step) {
+  M3 I{{{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}};
+  if (m == 0) return I;
+  int count = 0;
+  const int W = 2 * s + 1;
+  for (int i = 0; i < W; ++i)
+    for (int j = 0; j < W; ++j)
+      for (int k = 0; k < W; ++k) {
+        if (i == s && j == s && k == s) continue;
+        if (++count != m) continue;
+        const V3 v{step * (i - s), step * (j - s), step * (k - s)};
+        const double th = norm(v);
+        const V3 u = (1.0 / th) * v;
+        M3 R{};
+        const V3 ex{1, 0, 0}, ey{0, 1, 0}, ez{0, 0, 1};
+        const V3 cx = rodrigues(u, th, ex), cy = rodrigues(u, th, ey), cz = rodrigues(u, th, ez);
+        R.m[0][0] = cx.x; R.m[1][0] = cx.y; R.m[2][0] = cx.z;
+        R.m[0][1] = cy.x; R.m[1][1] = cy.y; R.m[2][1] = cy.z;
+        R.m[0][2] = cz.x; R.m[1][2] = cz.y; R.m[2][2] = cz.z;
+        return R;
+      }
+  return I;
+}
 
 struct Topo {
   int n = 0;
@@ -244,6 +273,7 @@ struct LigandOut {
   int32_t* orient_score_lo;    // [O]
   int32_t* orient_score_hi;    // [O]
   int16_t* orient_pick;        // [O * reps * R]
+  int16_t* orient_rigid;       // optional [O] rigid-sweep choice per restart
   int32_t* orient_fragile;     // [O] first fragile step (rep*R + r) or -1
   uint8_t* bump;               // optional [O * reps * R * A]: 0 free, 1 bumped, 2 uncertain
   int32_t* cand_score;         // optional [O * reps * R * A] exact candidate score (-1 if bumped)
@@ -288,13 +318,45 @@ bool prepare(const float* xyz_in, int n, const int32_t* bonds, int nb, const int
 // eps-interval, the first fragile step (-1: none) and the final coordinates x.
 void search_restart(const Prepared& L, const Pocket& P, const Params& prm, double eps, int o, int16_t* picks,
                     uint8_t* bump, int32_t* cand_score, int* score_out, int* lo_out, int* hi_out,
-                    int* fragile_out, std::vector<V3>& x) {
+                    int* fragile_out, std::vector<V3>& x, int16_t* rigid_out = nullptr) {
+  int16_t rigid_dummy = 0;
+  (void)rigid_dummy;
   const double pi = 3.14159265358979323846;
   const int n = L.n, R = L.R, A = prm.n_angles, reps = prm.repetitions;
   M3 Ro = euler_orientation(o, prm.n_alpha, prm.n_beta, prm.n_gamma);
   x.resize(n);
   for (int a = 0; a < n; ++a) x[a] = L.c_pocket + mul(Ro, L.x0[a] - L.c_lig);
   int fragile_step = -1;
+  if (rigid_out) *rigid_out = 0;
+  if (prm.rigid_span > 0) {  // align_ligand: best rigid rotation about the pocket centre
+    const int W = 2 * prm.rigid_span + 1, M = W * W * W;
+    std::vector<int> sc(M), lo(M), hi(M);
+    for (int m = 0; m < M; ++m) {
+      const M3 Rm = rigid_candidate(m, prm.rigid_span, prm.rigid_step);
+      int s = 0, l0 = 0, h0 = 0;
+      for (int a = 0; a < n; ++a) {
+        const V3 y = L.c_pocket + mul(Rm, x[a] - L.c_pocket);
+        s += cell_value(P, y);
+        int l, h;
+        cell_range(P, y, eps, &l, &h);
+        l0 += l;
+        h0 += h;
+      }
+      sc[m] = s;
+      lo[m] = l0;
+      hi[m] = h0;
+    }
+    int best = 0;
+    for (int m = 1; m < M; ++m)
+      if (sc[m] > sc[best]) best = m;
+    for (int m = 0; m < M; ++m) {  // can an eps move change the choice?
+      if (m == best) continue;
+      if ((m < best && !(hi[m] < lo[best])) || (m > best && !(hi[m] <= lo[best]))) fragile_step = 0;
+    }
+    const M3 Rb = rigid_candidate(best, prm.rigid_span, prm.rigid_step);
+    for (int a = 0; a < n; ++a) x[a] = L.c_pocket + mul(Rb, x[a] - L.c_pocket);
+    if (rigid_out) *rigid_out = best;
+  }
   std::vector<V3> xm(n);
   std::vector<int> score(A), lo(A), hi(A), status(A);
   std::vector<char> bumped(A);
@@ -334,7 +396,7 @@ void search_restart(const Prepared& L, const Pocket& P, const Params& prm, doubl
         if (!bumped[k] && (kstar < 0 || score[k] > score[kstar])) kstar = k;
       picks[step] = (int16_t)kstar;
       // Can an eps perturbation change the pick?
-      if (fragile_step < 0) {
+      if (fragile_step < 0) {  // (0 marks a fragile rigid choice: nothing after it compares)
         bool robust;
         if (kstar < 0) {  // every candidate bumped: robust only if every bump is sure
           robust = true;
@@ -389,7 +451,8 @@ int dock_ligand(const float* xyz_in, int n, const int32_t* bonds, int nb, const 
   for (int o = 0; o < O; ++o)
     search_restart(L, P, prm, eps, o, out.orient_pick + o * per_o, out.bump ? out.bump + o * per_o * A : nullptr,
                    out.cand_score ? out.cand_score + o * per_o * A : nullptr, &out.orient_score[o],
-                   &out.orient_score_lo[o], &out.orient_score_hi[o], &out.orient_fragile[o], final_x[o]);
+                   &out.orient_score_lo[o], &out.orient_score_hi[o], &out.orient_fragile[o], final_x[o],
+                   out.orient_rigid ? out.orient_rigid + o : nullptr);
   int best = 0;
   for (int o = 1; o < O; ++o)
     if (out.orient_score[o] > out.orient_score[best]) best = o;
@@ -423,6 +486,12 @@ const char* orc_last_error() { return g_err.c_str(); }
 
 void orc_euler(int o, int na, int nb, int ng, double* R9) {
   M3 R = euler_orientation(o, na, nb, ng);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R9[3 * i + j] = R.m[i][j];
+}
+
+void orc_rigid_candidate(int m, int span, double step, double* R9) {
+  const M3 R = rigid_candidate(m, span, step);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) R9[3 * i + j] = R.m[i][j];
 }
@@ -615,6 +684,8 @@ struct orc_params {
   int32_t n_alpha, n_beta, n_gamma, n_angles;
   double bump_dist;
   int32_t min_bond_sep, repetitions;
+  int32_t rigid_span;
+  double rigid_step;
 };
 
 // One restart o of one ligand: picks[reps*R], optional bump/cand_score[reps*R*A],
@@ -624,12 +695,15 @@ int orc_dock_pose(int n, const float* xyz, int nb, const int32_t* bonds, int R, 
                   const orc_params* p, double eps, int o, int16_t* picks, uint8_t* bump, int32_t* cand_score,
                   int32_t* score_lo_hi_fragile, double* xyz_out) {
   Pocket P{grid, nx, ny, nz, h, V3{origin[0], origin[1], origin[2]}};
-  Params prm{p->n_alpha, p->n_beta, p->n_gamma, p->n_angles, p->bump_dist, p->min_bond_sep, p->repetitions};
+  Params prm{p->n_alpha, p->n_beta, p->n_gamma, p->n_angles, p->bump_dist, p->min_bond_sep, p->repetitions,
+             p->rigid_span, p->rigid_step};
   Prepared L;
   if (!prepare(xyz, n, bonds, nb, rot_bond, R, P, prm, L, g_err)) return 1;
   std::vector<V3> x;
+  int16_t rigid = 0;
   search_restart(L, P, prm, eps, o, picks, bump, cand_score, &score_lo_hi_fragile[0], &score_lo_hi_fragile[1],
-                 &score_lo_hi_fragile[2], &score_lo_hi_fragile[3], x);
+                 &score_lo_hi_fragile[2], &score_lo_hi_fragile[3], x, &rigid);
+  score_lo_hi_fragile[4] = rigid;
   for (int a = 0; a < n; ++a) {
     xyz_out[3 * a] = x[a].x;
     xyz_out[3 * a + 1] = x[a].y;
@@ -651,10 +725,10 @@ int orc_dock_batch(int L, const int32_t* atom_off, const float* xyz, const int32
                    int32_t* orient_fragile, uint8_t* bump, int32_t* cand_score,
                    const int64_t* cand_off, double* best_xyz, int32_t* best_orient,
                    int32_t* best_score, int32_t* best_robust, int64_t* pair_tests_full,
-                   int64_t* evals, int32_t* status) {
+                   int64_t* evals, int32_t* status, int16_t* orient_rigid) {
   Pocket P{grid, nx, ny, nz, h, V3{origin[0], origin[1], origin[2]}};
   Params prm{p->n_alpha, p->n_beta, p->n_gamma, p->n_angles, p->bump_dist, p->min_bond_sep,
-             p->repetitions};
+             p->repetitions, p->rigid_span, p->rigid_step};
   const int O = prm.n_alpha * prm.n_beta * prm.n_gamma;
   std::atomic<int> next{0};
   std::vector<std::string> errs(L);
@@ -667,6 +741,7 @@ int orc_dock_batch(int L, const int32_t* atom_off, const float* xyz, const int32
       lo.orient_score_lo = orient_score_lo + (size_t)i * O;
       lo.orient_score_hi = orient_score_hi + (size_t)i * O;
       lo.orient_pick = orient_pick + (size_t)rot_off[i] * O * prm.repetitions;
+      lo.orient_rigid = orient_rigid ? orient_rigid + (size_t)i * O : nullptr;
       lo.orient_fragile = orient_fragile + (size_t)i * O;
       lo.bump = bump ? bump + cand_off[i] : nullptr;
       lo.cand_score = cand_score ? cand_score + cand_off[i] : nullptr;

@@ -173,7 +173,8 @@ InLayout in_layout(int L, long long N, long long Rt, long long n_excl) {
 }
 
 struct OutLayout {
-  size_t best_score, best_orient, best_angle, best_xyz, evals, pair_tests, atom_moves, reach_tests, err, total;
+  size_t best_score, best_orient, best_angle, best_xyz, evals, pair_tests, atom_moves, reach_tests, best_rigid, err,
+      total;
 };
 
 OutLayout out_layout(int L, long long N, long long Rt, int reps) {
@@ -187,13 +188,14 @@ OutLayout out_layout(int L, long long N, long long Rt, int reps) {
   l.pair_tests = o;  o = align_up(o + 8 * (size_t)L, 256);
   l.atom_moves = o;  o = align_up(o + 8 * (size_t)L, 256);
   l.reach_tests = o; o = align_up(o + 8 * (size_t)L, 256);
+  l.best_rigid = o;  o = align_up(o + 2 * (size_t)L, 256);
   l.err = o;         o = align_up(o + 4, 256);
   l.total = o;
   return l;
 }
 
 struct ScratchLayout {
-  size_t pose_score, pose_pick, pose_pairs, pose_reach, done, work, bump, total;
+  size_t pose_score, pose_pick, pose_pairs, pose_reach, pose_rigid, done, work, bump, total;
 };
 
 ScratchLayout scratch_layout(int L, int O, long long Rt, int reps, int A, bool debug) {
@@ -203,6 +205,7 @@ ScratchLayout scratch_layout(int L, int O, long long Rt, int reps, int A, bool d
   l.pose_pick = o;  o = align_up(o + 2 * (size_t)O * reps * Rt, 256);
   l.pose_pairs = o; o = align_up(o + 8 * (size_t)L * O, 256);
   l.pose_reach = o; o = align_up(o + 8 * (size_t)L * O, 256);
+  l.pose_rigid = o; o = align_up(o + 2 * (size_t)L * O, 256);
   l.done = o;       o = o + 4 * (size_t)L;          // done and work are cleared by one memset
   o = align_up(o, 8);
   l.work = o;       o = align_up(o + 8, 256);
@@ -224,6 +227,9 @@ gd_status check_params(const gd_search_params* p) {
   if (p->repetitions < 1 || p->repetitions > GD_MAX_REPS)
     return fail(GD_EINVAL, "repetitions outside [1, %d]", GD_MAX_REPS);
   if (p->tile < -1 || p->tile > gd::tile_count()) return fail(GD_EINVAL, "tile %d out of range", p->tile);
+  if (p->rigid_span < 0 || p->rigid_span > 3) return fail(GD_EINVAL, "rigid_span outside [0, 3]");
+  if (p->rigid_span > 0 && (!(p->rigid_step > 0.f) || !std::isfinite(p->rigid_step)))
+    return fail(GD_EINVAL, "rigid_step must be > 0");
   return GD_OK;
 }
 
@@ -401,9 +407,9 @@ gd_status job_release(gd_ctx* c, gd_job* j) {
 
 std::string signature(const gd_pocket* pk, const gd_search_params* p, int nmax, bool smem) {
   char b[256];
-  snprintf(b, sizeof b, "O%d_A%d_r%d_n%d_g%d_%dx%dx%d_f%d", p->n_alpha * p->n_beta * p->n_gamma, p->n_angles,
+  snprintf(b, sizeof b, "O%d_A%d_r%d_n%d_g%d_%dx%dx%d_f%d_s%d", p->n_alpha * p->n_beta * p->n_gamma, p->n_angles,
            p->repetitions, (nmax + 31) / 32, smem ? 1 : 0, pk->dev.cx, pk->dev.cy, pk->dev.cz,
-           (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1);
+           (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1, p->rigid_span);
   return b;
 }
 
@@ -582,11 +588,16 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.pair_tests = (unsigned long long*)(o + j->out.pair_tests);
   a.atom_moves = (unsigned long long*)(o + j->out.atom_moves);
   a.reach_tests = (unsigned long long*)(o + j->out.reach_tests);
+  a.best_rigid = (int16_t*)(o + j->out.best_rigid);
+  a.rigid_span = p->rigid_span;
+  a.rigid_step = p->rigid_step;
+  a.rigid_n = p->rigid_span > 0 ? (2 * p->rigid_span + 1) * (2 * p->rigid_span + 1) * (2 * p->rigid_span + 1) : 0;
   char* s = (char*)j->d_scr;
   a.pose_score = (uint32_t*)(s + j->scr.pose_score);
   a.pose_pick = (int16_t*)(s + j->scr.pose_pick);
   a.pose_pairs = (unsigned long long*)(s + j->scr.pose_pairs);
   a.pose_reach = (unsigned long long*)(s + j->scr.pose_reach);
+  a.pose_rigid = (int16_t*)(s + j->scr.pose_rigid);
   a.done = (int32_t*)(s + j->scr.done);
   a.work = (unsigned long long*)(s + j->scr.work);
   a.err = (int32_t*)(o + j->out.err);
@@ -996,12 +1007,14 @@ gd_status gd_fetch_results(gd_ctx* c, gd_job* j, gd_result_batch* r, int blockin
   if (r->pair_tests) memcpy(r->pair_tests, h + j->out.pair_tests, 8 * (size_t)L);
   if (r->atom_moves) memcpy(r->atom_moves, h + j->out.atom_moves, 8 * (size_t)L);
   if (r->reach_tests) memcpy(r->reach_tests, h + j->out.reach_tests, 8 * (size_t)L);
-  if (r->orient_score || r->orient_pick || r->bump_bits) {
+  if (r->best_rigid) memcpy(r->best_rigid, h + j->out.best_rigid, 2 * (size_t)L);
+  if (r->orient_score || r->orient_pick || r->bump_bits || r->orient_rigid) {
     if (!j->debug) return fail(GD_EINVAL, "debug outputs need GD_FLAG_DEBUG at dock time");
     if (r->bump_bits && !j->debug_bumps) return fail(GD_EINVAL, "bump_bits need GD_FLAG_DEBUG_BUMPS at dock time");
     const char* dh = (const char*)j->h_dbg;
     if (r->orient_score) memcpy(r->orient_score, dh + j->scr.pose_score, 4 * (size_t)L * j->O);
     if (r->orient_pick) memcpy(r->orient_pick, dh + j->scr.pose_pick, 2 * (size_t)j->O * j->reps * j->Rt);
+    if (r->orient_rigid) memcpy(r->orient_rigid, dh + j->scr.pose_rigid, 2 * (size_t)L * j->O);
     if (r->bump_bits) memcpy(r->bump_bits, dh + j->scr.bump, (size_t)j->O * j->reps * j->A * j->Rt);
   }
   return GD_OK;

@@ -76,6 +76,12 @@ struct SearchArgs {
   int warp_bytes;             // shared memory per warp (see warp_smem_bytes)
   unsigned long long* reach_tests;  // [L] (output) moving x static pairs checked by the reach filter
   unsigned long long* pose_reach;   // [L*O] (scratch)
+  // rigid alignment sweep (off when rigid_n <= 1)
+  int rigid_span;             // s: candidates are the (2s+1)^3 rotation vectors step * (i-s, j-s, k-s)
+  float rigid_step;           // radians
+  int rigid_n;                // (2s+1)^3 (identity first)
+  int16_t* pose_rigid;        // [L*O] (scratch) chosen rigid candidate per restart
+  int16_t* best_rigid;        // [L] (output) of the best restart
 };
 
 // Margin of the reach filter (A).  FP32 rounding moves a rotated atom by ~1e-5 A at

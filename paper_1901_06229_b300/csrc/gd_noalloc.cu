@@ -236,6 +236,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   if (out->orient_score || out->orient_pick || out->bump_bits)
     return nfail(GD_EINVAL, "debug outputs are not available without allocation");
   if (p->tile < -1 || p->tile > gd::tile_count()) return nfail(GD_EINVAL, "tile out of range");
+  if (p->rigid_span != 0) return nfail(GD_EINVAL, "the rigid alignment sweep is not available without allocation");
   const int L = b->n_ligands;
   if (L < 0) return nfail(GD_EINVAL, "n_ligands < 0");
   if (L == 0) return GD_OK;

@@ -461,6 +461,65 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
   return __reduce_max_sync(FULL, best);
 }
 
+// Rigid alignment sweep (align_ligand, Sec. 3.1 / 4.1): candidate m of a local grid of
+// rotation vectors step * (i - s, j - s, k - s), i, j, k in [0, 2s], about the pocket
+// centre (the origin of the pose's coordinates); m = 0 is the identity and the others
+// follow in lexicographic (i, j, k) order without it.
+__device__ __forceinline__ Rot3 rigid_rotation(const SearchArgs& a, int m) {
+  const int W = 2 * a.rigid_span + 1, centre = (a.rigid_span * W + a.rigid_span) * W + a.rigid_span;
+  const int g = m - 1, idx = g < centre ? g : g + 1;
+  const float vx = __fmul_rn(a.rigid_step, (float)(idx / (W * W) - a.rigid_span));
+  const float vy = __fmul_rn(a.rigid_step, (float)((idx / W) % W - a.rigid_span));
+  const float vz = __fmul_rn(a.rigid_step, (float)(idx % W - a.rigid_span));
+  const float th = __fsqrt_rn(__fmaf_rn(vx, vx, __fmaf_rn(vy, vy, __fmul_rn(vz, vz))));
+  float sn, cs;
+  sincosf(th, &sn, &cs);
+  const float inv = __frcp_rn(th);
+  return rodrigues(__fmul_rn(vx, inv), __fmul_rn(vy, inv), __fmul_rn(vz, inv), cs, sn, make_float4(0.f, 0.f, 0.f, 0.f));
+}
+
+__device__ void rigid_apply(const SearchArgs& a, float4* X, int n, int m, int lane) {
+  if (m <= 0) return;
+  const Rot3 R = rigid_rotation(a, m);
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = X[i];
+    float x, y, z;
+    rot_apply(R, v.x, v.y, v.z, x, y, z);
+    X[i] = make_float4(x, y, z, 0.f);
+  }
+  __syncwarp();
+}
+
+// Best rigid candidate by score (ties to the smaller m); applies it and returns m.
+template <bool SG>
+__device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, int n, int lane) {
+  unsigned best = 0;
+  for (int m = lane; m < a.rigid_n; m += 32) {
+    int sc = 0;
+    if (m == 0) {
+      for (int i = 0; i < n; ++i) {
+        const float4 v = X[i];
+        sc += cell<SG>(a.pk, sg, v.x, v.y, v.z);
+      }
+    } else {
+      const Rot3 R = rigid_rotation(a, m);
+      for (int i = 0; i < n; ++i) {
+        const float4 v = X[i];
+        float x, y, z;
+        rot_apply(R, v.x, v.y, v.z, x, y, z);
+        sc += cell<SG>(a.pk, sg, x, y, z);
+      }
+    }
+    const unsigned key = ((unsigned)(sc + 1) << 16) | (0xFFFFu - (unsigned)m);
+    best = key > best ? key : best;
+  }
+  best = __reduce_max_sync(FULL, best);
+  const int m = (int)(0xFFFFu - (best & 0xFFFFu));
+  rigid_apply(a, X, n, m, lane);
+  return m;
+}
+
 // a10: reduce over the ligand's restarts, replay the winner, write the results.
 __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane) {
   float4* X = w.X;
@@ -507,6 +566,12 @@ __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane
   for (int s = lane; s < a.reps * R; s += 32)
     a.best_angle[(size_t)r0 * a.reps + s] = __ldcg(a.pose_pick + pick_base + s);
   place(a, X, a.xyz + a0, n, ob, lane);
+  int rig = 0;
+  if (a.rigid_n > 1) {
+    rig = __ldcg(a.pose_rigid + (size_t)li * O + ob);
+    rigid_apply(a, X, n, rig, lane);
+  }
+  if (lane == 0 && a.best_rigid) a.best_rigid[li] = (int16_t)rig;
   for (int rep = 0; rep < a.reps; ++rep)
     for (int r = 0; r < R; ++r) {
       const int k = __ldcg(a.pose_pick + pick_base + rep * R + r);
@@ -534,6 +599,10 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
   const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
   place(a, X, a.xyz + a0, n, o, lane);
+  {
+    const int m = a.rigid_n > 1 ? rigid_align<SG>(a, sg, X, n, lane) : 0;
+    if (lane == 0 && a.pose_rigid) a.pose_rigid[(size_t)li * a.O + o] = (int16_t)m;
+  }
   int cur = score_atoms<SG>(a.pk, sg, X, n, lane);
   unsigned long long pairs = 0, reach = 0;
   const size_t pick_base = (size_t)r0 * a.reps * a.O + (size_t)o * a.reps * R;

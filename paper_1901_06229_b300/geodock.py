@@ -44,7 +44,8 @@ class LigandBatchC(C.Structure):
 class SearchParamsC(C.Structure):
     _fields_ = [("n_alpha", C.c_int32), ("n_beta", C.c_int32), ("n_gamma", C.c_int32),
                 ("n_angles", C.c_int32), ("bump_dist", C.c_float), ("min_bond_sep", C.c_int32),
-                ("repetitions", C.c_int32), ("flags", C.c_int32), ("tile", C.c_int32)]
+                ("repetitions", C.c_int32), ("flags", C.c_int32), ("tile", C.c_int32),
+                ("rigid_span", C.c_int32), ("rigid_step", C.c_float)]
 
 
 class ResultBatchC(C.Structure):
@@ -53,7 +54,8 @@ class ResultBatchC(C.Structure):
                 ("evals", C.POINTER(C.c_uint64)), ("pair_tests", C.POINTER(C.c_uint64)),
                 ("atom_moves", C.POINTER(C.c_uint64)), ("reach_tests", C.POINTER(C.c_uint64)),
                 ("orient_score", C.POINTER(C.c_uint32)), ("orient_pick", C.POINTER(C.c_int16)),
-                ("bump_bits", C.POINTER(C.c_uint8))]
+                ("bump_bits", C.POINTER(C.c_uint8)), ("best_rigid", C.POINTER(C.c_int16)),
+                ("orient_rigid", C.POINTER(C.c_int16))]
 
 
 _lib = None
@@ -119,7 +121,8 @@ def _stream_handle(stream):
 
 def params_c(params, flags=0, tile=0) -> SearchParamsC:
     return SearchParamsC(params.n_alpha, params.n_beta, params.n_gamma, params.n_angles,
-                         float(params.bump_dist), params.min_bond_sep, params.repetitions, flags, tile)
+                         float(params.bump_dist), params.min_bond_sep, params.repetitions, flags, tile,
+                         int(getattr(params, "rigid_span", 0)), float(getattr(params, "rigid_step", 0.0)))
 
 
 class _BatchArrays:
@@ -154,10 +157,12 @@ class Job:
             best_score=np.zeros(self.L, np.uint32), best_orient=np.zeros(self.L, np.int32),
             best_angle=np.zeros(Rt * reps, np.int16), best_xyz=np.zeros((self.N, 3), np.float32),
             evals=np.zeros(self.L, np.uint64), pair_tests=np.zeros(self.L, np.uint64),
-            atom_moves=np.zeros(self.L, np.uint64), reach_tests=np.zeros(self.L, np.uint64))
+            atom_moves=np.zeros(self.L, np.uint64), reach_tests=np.zeros(self.L, np.uint64),
+            best_rigid=np.zeros(self.L, np.int16))
         if self.debug and out is None:
             r["orient_score"] = np.zeros((self.L, O), np.uint32)
             r["orient_pick"] = np.zeros(Rt * reps * O, np.int16)
+            r["orient_rigid"] = np.zeros((self.L, O), np.int16)
         if self.bumps and out is None:
             r["bump_bits"] = np.zeros(Rt * reps * O * A, np.uint8)
         nul = lambda ct: C.cast(None, C.POINTER(ct))
@@ -167,7 +172,9 @@ class Job:
                           _ptr(r["atom_moves"], C.c_uint64), _ptr(r["reach_tests"], C.c_uint64),
                           _ptr(r["orient_score"], C.c_uint32) if "orient_score" in r else nul(C.c_uint32),
                           _ptr(r["orient_pick"], C.c_int16) if "orient_pick" in r else nul(C.c_int16),
-                          _ptr(r["bump_bits"], C.c_uint8) if "bump_bits" in r else nul(C.c_uint8))
+                          _ptr(r["bump_bits"], C.c_uint8) if "bump_bits" in r else nul(C.c_uint8),
+                          _ptr(r["best_rigid"], C.c_int16) if "best_rigid" in r else nul(C.c_int16),
+                          _ptr(r["orient_rigid"], C.c_int16) if "orient_rigid" in r else nul(C.c_int16))
         st = load().gd_fetch_results(self.ctx.h, self.handle, C.byref(rb), 1 if blocking else 0)
         if st == GD_ENOTREADY:
             return None

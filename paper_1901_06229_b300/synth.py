@@ -273,6 +273,8 @@ class SearchParams:
     bump_dist: float = 2.0
     min_bond_sep: int = 3
     repetitions: int = 1
+    rigid_span: int = 0        # rigid alignment sweep over (2s+1)^3 rotation vectors (0 = off)
+    rigid_step: float = 0.0    # radians
 
     @property
     def n_orient(self) -> int:

@@ -41,6 +41,9 @@ def compare_debug(gpu, orc, batch, params, bumps=True, coord_tol=COORD_TOL):
                 st.add("fragile_restarts")
             np.testing.assert_array_equal(gp[:upto], op[:upto], err_msg=f"picks ligand {i} restart {o}")
             st.add("picks_compared", upto)
+            if "orient_rigid" in gpu and "orient_rigid" in orc and fs != 0:
+                assert int(gpu["orient_rigid"][i, o]) == int(orc["orient_rigid"][i, o]), (i, o)
+                st.add("rigid_compared")
             gs = int(gpu["orient_score"][i, o])
             if fs < 0:
                 lo, hi = int(orc["orient_score_lo"][i, o]), int(orc["orient_score_hi"][i, o])
@@ -71,6 +74,8 @@ def check_ligand(gpu, orc, batch, params, i, st, coord_tol=COORD_TOL):
     if R:
         assert 0 <= int(gpu["pair_tests"][i]) <= int(orc["pair_tests_full"][i])
         assert int(gpu["atom_moves"][i]) > 0
+    if "orient_rigid" in gpu:
+        assert int(gpu["best_rigid"][i]) == int(gpu["orient_rigid"][i, gb])
     if "orient_score" in gpu:  # self-consistency of the reduction over restarts
         row = gpu["orient_score"][i].astype(np.int64)
         assert gs == row.max() and gb == int(np.argmax(row)), f"ligand {i}: best restart not the first max"

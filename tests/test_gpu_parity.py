@@ -72,7 +72,8 @@ def test_large_ligands_reduced_restarts(ctx):
 
 
 @pytest.mark.parametrize("case", ["ragged_angles", "one_angle", "odd_euler", "reps2", "min_sep4",
-                                  "bump25", "rigid_only", "two_atoms", "max_atoms"])
+                                  "bump25", "rigid_only", "two_atoms", "max_atoms", "rigid_sweep",
+                                  "rigid_sweep_span2"])
 def test_edge_cases(ctx, case):
     pocket = textured_pocket()
     rng = lambda s: synth.SplitMix64(synth.ligand_seed(4242, s))
@@ -95,11 +96,24 @@ def test_edge_cases(ctx, case):
         params = synth.SearchParams(4, 4, 4, 32)
     elif case == "two_atoms":
         ligs = [synth.gen_ligand(rng(20), 2, 0), synth.gen_ligand(rng(21), 9, 1)]
+    elif case == "rigid_sweep":
+        params = synth.SearchParams(2, 2, 2, 32, rigid_span=1, rigid_step=0.12)
+    elif case == "rigid_sweep_span2":
+        params = synth.SearchParams(2, 2, 2, 32, repetitions=2, rigid_span=2, rigid_step=0.07)
     elif case == "max_atoms":
         big = synth.workload_large(1).pocket
         ligs = [synth.gen_ligand(rng(30), 256, 40)]
         pocket, params = big, synth.SearchParams(1, 2, 1, 64)
     full_compare(ctx, pocket, synth.pack(ligs), params, min_exact=1)
+
+
+def test_rigid_sweep_on_the_batched_workload(ctx):
+    w = synth.workload_batched(16)
+    p = w.params
+    params = synth.SearchParams(p.n_alpha, p.n_beta, p.n_gamma, p.n_angles, rigid_span=1, rigid_step=0.1)
+    gpu, orc, st = full_compare(ctx, w.pocket, w.batch, params, min_exact=1000)
+    assert st.get("rigid_compared", 0) > 1000
+    assert (orc["orient_rigid"] != 0).mean() > 0.1  # the sweep moves many restarts
 
 
 def test_unfiltered_sweep_matches_oracle(ctx):

@@ -389,3 +389,45 @@ def test_counters():
             mv, _, _, dist = oracle.fragment(n, lig.bonds, int(rb))
             pairs += int(((dist >= 3) & mv[:, None] & ~mv[None, :]).sum())
         assert out["pair_tests_full"][i] == pairs * w.params.n_orient * w.params.n_angles
+
+
+# ----------------------------------------------------------------------------- rigid sweep
+
+def test_rigid_candidates_are_rotation_vectors_in_order():
+    for span, step in [(1, 0.1), (2, 0.05)]:
+        W = 2 * span + 1
+        vecs = [(i - span, j - span, k - span) for i in range(W) for j in range(W) for k in range(W)
+                if (i, j, k) != (span, span, span)]
+        np.testing.assert_allclose(oracle.rigid_candidate(0, span, step), np.eye(3), atol=0)
+        for m, v in enumerate(vecs, start=1):
+            ref = Rotation.from_rotvec(step * np.array(v, float)).as_matrix()
+            np.testing.assert_allclose(oracle.rigid_candidate(m, span, step), ref, atol=1e-14)
+
+
+def test_rigid_sweep_picks_the_best_rigid_candidate():
+    w = synth.workload_single()
+    lig = w.batch.ligand(0)
+    P = textured_pocket()
+    span, step = 1, 0.15
+    params = synth.SearchParams(2, 2, 2, 32, rigid_span=span, rigid_step=step)
+    nz, ny, nx_ = P.grid.shape
+    cp = P.origin.astype(np.float64) + 0.5 * P.spacing * np.array([nx_, ny, nz])
+    W = 2 * span + 1
+    vecs = [(0, 0, 0)] + [(i - span, j - span, k - span) for i in range(W) for j in range(W) for k in range(W)
+                          if (i, j, k) != (span, span, span)]
+    moved = 0
+    for o in range(params.n_orient):
+        start = oracle.place(lig.xyz, o, params, P)
+        scores = []
+        for v in vecs:  # numpy gather of the rigidly rotated pose
+            x = cp + Rotation.from_rotvec(step * np.array(v, float)).apply(start - cp)
+            idx = np.floor((x - P.origin.astype(np.float64)) / P.spacing).astype(int)
+            ok = np.all((idx >= 0) & (idx < [nx_, ny, nz]), axis=1)
+            scores.append(int(np.where(ok, P.grid[np.clip(idx[:, 2], 0, nz - 1), np.clip(idx[:, 1], 0, ny - 1),
+                                                   np.clip(idx[:, 0], 0, nx_ - 1)], 0).sum()))
+        r = oracle.dock_pose(lig, P, params, o)
+        if r["fragile"] == 0:
+            continue
+        assert r["rigid"] == int(np.argmax(scores)), (o, r["rigid"], np.argmax(scores))
+        moved += r["rigid"] != 0
+    assert moved > 0
