@@ -19,7 +19,6 @@
 using gd::RotDesc;
 using gd::SearchArgs;
 
-static_assert(gd::EXCL_SMEM == GD_MAX_EXCLUDED, "per-warp exclusion buffer must hold a rotamer's list");
 
 namespace {
 
@@ -604,10 +603,21 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.bump_bits = j->debug_bumps ? (uint8_t*)(s + j->scr.bump) : nullptr;
   a.nmax = nmax;
   a.near_cap = std::min(4096, std::max(512, (8 * nmax + 15) / 16 * 16));
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap);
-  // tile and grid staging mode
-  j->tile = tile;
+  a.rmax = 1;
+  a.emax = 1;
+  for (int i = 0; i < L; ++i) {
+    int ne = 0;
+    for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) ne += rots[r].n_excl;
+    a.rmax = std::max(a.rmax, rot_off[i + 1] - rot_off[i]);
+    a.emax = std::max(a.emax, ne);
+  }
+  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax);
+  // tile and grid staging mode; the default tile (8 warps) gives up warps, keeping its
+  // slots, when a warp's buffers are too large for 8 of them in one block
   const size_t smem_cap = 227 * 1024;
+  if (p->tile == 0)
+    for (int k = 0; k < 2 && gd::search_smem_bytes(a, tile, false) > smem_cap; ++k) tile += k == 0 ? 3 : 6;
+  j->tile = tile;
   j->grid_in_smem = pk->dev.bytes_pad <= gd::max_smem_grid_bytes() &&
                     gd::search_smem_bytes(a, tile, true) <= smem_cap;
   if (!j->grid_in_smem && gd::search_smem_bytes(a, tile, false) > smem_cap) {
@@ -797,6 +807,7 @@ gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, 
   if (max_ligands > 0 && sub.n_ligands > max_ligands) sub.n_ligands = max_ligands;
   gd_search_params q = *p;
   q.flags &= ~(GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS);
+  q.tile = -1;  // each candidate is timed as it is, never shrunk to fit
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   GD_CUDA(cudaEventCreate(&e0));

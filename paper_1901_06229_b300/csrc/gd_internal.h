@@ -73,6 +73,7 @@ struct SearchArgs {
   uint8_t* bump_bits;         // [O * reps * A * Rt]
   int nmax;                   // largest ligand of the batch (per-warp buffer size)
   int near_cap;               // capacity of a warp's near-pair list (multiple of 16)
+  int rmax, emax;             // largest rotamer / excluded-pair count of one ligand (>= 1)
   int warp_bytes;             // shared memory per warp (see warp_smem_bytes)
   unsigned long long* reach_tests;  // [L] (output) moving x static pairs checked by the reach filter
   unsigned long long* pose_reach;   // [L*O] (scratch)
@@ -89,15 +90,12 @@ struct SearchArgs {
 // this margin can never be flagged by the per-angle test.
 constexpr float REACH_MARGIN = 0.01f;
 
-// Capacity of a warp's copy of the current rotamer's excluded pairs (the per-rotamer
-// limit GD_MAX_EXCLUDED of the public header).
-constexpr int EXCL_SMEM = 128;
-
 // Per-warp shared memory: X float4[nmax] | HR float2[nmax] | MOFF uint16[nmax+2] |
-// NEAR uint8[near_cap] | EX uint16[EXCL_SMEM] | RotDesc.
-__host__ __device__ inline int warp_smem_bytes(int nmax, int near_cap) {
+// NEAR uint8[near_cap] | EXL uint16[emax] | RD RotDesc[rmax].  rmax / emax: the largest
+// rotamer count and excluded-pair count of one ligand in the batch (at least 1).
+__host__ __device__ inline int warp_smem_bytes(int nmax, int near_cap, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
-  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(near_cap) + 2 * EXCL_SMEM + 16;
+  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(near_cap) + a16(2 * emax) + 16 * rmax;
 }
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };

@@ -380,10 +380,21 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.bump_bits = nullptr;
   a.nmax = nmax;
   a.near_cap = nmax * 8 < 512 ? 512 : (nmax * 8 > 4096 ? 4096 : (8 * nmax + 15) / 16 * 16);
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap);
+  a.rmax = 1;
+  a.emax = 1;
+  for (int i = 0; i < L; ++i) {
+    int ne = 0;
+    const RotDesc* rr = (const RotDesc*)(h + o_rots);
+    for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) ne += rr[r].n_excl;
+    a.rmax = rot_off[i + 1] - rot_off[i] > a.rmax ? rot_off[i + 1] - rot_off[i] : a.rmax;
+    a.emax = ne > a.emax ? ne : a.emax;
+  }
+  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax);
 
-  const int tile = p->tile > 0 ? p->tile : (A >= 64 ? 2 : 1);
+  int tile = p->tile > 0 ? p->tile : (A >= 64 ? 2 : 1);
   const size_t smem_cap = 227 * 1024;
+  if (p->tile <= 0)  // 8 -> 4 -> 2 warps, same slots, when a warp's buffers are large
+    for (int k = 0; k < 2 && gd::search_smem_bytes(a, tile, false) > smem_cap; ++k) tile += k == 0 ? 3 : 6;
   bool smem_grid = (int)grid_pad <= gd::max_smem_grid_bytes() && gd::search_smem_bytes(a, tile, true) <= smem_cap;
   if (!smem_grid && gd::search_smem_bytes(a, tile, false) > smem_cap)
     return nfail(GD_EINVAL, "tile %d needs more shared memory than a block has", tile);

@@ -134,11 +134,6 @@ __device__ void place(const SearchArgs& a, float4* X, const float4* x0, int n, i
   __syncwarp();
 }
 
-__device__ __forceinline__ void load_desc(RotDesc* dst, const RotDesc* src, int lane) {
-  if (lane < 4) reinterpret_cast<uint32_t*>(dst)[lane] = __ldg(reinterpret_cast<const uint32_t*>(src) + lane);
-  __syncwarp();
-}
-
 // Unit bond axis from the static end p to the moving end q (current coordinates).
 __device__ __forceinline__ void bond_axis(const float4* X, const RotDesc& rd, float& ux, float& uy, float& uz) {
   const float4 xp = X[rd.p], xq = X[rd.q];
@@ -313,12 +308,12 @@ struct WarpMem {
   float2* HR;      // (height along the bond axis, distance from it) per atom
   uint16_t* MOFF;  // near-list offset per moving atom (in sweep order)
   uint8_t* NEAR;   // static atoms that can come within reach of each moving atom
-  uint16_t* EX;    // the current rotamer's excluded pairs
-  RotDesc* rd;
+  RotDesc* RD;     // the current ligand's rotamer descriptors
+  uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
   const float2* CS;  // (cos, sin) of every angle, shared by the block
 };
 
-__device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int near_cap) {
+__device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int near_cap, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
   WarpMem w;
   w.X = reinterpret_cast<float4*>(base);
@@ -329,9 +324,9 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int n
   base += a16(2 * (nmax + 2));
   w.NEAR = base;
   base += a16(near_cap);
-  w.EX = reinterpret_cast<uint16_t*>(base);
-  base += 2 * EXCL_SMEM;
-  w.rd = reinterpret_cast<RotDesc*>(base);
+  w.EXL = reinterpret_cast<uint16_t*>(base);
+  base += a16(2 * emax);
+  w.RD = reinterpret_cast<RotDesc*>(base);
   w.CS = nullptr;
   return w;
 }
@@ -341,8 +336,8 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int n
 // whole turn is at least sqrt((h_a - h_b)^2 + (rho_a - rho_b)^2), so only pairs below
 // bump_dist + margin (and not excluded by graph distance) need per-angle tests.
 // Builds MOFF/NEAR; returns the number of near pairs (> near_cap: list unusable).
-__device__ int build_near(const SearchArgs& a, const WarpMem& w, int n, const RotDesc& rd, float4 xp, float ux,
-                          float uy, float uz, int lane, unsigned long long& reach) {
+__device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
+                          float4 xp, float ux, float uy, float uz, int lane, unsigned long long& reach) {
   for (int i = lane; i < n; i += 32) {
     const float4 v = w.X[i];
     const float rx = __fsub_rn(v.x, xp.x), ry = __fsub_rn(v.y, xp.y), rz = __fsub_rn(v.z, xp.z);
@@ -360,7 +355,6 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, int n, const Ro
     s0a = 0; s0b = rd.lo; s1a = rd.hi; s1b = n;
   }
   const int n_static = (s0b - s0a) + (s1b - s1a);
-  const uint16_t* excl = w.EX;
   const int n_excl = rd.n_excl;
   int ex = 0, cnt = 0, ia = 0;
   const unsigned lt = (1u << lane) - 1u;
@@ -523,7 +517,6 @@ __device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, in
 // a10: reduce over the ligand's restarts, replay the winner, write the results.
 __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane) {
   float4* X = w.X;
-  RotDesc* rds = w.rd;
   const int O = a.O;
   unsigned best = 0;
   unsigned long long pairs = 0, reach = 0;
@@ -576,8 +569,7 @@ __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane
     for (int r = 0; r < R; ++r) {
       const int k = __ldcg(a.pose_pick + pick_base + rep * R + r);
       if (k < 0) continue;
-      load_desc(rds, a.rots + r0 + r, lane);
-      const RotDesc& rd = *rds;
+      const RotDesc rd = w.RD[r];  // registers: the loops below also write shared memory
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
       commit(X, n, rd, ux, uy, uz, w.CS[k], lane);
@@ -595,9 +587,19 @@ __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane
 template <int S, bool SG>
 __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int lane) {
   float4* X = w.X;
-  RotDesc* rds = w.rd;
   const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
   const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
+  // this ligand's rotamer descriptors and excluded pairs, once per pose
+  int e0 = 0;
+  if (R > 0) {
+    for (int i = lane; i < 4 * R; i += 32)
+      reinterpret_cast<uint32_t*>(w.RD)[i] = __ldg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i);
+    __syncwarp();
+    e0 = (int)w.RD[0].excl_off;
+    const int ne = (int)w.RD[R - 1].excl_off + w.RD[R - 1].n_excl - e0;
+    for (int i = lane; i < ne; i += 32) w.EXL[i] = __ldg(a.excl + e0 + i);
+  }
+  __syncwarp();
   place(a, X, a.xyz + a0, n, o, lane);
   {
     const int m = a.rigid_n > 1 ? rigid_align<SG>(a, sg, X, n, lane) : 0;
@@ -608,10 +610,8 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   const size_t pick_base = (size_t)r0 * a.reps * a.O + (size_t)o * a.reps * R;
   for (int rep = 0; rep < a.reps; ++rep)
     for (int r = 0; r < R; ++r) {
-      load_desc(rds, a.rots + r0 + r, lane);
-      const RotDesc& rd = *rds;
-      for (int e = lane; e < rd.n_excl; e += 32) w.EX[e] = __ldg(a.excl + rd.excl_off + e);
-      __syncwarp();
+      const RotDesc rd = w.RD[r];  // registers: the loops below also write shared memory
+      const uint16_t* excl = w.EXL + ((int)rd.excl_off - e0);
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
       const int s_static = cur - score_fragment<SG>(a.pk, sg, X, n, rd, lane);
@@ -620,10 +620,10 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
       unsigned key;
       const float4 xp = X[rd.p];
-      if (a.use_filter && build_near(a, w, n, rd, xp, ux, uy, uz, lane, reach) <= a.near_cap)
+      if (a.use_filter && build_near(a, w, excl, n, rd, xp, ux, uy, uz, lane, reach) <= a.near_cap)
         key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, lane, pairs, dbg);
       else
-        key = eval_step<S, SG>(a, sg, X, w.CS, w.EX, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
+        key = eval_step<S, SG>(a, sg, X, w.CS, excl, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
         commit(X, n, rd, ux, uy, uz, w.CS[k], lane);
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ Sea
   for (int k = threadIdx.x; k < a.A; k += blockDim.x) cs[k] = angle_entry(k, a.A);
   off += ((size_t)a.A * 8 + 15) / 16 * 16;
   __syncthreads();
-  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.near_cap);
+  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.near_cap, a.rmax, a.emax);
   w.CS = cs;
   // items: every (ligand, restart) in queue order, or an explicit list of rows li*O + o
   const unsigned long long n_items = a.items ? (unsigned long long)*a.n_items_dev : (unsigned long long)a.n_items;
@@ -1010,7 +1010,8 @@ int max_smem_grid_bytes() { return 200 * 1024; }
 
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
   const Tile t = tile_get(tile);
-  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.near_cap) + ((size_t)a.A * 8 + 15) / 16 * 16;
+  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax) +
+             ((size_t)a.A * 8 + 15) / 16 * 16;
   if (grid_in_smem) s += (size_t)a.pk.bytes_pad + 16;
   return s;
 }

@@ -22,7 +22,7 @@ from . import geodock as gdk
 from . import synth
 
 
-@dataclass
+@dataclass(eq=False)  # batches are compared by identity
 class _Batch:
     ids: np.ndarray
     job: object

@@ -71,9 +71,42 @@ def test_large_ligands_reduced_restarts(ctx):
     full_compare(ctx, w.pocket, w.batch, params, min_exact=4)
 
 
+def dense_exclusion_ligand(seed, min_sep, n_atoms=256, n_rot=128):
+    """A tree whose rotamers are the internal bonds with the most excluded pairs that
+    stay within the per-rotamer (128) and per-atom (32) limits at ``min_sep``."""
+    import collections
+    lig = synth.gen_ligand(synth.SplitMix64(synth.ligand_seed(4242, seed)), n_atoms, 0)
+    adj = collections.defaultdict(list)
+    for u, v in lig.bonds.tolist():
+        adj[u].append(v)
+        adj[v].append(u)
+
+    def hops(src, block):  # bond distance from src, not crossing to block
+        d, q = {src: 0}, collections.deque([src])
+        while q:
+            u = q.popleft()
+            for v in adj[u]:
+                if v != block and v not in d:
+                    d[v] = d[u] + 1
+                    q.append(v)
+        return d
+
+    ranked = []
+    for e, (p, q) in enumerate(lig.bonds.tolist()):
+        if len(adj[p]) < 2 or len(adj[q]) < 2:
+            continue
+        a, b = hops(q, p), hops(p, q)
+        pairs = [(m, t) for m, dm in a.items() for t, dt in b.items() if dm + dt + 1 < min_sep]
+        per_atom = collections.Counter(m for m, _ in pairs) + collections.Counter(t for _, t in pairs)
+        if len(pairs) <= 128 and max(per_atom.values()) <= 32:
+            ranked.append((-len(pairs), e))
+    chosen = sorted(e for _, e in sorted(ranked)[:n_rot])
+    return synth.Ligand(lig.xyz, lig.bonds, np.asarray(chosen, np.int32)), -sum(c for c, _ in sorted(ranked)[:n_rot])
+
+
 @pytest.mark.parametrize("case", ["ragged_angles", "one_angle", "odd_euler", "reps2", "min_sep4",
                                   "bump25", "rigid_only", "two_atoms", "max_atoms", "rigid_sweep",
-                                  "rigid_sweep_span2"])
+                                  "rigid_sweep_span2", "max_exclusions"])
 def test_edge_cases(ctx, case):
     pocket = textured_pocket()
     rng = lambda s: synth.SplitMix64(synth.ligand_seed(4242, s))
@@ -104,6 +137,11 @@ def test_edge_cases(ctx, case):
         big = synth.workload_large(1).pocket
         ligs = [synth.gen_ligand(rng(30), 256, 40)]
         pocket, params = big, synth.SearchParams(1, 2, 1, 64)
+    elif case == "max_exclusions":  # 128 rotamers, ~7.7k excluded pairs: ~205 KB of warp buffers
+        lig, n_excl = dense_exclusion_ligand(60, 7)
+        assert len(lig.rot_bond) == 128 and n_excl > 7000
+        ligs = [lig]
+        pocket, params = synth.workload_large(1).pocket, synth.SearchParams(2, 2, 2, 64, min_bond_sep=7)
     full_compare(ctx, pocket, synth.pack(ligs), params, min_exact=1)
 
 
