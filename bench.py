@@ -502,7 +502,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators; no public dataset)",
-        "config": workload_config(w, "flushed between steps (256 MB write)") | {"tile": tile},
+        "config": workload_config(w, "flushed between steps (256 MB write)") | {
+            "tile": tile, "tile_warps_slots_regs": list(gdk.tile_info(tile)) if tile > 0 else None},
         "pose_evals_per_s": evals * world * args.steps / dev_s,
         "pair_tests_per_s": pairs * world * args.steps / dev_s,
         "e2e": e2e,

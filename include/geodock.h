@@ -83,9 +83,11 @@ typedef struct {
 } gd_ligand_batch;
 
 /* Search settings.  Restart o = (i*n_beta + j)*n_gamma + k uses the ZYZ Euler angles
- * (2 pi i/n_alpha, pi (j+1/2)/n_beta, 2 pi k/n_gamma).  tile: 0 = built-in default,
- * -1 = autotuned (cached per context), > 0 = a tile id from gd_tile_count(); the
- * tile changes speed only, never results.
+ * (2 pi i/n_alpha, pi (j+1/2)/n_beta, 2 pi k/n_gamma).  tile: 0 = built-in default
+ * (an 8-warp tile: the 64-register kernel when four of its blocks fit in an SM's shared
+ * memory, else the 128-register one, with fewer warps if 8 do not fit), -1 = autotuned
+ * (cached per context), > 0 = a tile id from gd_tile_count(); the tile changes speed
+ * only, never results.
  * rigid_span s > 0 adds the rigid alignment sweep of align_ligand (Sec. 3.1, 4.1) after
  * each restart's placement: the (2s+1)^3 rotations about the pocket centre by rotation
  * vectors rigid_step * (i-s, j-s, k-s), i, j, k in [0, 2s] (identity first, then the
@@ -186,10 +188,13 @@ gd_status gd_job_free(gd_ctx* ctx, gd_job* job);
  * Returns GD_OK or GD_EINVAL with the reason in gd_last_error(NULL). */
 gd_status gd_check_batch(const gd_ligand_batch* batch, const gd_search_params* params);
 
-/* Launch tiles: number of ids (1..count) and the (warps per block, angles per lane)
- * of one id. */
+/* Launch tiles: number of ids (1..count) and, for one id, the warps per block, the
+ * angles per lane and the register budget per thread of its kernel (128: the pocket
+ * grid is staged in shared memory when it fits; 64: some state spills to local memory,
+ * but up to 32 warps stay resident per SM and the grid is read through L1).  Any
+ * output pointer may be NULL. */
 int gd_tile_count(void);
-gd_status gd_tile_info(int tile, int* warps_per_block, int* angles_per_lane);
+gd_status gd_tile_info(int tile, int* warps_per_block, int* angles_per_lane, int* max_registers);
 /* Time every tile on the batch (or its first max_ligands ligands) and return the
  * fastest; the choice is cached in the context for gd_search_params.tile = -1. */
 gd_status gd_autotune(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batch* batch,

@@ -612,13 +612,11 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
     a.emax = std::max(a.emax, ne);
   }
   a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax);
-  // tile and grid staging mode; the default tile (8 warps) gives up warps, keeping its
-  // slots, when a warp's buffers are too large for 8 of them in one block
+  // tile (0: chosen from the batch's buffer sizes) and grid staging mode
   const size_t smem_cap = 227 * 1024;
-  if (p->tile == 0)
-    for (int k = 0; k < 2 && gd::search_smem_bytes(a, tile, false) > smem_cap; ++k) tile += k == 0 ? 3 : 6;
+  if (tile == 0) tile = gd::default_tile(a);
   j->tile = tile;
-  j->grid_in_smem = pk->dev.bytes_pad <= gd::max_smem_grid_bytes() &&
+  j->grid_in_smem = !gd::tile_get(tile).lean && pk->dev.bytes_pad <= gd::max_smem_grid_bytes() &&
                     gd::search_smem_bytes(a, tile, true) <= smem_cap;
   if (!j->grid_in_smem && gd::search_smem_bytes(a, tile, false) > smem_cap) {
     job_release(c, j);
@@ -645,11 +643,6 @@ gd_status enqueue_download(gd_job* j, cudaStream_t s) {
   if (j->debug) GD_CUDA(cudaMemcpyAsync(j->h_dbg, j->d_scr, j->dbg_bytes, cudaMemcpyDeviceToHost, s));
   GD_CUDA(cudaEventRecord(j->done, s));
   return GD_OK;
-}
-
-int default_tile(const gd_search_params* p) {
-  // 8 warps per block; two angles per lane once there are at least 64 angles
-  return p->n_angles >= 64 ? 2 : 1;
 }
 
 }  // namespace
@@ -789,11 +782,12 @@ gd_status gd_check_batch(const gd_ligand_batch* b, const gd_search_params* p) {
 
 int gd_tile_count(void) { return gd::tile_count(); }
 
-gd_status gd_tile_info(int tile, int* warps, int* slots) {
+gd_status gd_tile_info(int tile, int* warps, int* slots, int* max_regs) {
   if (tile < 1 || tile > gd::tile_count()) return fail(GD_EINVAL, "tile %d out of range", tile);
   gd::Tile t = gd::tile_get(tile);
   if (warps) *warps = t.warps;
   if (slots) *slots = t.slots;
+  if (max_regs) *max_regs = gd::tile_max_regs(t);
   return GD_OK;
 }
 
@@ -807,7 +801,6 @@ gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, 
   if (max_ligands > 0 && sub.n_ligands > max_ligands) sub.n_ligands = max_ligands;
   gd_search_params q = *p;
   q.flags &= ~(GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS);
-  q.tile = -1;  // each candidate is timed as it is, never shrunk to fit
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   GD_CUDA(cudaEventCreate(&e0));
@@ -863,8 +856,7 @@ gd_status prepare(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, cons
   gd_status st = check_params(p);
   if (st) return st;
   cudaSetDevice(c->device);
-  int tile = p->tile;
-  if (tile == 0) tile = default_tile(p);
+  int tile = p->tile;  // 0 is resolved once the batch is packed
   if (tile == -1) {
     int nmax = 2;
     for (int i = 0; i < b->n_ligands; ++i) nmax = std::max(nmax, b->atom_off[i + 1] - b->atom_off[i]);

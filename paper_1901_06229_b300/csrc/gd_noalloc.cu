@@ -391,11 +391,10 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   }
   a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax);
 
-  int tile = p->tile > 0 ? p->tile : (A >= 64 ? 2 : 1);
+  const int tile = p->tile > 0 ? p->tile : gd::default_tile(a);
   const size_t smem_cap = 227 * 1024;
-  if (p->tile <= 0)  // 8 -> 4 -> 2 warps, same slots, when a warp's buffers are large
-    for (int k = 0; k < 2 && gd::search_smem_bytes(a, tile, false) > smem_cap; ++k) tile += k == 0 ? 3 : 6;
-  bool smem_grid = (int)grid_pad <= gd::max_smem_grid_bytes() && gd::search_smem_bytes(a, tile, true) <= smem_cap;
+  bool smem_grid = !gd::tile_get(tile).lean && (int)grid_pad <= gd::max_smem_grid_bytes() &&
+                   gd::search_smem_bytes(a, tile, true) <= smem_cap;
   if (!smem_grid && gd::search_smem_bytes(a, tile, false) > smem_cap)
     return nfail(GD_EINVAL, "tile %d needs more shared memory than a block has", tile);
   gd::LaunchCfg cfg;

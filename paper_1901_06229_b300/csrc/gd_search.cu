@@ -690,8 +690,8 @@ __device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
   return true;
 }
 
-template <int S, bool SG>
-__global__ void __launch_bounds__(512) search_kernel(const __grid_constant__ SearchArgs a) {
+template <int S, bool SG, bool LEAN>
+__global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 4 : 1) search_kernel(const __grid_constant__ SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* sg = nullptr;
@@ -979,9 +979,9 @@ __global__ void items_kernel(const int32_t* order, const int32_t* cnt, const int
   }
 }
 
-template <int S, bool SG>
+template <int S, bool SG, bool LEAN>
 cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, LaunchCfg* cfg) {
-  auto k = search_kernel<S, SG>;
+  auto k = search_kernel<S, SG, LEAN>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -999,8 +999,12 @@ cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, Lau
   return cudaSuccess;
 }
 
-constexpr Tile kTiles[] = {{8, 1}, {8, 2}, {8, 4}, {4, 1}, {4, 2}, {4, 4},
-                           {16, 1}, {16, 2}, {16, 4}, {2, 1}, {2, 2}, {2, 4}};
+// ids 1..12: <= 128 registers, one block of up to 16 warps per SM with the grid staged;
+// ids 13..15: <= 64 registers (some spilled) for up to 32 warps per SM, grid through L1.
+constexpr Tile kTiles[] = {{8, 1, 0}, {8, 2, 0},  {8, 4, 0},  {4, 1, 0}, {4, 2, 0}, {4, 4, 0},
+                           {16, 1, 0}, {16, 2, 0}, {16, 4, 0}, {2, 1, 0}, {2, 2, 0}, {2, 4, 0},
+                           {8, 1, 1}, {8, 2, 1},  {4, 2, 1}};
+constexpr int kLean8x1 = 13;
 
 }  // namespace
 
@@ -1016,20 +1020,38 @@ size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
   return s;
 }
 
+int default_tile(const SearchArgs& a) {
+  const int two = a.A >= 64 ? 1 : 0;  // two angles per lane once there are 64 angles
+  // lean 8-warp blocks when four of them fit in an SM's 228 KB (1 KB reserved per block)
+  if (4 * (search_smem_bytes(a, kLean8x1 + two, false) + 1024) <= 228 * 1024) return kLean8x1 + two;
+  // else the wide 8-warp tile, giving up warps (8 -> 4 -> 2, same slots) until one block fits
+  int t = 1 + two;
+  for (int k = 0; k < 2 && search_smem_bytes(a, t, false) > 227 * 1024; ++k) t += k == 0 ? 3 : 6;
+  return t;
+}
+
 cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int num_sms, LaunchCfg* cfg) {
   const Tile t = tile_get(tile);
   const size_t smem = search_smem_bytes(a, tile, grid_in_smem);
+  if (t.lean) {
+    if (grid_in_smem) return cudaErrorInvalidConfiguration;
+    switch (t.slots) {
+      case 1: return plan_t<1, false, true>(a, t.warps, smem, num_sms, cfg);
+      case 2: return plan_t<2, false, true>(a, t.warps, smem, num_sms, cfg);
+      default: return plan_t<4, false, true>(a, t.warps, smem, num_sms, cfg);
+    }
+  }
   if (grid_in_smem) {
     switch (t.slots) {
-      case 1: return plan_t<1, true>(a, t.warps, smem, num_sms, cfg);
-      case 2: return plan_t<2, true>(a, t.warps, smem, num_sms, cfg);
-      default: return plan_t<4, true>(a, t.warps, smem, num_sms, cfg);
+      case 1: return plan_t<1, true, false>(a, t.warps, smem, num_sms, cfg);
+      case 2: return plan_t<2, true, false>(a, t.warps, smem, num_sms, cfg);
+      default: return plan_t<4, true, false>(a, t.warps, smem, num_sms, cfg);
     }
   }
   switch (t.slots) {
-    case 1: return plan_t<1, false>(a, t.warps, smem, num_sms, cfg);
-    case 2: return plan_t<2, false>(a, t.warps, smem, num_sms, cfg);
-    default: return plan_t<4, false>(a, t.warps, smem, num_sms, cfg);
+    case 1: return plan_t<1, false, false>(a, t.warps, smem, num_sms, cfg);
+    case 2: return plan_t<2, false, false>(a, t.warps, smem, num_sms, cfg);
+    default: return plan_t<4, false, false>(a, t.warps, smem, num_sms, cfg);
   }
 }
 

@@ -92,7 +92,7 @@ def load():
     L.gd_job_selection.argtypes = [vp, vp, vp, vp]
     L.gd_job_selection.restype = C.c_int
     L.gd_tile_count.argtypes = []
-    L.gd_tile_info.argtypes = [C.c_int, P(C.c_int), P(C.c_int)]
+    L.gd_tile_info.argtypes = [C.c_int, P(C.c_int), P(C.c_int), P(C.c_int)]
     L.gd_autotune.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), C.c_int, vp, P(C.c_int), P(C.c_float)]
     for f in EXPORTS:
         if f not in ("gd_last_error",):
@@ -356,11 +356,12 @@ def tile_count() -> int:
 
 
 def tile_info(tile: int):
-    w, s = C.c_int(), C.c_int()
-    st = load().gd_tile_info(int(tile), C.byref(w), C.byref(s))
+    """(warps per block, angles per lane, register budget per thread) of a tile id."""
+    w, s, r = C.c_int(), C.c_int(), C.c_int()
+    st = load().gd_tile_info(int(tile), C.byref(w), C.byref(s), C.byref(r))
     if st:
         raise GeoDockError(st, load().gd_last_error(None).decode())
-    return w.value, s.value
+    return w.value, s.value, r.value
 
 
 def dock(batch, pocket, params, device=0, debug=False, bumps=False, tile=0, stream=None) -> dict:

@@ -39,9 +39,10 @@ def test_library_exports_every_declared_function():
 
 
 def test_tiles():
-    assert gdk.tile_count() == 12
-    seen = {gdk.tile_info(t) for t in range(1, 13)}
-    assert len(seen) == 12
+    assert gdk.tile_count() == 15
+    seen = {gdk.tile_info(t) for t in range(1, 16)}
+    assert len(seen) == 15
+    assert {r for _, _, r in seen} == {64, 128}
     with pytest.raises(gdk.GeoDockError):
         gdk.tile_info(0)
 
