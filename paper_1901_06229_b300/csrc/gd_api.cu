@@ -602,16 +602,20 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.err = (int32_t*)(o + j->out.err);
   a.bump_bits = j->debug_bumps ? (uint8_t*)(s + j->scr.bump) : nullptr;
   a.nmax = nmax;
-  a.near_cap = std::min(4096, std::max(512, (8 * nmax + 15) / 16 * 16));
+  a.mask_words = 1;
   a.rmax = 1;
   a.emax = 1;
   for (int i = 0; i < L; ++i) {
     int ne = 0;
-    for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) ne += rots[r].n_excl;
+    const int n = b->atom_off[i + 1] - b->atom_off[i];
+    for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) {
+      ne += rots[r].n_excl;
+      a.mask_words = std::max(a.mask_words, gd::step_mask_words(n, rots[r]));
+    }
     a.rmax = std::max(a.rmax, rot_off[i + 1] - rot_off[i]);
     a.emax = std::max(a.emax, ne);
   }
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax);
+  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.mask_words, a.rmax, a.emax);
   // tile (0: chosen from the batch's buffer sizes) and grid staging mode
   const size_t smem_cap = 227 * 1024;
   if (tile == 0) tile = gd::default_tile(a);

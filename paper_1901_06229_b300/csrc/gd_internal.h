@@ -25,6 +25,13 @@ struct alignas(16) RotDesc {
 };
 static_assert(sizeof(RotDesc) == 16, "RotDesc layout");
 
+// Words of one rotamer step's near-pair masks in a ligand of n atoms: one 32-bit word
+// per moving atom and per 32 static atoms.
+__host__ __device__ inline int step_mask_words(int n, const RotDesc& d) {
+  const int sub = (int)d.hi - (int)d.lo, f = d.comp ? n - sub : sub;
+  return f * ((n - f + 31) / 32);
+}
+
 struct PocketDev {
   const uint8_t* grid;   // cropped grid [cz][cy][cx]; cells outside the crop are 0
   int cx, cy, cz;        // crop extents (cells)
@@ -72,7 +79,7 @@ struct SearchArgs {
   // debug (may be null)
   uint8_t* bump_bits;         // [O * reps * A * Rt]
   int nmax;                   // largest ligand of the batch (per-warp buffer size)
-  int near_cap;               // capacity of a warp's near-pair list (multiple of 16)
+  int mask_words;             // largest step_mask_words of the batch (>= 1)
   int rmax, emax;             // largest rotamer / excluded-pair count of one ligand (>= 1)
   int warp_bytes;             // shared memory per warp (see warp_smem_bytes)
   unsigned long long* reach_tests;  // [L] (output) moving x static pairs checked by the reach filter
@@ -90,12 +97,12 @@ struct SearchArgs {
 // this margin can never be flagged by the per-angle test.
 constexpr float REACH_MARGIN = 0.01f;
 
-// Per-warp shared memory: X float4[nmax] | HR float2[nmax] | MOFF uint16[nmax+2] |
-// NEAR uint8[near_cap] | EXL uint16[emax] | RD RotDesc[rmax].  rmax / emax: the largest
-// rotamer count and excluded-pair count of one ligand in the batch (at least 1).
-__host__ __device__ inline int warp_smem_bytes(int nmax, int near_cap, int rmax, int emax) {
+// Per-warp shared memory: X float4[nmax] | HR float2[nmax] | MASK uint32[mask_words] |
+// EXL uint16[emax] | RD RotDesc[rmax].  rmax / emax: the largest rotamer count and
+// excluded-pair count of one ligand in the batch (at least 1).
+__host__ __device__ inline int warp_smem_bytes(int nmax, int mask_words, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
-  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(near_cap) + a16(2 * emax) + 16 * rmax;
+  return a16(16 * nmax) + a16(8 * nmax) + a16(4 * mask_words) + a16(2 * emax) + 16 * rmax;
 }
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };

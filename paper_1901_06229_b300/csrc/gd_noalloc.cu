@@ -379,17 +379,22 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.work = (unsigned long long*)(d + o_work);
   a.bump_bits = nullptr;
   a.nmax = nmax;
-  a.near_cap = nmax * 8 < 512 ? 512 : (nmax * 8 > 4096 ? 4096 : (8 * nmax + 15) / 16 * 16);
+  a.mask_words = 1;
   a.rmax = 1;
   a.emax = 1;
   for (int i = 0; i < L; ++i) {
     int ne = 0;
     const RotDesc* rr = (const RotDesc*)(h + o_rots);
-    for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) ne += rr[r].n_excl;
+    const int n = b->atom_off[i + 1] - b->atom_off[i];
+    for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) {
+      ne += rr[r].n_excl;
+      const int mw = gd::step_mask_words(n, rr[r]);
+      a.mask_words = mw > a.mask_words ? mw : a.mask_words;
+    }
     a.rmax = rot_off[i + 1] - rot_off[i] > a.rmax ? rot_off[i + 1] - rot_off[i] : a.rmax;
     a.emax = ne > a.emax ? ne : a.emax;
   }
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax);
+  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.mask_words, a.rmax, a.emax);
 
   const int tile = p->tile > 0 ? p->tile : gd::default_tile(a);
   const size_t smem_cap = 227 * 1024;

@@ -306,24 +306,21 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
 struct WarpMem {
   float4* X;       // current pose, preorder
   float2* HR;      // (height along the bond axis, distance from it) per atom
-  uint16_t* MOFF;  // near-list offset per moving atom (in sweep order)
-  uint8_t* NEAR;   // static atoms that can come within reach of each moving atom
+  uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
   RotDesc* RD;     // the current ligand's rotamer descriptors
   uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
   const float2* CS;  // (cos, sin) of every angle, shared by the block
 };
 
-__device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int near_cap, int rmax, int emax) {
+__device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int mask_words, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
   WarpMem w;
   w.X = reinterpret_cast<float4*>(base);
   base += a16(16 * nmax);
   w.HR = reinterpret_cast<float2*>(base);
   base += a16(8 * nmax);
-  w.MOFF = reinterpret_cast<uint16_t*>(base);
-  base += a16(2 * (nmax + 2));
-  w.NEAR = base;
-  base += a16(near_cap);
+  w.MASK = reinterpret_cast<uint32_t*>(base);
+  base += a16(4 * mask_words);
   w.EXL = reinterpret_cast<uint16_t*>(base);
   base += a16(2 * emax);
   w.RD = reinterpret_cast<RotDesc*>(base);
@@ -335,9 +332,12 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int n
 // axis: height h_a along it, radius rho_a.  For a static atom b the distance over the
 // whole turn is at least sqrt((h_a - h_b)^2 + (rho_a - rho_b)^2), so only pairs below
 // bump_dist + margin (and not excluded by graph distance) need per-angle tests.
-// Builds MOFF/NEAR; returns the number of near pairs (> near_cap: list unusable).
-__device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
-                          float4 xp, float ux, float uy, float uz, int lane, unsigned long long& reach) {
+// Moving atoms are numbered ia in sweep order, static atoms k in static order (both
+// ascending preorder ids); lane t of chunk c tests static atom 32 c + t against every
+// moving atom and the warp's ballot is the mask word MASK[ia * nch + c].  The rotamer's
+// excluded pairs are then cleared from the masks.  Returns the number of near pairs.
+__device__ int build_masks(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
+                           float4 xp, float ux, float uy, float uz, int lane, unsigned long long& reach) {
   for (int i = lane; i < n; i += 32) {
     const float4 v = w.X[i];
     const float rx = __fsub_rn(v.x, xp.x), ry = __fsub_rn(v.y, xp.y), rz = __fsub_rn(v.z, xp.z);
@@ -346,65 +346,74 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
     w.HR[i] = make_float2(h, __fsqrt_rn(fmaxf(__fmaf_rn(-h, h, r2), 0.0f)));
   }
   __syncwarp();
-  int m0a, m0b, m1a, m1b, s0a, s0b, s1a, s1b;
+  int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
   if (rd.comp) {
     m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
-    s0a = rd.lo; s0b = rd.hi; s1a = 0; s1b = 0;
+    s0a = rd.lo; s0b = rd.hi; s1a = 0;
   } else {
     m0a = rd.lo; m0b = rd.hi; m1a = 0; m1b = 0;
-    s0a = 0; s0b = rd.lo; s1a = rd.hi; s1b = n;
+    s0a = 0; s0b = rd.lo; s1a = rd.hi;
   }
-  const int n_static = (s0b - s0a) + (s1b - s1a);
-  const int n_excl = rd.n_excl;
-  int ex = 0, cnt = 0, ia = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int seg = 0; seg < 2; ++seg) {
-    const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
-    for (int ai = ma; ai < mb; ++ai, ++ia) {
-      if (lane == 0) w.MOFF[ia] = (uint16_t)(cnt < 65535 ? cnt : 65535);
-      const float2 ha = w.HR[ai];
-      int ex_end = ex;
-      while (ex_end < n_excl && (int)(excl[ex_end] & 0xFF) == ai) ++ex_end;
-      for (int t = 0; t < n_static; t += 32) {
-        const int k = t + lane;
-        bool near = false;
-        int b = 0;
-        if (k < n_static) {
-          b = k < s0b - s0a ? s0a + k : s1a + (k - (s0b - s0a));
-          const float2 hb = w.HR[b];
-          const float dh = __fsub_rn(ha.x, hb.x), dr = __fsub_rn(ha.y, hb.y);
-          near = __fmaf_rn(dh, dh, __fmul_rn(dr, dr)) < a.reach2;
-          for (int e = ex; e < ex_end && near; ++e)
-            if ((int)(excl[e] >> 8) == b) near = false;
-        }
-        const unsigned m = __ballot_sync(FULL, near);
-        const int pos = cnt + __popc(m & lt);
-        if (near && pos < a.near_cap) w.NEAR[pos] = (uint8_t)b;
-        cnt += __popc(m);
+  const int ns0 = s0b - s0a;
+  const int n_moving = (m0b - m0a) + (m1b - m1a), n_static = n - n_moving;
+  const int nch = (n_static + 31) >> 5;
+  int near = 0;
+  for (int c = 0; c < nch; ++c) {
+    const int k = (c << 5) + lane;
+    const bool real = k < n_static;
+    float2 hb = make_float2(3.0e18f, 0.f);  // lanes past the last static atom never pass
+    if (real) hb = w.HR[k < ns0 ? s0a + k : s1a + (k - ns0)];
+    uint32_t* col = w.MASK + c;
+    for (int seg = 0; seg < 2; ++seg) {
+      const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
+      for (int ai = ma; ai < mb; ++ai, col += nch) {
+        const float2 ha = w.HR[ai];
+        const float dh = __fsub_rn(ha.x, hb.x), dr = __fsub_rn(ha.y, hb.y);
+        const unsigned mk = __ballot_sync(FULL, __fmaf_rn(dh, dh, __fmul_rn(dr, dr)) < a.reach2);
+        if (lane == 0) *col = mk;
+        near += __popc(mk);
       }
-      ex = ex_end;
     }
   }
-  if (lane == 0) w.MOFF[ia] = (uint16_t)(cnt < 65535 ? cnt : 65535);
-  reach += (unsigned long long)ia * (unsigned long long)n_static;
   __syncwarp();
-  return cnt;
+  int cleared = 0;
+  for (int e = lane; e < rd.n_excl; e += 32) {
+    const int av = excl[e] & 0xFF, bv = excl[e] >> 8;
+    int ia, k;
+    if (rd.comp) {
+      ia = av < rd.lo ? av : av - (rd.hi - rd.lo);
+      k = bv - rd.lo;
+    } else {
+      ia = av - rd.lo;
+      k = bv < rd.lo ? bv : bv - (rd.hi - rd.lo);
+    }
+    const unsigned bit = 1u << (k & 31);
+    cleared += (atomicAnd(w.MASK + ia * nch + (k >> 5), ~bit) & bit) ? 1 : 0;
+  }
+  near -= __reduce_add_sync(FULL, cleared);
+  reach += (unsigned long long)n_moving * (unsigned long long)n_static;
+  __syncwarp();
+  return near;
 }
 
-// Every angle of one rotamer step, bump tests restricted to the near list.
+// Every angle of one rotamer step, bump tests restricted to the near pairs of the
+// step's masks (n_near of them).
 template <int S, bool SG>
 __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
                                    const RotDesc& rd, float4 xp, float ux, float uy, float uz, int s_static,
-                                   int lane, unsigned long long& pairs, uint8_t* dbg) {
+                                   int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
-  int m0a, m0b, m1a, m1b;
+  int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
   if (rd.comp) {
     m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
+    s0a = rd.lo; s0b = rd.hi; s1a = 0;
   } else {
     m0a = rd.lo; m0b = rd.hi; m1a = 0; m1b = 0;
+    s0a = 0; s0b = rd.lo; s1a = rd.hi;
   }
+  const int ns0 = s0b - s0a;
+  const int nch = (n - (m0b - m0a) - (m1b - m1a) + 31) >> 5;
   const int passes = (a.A + 32 * S - 1) / (32 * S);
-  const unsigned n_near = w.MOFF[(m0b - m0a) + (m1b - m1a)];
   unsigned best = 0;
   for (int pass = 0; pass < passes; ++pass) {
     Rot3 R[S];
@@ -417,12 +426,12 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
       R[j] = rodrigues(ux, uy, uz, cs.x, cs.y, xp);
       sc[j] = s_static;
       mind[j] = 3.0e38f;
-      if (kk[j] < a.A) pairs += n_near;
+      if (kk[j] < a.A) pairs += (unsigned)n_near;
     }
-    int ia = 0;
+    const uint32_t* row = w.MASK;
     for (int seg = 0; seg < 2; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
-      for (int ai = ma; ai < mb; ++ai, ++ia) {
+      for (int ai = ma; ai < mb; ++ai, row += nch) {
         const float4 xa = X[ai];
         float xr[S][3];
 #pragma unroll
@@ -430,15 +439,19 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
           rot_apply(R[j], xa.x, xa.y, xa.z, xr[j][0], xr[j][1], xr[j][2]);
           sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
         }
-        const int e1 = w.MOFF[ia + 1];
-        for (int e = w.MOFF[ia]; e < e1; ++e) {
-          const float4 xb = X[w.NEAR[e]];
+        for (int c = 0; c < nch; ++c) {
+          unsigned mk = row[c];
+          while (mk) {
+            const int k = (c << 5) + __ffs(mk) - 1;
+            mk &= mk - 1;
+            const float4 xb = X[k < ns0 ? s0a + k : s1a + (k - ns0)];
 #pragma unroll
-          for (int j = 0; j < S; ++j) {
-            const float dx = __fsub_rn(xr[j][0], xb.x);
-            const float dy = __fsub_rn(xr[j][1], xb.y);
-            const float dz = __fsub_rn(xr[j][2], xb.z);
-            mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+            for (int j = 0; j < S; ++j) {
+              const float dx = __fsub_rn(xr[j][0], xb.x);
+              const float dy = __fsub_rn(xr[j][1], xb.y);
+              const float dz = __fsub_rn(xr[j][2], xb.z);
+              mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+            }
           }
         }
       }
@@ -620,9 +633,10 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
       unsigned key;
       const float4 xp = X[rd.p];
-      if (a.use_filter && build_near(a, w, excl, n, rd, xp, ux, uy, uz, lane, reach) <= a.near_cap)
-        key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, lane, pairs, dbg);
-      else
+      if (a.use_filter) {
+        const int n_near = build_masks(a, w, excl, n, rd, xp, ux, uy, uz, lane, reach);
+        key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, n_near, lane, pairs, dbg);
+      } else
         key = eval_step<S, SG>(a, sg, X, w.CS, excl, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
@@ -711,7 +725,7 @@ __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 4 : 1) search_kernel(
   for (int k = threadIdx.x; k < a.A; k += blockDim.x) cs[k] = angle_entry(k, a.A);
   off += ((size_t)a.A * 8 + 15) / 16 * 16;
   __syncthreads();
-  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.near_cap, a.rmax, a.emax);
+  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.mask_words, a.rmax, a.emax);
   w.CS = cs;
   // items: every (ligand, restart) in queue order, or an explicit list of rows li*O + o
   const unsigned long long n_items = a.items ? (unsigned long long)*a.n_items_dev : (unsigned long long)a.n_items;
@@ -1014,7 +1028,7 @@ int max_smem_grid_bytes() { return 200 * 1024; }
 
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
   const Tile t = tile_get(tile);
-  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.near_cap, a.rmax, a.emax) +
+  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.mask_words, a.rmax, a.emax) +
              ((size_t)a.A * 8 + 15) / 16 * 16;
   if (grid_in_smem) s += (size_t)a.pk.bytes_pad + 16;
   return s;
