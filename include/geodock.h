@@ -58,6 +58,9 @@ typedef int gd_status;
 #define GD_FLAG_DEBUG_BUMPS 2   /* also keep per-candidate bump bits (bump_bits) */
 #define GD_FLAG_NO_FILTER 4     /* test every moving x static pair at every angle (no reach
                                    filter); results are identical, only slower */
+#define GD_FLAG_MASK_SWEEP 8    /* sweep every step's angles over the reach filter's bit masks
+                                   instead of its compacted near list (the path a step takes
+                                   when the list overflows); results are identical */
 
 typedef struct gd_ctx gd_ctx;
 typedef struct gd_pocket gd_pocket;

@@ -408,7 +408,7 @@ std::string signature(const gd_pocket* pk, const gd_search_params* p, int nmax, 
   char b[256];
   snprintf(b, sizeof b, "O%d_A%d_r%d_n%d_g%d_%dx%dx%d_f%d_s%d", p->n_alpha * p->n_beta * p->n_gamma, p->n_angles,
            p->repetitions, (nmax + 31) / 32, smem ? 1 : 0, pk->dev.cx, pk->dev.cy, pk->dev.cz,
-           (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1, p->rigid_span);
+           (p->flags & GD_FLAG_NO_FILTER) ? 0 : ((p->flags & GD_FLAG_MASK_SWEEP) ? 2 : 1), p->rigid_span);
   return b;
 }
 
@@ -578,6 +578,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.thr2 = p->bump_dist * p->bump_dist;
   a.reach2 = (p->bump_dist + gd::REACH_MARGIN) * (p->bump_dist + gd::REACH_MARGIN);
   a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
+  a.mask_sweep = (p->flags & GD_FLAG_MASK_SWEEP) ? 1 : 0;
   char* o = (char*)j->d_out;
   a.best_score = (uint32_t*)(o + j->out.best_score);
   a.best_orient = (int32_t*)(o + j->out.best_orient);

@@ -61,6 +61,7 @@ struct SearchArgs {
   float thr2;                 // bump_dist^2
   float reach2;               // (bump_dist + REACH_MARGIN)^2: pairs farther apart at every angle skip the test
   int use_filter;             // 1: per-rotamer reach filter; 0: test every moving x static pair
+  int mask_sweep;             // 1: always sweep the filter's masks, never its near list
   // outputs
   uint32_t* best_score;       // [L]
   int32_t* best_orient;       // [L]
@@ -97,12 +98,13 @@ struct SearchArgs {
 // this margin can never be flagged by the per-angle test.
 constexpr float REACH_MARGIN = 0.01f;
 
-// Per-warp shared memory: X float4[nmax] | HR float2[nmax] | MASK uint32[mask_words] |
-// EXL uint16[emax] | RD RotDesc[rmax].  rmax / emax: the largest rotamer count and
-// excluded-pair count of one ligand in the batch (at least 1).
+// Per-warp shared memory: X float4[nmax] | HR float2[nmax] (later the near list,
+// uint8[8 nmax]) | MOFF uint16[nmax+2] | MASK uint32[mask_words] | EXL uint16[emax] |
+// RD RotDesc[rmax].  rmax / emax: the largest rotamer count and excluded-pair count of
+// one ligand in the batch (at least 1).
 __host__ __device__ inline int warp_smem_bytes(int nmax, int mask_words, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
-  return a16(16 * nmax) + a16(8 * nmax) + a16(4 * mask_words) + a16(2 * emax) + 16 * rmax;
+  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(4 * mask_words) + a16(2 * emax) + 16 * rmax;
 }
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };

@@ -362,6 +362,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.thr2 = p->bump_dist * p->bump_dist;
   a.reach2 = (p->bump_dist + gd::REACH_MARGIN) * (p->bump_dist + gd::REACH_MARGIN);
   a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
+  a.mask_sweep = (p->flags & GD_FLAG_MASK_SWEEP) ? 1 : 0;
   a.best_score = (uint32_t*)(d + o_score);
   a.best_orient = (int32_t*)(d + o_orient);
   a.best_angle = (int16_t*)(d + o_angle);

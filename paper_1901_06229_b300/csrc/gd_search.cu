@@ -306,6 +306,8 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
 struct WarpMem {
   float4* X;       // current pose, preorder
   float2* HR;      // (height along the bond axis, distance from it) per atom
+  uint8_t* NEAR;   // near static atoms of each moving atom (overwrites HR once it is dead)
+  uint16_t* MOFF;  // NEAR offset per moving atom (sweep order), n_moving + 1 entries
   uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
   RotDesc* RD;     // the current ligand's rotamer descriptors
   uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
@@ -318,7 +320,10 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int m
   w.X = reinterpret_cast<float4*>(base);
   base += a16(16 * nmax);
   w.HR = reinterpret_cast<float2*>(base);
+  w.NEAR = base;
   base += a16(8 * nmax);
+  w.MOFF = reinterpret_cast<uint16_t*>(base);
+  base += a16(2 * (nmax + 2));
   w.MASK = reinterpret_cast<uint32_t*>(base);
   base += a16(4 * mask_words);
   w.EXL = reinterpret_cast<uint16_t*>(base);
@@ -335,8 +340,10 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int m
 // Moving atoms are numbered ia in sweep order, static atoms k in static order (both
 // ascending preorder ids); lane t of chunk c tests static atom 32 c + t against every
 // moving atom and the warp's ballot is the mask word MASK[ia * nch + c].  The rotamer's
-// excluded pairs are then cleared from the masks.  Returns the number of near pairs.
-__device__ int build_masks(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
+// excluded pairs are then cleared from the masks, and the masks are compacted into a
+// near list per moving atom (NEAR / MOFF, at most 8 nmax entries: the bytes of HR).
+// Returns the number of near pairs; above 8 nmax only the masks are usable.
+__device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
                            float4 xp, float ux, float uy, float uz, int lane, unsigned long long& reach) {
   for (int i = lane; i < n; i += 32) {
     const float4 v = w.X[i];
@@ -357,7 +364,6 @@ __device__ int build_masks(const SearchArgs& a, const WarpMem& w, const uint16_t
   const int ns0 = s0b - s0a;
   const int n_moving = (m0b - m0a) + (m1b - m1a), n_static = n - n_moving;
   const int nch = (n_static + 31) >> 5;
-  int near = 0;
   for (int c = 0; c < nch; ++c) {
     const int k = (c << 5) + lane;
     const bool real = k < n_static;
@@ -371,12 +377,10 @@ __device__ int build_masks(const SearchArgs& a, const WarpMem& w, const uint16_t
         const float dh = __fsub_rn(ha.x, hb.x), dr = __fsub_rn(ha.y, hb.y);
         const unsigned mk = __ballot_sync(FULL, __fmaf_rn(dh, dh, __fmul_rn(dr, dr)) < a.reach2);
         if (lane == 0) *col = mk;
-        near += __popc(mk);
       }
     }
   }
   __syncwarp();
-  int cleared = 0;
   for (int e = lane; e < rd.n_excl; e += 32) {
     const int av = excl[e] & 0xFF, bv = excl[e] >> 8;
     int ia, k;
@@ -387,19 +391,109 @@ __device__ int build_masks(const SearchArgs& a, const WarpMem& w, const uint16_t
       ia = av - rd.lo;
       k = bv < rd.lo ? bv : bv - (rd.hi - rd.lo);
     }
-    const unsigned bit = 1u << (k & 31);
-    cleared += (atomicAnd(w.MASK + ia * nch + (k >> 5), ~bit) & bit) ? 1 : 0;
+    atomicAnd(w.MASK + ia * nch + (k >> 5), ~(1u << (k & 31)));
   }
-  near -= __reduce_add_sync(FULL, cleared);
+  __syncwarp();
+  // compaction: lane t takes mask word w0 + t (row ia = word / nch, chunk c); an
+  // exclusive scan of the words' bit counts gives each word's first NEAR slot
+  const int words = n_moving * nch, cap = 8 * a.nmax;
+  const float inv_nch = __frcp_rn((float)nch);  // (wi + 1/2) / nch is >= 1/16 from an integer
+  int base = 0;
+  for (int w0 = 0; w0 < words; w0 += 32) {
+    const int wi = w0 + lane;
+    unsigned mk = wi < words ? w.MASK[wi] : 0u;
+    const int cnt = __popc(mk);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, off);
+      if (lane >= off) incl += v;
+    }
+    int pos = base + incl - cnt;
+    const int ia = __float2int_rz(__fmul_rn(__fadd_rn((float)wi, 0.5f), inv_nch));
+    const int c = wi - ia * nch;
+    if (wi < words && c == 0) w.MOFF[ia] = (uint16_t)(pos < 65535 ? pos : 65535);
+    while (mk) {
+      const int k = (c << 5) + __ffs(mk) - 1;
+      mk &= mk - 1;
+      if (pos < cap) w.NEAR[pos] = (uint8_t)(k < ns0 ? s0a + k : s1a + (k - ns0));
+      ++pos;
+    }
+    base += __shfl_sync(FULL, incl, 31);
+  }
+  if (lane == 0) w.MOFF[n_moving] = (uint16_t)(base < 65535 ? base : 65535);
   reach += (unsigned long long)n_moving * (unsigned long long)n_static;
   __syncwarp();
-  return near;
+  return base;
+}
+
+// Every angle of one rotamer step, bump tests restricted to the near list.
+template <int S, bool SG>
+__device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
+                                   const RotDesc& rd, float4 xp, float ux, float uy, float uz, int s_static,
+                                   int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
+  const float4* X = w.X;
+  int m0a, m0b, m1a, m1b;
+  if (rd.comp) {
+    m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
+  } else {
+    m0a = rd.lo; m0b = rd.hi; m1a = 0; m1b = 0;
+  }
+  const int passes = (a.A + 32 * S - 1) / (32 * S);
+  unsigned best = 0;
+  for (int pass = 0; pass < passes; ++pass) {
+    Rot3 R[S];
+    int kk[S], sc[S];
+    float mind[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      kk[j] = lane + 32 * (pass * S + j);
+      const float2 cs = w.CS[kk[j] < a.A ? kk[j] : 0];
+      R[j] = rodrigues(ux, uy, uz, cs.x, cs.y, xp);
+      sc[j] = s_static;
+      mind[j] = 3.0e38f;
+      if (kk[j] < a.A) pairs += (unsigned)n_near;
+    }
+    int ia = 0;
+    for (int seg = 0; seg < 2; ++seg) {
+      const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
+      for (int ai = ma; ai < mb; ++ai, ++ia) {
+        const float4 xa = X[ai];
+        float xr[S][3];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          rot_apply(R[j], xa.x, xa.y, xa.z, xr[j][0], xr[j][1], xr[j][2]);
+          sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
+        }
+        const int e1 = w.MOFF[ia + 1];
+        for (int e = w.MOFF[ia]; e < e1; ++e) {
+          const float4 xb = X[w.NEAR[e]];
+#pragma unroll
+          for (int j = 0; j < S; ++j) {
+            const float dx = __fsub_rn(xr[j][0], xb.x);
+            const float dy = __fsub_rn(xr[j][1], xb.y);
+            const float dz = __fsub_rn(xr[j][2], xb.z);
+            mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+      if (kk[j] < a.A) {
+        const bool bump = mind[j] < a.thr2;
+        const unsigned key = bump ? 0u : (((unsigned)(sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
+        best = key > best ? key : best;
+        if (dbg) dbg[kk[j]] = bump ? 1 : 0;
+      }
+  }
+  return __reduce_max_sync(FULL, best);
 }
 
 // Every angle of one rotamer step, bump tests restricted to the near pairs of the
-// step's masks (n_near of them).
+// step's masks (n_near of them); used when the near list overflowed.
 template <int S, bool SG>
-__device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
+__device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
                                    const RotDesc& rd, float4 xp, float ux, float uy, float uz, int s_static,
                                    int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
@@ -634,8 +728,11 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       unsigned key;
       const float4 xp = X[rd.p];
       if (a.use_filter) {
-        const int n_near = build_masks(a, w, excl, n, rd, xp, ux, uy, uz, lane, reach);
-        key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, n_near, lane, pairs, dbg);
+        const int n_near = build_near(a, w, excl, n, rd, xp, ux, uy, uz, lane, reach);
+        if (n_near <= 8 * a.nmax && !a.mask_sweep)
+          key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, n_near, lane, pairs, dbg);
+        else
+          key = eval_step_masks<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, n_near, lane, pairs, dbg);
       } else
         key = eval_step<S, SG>(a, sg, X, w.CS, excl, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;

@@ -23,17 +23,18 @@ def ctx():
     c.close()
 
 
-def run(ctx, w_pocket, batch, params, debug=True, bumps=True, tile=0, no_filter=False):
+def run(ctx, w_pocket, batch, params, debug=True, bumps=True, tile=0, no_filter=False, mask_sweep=False):
     pk = ctx.load_pocket(w_pocket)
-    job = ctx.dock_batch(pk, batch, params, debug=debug, bumps=bumps, tile=tile, no_filter=no_filter)
+    job = ctx.dock_batch(pk, batch, params, debug=debug, bumps=bumps, tile=tile, no_filter=no_filter,
+                         mask_sweep=mask_sweep)
     out = job.fetch()
     job.free()
     pk.free()
     return out
 
 
-def full_compare(ctx, pocket, batch, params, tile=0, min_exact=1, no_filter=False):
-    gpu = run(ctx, pocket, batch, params, tile=tile, no_filter=no_filter)
+def full_compare(ctx, pocket, batch, params, tile=0, min_exact=1, no_filter=False, mask_sweep=False):
+    gpu = run(ctx, pocket, batch, params, tile=tile, no_filter=no_filter, mask_sweep=mask_sweep)
     orc = oracle.dock_batch(batch, pocket, params, n_threads=8, debug=True)
     st = compare_debug(gpu, orc, batch, params)
     print(dict(st))
@@ -176,12 +177,53 @@ def test_reach_filter_is_exact(ctx, which):
             params = synth.SearchParams(2, 2, 2, 64, bump_dist=2.5)
     a = run(ctx, pocket, batch, params, no_filter=False)
     b = run(ctx, pocket, batch, params, no_filter=True)
+    m = run(ctx, pocket, batch, params, mask_sweep=True)
     for k in a:
+        np.testing.assert_array_equal(a[k], m[k], err_msg=f"mask sweep: {k}")  # counters too
         if k in ("pair_tests", "reach_tests"):
             continue
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
     assert a["pair_tests"].sum() < b["pair_tests"].sum()
     assert b["reach_tests"].sum() == 0 and a["reach_tests"].sum() > 0
+
+
+@pytest.mark.parametrize("tile", [9, 14])
+def test_mask_sweep_matches_oracle(ctx, tile):
+    """The overflow path of the reach filter (sweeping its bit masks) against the oracle,
+    on ligands whose static side spans several 32-atom mask words."""
+    w = synth.workload_large(3)
+    full_compare(ctx, w.pocket, w.batch, synth.SearchParams(2, 2, 2, 64), tile=tile, min_exact=4, mask_sweep=True)
+
+
+def _near_pairs(x, lig, rb, params):
+    """Reach-filter count of rotamer bond rb at coordinates x (FP64, on the CPU): moving x
+    static pairs at bond separation >= min_bond_sep whose (h, rho) about the bond axis
+    lie within bump_dist + 0.01 A."""
+    mv, p, q, dist = oracle.fragment(len(x), lig.bonds, rb)
+    u = (x[q] - x[p]) / np.linalg.norm(x[q] - x[p])
+    r = x - x[p]
+    h = r @ u
+    rho = np.sqrt(np.maximum((r * r).sum(1) - h * h, 0.0))
+    A, B = np.nonzero(mv)[0], np.nonzero(~mv)[0]
+    d2 = (h[A, None] - h[None, B]) ** 2 + (rho[A, None] - rho[None, B]) ** 2
+    return int(((d2 < (params.bump_dist + 0.01) ** 2) & (dist[np.ix_(A, B)] >= params.min_bond_sep)).sum())
+
+
+def test_near_list_overflow_takes_the_mask_sweep(ctx):
+    """A step whose near pairs exceed the list (8 x n_max) sweeps the bit masks instead:
+    results equal the forced mask sweep and the oracle."""
+    lig = synth.gen_ligand(synth.SplitMix64(synth.ligand_seed(4343, 96)), 96, 12)
+    small = synth.gen_ligand(synth.SplitMix64(synth.ligand_seed(4343, 40)), 40, 5)
+    batch, pocket = synth.pack([lig, small]), textured_pocket()
+    params = synth.SearchParams(2, 2, 2, 32, bump_dist=3.5)
+    # the first step of every restart starts from a rigid motion of the input pose
+    x0 = oracle.place(lig.xyz, 0, params, pocket)
+    assert _near_pairs(x0, lig, int(lig.rot_bond[0]), params) > 8 * 96 + 100
+    a = run(ctx, pocket, batch, params)
+    m = run(ctx, pocket, batch, params, mask_sweep=True)
+    for k in a:
+        np.testing.assert_array_equal(a[k], m[k], err_msg=k)
+    full_compare(ctx, pocket, batch, params, min_exact=1)
 
 
 def test_empty_batch(ctx):
