@@ -604,6 +604,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.bump_bits = j->debug_bumps ? (uint8_t*)(s + j->scr.bump) : nullptr;
   a.nmax = nmax;
   a.mask_words = 1;
+  a.fmax = 1;
   a.rmax = 1;
   a.emax = 1;
   for (int i = 0; i < L; ++i) {
@@ -612,11 +613,12 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
     for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) {
       ne += rots[r].n_excl;
       a.mask_words = std::max(a.mask_words, gd::step_mask_words(n, rots[r]));
+      a.fmax = std::max(a.fmax, gd::frag_atoms(n, rots[r]));
     }
     a.rmax = std::max(a.rmax, rot_off[i + 1] - rot_off[i]);
     a.emax = std::max(a.emax, ne);
   }
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.mask_words, a.rmax, a.emax);
+  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax);
   // tile (0: chosen from the batch's buffer sizes) and grid staging mode
   const size_t smem_cap = 227 * 1024;
   if (tile == 0) tile = gd::default_tile(a);

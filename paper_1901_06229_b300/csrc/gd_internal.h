@@ -81,6 +81,7 @@ struct SearchArgs {
   uint8_t* bump_bits;         // [O * reps * A * Rt]
   int nmax;                   // largest ligand of the batch (per-warp buffer size)
   int mask_words;             // largest step_mask_words of the batch (>= 1)
+  int fmax;                   // largest rotating fragment of the batch (>= 1)
   int rmax, emax;             // largest rotamer / excluded-pair count of one ligand (>= 1)
   int warp_bytes;             // shared memory per warp (see warp_smem_bytes)
   unsigned long long* reach_tests;  // [L] (output) moving x static pairs checked by the reach filter
@@ -99,12 +100,20 @@ struct SearchArgs {
 constexpr float REACH_MARGIN = 0.01f;
 
 // Per-warp shared memory: X float4[nmax] | HR float2[nmax] (later the near list,
-// uint8[8 nmax]) | MOFF uint16[nmax+2] | MASK uint32[mask_words] | EXL uint16[emax] |
-// RD RotDesc[rmax].  rmax / emax: the largest rotamer count and excluded-pair count of
-// one ligand in the batch (at least 1).
-__host__ __device__ inline int warp_smem_bytes(int nmax, int mask_words, int rmax, int emax) {
+// uint8[8 nmax]) | MOFF uint16[nmax+2] | DP float4[fmax] | W2 float2[fmax] |
+// MASK uint32[mask_words] | EXL uint16[emax] | RD RotDesc[rmax].  fmax / rmax / emax:
+// the largest fragment, rotamer count and excluded-pair count of one ligand in the
+// batch (at least 1).
+__host__ __device__ inline int warp_smem_bytes(int nmax, int fmax, int mask_words, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
-  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(4 * mask_words) + a16(2 * emax) + 16 * rmax;
+  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(16 * fmax) + a16(8 * fmax) +
+         a16(4 * mask_words) + a16(2 * emax) + 16 * rmax;
+}
+
+// Atoms of a rotamer's rotating fragment in a ligand of n atoms.
+__host__ __device__ inline int frag_atoms(int n, const RotDesc& d) {
+  const int sub = (int)d.hi - (int)d.lo;
+  return d.comp ? n - sub : sub;
 }
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };

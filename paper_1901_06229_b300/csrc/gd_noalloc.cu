@@ -381,6 +381,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.bump_bits = nullptr;
   a.nmax = nmax;
   a.mask_words = 1;
+  a.fmax = 1;
   a.rmax = 1;
   a.emax = 1;
   for (int i = 0; i < L; ++i) {
@@ -391,11 +392,13 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
       ne += rr[r].n_excl;
       const int mw = gd::step_mask_words(n, rr[r]);
       a.mask_words = mw > a.mask_words ? mw : a.mask_words;
+      const int fa = gd::frag_atoms(n, rr[r]);
+      a.fmax = fa > a.fmax ? fa : a.fmax;
     }
     a.rmax = rot_off[i + 1] - rot_off[i] > a.rmax ? rot_off[i + 1] - rot_off[i] : a.rmax;
     a.emax = ne > a.emax ? ne : a.emax;
   }
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.mask_words, a.rmax, a.emax);
+  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax);
 
   const int tile = p->tile > 0 ? p->tile : gd::default_tile(a);
   const size_t smem_cap = 227 * 1024;

@@ -67,11 +67,36 @@ __device__ __forceinline__ void rot_apply(const Rot3& R, float x, float y, float
   oz = __fadd_rn(R.p[2], __fmaf_rn(R.m[6], dx, __fmaf_rn(R.m[7], dy, __fmul_rn(R.m[8], dz))));
 }
 
-// Angle theta_k = 2 pi k / A as (cos, sin), computed once per block into a table.
+// Angle theta_k = 2 pi k / A as (cos theta - 1, sin theta), computed once per block into
+// a table; cos - 1 = -2 sin^2(theta / 2) keeps its relative precision at small angles.
 __device__ __forceinline__ float2 angle_entry(int k, int A) {
-  float c, s;
+  float sh, ch, s, c;
+  sincospif(__fdiv_rn((float)k, (float)A), &sh, &ch);
   sincospif(__fdiv_rn(2.0f * (float)k, (float)A), &s, &c);
-  return make_float2(c, s);
+  return make_float2(__fmul_rn(-2.0f, __fmul_rn(sh, sh)), s);
+}
+
+// Rotation about the axis through p along the unit vector u (Rodrigues' formula split
+// about the axis): with d = x - p, h = d.u, d_perp = d - h u and w = u x d, the point
+// turned by theta is x + (cos theta - 1) d_perp + sin theta w.  axis_frame gives
+// (d_perp, w.x) in dp and (w.y, w.z) in w2, once per atom and rotamer step; turn is then
+// six FMAs per angle.  The search and the commit of a step share both functions.
+__device__ __forceinline__ void axis_frame(float x, float y, float z, float4 p, float ux, float uy, float uz,
+                                           float4& dp, float2& w2, float& h) {
+  const float dx = __fsub_rn(x, p.x), dy = __fsub_rn(y, p.y), dz = __fsub_rn(z, p.z);
+  h = __fmaf_rn(dx, ux, __fmaf_rn(dy, uy, __fmul_rn(dz, uz)));
+  dp.x = __fmaf_rn(-h, ux, dx);
+  dp.y = __fmaf_rn(-h, uy, dy);
+  dp.z = __fmaf_rn(-h, uz, dz);
+  dp.w = __fmaf_rn(uy, dz, -__fmul_rn(uz, dy));
+  w2.x = __fmaf_rn(uz, dx, -__fmul_rn(ux, dz));
+  w2.y = __fmaf_rn(ux, dy, -__fmul_rn(uy, dx));
+}
+
+__device__ __forceinline__ void turn(float4 x, float4 dp, float2 w2, float2 cs, float& ox, float& oy, float& oz) {
+  ox = __fmaf_rn(cs.y, dp.w, __fmaf_rn(cs.x, dp.x, x.x));
+  oy = __fmaf_rn(cs.y, w2.x, __fmaf_rn(cs.x, dp.y, x.y));
+  oz = __fmaf_rn(cs.y, w2.y, __fmaf_rn(cs.x, dp.z, x.z));
 }
 
 // Grid cell under a point (pocket-centred coordinates); 0 outside the cropped box.
@@ -155,14 +180,17 @@ __device__ __forceinline__ int frag_size(const RotDesc& rd, int n) {
 
 // Commit the winning rotation to the fragment (same arithmetic as the candidate).
 __device__ void commit(float4* X, int n, const RotDesc& rd, float ux, float uy, float uz, float2 cs, int lane) {
-  const Rot3 R = rodrigues(ux, uy, uz, cs.x, cs.y, X[rd.p]);
+  const float4 xp = X[rd.p];
   __syncwarp();
   const int f = frag_size(rd, n);
   for (int i = lane; i < f; i += 32) {
     const int t = frag_atom(rd, i);
     const float4 v = X[t];
-    float x, y, z;
-    rot_apply(R, v.x, v.y, v.z, x, y, z);
+    float4 dp;
+    float2 w2;
+    float h, x, y, z;
+    axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
+    turn(v, dp, w2, cs, x, y, z);
     X[t] = make_float4(x, y, z, 0.f);
   }
   __syncwarp();
@@ -210,13 +238,71 @@ __device__ __forceinline__ void min_d2_range(const float4* X, int b0, int b1, co
   }
 }
 
+struct WarpMem {
+  float4* X;       // current pose, preorder
+  float2* HR;      // (height along the bond axis, distance from it) per atom
+  float4* DP;      // per moving atom (sweep order): d_perp and (u x d).x of axis_frame
+  float2* W2;      // per moving atom: (u x d).y, (u x d).z
+  uint8_t* NEAR;   // near static atoms of each moving atom (overwrites HR once it is dead)
+  uint16_t* MOFF;  // NEAR offset per moving atom (sweep order), n_moving + 1 entries
+  uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
+  RotDesc* RD;     // the current ligand's rotamer descriptors
+  uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
+  const float2* CS;  // (cos, sin) of every angle, shared by the block
+};
+
+__device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int fmax, int mask_words, int rmax,
+                                            int emax) {
+  auto a16 = [](int v) { return (v + 15) / 16 * 16; };
+  WarpMem w;
+  w.X = reinterpret_cast<float4*>(base);
+  base += a16(16 * nmax);
+  w.HR = reinterpret_cast<float2*>(base);
+  w.NEAR = base;
+  base += a16(8 * nmax);
+  w.MOFF = reinterpret_cast<uint16_t*>(base);
+  base += a16(2 * (nmax + 2));
+  w.DP = reinterpret_cast<float4*>(base);
+  base += a16(16 * fmax);
+  w.W2 = reinterpret_cast<float2*>(base);
+  base += a16(8 * fmax);
+  w.MASK = reinterpret_cast<uint32_t*>(base);
+  base += a16(4 * mask_words);
+  w.EXL = reinterpret_cast<uint16_t*>(base);
+  base += a16(2 * emax);
+  w.RD = reinterpret_cast<RotDesc*>(base);
+  w.CS = nullptr;
+  return w;
+}
+
+// Per rotamer step: (h, rho) of every atom about the bond axis for the reach filter, and
+// the axis frame of every moving atom (sweep order) for the candidate rotations.
+__device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp, float ux, float uy, float uz,
+                          int lane) {
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = w.X[i];
+    float4 dp;
+    float2 w2;
+    float h;
+    axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
+    w.HR[i] = make_float2(h, __fsqrt_rn(__fmaf_rn(dp.x, dp.x, __fmaf_rn(dp.y, dp.y, __fmul_rn(dp.z, dp.z)))));
+    const bool in = i >= rd.lo && i < rd.hi;
+    if (in != (rd.comp != 0)) {
+      const int ia = rd.comp ? (i < rd.lo ? i : i - (rd.hi - rd.lo)) : i - rd.lo;
+      w.DP[ia] = dp;
+      w.W2[ia] = w2;
+    }
+  }
+  __syncwarp();
+}
+
 // Evaluate every angle of one rotamer step; returns the warp-wide best key
 // ((score + 1) << 16 | (0xFFFF - k)), 0 if every candidate is bumped.
 template <int S, bool SG>
-__device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X, const float2* CS,
-                              const uint16_t* excl, int n, const RotDesc& rd, float ux, float uy, float uz,
-                              int s_static, int lane, unsigned long long& pairs, uint8_t* dbg) {
-  const float4 xp = X[rd.p];
+__device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, const uint16_t* excl,
+                              int n, const RotDesc& rd, int s_static, int lane, unsigned long long& pairs,
+                              uint8_t* dbg) {
+  float4* X = w.X;
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a, s1b;
   if (rd.comp) {
     m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
@@ -229,14 +315,13 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
   const int passes = (a.A + 32 * S - 1) / (32 * S);
   unsigned best = 0;
   for (int pass = 0; pass < passes; ++pass) {
-    Rot3 R[S];
+    float2 cs[S];
     int kk[S], sc[S];
     bool bump[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
-      const float2 cs = CS[kk[j] < a.A ? kk[j] : 0];
-      R[j] = rodrigues(ux, uy, uz, cs.x, cs.y, xp);
+      cs[j] = w.CS[kk[j] < a.A ? kk[j] : 0];
       sc[j] = s_static;
       bump[j] = kk[j] >= a.A;  // idle slots count as rejected
     }
@@ -244,10 +329,13 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
     int ex = 0;
     int next_a = n_excl ? (int)(excl[0] & 0xFF) : -1;  // moving atom of the next excluded pair
     bool stop = false;
+    int ia = 0;
     for (int seg = 0; seg < 2 && !stop; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
-      for (int ai = ma; ai < mb; ++ai) {
+      for (int ai = ma; ai < mb; ++ai, ++ia) {
         const float4 xa = X[ai];
+        const float4 dp = w.DP[ia];
+        const float2 w2 = w.W2[ia];
         // park the static atoms this moving atom must not be tested against
         int ex_end = ex;
         float4 saved = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -266,7 +354,7 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
         float xr[S][3], mind[S];
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-          rot_apply(R[j], xa.x, xa.y, xa.z, xr[j][0], xr[j][1], xr[j][2]);
+          turn(xa, dp, w2, cs[j], xr[j][0], xr[j][1], xr[j][2]);
           sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
           mind[j] = 3.0e38f;
         }
@@ -303,36 +391,6 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, float4* X,
   return __reduce_max_sync(FULL, best);
 }
 
-struct WarpMem {
-  float4* X;       // current pose, preorder
-  float2* HR;      // (height along the bond axis, distance from it) per atom
-  uint8_t* NEAR;   // near static atoms of each moving atom (overwrites HR once it is dead)
-  uint16_t* MOFF;  // NEAR offset per moving atom (sweep order), n_moving + 1 entries
-  uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
-  RotDesc* RD;     // the current ligand's rotamer descriptors
-  uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
-  const float2* CS;  // (cos, sin) of every angle, shared by the block
-};
-
-__device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int mask_words, int rmax, int emax) {
-  auto a16 = [](int v) { return (v + 15) / 16 * 16; };
-  WarpMem w;
-  w.X = reinterpret_cast<float4*>(base);
-  base += a16(16 * nmax);
-  w.HR = reinterpret_cast<float2*>(base);
-  w.NEAR = base;
-  base += a16(8 * nmax);
-  w.MOFF = reinterpret_cast<uint16_t*>(base);
-  base += a16(2 * (nmax + 2));
-  w.MASK = reinterpret_cast<uint32_t*>(base);
-  base += a16(4 * mask_words);
-  w.EXL = reinterpret_cast<uint16_t*>(base);
-  base += a16(2 * emax);
-  w.RD = reinterpret_cast<RotDesc*>(base);
-  w.CS = nullptr;
-  return w;
-}
-
 // Reach filter of one rotamer step.  A moving atom a sweeps a circle about the bond
 // axis: height h_a along it, radius rho_a.  For a static atom b the distance over the
 // whole turn is at least sqrt((h_a - h_b)^2 + (rho_a - rho_b)^2), so only pairs below
@@ -344,15 +402,7 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int m
 // near list per moving atom (NEAR / MOFF, at most 8 nmax entries: the bytes of HR).
 // Returns the number of near pairs; above 8 nmax only the masks are usable.
 __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
-                           float4 xp, float ux, float uy, float uz, int lane, unsigned long long& reach) {
-  for (int i = lane; i < n; i += 32) {
-    const float4 v = w.X[i];
-    const float rx = __fsub_rn(v.x, xp.x), ry = __fsub_rn(v.y, xp.y), rz = __fsub_rn(v.z, xp.z);
-    const float h = __fmaf_rn(rx, ux, __fmaf_rn(ry, uy, __fmul_rn(rz, uz)));
-    const float r2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmul_rn(rz, rz)));
-    w.HR[i] = make_float2(h, __fsqrt_rn(fmaxf(__fmaf_rn(-h, h, r2), 0.0f)));
-  }
-  __syncwarp();
+                          int lane, unsigned long long& reach) {
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
   if (rd.comp) {
     m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
@@ -430,8 +480,8 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
 // Every angle of one rotamer step, bump tests restricted to the near list.
 template <int S, bool SG>
 __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
-                                   const RotDesc& rd, float4 xp, float ux, float uy, float uz, int s_static,
-                                   int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
+                                   const RotDesc& rd, int s_static, int n_near, int lane,
+                                   unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
   int m0a, m0b, m1a, m1b;
   if (rd.comp) {
@@ -442,14 +492,13 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
   const int passes = (a.A + 32 * S - 1) / (32 * S);
   unsigned best = 0;
   for (int pass = 0; pass < passes; ++pass) {
-    Rot3 R[S];
+    float2 cs[S];
     int kk[S], sc[S];
     float mind[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
-      const float2 cs = w.CS[kk[j] < a.A ? kk[j] : 0];
-      R[j] = rodrigues(ux, uy, uz, cs.x, cs.y, xp);
+      cs[j] = w.CS[kk[j] < a.A ? kk[j] : 0];
       sc[j] = s_static;
       mind[j] = 3.0e38f;
       if (kk[j] < a.A) pairs += (unsigned)n_near;
@@ -459,10 +508,12 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
       for (int ai = ma; ai < mb; ++ai, ++ia) {
         const float4 xa = X[ai];
+        const float4 dp = w.DP[ia];
+        const float2 w2 = w.W2[ia];
         float xr[S][3];
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-          rot_apply(R[j], xa.x, xa.y, xa.z, xr[j][0], xr[j][1], xr[j][2]);
+          turn(xa, dp, w2, cs[j], xr[j][0], xr[j][1], xr[j][2]);
           sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
         }
         const int e1 = w.MOFF[ia + 1];
@@ -494,8 +545,8 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 // step's masks (n_near of them); used when the near list overflowed.
 template <int S, bool SG>
 __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
-                                   const RotDesc& rd, float4 xp, float ux, float uy, float uz, int s_static,
-                                   int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
+                                   const RotDesc& rd, int s_static, int n_near, int lane,
+                                   unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
   if (rd.comp) {
@@ -510,27 +561,29 @@ __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, cons
   const int passes = (a.A + 32 * S - 1) / (32 * S);
   unsigned best = 0;
   for (int pass = 0; pass < passes; ++pass) {
-    Rot3 R[S];
+    float2 cs[S];
     int kk[S], sc[S];
     float mind[S];
 #pragma unroll
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
-      const float2 cs = w.CS[kk[j] < a.A ? kk[j] : 0];
-      R[j] = rodrigues(ux, uy, uz, cs.x, cs.y, xp);
+      cs[j] = w.CS[kk[j] < a.A ? kk[j] : 0];
       sc[j] = s_static;
       mind[j] = 3.0e38f;
       if (kk[j] < a.A) pairs += (unsigned)n_near;
     }
     const uint32_t* row = w.MASK;
+    int ia = 0;
     for (int seg = 0; seg < 2; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
-      for (int ai = ma; ai < mb; ++ai, row += nch) {
+      for (int ai = ma; ai < mb; ++ai, ++ia, row += nch) {
         const float4 xa = X[ai];
+        const float4 dp = w.DP[ia];
+        const float2 w2 = w.W2[ia];
         float xr[S][3];
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-          rot_apply(R[j], xa.x, xa.y, xa.z, xr[j][0], xr[j][1], xr[j][2]);
+          turn(xa, dp, w2, cs[j], xr[j][0], xr[j][1], xr[j][2]);
           sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
         }
         for (int c = 0; c < nch; ++c) {
@@ -726,15 +779,15 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       if (a.bump_bits)
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
       unsigned key;
-      const float4 xp = X[rd.p];
+      prep_step(w, n, rd, X[rd.p], ux, uy, uz, lane);
       if (a.use_filter) {
-        const int n_near = build_near(a, w, excl, n, rd, xp, ux, uy, uz, lane, reach);
+        const int n_near = build_near(a, w, excl, n, rd, lane, reach);
         if (n_near <= 8 * a.nmax && !a.mask_sweep)
-          key = eval_step_near<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, n_near, lane, pairs, dbg);
+          key = eval_step_near<S, SG>(a, sg, w, n, rd, s_static, n_near, lane, pairs, dbg);
         else
-          key = eval_step_masks<S, SG>(a, sg, w, n, rd, xp, ux, uy, uz, s_static, n_near, lane, pairs, dbg);
+          key = eval_step_masks<S, SG>(a, sg, w, n, rd, s_static, n_near, lane, pairs, dbg);
       } else
-        key = eval_step<S, SG>(a, sg, X, w.CS, excl, n, rd, ux, uy, uz, s_static, lane, pairs, dbg);
+        key = eval_step<S, SG>(a, sg, w, excl, n, rd, s_static, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
         commit(X, n, rd, ux, uy, uz, w.CS[k], lane);
@@ -822,7 +875,7 @@ __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 4 : 1) search_kernel(
   for (int k = threadIdx.x; k < a.A; k += blockDim.x) cs[k] = angle_entry(k, a.A);
   off += ((size_t)a.A * 8 + 15) / 16 * 16;
   __syncthreads();
-  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.mask_words, a.rmax, a.emax);
+  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.fmax, a.mask_words, a.rmax, a.emax);
   w.CS = cs;
   // items: every (ligand, restart) in queue order, or an explicit list of rows li*O + o
   const unsigned long long n_items = a.items ? (unsigned long long)*a.n_items_dev : (unsigned long long)a.n_items;
@@ -1125,7 +1178,7 @@ int max_smem_grid_bytes() { return 200 * 1024; }
 
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
   const Tile t = tile_get(tile);
-  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.mask_words, a.rmax, a.emax) +
+  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax) +
              ((size_t)a.A * 8 + 15) / 16 * 16;
   if (grid_in_smem) s += (size_t)a.pk.bytes_pad + 16;
   return s;
