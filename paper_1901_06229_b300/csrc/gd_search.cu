@@ -178,8 +178,11 @@ __device__ __forceinline__ int frag_size(const RotDesc& rd, int n) {
   return rd.comp ? n - (rd.hi - rd.lo) : rd.hi - rd.lo;
 }
 
-// Commit the winning rotation to the fragment (same arithmetic as the candidate).
-__device__ void commit(float4* X, int n, const RotDesc& rd, float ux, float uy, float uz, float2 cs, int lane) {
+// Commit the winning rotation to the fragment (same arithmetic as the candidate); the
+// w component of each moved atom caches its new grid cell.
+template <bool SG>
+__device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n, const RotDesc& rd, float ux,
+                       float uy, float uz, float2 cs, int lane) {
   const float4 xp = X[rd.p];
   __syncwarp();
   const int f = frag_size(rd, n);
@@ -191,33 +194,23 @@ __device__ void commit(float4* X, int n, const RotDesc& rd, float ux, float uy, 
     float h, x, y, z;
     axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
     turn(v, dp, w2, cs, x, y, z);
-    X[t] = make_float4(x, y, z, 0.f);
+    X[t] = make_float4(x, y, z, __int_as_float(cell<SG>(pk, sg, x, y, z)));
   }
   __syncwarp();
 }
 
+// Rigid score of the pose (sum of the grid cells under its atoms); each atom's cell is
+// cached in the w component of its coordinates.
 template <bool SG>
-__device__ __forceinline__ int score_atoms(const PocketDev& pk, const uint8_t* sg, const float4* X, int n,
-                                           int lane) {
+__device__ __forceinline__ int score_atoms(const PocketDev& pk, const uint8_t* sg, float4* X, int n, int lane) {
   int s = 0;
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
-    s += cell<SG>(pk, sg, v.x, v.y, v.z);
+    const int c = cell<SG>(pk, sg, v.x, v.y, v.z);
+    X[i].w = __int_as_float(c);
+    s += c;
   }
-  return __reduce_add_sync(FULL, s);
-}
-
-// Cells under the fragment's current atoms.  The static part of every candidate's
-// score is the running score minus this (integer arithmetic, exact).
-template <bool SG>
-__device__ __forceinline__ int score_fragment(const PocketDev& pk, const uint8_t* sg, const float4* X, int n,
-                                              const RotDesc& rd, int lane) {
-  int s = 0;
-  const int f = frag_size(rd, n);
-  for (int i = lane; i < f; i += 32) {
-    const float4 v = X[frag_atom(rd, i)];
-    s += cell<SG>(pk, sg, v.x, v.y, v.z);
-  }
+  __syncwarp();
   return __reduce_add_sync(FULL, s);
 }
 
@@ -300,7 +293,7 @@ __device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp,
 // ((score + 1) << 16 | (0xFFFF - k)), 0 if every candidate is bumped.
 template <int S, bool SG>
 __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, const uint16_t* excl,
-                              int n, const RotDesc& rd, int s_static, int lane, unsigned long long& pairs,
+                              int n, const RotDesc& rd, int cur, int lane, unsigned long long& pairs,
                               uint8_t* dbg) {
   float4* X = w.X;
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a, s1b;
@@ -322,18 +315,20 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const Warp
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
       cs[j] = w.CS[kk[j] < a.A ? kk[j] : 0];
-      sc[j] = s_static;
+      sc[j] = 0;
       bump[j] = kk[j] >= a.A;  // idle slots count as rejected
     }
     const int n_excl = rd.n_excl;
     int ex = 0;
     int next_a = n_excl ? (int)(excl[0] & 0xFF) : -1;  // moving atom of the next excluded pair
     bool stop = false;
+    int stat = cur;  // running score minus the fragment's cached cells
     int ia = 0;
     for (int seg = 0; seg < 2 && !stop; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
       for (int ai = ma; ai < mb; ++ai, ++ia) {
         const float4 xa = X[ai];
+        stat -= __float_as_int(xa.w);
         const float4 dp = w.DP[ia];
         const float2 w2 = w.W2[ia];
         // park the static atoms this moving atom must not be tested against
@@ -383,7 +378,7 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const Warp
 #pragma unroll
     for (int j = 0; j < S; ++j)
       if (kk[j] < a.A) {
-        const unsigned key = bump[j] ? 0u : (((unsigned)(sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
+        const unsigned key = bump[j] ? 0u : (((unsigned)(stat + sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
         best = key > best ? key : best;
         if (dbg) dbg[kk[j]] = bump[j] ? 1 : 0;
       }
@@ -480,7 +475,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
 // Every angle of one rotamer step, bump tests restricted to the near list.
 template <int S, bool SG>
 __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
-                                   const RotDesc& rd, int s_static, int n_near, int lane,
+                                   const RotDesc& rd, int cur, int n_near, int lane,
                                    unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
   int m0a, m0b, m1a, m1b;
@@ -499,15 +494,17 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
       cs[j] = w.CS[kk[j] < a.A ? kk[j] : 0];
-      sc[j] = s_static;
+      sc[j] = 0;
       mind[j] = 3.0e38f;
       if (kk[j] < a.A) pairs += (unsigned)n_near;
     }
+    int stat = cur;  // running score minus the fragment's cached cells
     int ia = 0;
     for (int seg = 0; seg < 2; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
       for (int ai = ma; ai < mb; ++ai, ++ia) {
         const float4 xa = X[ai];
+        stat -= __float_as_int(xa.w);
         const float4 dp = w.DP[ia];
         const float2 w2 = w.W2[ia];
         float xr[S][3];
@@ -533,7 +530,7 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
     for (int j = 0; j < S; ++j)
       if (kk[j] < a.A) {
         const bool bump = mind[j] < a.thr2;
-        const unsigned key = bump ? 0u : (((unsigned)(sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
+        const unsigned key = bump ? 0u : (((unsigned)(stat + sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
         best = key > best ? key : best;
         if (dbg) dbg[kk[j]] = bump ? 1 : 0;
       }
@@ -545,7 +542,7 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 // step's masks (n_near of them); used when the near list overflowed.
 template <int S, bool SG>
 __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
-                                   const RotDesc& rd, int s_static, int n_near, int lane,
+                                   const RotDesc& rd, int cur, int n_near, int lane,
                                    unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
@@ -568,16 +565,18 @@ __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, cons
     for (int j = 0; j < S; ++j) {
       kk[j] = lane + 32 * (pass * S + j);
       cs[j] = w.CS[kk[j] < a.A ? kk[j] : 0];
-      sc[j] = s_static;
+      sc[j] = 0;
       mind[j] = 3.0e38f;
       if (kk[j] < a.A) pairs += (unsigned)n_near;
     }
+    int stat = cur;  // running score minus the fragment's cached cells
     const uint32_t* row = w.MASK;
     int ia = 0;
     for (int seg = 0; seg < 2; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
       for (int ai = ma; ai < mb; ++ai, ++ia, row += nch) {
         const float4 xa = X[ai];
+        stat -= __float_as_int(xa.w);
         const float4 dp = w.DP[ia];
         const float2 w2 = w.W2[ia];
         float xr[S][3];
@@ -607,7 +606,7 @@ __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, cons
     for (int j = 0; j < S; ++j)
       if (kk[j] < a.A) {
         const bool bump = mind[j] < a.thr2;
-        const unsigned key = bump ? 0u : (((unsigned)(sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
+        const unsigned key = bump ? 0u : (((unsigned)(stat + sc[j] + 1) << 16) | (0xFFFFu - (unsigned)kk[j]));
         best = key > best ? key : best;
         if (dbg) dbg[kk[j]] = bump ? 1 : 0;
       }
@@ -675,7 +674,8 @@ __device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, in
 }
 
 // a10: reduce over the ligand's restarts, replay the winner, write the results.
-__device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane) {
+template <bool SG>
+__device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int lane) {
   float4* X = w.X;
   const int O = a.O;
   unsigned best = 0;
@@ -732,7 +732,7 @@ __device__ void finalize(const SearchArgs& a, const WarpMem& w, int li, int lane
       const RotDesc rd = w.RD[r];  // registers: the loops below also write shared memory
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
-      commit(X, n, rd, ux, uy, uz, w.CS[k], lane);
+      commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane);
     }
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
@@ -774,7 +774,6 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       const uint16_t* excl = w.EXL + ((int)rd.excl_off - e0);
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
-      const int s_static = cur - score_fragment<SG>(a.pk, sg, X, n, rd, lane);
       uint8_t* dbg = nullptr;
       if (a.bump_bits)
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
@@ -783,14 +782,14 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       if (a.use_filter) {
         const int n_near = build_near(a, w, excl, n, rd, lane, reach);
         if (n_near <= 8 * a.nmax && !a.mask_sweep)
-          key = eval_step_near<S, SG>(a, sg, w, n, rd, s_static, n_near, lane, pairs, dbg);
+          key = eval_step_near<S, SG>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
         else
-          key = eval_step_masks<S, SG>(a, sg, w, n, rd, s_static, n_near, lane, pairs, dbg);
+          key = eval_step_masks<S, SG>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
       } else
-        key = eval_step<S, SG>(a, sg, w, excl, n, rd, s_static, lane, pairs, dbg);
+        key = eval_step<S, SG>(a, sg, w, excl, n, rd, cur, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
-        commit(X, n, rd, ux, uy, uz, w.CS[k], lane);
+        commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane);
         cur = (int)(key >> 16) - 1;
       }
       if (lane == 0) a.pose_pick[pick_base + rep * R + r] = (int16_t)k;
@@ -810,7 +809,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   prev = __shfl_sync(FULL, prev, 0);
   if (prev == (a.item_cnt ? a.item_cnt[li] : a.O) - 1) {
     __threadfence();
-    finalize(a, w, li, lane);
+    finalize<SG>(a, sg, w, li, lane);
   }
 }
 
