@@ -3,14 +3,16 @@
 A step is one pass of the whole hot path over one batch: every ligand of the batched
 workload (4,096 ligands of 20-80 atoms, 2-12 rotamers; 64^3 pocket at 0.375 A;
 256 Euler restarts x 64 angles) placed, swept and reduced to its best pose by one
-graph-captured persistent launch of the fused search kernel.
+graph replay: a small pose-setup kernel (restart rotations, centred ligands) and the
+persistent fused search kernel.
 
   value : ligands/s with the packed batch resident in HBM (gd_job_launch replays the
           search; the L2 is flushed between steps, outside the timed events)
   e2e   : the same metric through gd_dock_batch + gd_fetch_results with host buffers:
           validation/packing, the host->device copy, the search and the copy of the
           results back are all inside the timed region
-  roofline : FP32-pipe bound of the search kernel (see the design doc for the op counts)
+  roofline : FP32-pipe bound of the search kernel: algorithmic FP32 operations (7 per
+             pair test, 9 per atom move) over the FP32 lanes x the SM clock
   cpu_baseline : the FP64 oracle on the host cores, on a bounded sample
 
 --impl reference times the oracle itself (the paper has no code to run) on the same
@@ -35,8 +37,8 @@ from paper_1901_06229_b300 import synth  # noqa: E402
 
 METRIC = "ligands/s (pose search, 1 B300)"
 FP32_OPS_PER_PAIR = 7        # 3 FSUB, FMUL, 2 FFMA, 1 FMNMX
-FP32_OPS_PER_ATOM_MOVE = 18  # rotation about the bond axis (15) + cell coordinates (3 FFMA)
-FP32_OPS_PER_CANDIDATE = 19  # Rodrigues matrix of the candidate angle
+FP32_OPS_PER_ATOM_MOVE = 9   # turn about the bond axis (6 FFMA) + cell coordinates (3 FFMA)
+FP32_OPS_PER_CANDIDATE = 0   # (cos - 1, sin) come from a per-block table
 FP32_LANES_PER_SM = 128
 
 
@@ -290,7 +292,7 @@ def run_learned(args, world, rank, local):
         "plain_value": plain_v, "speedup_vs_plain": value / plain_v,
         "best_pose_recall": recall, "score_regret": regret, "fallback_fraction": float(np.mean(cnt > k)),
         "restarts_searched_per_ligand": float(cnt.mean()),
-        "gpu_launches": args.steps * 6,
+        "gpu_launches": args.steps * 7,  # features, MLP, 3 selection kernels, pose setup, search
         "roofline": {"bound": "tensor", "kernel": "mlp_infer_kernel (fused two-layer forward, 1 launch)",
                      "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak, "traffic": None,
                      "peak_kind": "bf16_tflops of MEASURED_PEAKS.json (burst)"},
@@ -507,7 +509,7 @@ def main():
         "pose_evals_per_s": evals * world * args.steps / dev_s,
         "pair_tests_per_s": pairs * world * args.steps / dev_s,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,  # pose setup + search per step
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tops, "traffic": None,
                      "peak_kind": f"FP32 pipe: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x {mhz:.0f} MHz "

@@ -194,12 +194,14 @@ OutLayout out_layout(int L, long long N, long long Rt, int reps) {
 }
 
 struct ScratchLayout {
-  size_t pose_score, pose_pick, pose_pairs, pose_reach, pose_rigid, done, work, bump, total;
+  size_t pose_score, pose_pick, pose_pairs, pose_reach, pose_rigid, xc, rmat, done, work, bump, total;
 };
 
-ScratchLayout scratch_layout(int L, int O, long long Rt, int reps, int A, bool debug) {
+ScratchLayout scratch_layout(int L, int O, long long N, long long Rt, int reps, int A, bool debug) {
   ScratchLayout l{};
   size_t o = 0;
+  l.xc = o;         o = align_up(o + 16 * (size_t)N, 256);
+  l.rmat = o;       o = align_up(o + 36 * (size_t)O, 256);
   l.pose_score = o; o = align_up(o + 4 * (size_t)L * O, 256);
   l.pose_pick = o;  o = align_up(o + 2 * (size_t)O * reps * Rt, 256);
   l.pose_pairs = o; o = align_up(o + 8 * (size_t)L * O, 256);
@@ -458,7 +460,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   // staging (their sizes are known); exclusions are gathered first and copied after
   j->in = in_layout(L, N, Rt, 0);
   j->out = out_layout(L, N, Rt, j->reps);
-  j->scr = scratch_layout(L, j->O, Rt, j->reps, j->A, j->debug_bumps);
+  j->scr = scratch_layout(L, j->O, N, Rt, j->reps, j->A, j->debug_bumps);
   const size_t in_cap = j->in.total + align_up(2 * (size_t)Rt * GD_MAX_EXCLUDED, 256);
   gd_status st;
   if ((st = host_alloc(c, in_cap, &j->h_in))) {
@@ -598,6 +600,8 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.pose_pairs = (unsigned long long*)(s + j->scr.pose_pairs);
   a.pose_reach = (unsigned long long*)(s + j->scr.pose_reach);
   a.pose_rigid = (int16_t*)(s + j->scr.pose_rigid);
+  a.xc = (float4*)(s + j->scr.xc);
+  a.rmat = (float*)(s + j->scr.rmat);
   a.done = (int32_t*)(s + j->scr.done);
   a.work = (unsigned long long*)(s + j->scr.work);
   a.err = (int32_t*)(o + j->out.err);

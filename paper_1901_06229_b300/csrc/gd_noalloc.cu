@@ -290,6 +290,8 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   const size_t o_ppick = o;      o = a256(o + 2 * (size_t)O * reps * Rt);
   const size_t o_ppairs = o;     o = a256(o + 8 * (size_t)L * O);
   const size_t o_preach = o;     o = a256(o + 8 * (size_t)L * O);
+  const size_t o_xc = o;         o = a256(o + 16 * (size_t)N);
+  const size_t o_rmat = o;       o = a256(o + 36 * (size_t)O);
   const size_t o_done = o;       o = o + 4 * (size_t)L;
   o = (o + 7) / 8 * 8;
   const size_t o_work = o;       o = a256(o + 8);
@@ -376,6 +378,8 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.pose_pick = (int16_t*)(d + o_ppick);
   a.pose_pairs = (unsigned long long*)(d + o_ppairs);
   a.pose_reach = (unsigned long long*)(d + o_preach);
+  a.xc = (float4*)(d + o_xc);
+  a.rmat = (float*)(d + o_rmat);
   a.done = (int32_t*)(d + o_done);
   a.work = (unsigned long long*)(d + o_work);
   a.bump_bits = nullptr;

@@ -120,43 +120,64 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// a3: x <- R_o (x0 - c_lig), coordinates relative to the pocket centre.
-__device__ void place(const SearchArgs& a, float4* X, const float4* x0, int n, int o, int lane) {
-  float sx = 0.f, sy = 0.f, sz = 0.f;
+// a3: x <- R_o (x0 - c_lig), coordinates relative to the pocket centre.  The centred
+// coordinates x0 - c_lig and the restart rotations R_o come from pose_setup_kernel.
+__device__ void place(const SearchArgs& a, float4* X, int a0, int n, int o, int lane) {
+  const float* r = a.rmat + 9 * (size_t)o;
+  const float r00 = __ldg(r + 0), r01 = __ldg(r + 1), r02 = __ldg(r + 2);
+  const float r10 = __ldg(r + 3), r11 = __ldg(r + 4), r12 = __ldg(r + 5);
+  const float r20 = __ldg(r + 6), r21 = __ldg(r + 7), r22 = __ldg(r + 8);
   for (int i = lane; i < n; i += 32) {
-    const float4 v = x0[i];
-    sx = __fadd_rn(sx, v.x);
-    sy = __fadd_rn(sy, v.y);
-    sz = __fadd_rn(sz, v.z);
-  }
-  sx = warp_sum_f(sx);
-  sy = warp_sum_f(sy);
-  sz = warp_sum_f(sz);
-  const float cx = __fdiv_rn(sx, (float)n), cy = __fdiv_rn(sy, (float)n), cz = __fdiv_rn(sz, (float)n);
-  const int ia = o / (a.nb * a.ng), jb = (o / a.ng) % a.nb, kg = o % a.ng;
-  float sa, ca, sb, cb, sg, cg;
-  sincospif(__fdiv_rn(2.0f * (float)ia, (float)a.na), &sa, &ca);
-  sincospif(__fdiv_rn(__fadd_rn((float)jb, 0.5f), (float)a.nb), &sb, &cb);
-  sincospif(__fdiv_rn(2.0f * (float)kg, (float)a.ng), &sg, &cg);
-  // R = Rz(alpha) Ry(beta) Rz(gamma)
-  const float cacb = __fmul_rn(ca, cb), sacb = __fmul_rn(sa, cb);
-  const float r00 = __fsub_rn(__fmul_rn(cacb, cg), __fmul_rn(sa, sg));
-  const float r01 = __fsub_rn(__fmul_rn(-cacb, sg), __fmul_rn(sa, cg));
-  const float r02 = __fmul_rn(ca, sb);
-  const float r10 = __fadd_rn(__fmul_rn(sacb, cg), __fmul_rn(ca, sg));
-  const float r11 = __fadd_rn(__fmul_rn(-sacb, sg), __fmul_rn(ca, cg));
-  const float r12 = __fmul_rn(sa, sb);
-  const float r20 = __fmul_rn(-sb, cg);
-  const float r21 = __fmul_rn(sb, sg);
-  const float r22 = cb;
-  for (int i = lane; i < n; i += 32) {
-    const float4 v = x0[i];
-    const float dx = __fsub_rn(v.x, cx), dy = __fsub_rn(v.y, cy), dz = __fsub_rn(v.z, cz);
-    X[i] = make_float4(__fmaf_rn(r00, dx, __fmaf_rn(r01, dy, __fmul_rn(r02, dz))),
-                       __fmaf_rn(r10, dx, __fmaf_rn(r11, dy, __fmul_rn(r12, dz))),
-                       __fmaf_rn(r20, dx, __fmaf_rn(r21, dy, __fmul_rn(r22, dz))), 0.f);
+    const float4 d = __ldg(a.xc + a0 + i);
+    X[i] = make_float4(__fmaf_rn(r00, d.x, __fmaf_rn(r01, d.y, __fmul_rn(r02, d.z))),
+                       __fmaf_rn(r10, d.x, __fmaf_rn(r11, d.y, __fmul_rn(r12, d.z))),
+                       __fmaf_rn(r20, d.x, __fmaf_rn(r21, d.y, __fmul_rn(r22, d.z))), 0.f);
   }
   __syncwarp();
+}
+
+// Per launch, before the search: R_o of every restart (ZYZ Euler angles, Listing 1:
+// R = Rz(alpha) Ry(beta) Rz(gamma)) and every ligand's coordinates minus its centroid.
+__global__ void __launch_bounds__(256) pose_setup_kernel(const __grid_constant__ SearchArgs a) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int o = tid; o < a.O; o += nth) {
+    const int ia = o / (a.nb * a.ng), jb = (o / a.ng) % a.nb, kg = o % a.ng;
+    float sa, ca, sb, cb, sg, cg;
+    sincospif(__fdiv_rn(2.0f * (float)ia, (float)a.na), &sa, &ca);
+    sincospif(__fdiv_rn(__fadd_rn((float)jb, 0.5f), (float)a.nb), &sb, &cb);
+    sincospif(__fdiv_rn(2.0f * (float)kg, (float)a.ng), &sg, &cg);
+    const float cacb = __fmul_rn(ca, cb), sacb = __fmul_rn(sa, cb);
+    float* r = a.rmat + 9 * (size_t)o;
+    r[0] = __fsub_rn(__fmul_rn(cacb, cg), __fmul_rn(sa, sg));
+    r[1] = __fsub_rn(__fmul_rn(-cacb, sg), __fmul_rn(sa, cg));
+    r[2] = __fmul_rn(ca, sb);
+    r[3] = __fadd_rn(__fmul_rn(sacb, cg), __fmul_rn(ca, sg));
+    r[4] = __fadd_rn(__fmul_rn(-sacb, sg), __fmul_rn(ca, cg));
+    r[5] = __fmul_rn(sa, sb);
+    r[6] = __fmul_rn(-sb, cg);
+    r[7] = __fmul_rn(sb, sg);
+    r[8] = cb;
+  }
+  const int lane = threadIdx.x & 31;
+  for (int li = tid >> 5; li < a.L; li += nth >> 5) {
+    const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
+    const float4* x0 = a.xyz + a0;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const float4 v = x0[i];
+      sx = __fadd_rn(sx, v.x);
+      sy = __fadd_rn(sy, v.y);
+      sz = __fadd_rn(sz, v.z);
+    }
+    sx = warp_sum_f(sx);
+    sy = warp_sum_f(sy);
+    sz = warp_sum_f(sz);
+    const float cx = __fdiv_rn(sx, (float)n), cy = __fdiv_rn(sy, (float)n), cz = __fdiv_rn(sz, (float)n);
+    for (int i = lane; i < n; i += 32) {
+      const float4 v = x0[i];
+      a.xc[a0 + i] = make_float4(__fsub_rn(v.x, cx), __fsub_rn(v.y, cy), __fsub_rn(v.z, cz), 0.f);
+    }
+  }
 }
 
 // Unit bond axis from the static end p to the moving end q (current coordinates).
@@ -179,10 +200,11 @@ __device__ __forceinline__ int frag_size(const RotDesc& rd, int n) {
 }
 
 // Commit the winning rotation to the fragment (same arithmetic as the candidate); the
-// w component of each moved atom caches its new grid cell.
+// w component of each moved atom caches its new grid cell.  DP / W2: the step's axis
+// frames in sweep order when the search has them, else (replay) NULL and recomputed.
 template <bool SG>
 __device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n, const RotDesc& rd, float ux,
-                       float uy, float uz, float2 cs, int lane) {
+                       float uy, float uz, float2 cs, int lane, const float4* DP, const float2* W2) {
   const float4 xp = X[rd.p];
   __syncwarp();
   const int f = frag_size(rd, n);
@@ -192,7 +214,12 @@ __device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n,
     float4 dp;
     float2 w2;
     float h, x, y, z;
-    axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
+    if (DP) {
+      dp = DP[i];
+      w2 = W2[i];
+    } else {
+      axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
+    }
     turn(v, dp, w2, cs, x, y, z);
     X[t] = make_float4(x, y, z, __int_as_float(cell<SG>(pk, sg, x, y, z)));
   }
@@ -718,7 +745,7 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   }
   for (int s = lane; s < a.reps * R; s += 32)
     a.best_angle[(size_t)r0 * a.reps + s] = __ldcg(a.pose_pick + pick_base + s);
-  place(a, X, a.xyz + a0, n, ob, lane);
+  place(a, X, a0, n, ob, lane);
   int rig = 0;
   if (a.rigid_n > 1) {
     rig = __ldcg(a.pose_rigid + (size_t)li * O + ob);
@@ -732,7 +759,7 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
       const RotDesc rd = w.RD[r];  // registers: the loops below also write shared memory
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
-      commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane);
+      commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, nullptr, nullptr);
     }
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
@@ -760,7 +787,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
     for (int i = lane; i < ne; i += 32) w.EXL[i] = __ldg(a.excl + e0 + i);
   }
   __syncwarp();
-  place(a, X, a.xyz + a0, n, o, lane);
+  place(a, X, a0, n, o, lane);
   {
     const int m = a.rigid_n > 1 ? rigid_align<SG>(a, sg, X, n, lane) : 0;
     if (lane == 0 && a.pose_rigid) a.pose_rigid[(size_t)li * a.O + o] = (int16_t)m;
@@ -789,7 +816,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
         key = eval_step<S, SG>(a, sg, w, excl, n, rd, cur, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
-        commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane);
+        commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, w.DP, w.W2);
         cur = (int)(key >> 16) - 1;
       }
       if (lane == 0) a.pose_pick[pick_base + rep * R + r] = (int16_t)k;
@@ -1238,6 +1265,9 @@ cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, i
 }
 
 cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t st) {
+  const long long need = std::max((long long)a.O, 32LL * a.L);
+  const int blocks = (int)std::min(1024LL, std::max(1LL, (need + 255) / 256));
+  pose_setup_kernel<<<blocks, 256, 0, st>>>(a);
   void* args[] = {const_cast<SearchArgs*>(&a)};
   return cudaLaunchKernel(cfg.fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
 }
