@@ -41,6 +41,24 @@ FP32_OPS_PER_ATOM_MOVE = 9   # turn about the bond axis (6 FFMA) + cell coordina
 FP32_OPS_PER_CANDIDATE = 0   # (cos - 1, sin) come from a per-block table
 FP32_LANES_PER_SM = 128
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one search-kernel launch,
+# from one ncu capture of the full-size workload, keyed by a hash of the kernel sources
+# and by (workload, tile): reported only while the kernel is the one that was measured.
+SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
+MEASURED_TRAFFIC = {
+    "817cdb1afb561670": {("batched-4096lig-64grid", 14): 4566272 + 5074944,
+                         ("large-512lig-128grid", 9): 3028736 + 1024},
+}
+
+
+def search_kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in SEARCH_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def workload_for(name, rank, ligands=None):
     if name == "batched":
@@ -511,7 +529,8 @@ def main():
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,  # pose setup + search per step
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tops, "traffic": None,
+                     "frac": achieved / peak_tops,
+                     "traffic": MEASURED_TRAFFIC.get(search_kernel_hash(), {}).get((w.name, tile)),
                      "peak_kind": f"FP32 pipe: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x {mhz:.0f} MHz "
                                   "(sm_max_mhz of MEASURED_PEAKS.json)",
                      "ops_per_launch": per_launch_ops},
