@@ -194,7 +194,7 @@ OutLayout out_layout(int L, long long N, long long Rt, int reps) {
 }
 
 struct ScratchLayout {
-  size_t pose_score, pose_pick, pose_pairs, pose_reach, pose_rigid, xc, rmat, done, work, bump, total;
+  size_t pose_score, pose_pick, pose_pairs, pose_reach, pose_rigid, xc, rmat, quat, done, work, bump, total;
 };
 
 ScratchLayout scratch_layout(int L, int O, long long N, long long Rt, int reps, int A, bool debug) {
@@ -202,6 +202,7 @@ ScratchLayout scratch_layout(int L, int O, long long N, long long Rt, int reps, 
   size_t o = 0;
   l.xc = o;         o = align_up(o + 16 * (size_t)N, 256);
   l.rmat = o;       o = align_up(o + 36 * (size_t)O, 256);
+  l.quat = o;       o = align_up(o + 16 * (size_t)O, 256);
   l.pose_score = o; o = align_up(o + 4 * (size_t)L * O, 256);
   l.pose_pick = o;  o = align_up(o + 2 * (size_t)O * reps * Rt, 256);
   l.pose_pairs = o; o = align_up(o + 8 * (size_t)L * O, 256);
@@ -602,6 +603,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.pose_rigid = (int16_t*)(s + j->scr.pose_rigid);
   a.xc = (float4*)(s + j->scr.xc);
   a.rmat = (float*)(s + j->scr.rmat);
+  a.quat = (float4*)(s + j->scr.quat);
   a.done = (int32_t*)(s + j->scr.done);
   a.work = (unsigned long long*)(s + j->scr.work);
   a.err = (int32_t*)(o + j->out.err);

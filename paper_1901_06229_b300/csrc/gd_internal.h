@@ -83,6 +83,7 @@ struct SearchArgs {
   int mask_words;             // largest step_mask_words of the batch (>= 1)
   float4* xc;                 // [N] (scratch) centred input coordinates x0 - c_lig, preorder
   float* rmat;                // [O * 9] (scratch) restart rotation matrices, row-major
+  float4* quat;               // [O] (scratch) restart unit quaternions (w >= 0)
   int fmax;                   // largest rotating fragment of the batch (>= 1)
   int rmax, emax;             // largest rotamer / excluded-pair count of one ligand (>= 1)
   int warp_bytes;             // shared memory per warp (see warp_smem_bytes)

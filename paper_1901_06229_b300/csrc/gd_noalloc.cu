@@ -292,6 +292,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   const size_t o_preach = o;     o = a256(o + 8 * (size_t)L * O);
   const size_t o_xc = o;         o = a256(o + 16 * (size_t)N);
   const size_t o_rmat = o;       o = a256(o + 36 * (size_t)O);
+  const size_t o_quat = o;       o = a256(o + 16 * (size_t)O);
   const size_t o_done = o;       o = o + 4 * (size_t)L;
   o = (o + 7) / 8 * 8;
   const size_t o_work = o;       o = a256(o + 8);
@@ -380,6 +381,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.pose_reach = (unsigned long long*)(d + o_preach);
   a.xc = (float4*)(d + o_xc);
   a.rmat = (float*)(d + o_rmat);
+  a.quat = (float4*)(d + o_quat);
   a.done = (int32_t*)(d + o_done);
   a.work = (unsigned long long*)(d + o_work);
   a.bump_bits = nullptr;

@@ -157,6 +157,17 @@ __global__ void __launch_bounds__(256) pose_setup_kernel(const __grid_constant__
     r[6] = __fmul_rn(-sb, cg);
     r[7] = __fmul_rn(sb, sg);
     r[8] = cb;
+    // half-angle quaternion of Rz(alpha) Ry(beta) Rz(gamma):
+    // (cos(b/2) cos((a+g)/2), sin(b/2) sin((g-a)/2), sin(b/2) cos((g-a)/2), cos(b/2) sin((a+g)/2))
+    float hb_s, hb_c, hp_s, hp_c, hm_s, hm_c;
+    sincospif(__fdiv_rn((float)jb + 0.5f, 2.0f * (float)a.nb), &hb_s, &hb_c);
+    const float apg = (float)ia / (float)a.na + (float)kg / (float)a.ng;  // (alpha + gamma) / 2 in units of pi
+    const float gma = (float)kg / (float)a.ng - (float)ia / (float)a.na;  // (gamma - alpha) / 2
+    sincospif(apg, &hp_s, &hp_c);
+    sincospif(gma, &hm_s, &hm_c);
+    float4 q = make_float4(hb_c * hp_c, hb_s * hm_s, hb_s * hm_c, hb_c * hp_s);
+    if (q.x < 0.f) q = make_float4(-q.x, -q.y, -q.z, -q.w);
+    a.quat[o] = q;
   }
   const int lane = threadIdx.x & 31;
   for (int li = tid >> 5; li < a.L; li += nth >> 5) {
@@ -939,7 +950,11 @@ __global__ void __launch_bounds__(256) feature_kernel(const __grid_constant__ Se
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   __shared__ int fps_s[8][NFPS];
+  __shared__ float inv_s[8][19];
+  __shared__ float4 fx_s[8][NFPS];
   int* fps = fps_s[threadIdx.x >> 5];
+  float* inv = inv_s[threadIdx.x >> 5];
+  float4* fx = fx_s[threadIdx.x >> 5];
   for (int li = gw; li < a.L; li += nw) {
     const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
     const int R = a.rot_off[li + 1] - a.rot_off[li];
@@ -1018,65 +1033,57 @@ __global__ void __launch_bounds__(256) feature_kernel(const __grid_constant__ Se
       }
     }
     __syncwarp();
-    // restart-independent features: lanes hold feature e = lane and e = lane + 32
-    float inv[2];
-    for (int h = 0; h < 2; ++h) {
-      const int e = lane + 32 * h;
-      float v = 0.f;
-      if (e == 4) v = (float)n / 250.f;
-      else if (e == 5) v = (float)R / 60.f;
-      else if (e == 6) v = sqrtf(r2sum / (float)n) / 10.f;
-      inv[h] = v;
+    // restart-independent features 4..22 and the sampled atoms (centred), per warp
+    const int hb = __shfl_sync(FULL, hist, (lane - 3) & 31);  // lane 3 + b gets bin b
+    if (lane < 19) {
+      float v;
+      if (lane == 0) v = (float)n / 250.f;
+      else if (lane == 1) v = (float)R / 60.f;
+      else if (lane == 2) v = sqrtf(r2sum / (float)n) / 10.f;
+      else v = (float)hb / (float)n;
+      inv[lane] = v;
     }
-    const float hfrac = (float)hist / (float)n;  // lanes 0..15: bins
-    const float h7 = __shfl_sync(FULL, hfrac, (lane - 7) & 31);  // feature e = 7 + b holds bin b
-    const int samp0 = lane - 23, samp1 = lane + 32 - 23;          // grid sample index per slot
-    const int at0 = samp0 >= 0 ? fps[samp0 % nsel] : 0, at1 = (lane + 32 < NFEAT) ? fps[samp1 % nsel] : 0;
-    const float4 p0 = x0[at0], p1 = x0[at1];
-    for (int o = 0; o < a.O; ++o) {
-      const int ia = o / (a.nb * a.ng), jb = (o / a.ng) % a.nb, kg = o % a.ng;
-      float sa, ca, sb, cb, sg, cg;
-      sincospif(__fdiv_rn(2.0f * (float)ia, (float)a.na), &sa, &ca);
-      sincospif(__fdiv_rn(__fadd_rn((float)jb, 0.5f), (float)a.nb), &sb, &cb);
-      sincospif(__fdiv_rn(2.0f * (float)kg, (float)a.ng), &sg, &cg);
-      const float cacb = ca * cb, sacb = sa * cb;
-      const float r[9] = {cacb * cg - sa * sg, -cacb * sg - sa * cg, ca * sb, sacb * cg + ca * sg,
-                          -sacb * sg + ca * cg, sa * sb, -sb * cg, sb * sg, cb};
-      // half-angle quaternion of Rz(alpha) Ry(beta) Rz(gamma):
-      // (cos b cos((a+g)), sin b sin(g-a), sin b cos(g-a), cos b sin(a+g)), half angles
-      float hb_s, hb_c, hp_s, hp_c, hm_s, hm_c;
-      sincospif(__fdiv_rn((float)jb + 0.5f, 2.0f * (float)a.nb), &hb_s, &hb_c);
-      // (alpha + gamma) / 2 and (gamma - alpha) / 2 in units of pi
-      const float apg = (float)ia / (float)a.na + (float)kg / (float)a.ng;
-      const float gma = (float)kg / (float)a.ng - (float)ia / (float)a.na;
-      sincospif(apg, &hp_s, &hp_c);
-      sincospif(gma, &hm_s, &hm_c);
-      float q[4] = {hb_c * hp_c, hb_s * hm_s, hb_s * hm_c, hb_c * hp_s};
-      if (q[0] < 0.f)
-        for (int t = 0; t < 4; ++t) q[t] = -q[t];
-      float out[2];
-      for (int h = 0; h < 2; ++h) {
-        const int e = lane + 32 * h;
-        float v = inv[h];
-        if (e < 4) v = q[e];
-        else if (e >= 7 && e < 23) v = h7;
-        else if (e >= 23 && e < NFEAT) {
-          const float4 p = h ? p1 : p0;
-          const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
-          const float X = r[0] * dx + r[1] * dy + r[2] * dz;
-          const float Y = r[3] * dx + r[4] * dy + r[5] * dz;
-          const float Z = r[6] * dx + r[7] * dy + r[8] * dz;
-          v = (float)cell<false>(a.pk, nullptr, X, Y, Z) / 255.f;
-        }
-        out[h] = v;
+    if (lane < NFPS) {
+      const float4 p = x0[fps[lane % nsel]];
+      fx[lane] = make_float4(p.x - cx, p.y - cy, p.z - cz, 0.f);
+    }
+    __syncwarp();
+    // one restart per lane: quaternion, the shared part, the 25 grid samples
+    for (int o = lane; o < a.O; o += 32) {
+      const float* r = a.rmat + 9 * (size_t)o;
+      const float r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3), r4 = __ldg(r + 4);
+      const float r5 = __ldg(r + 5), r6 = __ldg(r + 6), r7 = __ldg(r + 7), r8 = __ldg(r + 8);
+      float f[NFEAT];
+      const float4 q = a.quat[o];
+      f[0] = q.x;
+      f[1] = q.y;
+      f[2] = q.z;
+      f[3] = q.w;
+#pragma unroll
+      for (int e = 0; e < 19; ++e) f[4 + e] = inv[e];
+#pragma unroll
+      for (int t = 0; t < NFPS; ++t) {
+        const float4 d = fx[t];
+        const float X = __fmaf_rn(r0, d.x, __fmaf_rn(r1, d.y, __fmul_rn(r2, d.z)));
+        const float Y = __fmaf_rn(r3, d.x, __fmaf_rn(r4, d.y, __fmul_rn(r5, d.z)));
+        const float Z = __fmaf_rn(r6, d.x, __fmaf_rn(r7, d.y, __fmul_rn(r8, d.z)));
+        f[23 + t] = (float)cell<false>(a.pk, nullptr, X, Y, Z) / 255.f;
       }
-      const size_t row = ((size_t)li * a.O + o) * NFEAT;
-      for (int h = 0; h < 2; ++h) {
-        const int e = lane + 32 * h;
-        if (e < NFEAT) {
-          if (Xb) Xb[row + e] = __float2bfloat16(out[h]);
-          if (Xf) Xf[row + e] = out[h];
+      const size_t row = (size_t)li * a.O + o;
+      if (Xb) {
+        uint4* dst = reinterpret_cast<uint4*>(Xb + row * NFEAT);
+#pragma unroll
+        for (int g = 0; g < NFEAT / 8; ++g) {
+          __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(f[8 * g + e]);
+          dst[g] = *reinterpret_cast<const uint4*>(h);
         }
+      }
+      if (Xf) {
+        float4* dst = reinterpret_cast<float4*>(Xf + row * NFEAT);
+#pragma unroll
+        for (int g = 0; g < NFEAT / 4; ++g) dst[g] = make_float4(f[4 * g], f[4 * g + 1], f[4 * g + 2], f[4 * g + 3]);
       }
     }
     __syncwarp();
@@ -1258,6 +1265,10 @@ cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, floa
 
 cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, int num_sms, cudaStream_t st) {
   if (a.L == 0) return cudaSuccess;
+  {
+    const long long need = std::max((long long)a.O, 32LL * a.L);
+    pose_setup_kernel<<<(int)std::min(1024LL, std::max(1LL, (need + 255) / 256)), 256, 0, st>>>(a);
+  }
   int blocks = (a.L + 7) / 8;
   if (blocks > num_sms * 8) blocks = num_sms * 8;
   feature_kernel<<<blocks, 256, 0, st>>>(a, Xb, Xf);
