@@ -201,14 +201,37 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 }
 
 // Fused inference: y = relu(relu(X W1^T + b1) W2^T + b2) . w3 + b3 for 128-row tiles.
-// One persistent CTA per SM keeps W1 (24 KB) and W2 (128 KB) in shared memory in the
-// tensor core's layout; per tile the X rows are staged into the H1 buffer, layer 1 runs
-// as 3 MMAs (K = 48) into TMEM, the epilogue writes bias+ReLU BF16 activations back into
-// the same buffer as layer 2's A operand, layer 2 runs as 16 MMAs (K = 256) into the same
-// TMEM columns, and the second epilogue reduces bias+ReLU activations against w3.  Eight
-// warps: warp w reads TMEM lanes 32 (w % 4) and columns 128 (w / 4) .. + 128.
+// One persistent CTA per SM keeps W1 (24 KB), W2 (128 KB), b1, b2 and w3 in shared
+// memory and owns all 512 TMEM columns: layer 1 accumulates in columns [0, 256), layer 2
+// in [256, 512).  Per tile t, in order:
+//   A  wait for layer 1 of t;  B  epilogue 1: bias + ReLU + BF16 into the H1 buffer as
+//   layer 2's A operand;  C  16 MMAs of layer 2 (K = 256);  D  meanwhile, every thread
+//   loads its share of tile t+1's X rows into registers;  E  wait for layer 2;  F  the X
+//   rows go into the H1 buffer (free again) and the 3 MMAs of tile t+1's layer 1 are
+//   issued;  G  epilogue 2 (bias + ReLU + BF16 + dot with w3) of tile t runs while they do.
+// Eight warps: warp w reads TMEM lanes 32 (w % 4) and columns 128 (w / 4) .. + 128.
 constexpr int INF_THREADS = 256;
-constexpr size_t INF_W1 = 256 * 48 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2;
+constexpr size_t INF_W1 = 256 * 48 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2, INF_VEC = 3 * 256 * 4;
+constexpr int INF_XCH = 128 * 6 / INF_THREADS;  // 16-byte X chunks per thread and tile (128 rows x 6)
+
+// This thread's X chunks of the tile at row r0 (rows past M read as zero).
+__device__ __forceinline__ void x_load(const __nv_bfloat16* X, int M, int r0, uint4 (&v)[INF_XCH]) {
+#pragma unroll
+  for (int j = 0; j < INF_XCH; ++j) {
+    const int idx = threadIdx.x + INF_THREADS * j, r = idx / 6, c = idx % 6;
+    v[j] = r0 + r < M ? __ldg(reinterpret_cast<const uint4*>(X + (size_t)(r0 + r) * 48 + c * 8))
+                      : make_uint4(0, 0, 0, 0);
+  }
+}
+
+// The same chunks into the core-matrix layout of layer 1's A operand (K = 48).
+__device__ __forceinline__ void x_store(uint8_t* dst, const uint4 (&v)[INF_XCH]) {
+#pragma unroll
+  for (int j = 0; j < INF_XCH; ++j) {
+    const int idx = threadIdx.x + INF_THREADS * j, r = idx / 6, c = idx % 6;
+    *reinterpret_cast<uint4*>(dst + (size_t)(r >> 3) * 768 + c * 128 + (r & 7) * 16) = v[j];
+  }
+}
 
 __global__ void __launch_bounds__(INF_THREADS, 1)
     mlp_infer_kernel(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
@@ -217,57 +240,72 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   uint8_t* w1s = smem;
   uint8_t* w2s = smem + INF_W1;
   uint8_t* h1s = smem + INF_W1 + INF_W2;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* b1s = reinterpret_cast<float*>(smem + INF_W1 + INF_W2 + INF_H1);
+  float* b2s = b1s + 256;
+  float* w3s = b2s + 256;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1 + INF_VEC);  // [0] layer 1, [1] layer 2
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   __shared__ float red[2][128];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quad = warp & 3, half = warp >> 2;
+  const int ntiles = (M + 127) / 128;
+  if ((int)blockIdx.x >= ntiles) return;
   stage(w1s, W1b, 48, 256, 48, 0, 256, 0, 48, false);
   stage(w2s, W2b, 256, 256, 256, 0, 256, 0, 256, false);
+  for (int i = threadIdx.x; i < 256; i += INF_THREADS) {
+    b1s[i] = b1[i];
+    b2s[i] = b2[i];
+    w3s[i] = w3r[i];
+  }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(tslot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  uint4 xv[INF_XCH];
+  x_load(X, M, (int)blockIdx.x * 128, xv);
+  x_store(h1s, xv);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem = *tslot, acc1 = tmem, acc2 = tmem + 256;
   const uint32_t idesc = make_idesc(128, 256);
-  const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
-  uint32_t phase = 0;
+  const uint32_t lanebase = ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
+  const int row = quad * 32 + lane;
+  const float bias3 = *b3;
+  uint32_t ph1 = 0, ph2 = 0;
   bool ok = true;
-  const int ntiles = (M + 127) / 128;
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const int r0 = tile * 128;
-    stage(h1s, X, 48, M, 48, r0, 128, 0, 48, false);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+  auto issue_l1 = [&]() {
     if (threadIdx.x == 0) {
       tc_fence_after();
       for (int kk = 0; kk < 3; ++kk)
-        mma_bf16(tmem, make_desc(smem_addr(h1s) + kk * 256, 128, 768), make_desc(smem_addr(w1s) + kk * 256, 128, 768),
+        mma_bf16(acc1, make_desc(smem_addr(h1s) + kk * 256, 128, 768), make_desc(smem_addr(w1s) + kk * 256, 128, 768),
                  idesc, kk > 0);
       mma_commit(mbar);
     }
-    ok = mbar_wait(mbar, phase);
-    phase ^= 1;
+  };
+  issue_l1();
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int r0 = tile * 128, next = tile + (int)gridDim.x;
+    // A, B: layer 1 of this tile, then its epilogue into H1 (the X rows there are consumed)
+    ok = mbar_wait(mbar, ph1);
+    ph1 ^= 1;
     tc_fence_after();
     if (!ok) break;
-    // layer-1 epilogue: bias, ReLU, BF16 into the core-matrix layout of layer 2's A
-    const int row = quad * 32 + lane;
     for (int c0 = 0; c0 < 128; c0 += 32) {
       float v[32];
-      tmem_ld32(taddr + (uint32_t)c0, v);
+      tmem_ld32(acc1 + lanebase + (uint32_t)c0, v);
       const int col0 = half * 128 + c0;
 #pragma unroll
       for (int c8 = 0; c8 < 4; ++c8) {
         __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(fmaxf(v[c8 * 8 + e] + b1[col0 + c8 * 8 + e], 0.f));
+        for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(fmaxf(v[c8 * 8 + e] + b1s[col0 + c8 * 8 + e], 0.f));
         const int kc = (col0 >> 3) + c8;
         *reinterpret_cast<uint4*>(h1s + (size_t)(row >> 3) * 4096 + kc * 128 + (row & 7) * 16) =
             *reinterpret_cast<uint4*>(h);
@@ -276,50 +314,64 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     tc_fence_before();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    // C: layer 2 (the previous tile's epilogue 2 has read its TMEM columns)
     if (threadIdx.x == 0) {
       tc_fence_after();
       for (int kk = 0; kk < 16; ++kk)
-        mma_bf16(tmem, make_desc(smem_addr(h1s) + kk * 256, 128, 4096),
+        mma_bf16(acc2, make_desc(smem_addr(h1s) + kk * 256, 128, 4096),
                  make_desc(smem_addr(w2s) + kk * 256, 128, 4096), idesc, kk > 0);
-      mma_commit(mbar);
+      mma_commit(mbar + 1);
     }
-    ok = mbar_wait(mbar, phase);
-    phase ^= 1;
+    // D: the next tile's X rows into registers while the tensor core works
+    if (next < ntiles) x_load(X, M, next * 128, xv);
+    // E: layer 2 done; H1 and layer 1's columns are free
+    ok = mbar_wait(mbar + 1, ph2);
+    ph2 ^= 1;
     tc_fence_after();
     if (!ok) break;
-    // layer-2 epilogue: bias, ReLU, BF16, dot with w3 (two column halves, then added)
+    // F: the next tile's layer 1 runs during this tile's second epilogue
+    if (next < ntiles) {
+      x_store(h1s, xv);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      issue_l1();
+    }
+    // G: epilogue 2
     float dot = 0.f;
     for (int c0 = 0; c0 < 128; c0 += 32) {
       float v[32];
-      tmem_ld32(taddr + (uint32_t)c0, v);
+      tmem_ld32(acc2 + lanebase + (uint32_t)c0, v);
       const int col0 = half * 128 + c0;
 #pragma unroll
       for (int e = 0; e < 32; ++e)
-        dot = fmaf(__bfloat162float(__float2bfloat16(fmaxf(v[e] + b2[col0 + e], 0.f))), w3r[col0 + e], dot);
+        dot = fmaf(__bfloat162float(__float2bfloat16(fmaxf(v[e] + b2s[col0 + e], 0.f))), w3s[col0 + e], dot);
     }
     red[half][row] = dot;
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x < 128 && r0 + (int)threadIdx.x < M)
-      y[r0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x] + *b3;
+      y[r0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x] + bias3;
+    __syncthreads();
   }
   if (!ok && threadIdx.x == 0 && err) atomicExch(err, 1);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 }  // namespace
 
 // Operand staging (48 KB) plus 32 KB of headroom: at most two CTAs share an SM, so the
-// two 256-column TMEM allocations always fit the SM's 512 columns.
+// two 256-column TMEM allocations always fit the SM's 512 columns.  (The inference
+// kernel takes all 512 columns, but its 225 KB of shared memory keeps any other
+// tensor-core CTA off its SM.)
 size_t gemm_smem_bytes() { return 128 * KC * 2 + 256 * KC * 2 + 16 + 32 * 1024; }
 
 cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
                          const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
                          int num_sms, cudaStream_t st) {
   static bool attr = false;
-  const size_t smem = INF_W1 + INF_W2 + INF_H1 + 16;
+  const size_t smem = INF_W1 + INF_W2 + INF_H1 + INF_VEC + 32;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
