@@ -203,22 +203,23 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 // Fused inference: y = relu(relu(X W1^T + b1) W2^T + b2) . w3 + b3 for 128-row tiles.
 // One persistent CTA per SM keeps W1 (24 KB), W2 (128 KB), b1, b2 and w3 in shared
 // memory and owns all 512 TMEM columns: layer 1 accumulates in columns [0, 256), layer 2
-// in [256, 512).  Per tile t, in order:
-//   A  wait for layer 1 of t;  B  epilogue 1: bias + ReLU + BF16 into the H1 buffer as
-//   layer 2's A operand;  C  16 MMAs of layer 2 (K = 256);  D  meanwhile, every thread
-//   loads its share of tile t+1's X rows into registers;  E  wait for layer 2;  F  the X
-//   rows go into the H1 buffer (free again) and the 3 MMAs of tile t+1's layer 1 are
-//   issued;  G  epilogue 2 (bias + ReLU + BF16 + dot with w3) of tile t runs while they do.
-// Eight warps: warp w reads TMEM lanes 32 (w % 4) and columns 128 (w / 4) .. + 128.
-constexpr int INF_THREADS = 256;
+// in [256, 512).  Warp 8 only issues MMAs: layer 1 of a tile once the eight epilogue
+// warps have stored its X rows in the H1 buffer, then layer 2 four K = 16 slices at a
+// time as epilogue 1 completes 32-column chunks of H1.  Epilogue warp w reads TMEM lanes
+// 32 (w % 4) and columns 128 (w / 4) .. + 128; per tile it runs epilogue 1 (bias, ReLU,
+// BF16 into H1), loads the next tile's X rows into registers while layer 2 runs, stores
+// them once layer 2 has released H1 (so the next layer 1 overlaps), then epilogue 2
+// (bias, ReLU, BF16, dot with w3).
+constexpr int INF_EPI = 256;                // epilogue threads (8 warps)
+constexpr int INF_THREADS = INF_EPI + 32;   // + the issuing warp
 constexpr size_t INF_W1 = 256 * 48 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2, INF_VEC = 3 * 256 * 4;
-constexpr int INF_XCH = 128 * 6 / INF_THREADS;  // 16-byte X chunks per thread and tile (128 rows x 6)
+constexpr int INF_XCH = 128 * 6 / INF_EPI;  // 16-byte X chunks per epilogue thread and tile (128 rows x 6)
 
 // This thread's X chunks of the tile at row r0 (rows past M read as zero).
 __device__ __forceinline__ void x_load(const __nv_bfloat16* X, int M, int r0, uint4 (&v)[INF_XCH]) {
 #pragma unroll
   for (int j = 0; j < INF_XCH; ++j) {
-    const int idx = threadIdx.x + INF_THREADS * j, r = idx / 6, c = idx % 6;
+    const int idx = threadIdx.x + INF_EPI * j, r = idx / 6, c = idx % 6;
     v[j] = r0 + r < M ? __ldg(reinterpret_cast<const uint4*>(X + (size_t)(r0 + r) * 48 + c * 8))
                       : make_uint4(0, 0, 0, 0);
   }
@@ -228,10 +229,16 @@ __device__ __forceinline__ void x_load(const __nv_bfloat16* X, int M, int r0, ui
 __device__ __forceinline__ void x_store(uint8_t* dst, const uint4 (&v)[INF_XCH]) {
 #pragma unroll
   for (int j = 0; j < INF_XCH; ++j) {
-    const int idx = threadIdx.x + INF_THREADS * j, r = idx / 6, c = idx % 6;
+    const int idx = threadIdx.x + INF_EPI * j, r = idx / 6, c = idx % 6;
     *reinterpret_cast<uint4*>(dst + (size_t)(r >> 3) * 768 + c * 128 + (r & 7) * 16) = v[j];
   }
 }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(INF_EPI) : "memory"); }
 
 __global__ void __launch_bounds__(INF_THREADS, 1)
     mlp_infer_kernel(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
@@ -243,11 +250,14 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   float* b1s = reinterpret_cast<float*>(smem + INF_W1 + INF_W2 + INF_H1);
   float* b2s = b1s + 256;
   float* w3s = b2s + 256;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1 + INF_VEC);  // [0] layer 1, [1] layer 2
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  // mbar[0] layer 1 done, [1] layer 2 done (MMA commits); [2] X rows stored, [3 + c]
+  // chunk c of epilogue 1 written (one arrival per epilogue warp).  One barrier per
+  // chunk: a warp reaches chunk c of the next tile only after every warp has passed
+  // chunk c of this one (the next layer 1 waits for all their X stores).
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1 + INF_VEC);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 7);
   __shared__ float red[2][128];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int quad = warp & 3, half = warp >> 2;
   const int ntiles = (M + 127) / 128;
   if ((int)blockIdx.x >= ntiles) return;
   stage(w1s, W1b, 48, 256, 48, 0, 256, 0, 48, false);
@@ -264,96 +274,111 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
     mbar_init(mbar + 1, 1);
+    for (int b = 2; b < 7; ++b) mbar_init(mbar + b, INF_EPI / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  uint4 xv[INF_XCH];
-  x_load(X, M, (int)blockIdx.x * 128, xv);
-  x_store(h1s, xv);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // W1 / W2 for the tensor core
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot, acc1 = tmem, acc2 = tmem + 256;
-  const uint32_t idesc = make_idesc(128, 256);
-  const uint32_t lanebase = ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
-  const int row = quad * 32 + lane;
-  const float bias3 = *b3;
-  uint32_t ph1 = 0, ph2 = 0;
   bool ok = true;
-  auto issue_l1 = [&]() {
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      for (int kk = 0; kk < 3; ++kk)
-        mma_bf16(acc1, make_desc(smem_addr(h1s) + kk * 256, 128, 768), make_desc(smem_addr(w1s) + kk * 256, 128, 768),
-                 idesc, kk > 0);
-      mma_commit(mbar);
-    }
-  };
-  issue_l1();
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int r0 = tile * 128, next = tile + (int)gridDim.x;
-    // A, B: layer 1 of this tile, then its epilogue into H1 (the X rows there are consumed)
-    ok = mbar_wait(mbar, ph1);
-    ph1 ^= 1;
-    tc_fence_after();
-    if (!ok) break;
-    for (int c0 = 0; c0 < 128; c0 += 32) {
-      float v[32];
-      tmem_ld32(acc1 + lanebase + (uint32_t)c0, v);
-      const int col0 = half * 128 + c0;
-#pragma unroll
-      for (int c8 = 0; c8 < 4; ++c8) {
-        __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(fmaxf(v[c8 * 8 + e] + b1s[col0 + c8 * 8 + e], 0.f));
-        const int kc = (col0 >> 3) + c8;
-        *reinterpret_cast<uint4*>(h1s + (size_t)(row >> 3) * 4096 + kc * 128 + (row & 7) * 16) =
-            *reinterpret_cast<uint4*>(h);
+  if (warp == INF_EPI / 32) {
+    // ---- issuing warp
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(128, 256);
+      uint32_t px = 0, pc = 0;  // pc: parity of the four chunk barriers (one phase per tile)
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        ok = mbar_wait(mbar + 2, px);
+        px ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+        for (int kk = 0; kk < 3; ++kk)
+          mma_bf16(acc1, make_desc(smem_addr(h1s) + kk * 256, 128, 768),
+                   make_desc(smem_addr(w1s) + kk * 256, 128, 768), idesc, kk > 0);
+        mma_commit(mbar);
+        for (int c = 0; c < 4 && ok; ++c) {
+          ok = mbar_wait(mbar + 3 + c, pc);
+          if (!ok) break;
+          tc_fence_after();
+          const int ks[4] = {2 * c, 2 * c + 1, 8 + 2 * c, 9 + 2 * c};
+          for (int t = 0; t < 4; ++t)
+            mma_bf16(acc2, make_desc(smem_addr(h1s) + ks[t] * 256, 128, 4096),
+                     make_desc(smem_addr(w2s) + ks[t] * 256, 128, 4096), idesc, c > 0 || t > 0);
+        }
+        pc ^= 1;
+        if (ok) mma_commit(mbar + 1);
       }
     }
-    tc_fence_before();
+    __syncwarp();
+  } else {
+    // ---- epilogue warps
+    const int quad = warp & 3, half = warp >> 2;
+    const uint32_t lanebase = ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
+    const int row = quad * 32 + lane;
+    const float bias3 = *b3;
+    uint32_t ph1 = 0, ph2 = 0;
+    uint4 xv[INF_XCH];
+    x_load(X, M, (int)blockIdx.x * 128, xv);
+    x_store(h1s, xv);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    // C: layer 2 (the previous tile's epilogue 2 has read its TMEM columns)
-    if (threadIdx.x == 0) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(mbar + 2);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int r0 = tile * 128, next = tile + (int)gridDim.x;
+      ok = mbar_wait(mbar, ph1);  // layer 1 of this tile
+      ph1 ^= 1;
       tc_fence_after();
-      for (int kk = 0; kk < 16; ++kk)
-        mma_bf16(acc2, make_desc(smem_addr(h1s) + kk * 256, 128, 4096),
-                 make_desc(smem_addr(w2s) + kk * 256, 128, 4096), idesc, kk > 0);
-      mma_commit(mbar + 1);
-    }
-    // D: the next tile's X rows into registers while the tensor core works
-    if (next < ntiles) x_load(X, M, next * 128, xv);
-    // E: layer 2 done; H1 and layer 1's columns are free
-    ok = mbar_wait(mbar + 1, ph2);
-    ph2 ^= 1;
-    tc_fence_after();
-    if (!ok) break;
-    // F: the next tile's layer 1 runs during this tile's second epilogue
-    if (next < ntiles) {
-      x_store(h1s, xv);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      issue_l1();
-    }
-    // G: epilogue 2
-    float dot = 0.f;
-    for (int c0 = 0; c0 < 128; c0 += 32) {
-      float v[32];
-      tmem_ld32(acc2 + lanebase + (uint32_t)c0, v);
-      const int col0 = half * 128 + c0;
+      if (!ok) break;
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        float v[32];
+        tmem_ld32(acc1 + lanebase + (uint32_t)c0, v);
+        const int col0 = half * 128 + c0;
 #pragma unroll
-      for (int e = 0; e < 32; ++e)
-        dot = fmaf(__bfloat162float(__float2bfloat16(fmaxf(v[e] + b2s[col0 + e], 0.f))), w3s[col0 + e], dot);
+        for (int c8 = 0; c8 < 4; ++c8) {
+          __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(fmaxf(v[c8 * 8 + e] + b1s[col0 + c8 * 8 + e], 0.f));
+          const int kc = (col0 >> 3) + c8;
+          *reinterpret_cast<uint4*>(h1s + (size_t)(row >> 3) * 4096 + kc * 128 + (row & 7) * 16) =
+              *reinterpret_cast<uint4*>(h);
+        }
+        // this chunk (and, before the first, the previous tile's reads of layer 2's
+        // columns) is done: the issuing warp may run its slices of layer 2
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(mbar + 3 + (c0 >> 5));
+      }
+      if (next < ntiles) x_load(X, M, next * 128, xv);  // during layer 2
+      ok = mbar_wait(mbar + 1, ph2);                      // layer 2 done: H1 is free
+      ph2 ^= 1;
+      tc_fence_after();
+      if (!ok) break;
+      if (next < ntiles) {  // the next tile's layer 1 overlaps epilogue 2
+        x_store(h1s, xv);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(mbar + 2);
+      }
+      float dot = 0.f;
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        float v[32];
+        tmem_ld32(acc2 + lanebase + (uint32_t)c0, v);
+        const int col0 = half * 128 + c0;
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          dot = fmaf(__bfloat162float(__float2bfloat16(fmaxf(v[e] + b2s[col0 + e], 0.f))), w3s[col0 + e], dot);
+      }
+      red[half][row] = dot;
+      epi_sync();
+      if (threadIdx.x < 128 && r0 + (int)threadIdx.x < M)
+        y[r0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x] + bias3;
+      epi_sync();
     }
-    red[half][row] = dot;
-    tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x < 128 && r0 + (int)threadIdx.x < M)
-      y[r0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x] + bias3;
-    __syncthreads();
   }
-  if (!ok && threadIdx.x == 0 && err) atomicExch(err, 1);
+  if (!ok && err) atomicExch(err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
@@ -371,7 +396,7 @@ cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b
                          const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
                          int num_sms, cudaStream_t st) {
   static bool attr = false;
-  const size_t smem = INF_W1 + INF_W2 + INF_H1 + INF_VEC + 32;
+  const size_t smem = INF_W1 + INF_W2 + INF_H1 + INF_VEC + 64;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
