@@ -144,6 +144,8 @@ struct gd_pocket {
   gd::PocketDev dev{};
   void* buf = nullptr;
   size_t buf_bytes = 0;
+  cudaArray_t arr = nullptr;  // the crop again as a 3D array, behind dev.tex
+  size_t arr_bytes = 0;
   int nx = 0, ny = 0, nz = 0;
 };
 
@@ -736,6 +738,54 @@ gd_status gd_load_pocket(gd_ctx* c, const uint8_t* grid, int nx, int ny, int nz,
     delete P;
     return fail(GD_ECUDA, "pocket upload: %s", cudaGetErrorString(e));
   }
+  // the same crop as a 3D array behind a texture object (point sampling, border 0)
+  {
+    const size_t abytes = (size_t)cx * cy * cz;
+    bool over = false;
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      over = c->budget && c->used + abytes > c->budget;
+    }
+    if (over) {
+      dev_release(c, P->buf, pad);
+      delete P;
+      return fail(GD_EBUDGET, "device budget %zu B exceeded by the pocket texture", c->budget);
+    }
+    cudaChannelFormatDesc cd = cudaCreateChannelDesc<unsigned char>();
+    const cudaExtent ext = make_cudaExtent(cx, cy, cz);
+    e = cudaMalloc3DArray(&P->arr, &cd, ext);
+    if (e == cudaSuccess) {
+      cudaMemcpy3DParms cp = {};
+      cp.srcPtr = make_cudaPitchedPtr(crop.data(), cx, cx, cy);
+      cp.dstArray = P->arr;
+      cp.extent = ext;
+      cp.kind = cudaMemcpyHostToDevice;
+      e = cudaMemcpy3D(&cp);
+    }
+    cudaTextureObject_t tex = 0;
+    if (e == cudaSuccess) {
+      cudaResourceDesc rd = {};
+      rd.resType = cudaResourceTypeArray;
+      rd.res.array.array = P->arr;
+      cudaTextureDesc td = {};
+      td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeBorder;
+      td.filterMode = cudaFilterModePoint;
+      td.readMode = cudaReadModeElementType;
+      td.normalizedCoords = 0;
+      e = cudaCreateTextureObject(&tex, &rd, &td, nullptr);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (P->arr) cudaFreeArray(P->arr);
+      dev_release(c, P->buf, pad);
+      delete P;
+      return fail(GD_ECUDA, "pocket texture: %s", cudaGetErrorString(e));
+    }
+    P->arr_bytes = abytes;
+    P->dev.tex = (unsigned long long)tex;
+    std::lock_guard<std::mutex> g(c->mu);
+    c->used += abytes;
+  }
   P->nx = nx; P->ny = ny; P->nz = nz;
   gd::PocketDev& d = P->dev;
   d.grid = (const uint8_t*)P->buf;
@@ -756,6 +806,12 @@ gd_status gd_free_pocket(gd_ctx* c, gd_pocket* P) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();  // a queued job may still read the grid
   dev_release(c, P->buf, P->buf_bytes);
+  if (P->dev.tex) cudaDestroyTextureObject((cudaTextureObject_t)P->dev.tex);
+  if (P->arr) {
+    cudaFreeArray(P->arr);
+    std::lock_guard<std::mutex> g(c->mu);
+    c->used -= P->arr_bytes;
+  }
   delete P;
   return GD_OK;
 }

@@ -39,6 +39,8 @@ struct PocketDev {
   float inv_h;
   float shift[3];        // n/2 - crop_lo per axis: cell = floor(x_rel * inv_h + shift)
   float centre[3];       // pocket centre (world): x_world = x_rel + centre
+  unsigned long long tex;  // texture object over the crop (point sampling, border 0,
+                           // unnormalised coordinates); 0: none (grid read through L1)
 };
 
 struct SearchArgs {

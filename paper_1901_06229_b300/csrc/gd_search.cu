@@ -99,16 +99,24 @@ __device__ __forceinline__ void turn(float4 x, float4 dp, float2 w2, float2 cs, 
   oz = __fmaf_rn(cs.y, w2.y, __fmaf_rn(cs.x, dp.z, x.z));
 }
 
+// Grid access modes of the search: the cropped grid read through L1 (GRID_LDG), staged
+// in shared memory (GRID_SMEM), or fetched by the texture unit (GRID_TEX: point
+// sampling of unnormalised coordinates selects texel floor(f) exactly, and the border
+// mode returns 0 outside the crop, so the fetch is the same lookup in one instruction).
+constexpr int GRID_LDG = 0, GRID_SMEM = 1, GRID_TEX = 2;
+
 // Grid cell under a point (pocket-centred coordinates); 0 outside the cropped box.
-template <bool SG>
+template <int G>
 __device__ __forceinline__ int cell(const PocketDev& pk, const uint8_t* sg, float x, float y, float z) {
-  const int ix = __float2int_rd(__fmaf_rn(x, pk.inv_h, pk.shift[0]));
-  const int iy = __float2int_rd(__fmaf_rn(y, pk.inv_h, pk.shift[1]));
-  const int iz = __float2int_rd(__fmaf_rn(z, pk.inv_h, pk.shift[2]));
+  const float fx = __fmaf_rn(x, pk.inv_h, pk.shift[0]);
+  const float fy = __fmaf_rn(y, pk.inv_h, pk.shift[1]);
+  const float fz = __fmaf_rn(z, pk.inv_h, pk.shift[2]);
+  if (G == GRID_TEX) return (int)tex3D<unsigned char>((cudaTextureObject_t)pk.tex, fx, fy, fz);
+  const int ix = __float2int_rd(fx), iy = __float2int_rd(fy), iz = __float2int_rd(fz);
   if ((unsigned)ix >= (unsigned)pk.cx || (unsigned)iy >= (unsigned)pk.cy || (unsigned)iz >= (unsigned)pk.cz)
     return 0;
   const int idx = (iz * pk.cy + iy) * pk.cx + ix;
-  if (SG) return sg[idx];
+  if (G == GRID_SMEM) return sg[idx];
   return __ldg(pk.grid + idx);
 }
 
@@ -213,7 +221,7 @@ __device__ __forceinline__ int frag_size(const RotDesc& rd, int n) {
 // Commit the winning rotation to the fragment (same arithmetic as the candidate); the
 // w component of each moved atom caches its new grid cell.  DP / W2: the step's axis
 // frames in sweep order when the search has them, else (replay) NULL and recomputed.
-template <bool SG>
+template <int G>
 __device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n, const RotDesc& rd, float ux,
                        float uy, float uz, float2 cs, int lane, const float4* DP, const float2* W2) {
   const float4 xp = X[rd.p];
@@ -232,19 +240,19 @@ __device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n,
       axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
     }
     turn(v, dp, w2, cs, x, y, z);
-    X[t] = make_float4(x, y, z, __int_as_float(cell<SG>(pk, sg, x, y, z)));
+    X[t] = make_float4(x, y, z, __int_as_float(cell<G>(pk, sg, x, y, z)));
   }
   __syncwarp();
 }
 
 // Rigid score of the pose (sum of the grid cells under its atoms); each atom's cell is
 // cached in the w component of its coordinates.
-template <bool SG>
+template <int G>
 __device__ __forceinline__ int score_atoms(const PocketDev& pk, const uint8_t* sg, float4* X, int n, int lane) {
   int s = 0;
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
-    const int c = cell<SG>(pk, sg, v.x, v.y, v.z);
+    const int c = cell<G>(pk, sg, v.x, v.y, v.z);
     X[i].w = __int_as_float(c);
     s += c;
   }
@@ -329,7 +337,7 @@ __device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp,
 
 // Evaluate every angle of one rotamer step; returns the warp-wide best key
 // ((score + 1) << 16 | (0xFFFF - k)), 0 if every candidate is bumped.
-template <int S, bool SG>
+template <int S, int G>
 __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, const uint16_t* excl,
                               int n, const RotDesc& rd, int cur, int lane, unsigned long long& pairs,
                               uint8_t* dbg) {
@@ -388,7 +396,7 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const Warp
 #pragma unroll
         for (int j = 0; j < S; ++j) {
           turn(xa, dp, w2, cs[j], xr[j][0], xr[j][1], xr[j][2]);
-          sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
+          sc[j] += cell<G>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
           mind[j] = 3.0e38f;
         }
         min_d2_range<S>(X, s0a, s0b, xr, mind);
@@ -511,7 +519,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
 }
 
 // Every angle of one rotamer step, bump tests restricted to the near list.
-template <int S, bool SG>
+template <int S, int G>
 __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
                                    const RotDesc& rd, int cur, int n_near, int lane,
                                    unsigned long long& pairs, uint8_t* dbg) {
@@ -549,7 +557,7 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 #pragma unroll
         for (int j = 0; j < S; ++j) {
           turn(xa, dp, w2, cs[j], xr[j][0], xr[j][1], xr[j][2]);
-          sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
+          sc[j] += cell<G>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
         }
         const int e1 = w.MOFF[ia + 1];
         for (int e = w.MOFF[ia]; e < e1; ++e) {
@@ -578,7 +586,7 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 
 // Every angle of one rotamer step, bump tests restricted to the near pairs of the
 // step's masks (n_near of them); used when the near list overflowed.
-template <int S, bool SG>
+template <int S, int G>
 __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
                                    const RotDesc& rd, int cur, int n_near, int lane,
                                    unsigned long long& pairs, uint8_t* dbg) {
@@ -621,7 +629,7 @@ __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, cons
 #pragma unroll
         for (int j = 0; j < S; ++j) {
           turn(xa, dp, w2, cs[j], xr[j][0], xr[j][1], xr[j][2]);
-          sc[j] += cell<SG>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
+          sc[j] += cell<G>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
         }
         for (int c = 0; c < nch; ++c) {
           unsigned mk = row[c];
@@ -683,7 +691,7 @@ __device__ void rigid_apply(const SearchArgs& a, float4* X, int n, int m, int la
 }
 
 // Best rigid candidate by score (ties to the smaller m); applies it and returns m.
-template <bool SG>
+template <int G>
 __device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, int n, int lane) {
   unsigned best = 0;
   for (int m = lane; m < a.rigid_n; m += 32) {
@@ -691,7 +699,7 @@ __device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, in
     if (m == 0) {
       for (int i = 0; i < n; ++i) {
         const float4 v = X[i];
-        sc += cell<SG>(a.pk, sg, v.x, v.y, v.z);
+        sc += cell<G>(a.pk, sg, v.x, v.y, v.z);
       }
     } else {
       const Rot3 R = rigid_rotation(a, m);
@@ -699,7 +707,7 @@ __device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, in
         const float4 v = X[i];
         float x, y, z;
         rot_apply(R, v.x, v.y, v.z, x, y, z);
-        sc += cell<SG>(a.pk, sg, x, y, z);
+        sc += cell<G>(a.pk, sg, x, y, z);
       }
     }
     const unsigned key = ((unsigned)(sc + 1) << 16) | (0xFFFFu - (unsigned)m);
@@ -712,7 +720,7 @@ __device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, in
 }
 
 // a10: reduce over the ligand's restarts, replay the winner, write the results.
-template <bool SG>
+template <int G>
 __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int lane) {
   float4* X = w.X;
   const int O = a.O;
@@ -770,7 +778,7 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
       const RotDesc rd = w.RD[r];  // registers: the loops below also write shared memory
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
-      commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, nullptr, nullptr);
+      commit<G>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, nullptr, nullptr);
     }
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
@@ -782,7 +790,7 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   __syncwarp();
 }
 
-template <int S, bool SG>
+template <int S, int G>
 __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int lane) {
   float4* X = w.X;
   const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
@@ -800,10 +808,10 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   __syncwarp();
   place(a, X, a0, n, o, lane);
   {
-    const int m = a.rigid_n > 1 ? rigid_align<SG>(a, sg, X, n, lane) : 0;
+    const int m = a.rigid_n > 1 ? rigid_align<G>(a, sg, X, n, lane) : 0;
     if (lane == 0 && a.pose_rigid) a.pose_rigid[(size_t)li * a.O + o] = (int16_t)m;
   }
-  int cur = score_atoms<SG>(a.pk, sg, X, n, lane);
+  int cur = score_atoms<G>(a.pk, sg, X, n, lane);
   unsigned long long pairs = 0, reach = 0;
   const size_t pick_base = (size_t)r0 * a.reps * a.O + (size_t)o * a.reps * R;
   for (int rep = 0; rep < a.reps; ++rep)
@@ -820,14 +828,14 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       if (a.use_filter) {
         const int n_near = build_near(a, w, excl, n, rd, lane, reach);
         if (n_near <= 8 * a.nmax && !a.mask_sweep)
-          key = eval_step_near<S, SG>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
+          key = eval_step_near<S, G>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
         else
-          key = eval_step_masks<S, SG>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
+          key = eval_step_masks<S, G>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
       } else
-        key = eval_step<S, SG>(a, sg, w, excl, n, rd, cur, lane, pairs, dbg);
+        key = eval_step<S, G>(a, sg, w, excl, n, rd, cur, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
-        commit<SG>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, w.DP, w.W2);
+        commit<G>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, w.DP, w.W2);
         cur = (int)(key >> 16) - 1;
       }
       if (lane == 0) a.pose_pick[pick_base + rep * R + r] = (int16_t)k;
@@ -847,7 +855,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   prev = __shfl_sync(FULL, prev, 0);
   if (prev == (a.item_cnt ? a.item_cnt[li] : a.O) - 1) {
     __threadfence();
-    finalize<SG>(a, sg, w, li, lane);
+    finalize<G>(a, sg, w, li, lane);
   }
 }
 
@@ -891,13 +899,13 @@ __device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
   return true;
 }
 
-template <int S, bool SG, bool LEAN>
+template <int S, int G, bool LEAN>
 __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 4 : 1) search_kernel(const __grid_constant__ SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* sg = nullptr;
   size_t off = 0;
-  if (SG) {
+  if (G == GRID_SMEM) {
     sg = smem;
     off = (size_t)a.pk.bytes_pad;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + off);
@@ -930,7 +938,7 @@ __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 4 : 1) search_kernel(
       li = a.order[t / (unsigned long long)a.O];
       o = (int)(t % (unsigned long long)a.O);
     }
-    search_pose<S, SG>(a, sg, w, li, o, lane);
+    search_pose<S, G>(a, sg, w, li, o, lane);
   }
 }
 
@@ -1067,7 +1075,7 @@ __global__ void __launch_bounds__(256) feature_kernel(const __grid_constant__ Se
         const float X = __fmaf_rn(r0, d.x, __fmaf_rn(r1, d.y, __fmul_rn(r2, d.z)));
         const float Y = __fmaf_rn(r3, d.x, __fmaf_rn(r4, d.y, __fmul_rn(r5, d.z)));
         const float Z = __fmaf_rn(r6, d.x, __fmaf_rn(r7, d.y, __fmul_rn(r8, d.z)));
-        f[23 + t] = (float)cell<false>(a.pk, nullptr, X, Y, Z) / 255.f;
+        f[23 + t] = (float)cell<GRID_LDG>(a.pk, nullptr, X, Y, Z) / 255.f;
       }
       const size_t row = (size_t)li * a.O + o;
       if (Xb) {
@@ -1176,9 +1184,9 @@ __global__ void items_kernel(const int32_t* order, const int32_t* cnt, const int
   }
 }
 
-template <int S, bool SG, bool LEAN>
+template <int S, int G, bool LEAN>
 cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, LaunchCfg* cfg) {
-  auto k = search_kernel<S, SG, LEAN>;
+  auto k = search_kernel<S, G, LEAN>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1230,25 +1238,32 @@ int default_tile(const SearchArgs& a) {
 cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int num_sms, LaunchCfg* cfg) {
   const Tile t = tile_get(tile);
   const size_t smem = search_smem_bytes(a, tile, grid_in_smem);
+  const bool tex = !grid_in_smem && a.pk.tex != 0;
   if (t.lean) {
     if (grid_in_smem) return cudaErrorInvalidConfiguration;
-    switch (t.slots) {
-      case 1: return plan_t<1, false, true>(a, t.warps, smem, num_sms, cfg);
-      case 2: return plan_t<2, false, true>(a, t.warps, smem, num_sms, cfg);
-      default: return plan_t<4, false, true>(a, t.warps, smem, num_sms, cfg);
+    switch (t.slots * 2 + (tex ? 1 : 0)) {
+      case 2: return plan_t<1, GRID_LDG, true>(a, t.warps, smem, num_sms, cfg);
+      case 3: return plan_t<1, GRID_TEX, true>(a, t.warps, smem, num_sms, cfg);
+      case 4: return plan_t<2, GRID_LDG, true>(a, t.warps, smem, num_sms, cfg);
+      case 5: return plan_t<2, GRID_TEX, true>(a, t.warps, smem, num_sms, cfg);
+      case 8: return plan_t<4, GRID_LDG, true>(a, t.warps, smem, num_sms, cfg);
+      default: return plan_t<4, GRID_TEX, true>(a, t.warps, smem, num_sms, cfg);
     }
   }
   if (grid_in_smem) {
     switch (t.slots) {
-      case 1: return plan_t<1, true, false>(a, t.warps, smem, num_sms, cfg);
-      case 2: return plan_t<2, true, false>(a, t.warps, smem, num_sms, cfg);
-      default: return plan_t<4, true, false>(a, t.warps, smem, num_sms, cfg);
+      case 1: return plan_t<1, GRID_SMEM, false>(a, t.warps, smem, num_sms, cfg);
+      case 2: return plan_t<2, GRID_SMEM, false>(a, t.warps, smem, num_sms, cfg);
+      default: return plan_t<4, GRID_SMEM, false>(a, t.warps, smem, num_sms, cfg);
     }
   }
-  switch (t.slots) {
-    case 1: return plan_t<1, false, false>(a, t.warps, smem, num_sms, cfg);
-    case 2: return plan_t<2, false, false>(a, t.warps, smem, num_sms, cfg);
-    default: return plan_t<4, false, false>(a, t.warps, smem, num_sms, cfg);
+  switch (t.slots * 2 + (tex ? 1 : 0)) {
+    case 2: return plan_t<1, GRID_LDG, false>(a, t.warps, smem, num_sms, cfg);
+    case 3: return plan_t<1, GRID_TEX, false>(a, t.warps, smem, num_sms, cfg);
+    case 4: return plan_t<2, GRID_LDG, false>(a, t.warps, smem, num_sms, cfg);
+    case 5: return plan_t<2, GRID_TEX, false>(a, t.warps, smem, num_sms, cfg);
+    case 8: return plan_t<4, GRID_LDG, false>(a, t.warps, smem, num_sms, cfg);
+    default: return plan_t<4, GRID_TEX, false>(a, t.warps, smem, num_sms, cfg);
   }
 }
 
