@@ -574,6 +574,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.order = (const int32_t*)(d + j->in.order);
   a.excl = (const uint16_t*)(d + j->in.excl);
   a.n_items = (long long)L * j->O;
+  a.chunk = gd::work_chunk(a.n_items);
   a.na = p->n_alpha;
   a.nb = p->n_beta;
   a.ng = p->n_gamma;

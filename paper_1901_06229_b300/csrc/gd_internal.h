@@ -55,6 +55,7 @@ struct SearchArgs {
   const uint16_t* excl;       // [sum n_excl] excluded pairs (a | b << 8)
   const int32_t* order;       // [L] ligand processing order (largest cost first)
   long long n_items;          // L * O
+  int chunk;                  // items a warp takes at a time (4 for large batches, else 1)
   const uint32_t* items;      // optional explicit (ligand, restart) list, rows li * O + o
   const int32_t* item_cnt;    // with items: restarts searched per ligand (>= 1)
   const int32_t* n_items_dev; // with items: list length (device scalar)
@@ -122,6 +123,10 @@ __host__ __device__ inline int frag_atoms(int n, const RotDesc& d) {
 }
 
 enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };
+
+// Items per work-queue grab: 4 once there are at least 8 per warp a full GPU holds
+// (148 SMs x 32 warps), so chunking never idles warps on small batches.
+inline int work_chunk(long long n_items) { return n_items >= 8LL * 148 * 32 ? 4 : 1; }
 
 // pose_score of a restart that a subset launch leaves out (buffers are filled with it)
 constexpr uint32_t NOT_SEARCHED = 0xFFFFFFFFu;

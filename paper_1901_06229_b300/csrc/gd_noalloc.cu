@@ -356,6 +356,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.excl = (const uint16_t*)(d + o_excl);
   a.order = (const int32_t*)(d + o_order);
   a.n_items = (long long)L * O;
+  a.chunk = gd::work_chunk(a.n_items);
   a.na = p->n_alpha;
   a.nb = p->n_beta;
   a.ng = p->n_gamma;

@@ -791,21 +791,11 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
 }
 
 template <int S, int G>
-__device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int lane) {
+__device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int e0,
+                            int lane) {
   float4* X = w.X;
   const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
   const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
-  // this ligand's rotamer descriptors and excluded pairs, once per pose
-  int e0 = 0;
-  if (R > 0) {
-    for (int i = lane; i < 4 * R; i += 32)
-      reinterpret_cast<uint32_t*>(w.RD)[i] = __ldg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i);
-    __syncwarp();
-    e0 = (int)w.RD[0].excl_off;
-    const int ne = (int)w.RD[R - 1].excl_off + w.RD[R - 1].n_excl - e0;
-    for (int i = lane; i < ne; i += 32) w.EXL[i] = __ldg(a.excl + e0 + i);
-  }
-  __syncwarp();
   place(a, X, a0, n, o, lane);
   {
     const int m = a.rigid_n > 1 ? rigid_align<G>(a, sg, X, n, lane) : 0;
@@ -849,11 +839,35 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
     a.pose_reach[(size_t)li * a.O + o] = reach;
   }
   __syncwarp();
+}
+
+// A ligand's rotamer descriptors and excluded pairs into the warp's buffers; returns the
+// offset of its first excluded pair.
+__device__ int load_ligand(const SearchArgs& a, const WarpMem& w, int li, int lane) {
+  const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
+  int e0 = 0;
+  __syncwarp();
+  if (R > 0) {
+    for (int i = lane; i < 4 * R; i += 32)
+      reinterpret_cast<uint32_t*>(w.RD)[i] = __ldg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i);
+    __syncwarp();
+    e0 = (int)w.RD[0].excl_off;
+    const int ne = (int)w.RD[R - 1].excl_off + w.RD[R - 1].n_excl - e0;
+    for (int i = lane; i < ne; i += 32) w.EXL[i] = __ldg(a.excl + e0 + i);
+  }
+  __syncwarp();
+  return e0;
+}
+
+// Completion of `done` poses of ligand li by this warp: the warp that completes the
+// ligand's count reduces its restarts (a10); the fence orders the poses' results first.
+template <int G>
+__device__ void complete(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int done, int lane) {
   __threadfence();
   int prev = 0;
-  if (lane == 0) prev = atomicAdd(a.done + li, 1);
+  if (lane == 0) prev = atomicAdd(a.done + li, done);
   prev = __shfl_sync(FULL, prev, 0);
-  if (prev == (a.item_cnt ? a.item_cnt[li] : a.O) - 1) {
+  if (prev + done == (a.item_cnt ? a.item_cnt[li] : a.O)) {
     __threadfence();
     finalize<G>(a, sg, w, li, lane);
   }
@@ -922,24 +936,41 @@ __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 4 : 1) search_kernel(
   __syncthreads();
   WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.fmax, a.mask_words, a.rmax, a.emax);
   w.CS = cs;
-  // items: every (ligand, restart) in queue order, or an explicit list of rows li*O + o
+  // items: every (ligand, restart) in queue order, or an explicit list of rows li*O + o;
+  // a warp takes a.chunk consecutive items at a time (mostly restarts of one ligand), loads
+  // a ligand's descriptors once per run of its restarts and reports the run's completion
+  // with one atomic
+  const unsigned long long CHUNK = (unsigned long long)a.chunk;
   const unsigned long long n_items = a.items ? (unsigned long long)*a.n_items_dev : (unsigned long long)a.n_items;
+  const unsigned long long n_chunks = (n_items + CHUNK - 1) / CHUNK;
+  int cur = -1, e0 = 0, pending = 0;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(a.work, 1ull);
     t = __shfl_sync(FULL, t, 0);
-    if (t >= n_items) break;
-    int li, o;
-    if (a.items) {
-      const unsigned row = __ldg(a.items + t);
-      li = (int)(row / (unsigned)a.O);
-      o = (int)(row % (unsigned)a.O);
-    } else {
-      li = a.order[t / (unsigned long long)a.O];
-      o = (int)(t % (unsigned long long)a.O);
+    if (t >= n_chunks) break;
+    const unsigned long long q1 = (t + 1) * CHUNK < n_items ? (t + 1) * CHUNK : n_items;
+    for (unsigned long long q = t * CHUNK; q < q1; ++q) {
+      int li, o;
+      if (a.items) {
+        const unsigned row = __ldg(a.items + q);
+        li = (int)(row / (unsigned)a.O);
+        o = (int)(row % (unsigned)a.O);
+      } else {
+        li = a.order[q / (unsigned long long)a.O];
+        o = (int)(q % (unsigned long long)a.O);
+      }
+      if (li != cur) {
+        if (pending) complete<G>(a, sg, w, cur, pending, lane);
+        cur = li;
+        pending = 0;
+        e0 = load_ligand(a, w, li, lane);
+      }
+      search_pose<S, G>(a, sg, w, li, o, e0, lane);
+      ++pending;
     }
-    search_pose<S, G>(a, sg, w, li, o, lane);
   }
+  if (pending) complete<G>(a, sg, w, cur, pending, lane);
 }
 
 // ---- features of the learned orientation proposer -----------------------------------
@@ -1194,7 +1225,7 @@ cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, Lau
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = (long long)per_sm * num_sms;
-  const long long need = (a.n_items + warps - 1) / warps;
+  const long long need = ((a.n_items + a.chunk - 1) / a.chunk + warps - 1) / warps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   cfg->fn = (const void*)k;
