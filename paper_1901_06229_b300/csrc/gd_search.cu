@@ -203,7 +203,9 @@ __global__ void __launch_bounds__(256) pose_setup_kernel(const __grid_constant__
 __device__ __forceinline__ void bond_axis(const float4* X, const RotDesc& rd, float& ux, float& uy, float& uz) {
   const float4 xp = X[rd.p], xq = X[rd.q];
   const float dx = __fsub_rn(xq.x, xp.x), dy = __fsub_rn(xq.y, xp.y), dz = __fsub_rn(xq.z, xp.z);
-  const float inv = __frsqrt_rn(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
+  // hardware reciprocal square root: deterministic, so the search and its replay agree,
+  // and within 1e-7 relative of the rounded one
+  const float inv = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
   ux = __fmul_rn(dx, inv);
   uy = __fmul_rn(dy, inv);
   uz = __fmul_rn(dz, inv);
@@ -324,7 +326,10 @@ __device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp,
     float2 w2;
     float h;
     axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
-    w.HR[i] = make_float2(h, __fsqrt_rn(__fmaf_rn(dp.x, dp.x, __fmaf_rn(dp.y, dp.y, __fmul_rn(dp.z, dp.z)))));
+    // rho from the hardware reciprocal square root (error ~1e-6 A, far inside the
+    // filter's 0.01 A margin; rho only feeds the filter)
+    const float r2 = fmaxf(__fmaf_rn(dp.x, dp.x, __fmaf_rn(dp.y, dp.y, __fmul_rn(dp.z, dp.z))), 1e-30f);
+    w.HR[i] = make_float2(h, __fmul_rn(r2, rsqrtf(r2)));
     const bool in = i >= rd.lo && i < rd.hi;
     if (in != (rd.comp != 0)) {
       const int ia = rd.comp ? (i < rd.lo ? i : i - (rd.hi - rd.lo)) : i - rd.lo;
@@ -463,6 +468,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
     uint32_t* col = w.MASK + c;
     for (int seg = 0; seg < 2; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
+#pragma unroll 4
       for (int ai = ma; ai < mb; ++ai, col += nch) {
         const float2 ha = w.HR[ai];
         const float dh = __fsub_rn(ha.x, hb.x), dr = __fsub_rn(ha.y, hb.y);
