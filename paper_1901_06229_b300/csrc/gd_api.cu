@@ -581,8 +581,11 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.O = j->O;
   a.A = j->A;
   a.reps = j->reps;
-  a.thr2 = p->bump_dist * p->bump_dist;
-  a.reach2 = (p->bump_dist + gd::REACH_MARGIN) * (p->bump_dist + gd::REACH_MARGIN);
+  {
+    const float ih = a.pk.inv_h, bd = p->bump_dist * ih, rd = (p->bump_dist + gd::REACH_MARGIN) * ih;
+    a.thr2 = bd * bd;
+    a.reach2 = rd * rd;
+  }
   a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
   a.mask_sweep = (p->flags & GD_FLAG_MASK_SWEEP) ? 1 : 0;
   char* o = (char*)j->d_out;
@@ -793,6 +796,7 @@ gd_status gd_load_pocket(gd_ctx* c, const uint8_t* grid, int nx, int ny, int nz,
   d.cx = cx; d.cy = cy; d.cz = cz;
   d.bytes_pad = (int)pad;
   d.inv_h = (float)(1.0 / (double)h);
+  d.h = h;
   const int n[3] = {nx, ny, nz};
   for (int a = 0; a < 3; ++a) {
     d.shift[a] = (float)(0.5 * n[a] - lo[a]);

@@ -36,7 +36,7 @@ struct PocketDev {
   const uint8_t* grid;   // cropped grid [cz][cy][cx]; cells outside the crop are 0
   int cx, cy, cz;        // crop extents (cells)
   int bytes_pad;         // cx*cy*cz rounded up to 16 (bulk-copy granule)
-  float inv_h;
+  float inv_h, h;        // 1 / spacing, spacing (A)
   float shift[3];        // n/2 - crop_lo per axis: cell = floor(x_rel * inv_h + shift)
   float centre[3];       // pocket centre (world): x_world = x_rel + centre
   unsigned long long tex;  // texture object over the crop (point sampling, border 0,
@@ -61,8 +61,10 @@ struct SearchArgs {
   const int32_t* n_items_dev; // with items: list length (device scalar)
   // search parameters
   int na, nb, ng, O, A, reps;
-  float thr2;                 // bump_dist^2
-  float reach2;               // (bump_dist + REACH_MARGIN)^2: pairs farther apart at every angle skip the test
+  // The search keeps pose coordinates in grid units, g = x_rel * inv_h + shift (so a
+  // point's cell is floor(g)); both squared distances are in those units.
+  float thr2;                 // (bump_dist inv_h)^2
+  float reach2;               // ((bump_dist + REACH_MARGIN) inv_h)^2: pairs farther apart at every angle skip the test
   int use_filter;             // 1: per-rotamer reach filter; 0: test every moving x static pair
   int mask_sweep;             // 1: always sweep the filter's masks, never its near list
   // outputs

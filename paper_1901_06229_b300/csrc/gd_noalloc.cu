@@ -342,6 +342,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.pk.cz = cz;
   a.pk.bytes_pad = (int)grid_pad;
   a.pk.inv_h = (float)(1.0 / (double)spacing);
+  a.pk.h = spacing;
   const int nn[3] = {nx, ny, nz};
   for (int k = 0; k < 3; ++k) {
     a.pk.shift[k] = (float)(0.5 * nn[k] - lo[k]);
@@ -363,8 +364,11 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   a.O = O;
   a.A = A;
   a.reps = reps;
-  a.thr2 = p->bump_dist * p->bump_dist;
-  a.reach2 = (p->bump_dist + gd::REACH_MARGIN) * (p->bump_dist + gd::REACH_MARGIN);
+  {
+    const float ih = a.pk.inv_h, bd = p->bump_dist * ih, rd = (p->bump_dist + gd::REACH_MARGIN) * ih;
+    a.thr2 = bd * bd;
+    a.reach2 = rd * rd;
+  }
   a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
   a.mask_sweep = (p->flags & GD_FLAG_MASK_SWEEP) ? 1 : 0;
   a.best_score = (uint32_t*)(d + o_score);

@@ -105,12 +105,9 @@ __device__ __forceinline__ void turn(float4 x, float4 dp, float2 w2, float2 cs, 
 // mode returns 0 outside the crop, so the fetch is the same lookup in one instruction).
 constexpr int GRID_LDG = 0, GRID_SMEM = 1, GRID_TEX = 2;
 
-// Grid cell under a point (pocket-centred coordinates); 0 outside the cropped box.
+// Grid cell under a point in grid units (cell = floor per axis); 0 outside the crop.
 template <int G>
-__device__ __forceinline__ int cell(const PocketDev& pk, const uint8_t* sg, float x, float y, float z) {
-  const float fx = __fmaf_rn(x, pk.inv_h, pk.shift[0]);
-  const float fy = __fmaf_rn(y, pk.inv_h, pk.shift[1]);
-  const float fz = __fmaf_rn(z, pk.inv_h, pk.shift[2]);
+__device__ __forceinline__ int cell(const PocketDev& pk, const uint8_t* sg, float fx, float fy, float fz) {
   if (G == GRID_TEX) return (int)tex3D<unsigned char>((cudaTextureObject_t)pk.tex, fx, fy, fz);
   const int ix = __float2int_rd(fx), iy = __float2int_rd(fy), iz = __float2int_rd(fz);
   if ((unsigned)ix >= (unsigned)pk.cx || (unsigned)iy >= (unsigned)pk.cy || (unsigned)iz >= (unsigned)pk.cz)
@@ -128,8 +125,9 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// a3: x <- R_o (x0 - c_lig), coordinates relative to the pocket centre.  The centred
-// coordinates x0 - c_lig and the restart rotations R_o come from pose_setup_kernel.
+// a3: x <- R_o (x0 - c_lig), coordinates relative to the pocket centre, kept in grid
+// units (x inv_h + shift).  The centred coordinates x0 - c_lig and the restart
+// rotations R_o come from pose_setup_kernel.
 __device__ void place(const SearchArgs& a, float4* X, int a0, int n, int o, int lane) {
   const float* r = a.rmat + 9 * (size_t)o;
   const float r00 = __ldg(r + 0), r01 = __ldg(r + 1), r02 = __ldg(r + 2);
@@ -137,9 +135,11 @@ __device__ void place(const SearchArgs& a, float4* X, int a0, int n, int o, int 
   const float r20 = __ldg(r + 6), r21 = __ldg(r + 7), r22 = __ldg(r + 8);
   for (int i = lane; i < n; i += 32) {
     const float4 d = __ldg(a.xc + a0 + i);
-    X[i] = make_float4(__fmaf_rn(r00, d.x, __fmaf_rn(r01, d.y, __fmul_rn(r02, d.z))),
-                       __fmaf_rn(r10, d.x, __fmaf_rn(r11, d.y, __fmul_rn(r12, d.z))),
-                       __fmaf_rn(r20, d.x, __fmaf_rn(r21, d.y, __fmul_rn(r22, d.z))), 0.f);
+    const float x = __fmaf_rn(r00, d.x, __fmaf_rn(r01, d.y, __fmul_rn(r02, d.z)));
+    const float y = __fmaf_rn(r10, d.x, __fmaf_rn(r11, d.y, __fmul_rn(r12, d.z)));
+    const float z = __fmaf_rn(r20, d.x, __fmaf_rn(r21, d.y, __fmul_rn(r22, d.z)));
+    X[i] = make_float4(__fmaf_rn(x, a.pk.inv_h, a.pk.shift[0]), __fmaf_rn(y, a.pk.inv_h, a.pk.shift[1]),
+                       __fmaf_rn(z, a.pk.inv_h, a.pk.shift[2]), 0.f);
   }
   __syncwarp();
 }
@@ -680,7 +680,9 @@ __device__ __forceinline__ Rot3 rigid_rotation(const SearchArgs& a, int m) {
   float sn, cs;
   sincosf(th, &sn, &cs);
   const float inv = __frcp_rn(th);
-  return rodrigues(__fmul_rn(vx, inv), __fmul_rn(vy, inv), __fmul_rn(vz, inv), cs, sn, make_float4(0.f, 0.f, 0.f, 0.f));
+  // about the pocket centre, which sits at `shift` in grid units
+  return rodrigues(__fmul_rn(vx, inv), __fmul_rn(vy, inv), __fmul_rn(vz, inv), cs, sn,
+                   make_float4(a.pk.shift[0], a.pk.shift[1], a.pk.shift[2], 0.f));
 }
 
 __device__ void rigid_apply(const SearchArgs& a, float4* X, int n, int m, int lane) {
@@ -789,9 +791,9 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
     float* dst = a.best_xyz + 3 * ((size_t)a0 + a.perm[a0 + i]);
-    dst[0] = __fadd_rn(v.x, a.pk.centre[0]);
-    dst[1] = __fadd_rn(v.y, a.pk.centre[1]);
-    dst[2] = __fadd_rn(v.z, a.pk.centre[2]);
+    dst[0] = __fadd_rn(__fmul_rn(__fsub_rn(v.x, a.pk.shift[0]), a.pk.h), a.pk.centre[0]);
+    dst[1] = __fadd_rn(__fmul_rn(__fsub_rn(v.y, a.pk.shift[1]), a.pk.h), a.pk.centre[1]);
+    dst[2] = __fadd_rn(__fmul_rn(__fsub_rn(v.z, a.pk.shift[2]), a.pk.h), a.pk.centre[2]);
   }
   __syncwarp();
 }
@@ -1112,7 +1114,9 @@ __global__ void __launch_bounds__(256) feature_kernel(const __grid_constant__ Se
         const float X = __fmaf_rn(r0, d.x, __fmaf_rn(r1, d.y, __fmul_rn(r2, d.z)));
         const float Y = __fmaf_rn(r3, d.x, __fmaf_rn(r4, d.y, __fmul_rn(r5, d.z)));
         const float Z = __fmaf_rn(r6, d.x, __fmaf_rn(r7, d.y, __fmul_rn(r8, d.z)));
-        f[23 + t] = (float)cell<GRID_LDG>(a.pk, nullptr, X, Y, Z) / 255.f;
+        f[23 + t] = (float)cell<GRID_LDG>(a.pk, nullptr, __fmaf_rn(X, a.pk.inv_h, a.pk.shift[0]),
+                                          __fmaf_rn(Y, a.pk.inv_h, a.pk.shift[1]),
+                                          __fmaf_rn(Z, a.pk.inv_h, a.pk.shift[2])) / 255.f;
       }
       const size_t row = (size_t)li * a.O + o;
       if (Xb) {
