@@ -107,15 +107,15 @@ struct SearchArgs {
 // this margin can never be flagged by the per-angle test.
 constexpr float REACH_MARGIN = 0.01f;
 
-// Per-warp shared memory: X float4[nmax] | HR float2[nmax] (later the near list,
-// uint8[8 nmax]) | MOFF uint16[nmax+2] | DP float4[fmax] | W2 float2[fmax] |
+// Per-warp shared memory: X float4[nmax] | HR float2[nmax] (later the near-pair list,
+// uint16[4 nmax]) | DP float4[fmax] | W2 float2[fmax] |
 // MASK uint32[mask_words] | EXL uint16[emax] | RD RotDesc[rmax].  fmax / rmax / emax:
 // the largest fragment, rotamer count and excluded-pair count of one ligand in the
 // batch (at least 1).
 __host__ __device__ inline int warp_smem_bytes(int nmax, int fmax, int mask_words, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
-  return a16(16 * nmax) + a16(8 * nmax) + a16(2 * (nmax + 2)) + a16(16 * fmax) + a16(8 * fmax) +
-         a16(4 * mask_words) + a16(2 * emax) + 16 * rmax;
+  return a16(16 * nmax) + a16(8 * nmax) + a16(16 * fmax) + a16(8 * fmax) + a16(4 * mask_words) + a16(2 * emax) +
+         16 * rmax;
 }
 
 // Atoms of a rotamer's rotating fragment in a ligand of n atoms.

@@ -99,6 +99,29 @@ __device__ __forceinline__ void turn(float4 x, float4 dp, float2 w2, float2 cs, 
   oz = __fmaf_rn(cs.y, w2.y, __fmaf_rn(cs.x, dp.z, x.z));
 }
 
+// Bump test of a moving atom a against a static atom b.  Both decomposed about the
+// axis, the squared distance with a turned by theta is
+//   |x_a - x_b|^2 + (cos theta - 1) P + sin theta Q,
+//   P = -2 d_perp,a . d_perp,b,  Q = -2 (u x d_a) . d_perp,b,
+// so pair_coef (once per pair and step) leaves two FMAs per angle (pair_d2).  Every
+// bump test of the search goes through these two functions.
+__device__ __forceinline__ float4 pair_coef(float4 xa, float4 dpa, float2 w2a, float4 xb, float4 p, float ux,
+                                            float uy, float uz) {
+  float4 dpb;
+  float2 w2b;
+  float hb;
+  axis_frame(xb.x, xb.y, xb.z, p, ux, uy, uz, dpb, w2b, hb);
+  const float dx = __fsub_rn(xa.x, xb.x), dy = __fsub_rn(xa.y, xb.y), dz = __fsub_rn(xa.z, xb.z);
+  const float c0 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+  const float P = __fmul_rn(-2.0f, __fmaf_rn(dpa.x, dpb.x, __fmaf_rn(dpa.y, dpb.y, __fmul_rn(dpa.z, dpb.z))));
+  const float Q = __fmul_rn(-2.0f, __fmaf_rn(dpa.w, dpb.x, __fmaf_rn(w2a.x, dpb.y, __fmul_rn(w2a.y, dpb.z))));
+  return make_float4(c0, P, Q, 0.f);
+}
+
+__device__ __forceinline__ float pair_d2(float c0, float P, float Q, float2 cs) {
+  return __fmaf_rn(cs.x, P, __fmaf_rn(cs.y, Q, c0));
+}
+
 // Grid access modes of the search: the cropped grid read through L1 (GRID_LDG), staged
 // in shared memory (GRID_SMEM), or fetched by the texture unit (GRID_TEX: point
 // sampling of unnormalised coordinates selects texel floor(f) exactly, and the border
@@ -262,20 +285,16 @@ __device__ __forceinline__ int score_atoms(const PocketDev& pk, const uint8_t* s
   return __reduce_add_sync(FULL, s);
 }
 
-// Smallest squared distance from the S rotated points to static atoms [b0, b1).
+// Smallest squared distance from moving atom a, turned by each of the S angles, to the
+// static atoms [b0, b1).
 template <int S>
-__device__ __forceinline__ void min_d2_range(const float4* X, int b0, int b1, const float (&xr)[S][3],
+__device__ __forceinline__ void min_d2_range(const float4* X, int b0, int b1, float4 xa, float4 dpa, float2 w2a,
+                                             float4 xp, float ux, float uy, float uz, const float2 (&cs)[S],
                                              float (&mind)[S]) {
-#pragma unroll 4
   for (int b = b0; b < b1; ++b) {
-    const float4 xb = X[b];
+    const float4 k = pair_coef(xa, dpa, w2a, X[b], xp, ux, uy, uz);
 #pragma unroll
-    for (int j = 0; j < S; ++j) {
-      const float dx = __fsub_rn(xr[j][0], xb.x);
-      const float dy = __fsub_rn(xr[j][1], xb.y);
-      const float dz = __fsub_rn(xr[j][2], xb.z);
-      mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
-    }
+    for (int j = 0; j < S; ++j) mind[j] = fminf(mind[j], pair_d2(k.x, k.y, k.z, cs[j]));
   }
 }
 
@@ -284,8 +303,7 @@ struct WarpMem {
   float2* HR;      // (height along the bond axis, distance from it) per atom
   float4* DP;      // per moving atom (sweep order): d_perp and (u x d).x of axis_frame
   float2* W2;      // per moving atom: (u x d).y, (u x d).z
-  uint8_t* NEAR;   // near static atoms of each moving atom (overwrites HR once it is dead)
-  uint16_t* MOFF;  // NEAR offset per moving atom (sweep order), n_moving + 1 entries
+  uint16_t* NEAR;  // the step's near pairs (ia << 8 | b), at most 4 nmax (overwrites HR once dead)
   uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
   RotDesc* RD;     // the current ligand's rotamer descriptors
   uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
@@ -299,10 +317,8 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int f
   w.X = reinterpret_cast<float4*>(base);
   base += a16(16 * nmax);
   w.HR = reinterpret_cast<float2*>(base);
-  w.NEAR = base;
+  w.NEAR = reinterpret_cast<uint16_t*>(base);
   base += a16(8 * nmax);
-  w.MOFF = reinterpret_cast<uint16_t*>(base);
-  base += a16(2 * (nmax + 2));
   w.DP = reinterpret_cast<float4*>(base);
   base += a16(16 * fmax);
   w.W2 = reinterpret_cast<float2*>(base);
@@ -344,8 +360,8 @@ __device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp,
 // ((score + 1) << 16 | (0xFFFF - k)), 0 if every candidate is bumped.
 template <int S, int G>
 __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, const uint16_t* excl,
-                              int n, const RotDesc& rd, int cur, int lane, unsigned long long& pairs,
-                              uint8_t* dbg) {
+                              int n, const RotDesc& rd, float4 xp, float ux, float uy, float uz, int cur,
+                              int lane, unsigned long long& pairs, uint8_t* dbg) {
   float4* X = w.X;
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a, s1b;
   if (rd.comp) {
@@ -404,8 +420,8 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const Warp
           sc[j] += cell<G>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
           mind[j] = 3.0e38f;
         }
-        min_d2_range<S>(X, s0a, s0b, xr, mind);
-        min_d2_range<S>(X, s1a, s1b, xr, mind);
+        min_d2_range<S>(X, s0a, s0b, xa, dp, w2, xp, ux, uy, uz, cs, mind);
+        min_d2_range<S>(X, s1a, s1b, xa, dp, w2, xp, ux, uy, uz, cs, mind);
         bool done = true;
         const unsigned tested = n_static - (unsigned)(ex_end - ex);  // parked pairs are not tests
 #pragma unroll
@@ -444,9 +460,9 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const Warp
 // Moving atoms are numbered ia in sweep order, static atoms k in static order (both
 // ascending preorder ids); lane t of chunk c tests static atom 32 c + t against every
 // moving atom and the warp's ballot is the mask word MASK[ia * nch + c].  The rotamer's
-// excluded pairs are then cleared from the masks, and the masks are compacted into a
-// near list per moving atom (NEAR / MOFF, at most 8 nmax entries: the bytes of HR).
-// Returns the number of near pairs; above 8 nmax only the masks are usable.
+// excluded pairs are then cleared from the masks, and the masks are compacted into the
+// step's list of near pairs (NEAR, at most 4 nmax entries: the bytes of HR).  Returns
+// the number of near pairs; above 4 nmax only the masks are usable.
 __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
                           int lane, unsigned long long& reach) {
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
@@ -493,7 +509,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
   __syncwarp();
   // compaction: lane t takes mask word w0 + t (row ia = word / nch, chunk c); an
   // exclusive scan of the words' bit counts gives each word's first NEAR slot
-  const int words = n_moving * nch, cap = 8 * a.nmax;
+  const int words = n_moving * nch, cap = 4 * a.nmax;
   const float inv_nch = __frcp_rn((float)nch);  // (wi + 1/2) / nch is >= 1/16 from an integer
   int base = 0;
   for (int w0 = 0; w0 < words; w0 += 32) {
@@ -509,26 +525,26 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
     int pos = base + incl - cnt;
     const int ia = __float2int_rz(__fmul_rn(__fadd_rn((float)wi, 0.5f), inv_nch));
     const int c = wi - ia * nch;
-    if (wi < words && c == 0) w.MOFF[ia] = (uint16_t)(pos < 65535 ? pos : 65535);
     while (mk) {
       const int k = (c << 5) + __ffs(mk) - 1;
       mk &= mk - 1;
-      if (pos < cap) w.NEAR[pos] = (uint8_t)(k < ns0 ? s0a + k : s1a + (k - ns0));
+      if (pos < cap) w.NEAR[pos] = (uint16_t)((ia << 8) | (k < ns0 ? s0a + k : s1a + (k - ns0)));
       ++pos;
     }
     base += __shfl_sync(FULL, incl, 31);
   }
-  if (lane == 0) w.MOFF[n_moving] = (uint16_t)(base < 65535 ? base : 65535);
   reach += (unsigned long long)n_moving * (unsigned long long)n_static;
   __syncwarp();
   return base;
 }
 
-// Every angle of one rotamer step, bump tests restricted to the near list.
+// Every angle of one rotamer step: bump tests over the step's near pairs (chunks of 32:
+// lane t computes pair t's coefficients, shuffles hand them to every lane), then the grid
+// gathers of the moving atoms.
 template <int S, int G>
 __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
-                                   const RotDesc& rd, int cur, int n_near, int lane,
-                                   unsigned long long& pairs, uint8_t* dbg) {
+                                   const RotDesc& rd, float4 xp, float ux, float uy, float uz, int cur,
+                                   int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
   int m0a, m0b, m1a, m1b;
   if (rd.comp) {
@@ -550,6 +566,19 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
       mind[j] = 3.0e38f;
       if (kk[j] < a.A) pairs += (unsigned)n_near;
     }
+    for (int e0 = 0; e0 < n_near; e0 += 32) {
+      float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e0 + lane < n_near) {
+        const int ent = w.NEAR[e0 + lane], ia = ent >> 8;
+        k = pair_coef(X[frag_atom(rd, ia)], w.DP[ia], w.W2[ia], X[ent & 0xFF], xp, ux, uy, uz);
+      }
+      const int cnt = n_near - e0 < 32 ? n_near - e0 : 32;
+      for (int t = 0; t < cnt; ++t) {
+        const float c0 = __shfl_sync(FULL, k.x, t), P = __shfl_sync(FULL, k.y, t), Q = __shfl_sync(FULL, k.z, t);
+#pragma unroll
+        for (int j = 0; j < S; ++j) mind[j] = fminf(mind[j], pair_d2(c0, P, Q, cs[j]));
+      }
+    }
     int stat = cur;  // running score minus the fragment's cached cells
     int ia = 0;
     for (int seg = 0; seg < 2; ++seg) {
@@ -559,22 +588,11 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
         stat -= __float_as_int(xa.w);
         const float4 dp = w.DP[ia];
         const float2 w2 = w.W2[ia];
-        float xr[S][3];
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-          turn(xa, dp, w2, cs[j], xr[j][0], xr[j][1], xr[j][2]);
-          sc[j] += cell<G>(a.pk, sg, xr[j][0], xr[j][1], xr[j][2]);
-        }
-        const int e1 = w.MOFF[ia + 1];
-        for (int e = w.MOFF[ia]; e < e1; ++e) {
-          const float4 xb = X[w.NEAR[e]];
-#pragma unroll
-          for (int j = 0; j < S; ++j) {
-            const float dx = __fsub_rn(xr[j][0], xb.x);
-            const float dy = __fsub_rn(xr[j][1], xb.y);
-            const float dz = __fsub_rn(xr[j][2], xb.z);
-            mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
-          }
+          float x, y, z;
+          turn(xa, dp, w2, cs[j], x, y, z);
+          sc[j] += cell<G>(a.pk, sg, x, y, z);
         }
       }
     }
@@ -594,8 +612,8 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 // step's masks (n_near of them); used when the near list overflowed.
 template <int S, int G>
 __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
-                                   const RotDesc& rd, int cur, int n_near, int lane,
-                                   unsigned long long& pairs, uint8_t* dbg) {
+                                   const RotDesc& rd, float4 xp, float ux, float uy, float uz, int cur,
+                                   int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
   if (rd.comp) {
@@ -642,14 +660,9 @@ __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, cons
           while (mk) {
             const int k = (c << 5) + __ffs(mk) - 1;
             mk &= mk - 1;
-            const float4 xb = X[k < ns0 ? s0a + k : s1a + (k - ns0)];
+            const float4 kc = pair_coef(xa, dp, w2, X[k < ns0 ? s0a + k : s1a + (k - ns0)], xp, ux, uy, uz);
 #pragma unroll
-            for (int j = 0; j < S; ++j) {
-              const float dx = __fsub_rn(xr[j][0], xb.x);
-              const float dy = __fsub_rn(xr[j][1], xb.y);
-              const float dz = __fsub_rn(xr[j][2], xb.z);
-              mind[j] = fminf(mind[j], __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz))));
-            }
+            for (int j = 0; j < S; ++j) mind[j] = fminf(mind[j], pair_d2(kc.x, kc.y, kc.z, cs[j]));
           }
         }
       }
@@ -822,15 +835,16 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       if (a.bump_bits)
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
       unsigned key;
-      prep_step(w, n, rd, X[rd.p], ux, uy, uz, lane);
+      const float4 xp = X[rd.p];
+      prep_step(w, n, rd, xp, ux, uy, uz, lane);
       if (a.use_filter) {
         const int n_near = build_near(a, w, excl, n, rd, lane, reach);
-        if (n_near <= 8 * a.nmax && !a.mask_sweep)
-          key = eval_step_near<S, G>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
+        if (n_near <= 4 * a.nmax && !a.mask_sweep)
+          key = eval_step_near<S, G>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, lane, pairs, dbg);
         else
-          key = eval_step_masks<S, G>(a, sg, w, n, rd, cur, n_near, lane, pairs, dbg);
+          key = eval_step_masks<S, G>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, lane, pairs, dbg);
       } else
-        key = eval_step<S, G>(a, sg, w, excl, n, rd, cur, lane, pairs, dbg);
+        key = eval_step<S, G>(a, sg, w, excl, n, rd, xp, ux, uy, uz, cur, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
         commit<G>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, w.DP, w.W2);
