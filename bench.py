@@ -11,8 +11,8 @@ persistent fused search kernel.
   e2e   : the same metric through gd_dock_batch + gd_fetch_results with host buffers:
           validation/packing, the host->device copy, the search and the copy of the
           results back are all inside the timed region
-  roofline : FP32-pipe bound of the search kernel: algorithmic FP32 operations (7 per
-             pair test, 9 per atom move) over the FP32 lanes x the SM clock
+  roofline : FP32-pipe bound of the search kernel: algorithmic FP32 operations (3 per
+             pair test, 6 per atom move) over the FP32 lanes x the SM clock
   cpu_baseline : the FP64 oracle on the host cores, on a bounded sample
 
 --impl reference times the oracle itself (the paper has no code to run) on the same
@@ -36,8 +36,8 @@ sys.path.insert(0, ROOT)
 from paper_1901_06229_b300 import synth  # noqa: E402
 
 METRIC = "ligands/s (pose search, 1 B300)"
-FP32_OPS_PER_PAIR = 7        # 3 FSUB, FMUL, 2 FFMA, 1 FMNMX
-FP32_OPS_PER_ATOM_MOVE = 9   # turn about the bond axis (6 FFMA) + cell coordinates (3 FFMA)
+FP32_OPS_PER_PAIR = 3        # 2 FFMA (|x_a - x_b|^2 + (cos-1) P + sin Q) + FMNMX
+FP32_OPS_PER_ATOM_MOVE = 6   # turn about the bond axis (6 FFMA; coordinates are grid units)
 FP32_OPS_PER_CANDIDATE = 0   # (cos - 1, sin) come from a per-block table
 FP32_LANES_PER_SM = 128
 
