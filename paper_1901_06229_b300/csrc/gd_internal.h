@@ -109,13 +109,13 @@ constexpr float REACH_MARGIN = 0.01f;
 
 // Per-warp shared memory: X float4[nmax] | HR float2[nmax] (later the near-pair list,
 // uint16[4 nmax]) | DP float4[fmax] | W2 float2[fmax] |
-// MASK uint32[mask_words] | EXL uint16[emax] | RD RotDesc[rmax].  fmax / rmax / emax:
-// the largest fragment, rotamer count and excluded-pair count of one ligand in the
-// batch (at least 1).
+// MASK uint32[mask_words] | EXL uint16[emax] | RD RotDesc[rmax] | PC float4[32] (the
+// coefficients of the near pairs being swept).  fmax / rmax / emax: the largest
+// fragment, rotamer count and excluded-pair count of one ligand in the batch (>= 1).
 __host__ __device__ inline int warp_smem_bytes(int nmax, int fmax, int mask_words, int rmax, int emax) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
   return a16(16 * nmax) + a16(8 * nmax) + a16(16 * fmax) + a16(8 * fmax) + a16(4 * mask_words) + a16(2 * emax) +
-         16 * rmax;
+         16 * rmax + 32 * 16;
 }
 
 // Atoms of a rotamer's rotating fragment in a ligand of n atoms.

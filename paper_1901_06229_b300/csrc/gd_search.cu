@@ -304,6 +304,7 @@ struct WarpMem {
   float4* DP;      // per moving atom (sweep order): d_perp and (u x d).x of axis_frame
   float2* W2;      // per moving atom: (u x d).y, (u x d).z
   uint16_t* NEAR;  // the step's near pairs (ia << 8 | b), at most 4 nmax (overwrites HR once dead)
+  float4* PC;      // pair_coef of the 32 near pairs being swept (lane t writes entry t)
   uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
   RotDesc* RD;     // the current ligand's rotamer descriptors
   uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
@@ -328,6 +329,8 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int f
   w.EXL = reinterpret_cast<uint16_t*>(base);
   base += a16(2 * emax);
   w.RD = reinterpret_cast<RotDesc*>(base);
+  base += 16 * rmax;
+  w.PC = reinterpret_cast<float4*>(base);
   w.CS = nullptr;
   return w;
 }
@@ -567,16 +570,18 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
       if (kk[j] < a.A) pairs += (unsigned)n_near;
     }
     for (int e0 = 0; e0 < n_near; e0 += 32) {
-      float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
       if (e0 + lane < n_near) {
         const int ent = w.NEAR[e0 + lane], ia = ent >> 8;
-        k = pair_coef(X[frag_atom(rd, ia)], w.DP[ia], w.W2[ia], X[ent & 0xFF], xp, ux, uy, uz);
+        w.PC[lane] = pair_coef(X[frag_atom(rd, ia)], w.DP[ia], w.W2[ia], X[ent & 0xFF], xp, ux, uy, uz);
       }
+      __syncwarp();
       const int cnt = n_near - e0 < 32 ? n_near - e0 : 32;
+#pragma unroll 4
       for (int t = 0; t < cnt; ++t) {
-        const float c0 = __shfl_sync(FULL, k.x, t), P = __shfl_sync(FULL, k.y, t), Q = __shfl_sync(FULL, k.z, t);
+        const float4 k = w.PC[t];
 #pragma unroll
-        for (int j = 0; j < S; ++j) mind[j] = fminf(mind[j], pair_d2(c0, P, Q, cs[j]));
+        for (int j = 0; j < S; ++j) mind[j] = fminf(mind[j], pair_d2(k.x, k.y, k.z, cs[j]));
       }
     }
     int stat = cur;  // running score minus the fragment's cached cells
