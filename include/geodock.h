@@ -87,7 +87,7 @@ typedef struct {
 
 /* Search settings.  Restart o = (i*n_beta + j)*n_gamma + k uses the ZYZ Euler angles
  * (2 pi i/n_alpha, pi (j+1/2)/n_beta, 2 pi k/n_gamma).  tile: 0 = built-in default
- * (an 8-warp tile: the 64-register kernel when four of its blocks fit in an SM's shared
+ * (an 8-warp tile: the 80-register kernel when three of its blocks fit in an SM's shared
  * memory, else the 128-register one, with fewer warps if 8 do not fit), -1 = autotuned
  * (cached per context), > 0 = a tile id from gd_tile_count(); the tile changes speed
  * only, never results.
@@ -193,8 +193,9 @@ gd_status gd_check_batch(const gd_ligand_batch* batch, const gd_search_params* p
 
 /* Launch tiles: number of ids (1..count) and, for one id, the warps per block, the
  * angles per lane and the register budget per thread of its kernel (128: the pocket
- * grid is staged in shared memory when it fits; 64: some state spills to local memory,
- * but up to 32 warps stay resident per SM and the grid is read through L1).  Any
+ * grid is staged in shared memory when it fits; 80: a little state spills to local
+ * memory, but up to 24 warps stay resident per SM and the grid is read through the
+ * texture path).  Any
  * output pointer may be NULL. */
 int gd_tile_count(void);
 gd_status gd_tile_info(int tile, int* warps_per_block, int* angles_per_lane, int* max_registers);

@@ -137,8 +137,8 @@ constexpr uint32_t NOT_SEARCHED = 0xFFFFFFFFu;
 struct Tile {
   int warps;        // warps (poses in flight) per block
   int slots;        // angles per lane evaluated together
-  int lean;         // 1: kernel built for <= 64 registers (up to 32 resident warps per SM);
-                    //    the grid is then read through L1, never staged in shared memory
+  int lean;         // 1: kernel built for <= 80 registers (up to 24 resident warps per SM);
+                    //    the grid is then read through the texture path, never staged
 };
 int tile_count();
 Tile tile_get(int id);  // id in [1, tile_count()]
@@ -168,6 +168,6 @@ int max_smem_grid_bytes();
 // Tile used for tile 0 (the built-in default) given the batch's buffer sizes.
 int default_tile(const SearchArgs& a);
 // Register budget per thread of a tile's kernel.
-inline int tile_max_regs(const Tile& t) { return t.lean ? 64 : 128; }
+inline int tile_max_regs(const Tile& t) { return t.lean ? 80 : 128; }
 
 }  // namespace gd

@@ -941,7 +941,7 @@ __device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
 }
 
 template <int S, int G, bool LEAN>
-__global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 4 : 1) search_kernel(const __grid_constant__ SearchArgs a) {
+__global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 3 : 1) search_kernel(const __grid_constant__ SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* sg = nullptr;
@@ -1265,7 +1265,7 @@ cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, Lau
 }
 
 // ids 1..12: <= 128 registers, one block of up to 16 warps per SM with the grid staged;
-// ids 13..15: <= 64 registers (some spilled) for up to 32 warps per SM, grid through L1.
+// ids 13..15: <= 80 registers (a little spilled) for up to 24 warps per SM, grid not staged.
 constexpr Tile kTiles[] = {{8, 1, 0}, {8, 2, 0},  {8, 4, 0},  {4, 1, 0}, {4, 2, 0}, {4, 4, 0},
                            {16, 1, 0}, {16, 2, 0}, {16, 4, 0}, {2, 1, 0}, {2, 2, 0}, {2, 4, 0},
                            {8, 1, 1}, {8, 2, 1},  {4, 2, 1}};
@@ -1287,8 +1287,8 @@ size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
 
 int default_tile(const SearchArgs& a) {
   const int two = a.A >= 64 ? 1 : 0;  // two angles per lane once there are 64 angles
-  // lean 8-warp blocks when four of them fit in an SM's 228 KB (1 KB reserved per block)
-  if (4 * (search_smem_bytes(a, kLean8x1 + two, false) + 1024) <= 228 * 1024) return kLean8x1 + two;
+  // lean 8-warp blocks when three of them fit in an SM's 228 KB (1 KB reserved per block)
+  if (3 * (search_smem_bytes(a, kLean8x1 + two, false) + 1024) <= 228 * 1024) return kLean8x1 + two;
   // else the wide 8-warp tile, giving up warps (8 -> 4 -> 2, same slots) until one block fits
   int t = 1 + two;
   for (int k = 0; k < 2 && search_smem_bytes(a, t, false) > 227 * 1024; ++k) t += k == 0 ? 3 : 6;

@@ -42,7 +42,7 @@ def test_tiles():
     assert gdk.tile_count() == 15
     seen = {gdk.tile_info(t) for t in range(1, 16)}
     assert len(seen) == 15
-    assert {r for _, _, r in seen} == {64, 128}
+    assert {r for _, _, r in seen} == {80, 128}
     with pytest.raises(gdk.GeoDockError):
         gdk.tile_info(0)
 
