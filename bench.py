@@ -487,11 +487,13 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     # gd_dock_batch returns once the work is queued, so a streaming caller packs and
-    # submits batch k+1 while batch k runs; two jobs are in flight
+    # submits batch k+1 while batch k runs; two jobs are in flight, on two streams, so one
+    # job's copies run on the copy engines while the other's search runs
+    streams = [stream, torch.cuda.Stream()]
     t0 = time.perf_counter()
     inflight = []
-    for _ in range(e2e_steps):
-        inflight.append(ctx.dock_batch(pk, w.batch, w.params, stream=stream, tile=tile))
+    for step in range(e2e_steps):
+        inflight.append(ctx.dock_batch(pk, w.batch, w.params, stream=streams[step % 2], tile=tile))
         if len(inflight) == 2:
             j = inflight.pop(0)
             out = j.fetch()
@@ -505,7 +507,7 @@ def main():
     e2e_s = reduce_max(time.perf_counter() - t0, world)
     assert np.array_equal(out["best_score"], first["best_score"])
     e2e = {"value": L * world * e2e_steps / e2e_s, "unit": "ligands/s", "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps, "jobs_in_flight": 2}
+           "d2h_bytes_per_step": int(d2h), "steps": e2e_steps, "jobs_in_flight": 2, "streams": 2}
 
     pk.free()
     ctx.close()
