@@ -247,42 +247,50 @@ gd_status pack_ligand(int li, int n, const float* xyz, int nb, const int32_t* bo
   if (R < 0 || R > GD_MAX_ROTAMERS) return fail(GD_EINVAL, "ligand %d: %d rotamers > %d", li, R, GD_MAX_ROTAMERS);
   for (int i = 0; i < 3 * n; ++i)
     if (!std::isfinite(xyz[i])) return fail(GD_EINVAL, "ligand %d: non-finite coordinate", li);
-  // adjacency (CSR)
-  std::vector<int> deg(n, 0), adj_off(n + 1, 0), adj(2 * nb);
+  // fixed-size working arrays (n <= GD_MAX_ATOMS): no heap traffic while many host
+  // threads pack at once
+  constexpr int NA = GD_MAX_ATOMS;
+  int adj_off[NA + 1], adj[2 * NA], fill[NA];
+  for (int i = 0; i <= n; ++i) adj_off[i] = 0;
   for (int b = 0; b < nb; ++b) {
     int u = bonds[2 * b], v = bonds[2 * b + 1];
     if (u < 0 || v < 0 || u >= n || v >= n || u == v) return fail(GD_EINVAL, "ligand %d: bad bond %d", li, b);
-    deg[u]++;
-    deg[v]++;
+    adj_off[u + 1]++;
+    adj_off[v + 1]++;
   }
-  for (int i = 0; i < n; ++i) adj_off[i + 1] = adj_off[i] + deg[i];
-  std::vector<int> fill(adj_off.begin(), adj_off.end() - 1);
+  for (int i = 0; i < n; ++i) {
+    adj_off[i + 1] += adj_off[i];
+    fill[i] = adj_off[i];
+  }
   for (int b = 0; b < nb; ++b) {
     int u = bonds[2 * b], v = bonds[2 * b + 1];
     adj[fill[u]++] = v;
     adj[fill[v]++] = u;
   }
   // DFS preorder from atom 0; subtrees become contiguous ranges
-  std::vector<int> parent(n, -2), pre(n, -1), order;
-  order.reserve(n);
-  std::vector<int> stack{0};
+  int parent[NA], pre[NA], order[NA], stack[2 * NA], size[NA];
+  for (int i = 0; i < n; ++i) {
+    parent[i] = -2;
+    pre[i] = -1;
+  }
+  int n_order = 0, top = 0;
+  stack[top++] = 0;
   parent[0] = -1;
-  while (!stack.empty()) {
-    int v = stack.back();
-    stack.pop_back();
+  while (top) {
+    int v = stack[--top];
     if (pre[v] >= 0) return fail(GD_EINVAL, "ligand %d: bonds contain a cycle (not a tree)", li);
-    pre[v] = (int)order.size();
-    order.push_back(v);
+    pre[v] = n_order;
+    order[n_order++] = v;
     for (int e = adj_off[v + 1] - 1; e >= adj_off[v]; --e) {
       int w = adj[e];
       if (w == parent[v]) continue;
-      if (pre[w] >= 0) return fail(GD_EINVAL, "ligand %d: bonds contain a cycle (not a tree)", li);
+      if (pre[w] >= 0 || top >= 2 * NA) return fail(GD_EINVAL, "ligand %d: bonds contain a cycle (not a tree)", li);
       parent[w] = v;
-      stack.push_back(w);
+      stack[top++] = w;
     }
   }
-  if ((int)order.size() != n) return fail(GD_EINVAL, "ligand %d: bond graph is not connected", li);
-  std::vector<int> size(n, 1);
+  if (n_order != n) return fail(GD_EINVAL, "ligand %d: bond graph is not connected", li);
+  for (int i = 0; i < n; ++i) size[i] = 1;
   for (int t = n - 1; t > 0; --t) size[parent[order[t]]] += size[order[t]];
   for (int t = 0; t < n; ++t) {
     int v = order[t];
@@ -290,7 +298,8 @@ gd_status pack_ligand(int li, int n, const float* xyz, int nb, const int32_t* bo
     out_perm[t] = (uint8_t)v;
   }
   double c = n;
-  std::vector<int> depth(n, -1), queue;
+  int depth[NA], queue[NA], near_m[NA], near_s[NA];
+  uint16_t ex[GD_MAX_EXCLUDED];
   for (int r = 0; r < R; ++r) {
     const int b = rot_bond[r];
     if (b < 0 || b >= nb) return fail(GD_EINVAL, "ligand %d: rotamer %d names bond %d of %d", li, r, b, nb);
@@ -311,40 +320,46 @@ gd_status pack_ligand(int li, int n, const float* xyz, int nb, const int32_t* bo
       return d.comp ? !in : in;
     };
     // atoms within min_sep-2 bonds of q (moving side) and of p (static side)
-    std::fill(depth.begin(), depth.end(), -1);
-    std::vector<std::pair<int, int>> near_m, near_s;
+    for (int i = 0; i < n; ++i) depth[i] = -1;
+    int nm = 0, ns = 0;
     for (int side = 0; side < 2; ++side) {
-      int root = side ? p : q;
-      queue.assign(1, root);
+      int root = side ? p : q, qh = 0, qt = 0;
+      queue[qt++] = root;
       depth[root] = 0;
-      for (size_t h = 0; h < queue.size(); ++h) {
-        int a = queue[h];
-        (side ? near_s : near_m).push_back({a, depth[a]});
+      while (qh < qt) {
+        int a = queue[qh++];
+        if (side) near_s[ns++] = a;
+        else near_m[nm++] = a;
         if (depth[a] >= min_sep - 2) continue;
         for (int e = adj_off[a]; e < adj_off[a + 1]; ++e) {
           int w = adj[e];
           if (depth[w] >= 0 || moving(w) != (side == 0)) continue;
           depth[w] = depth[a] + 1;
-          queue.push_back(w);
+          queue[qt++] = w;
         }
       }
     }
-    std::vector<std::pair<int, int>> ex;
-    for (auto& m : near_m)
-      for (auto& s : near_s)
-        if (m.second + s.second + 1 < min_sep) ex.push_back({pre[m.first], pre[s.first]});
-    if ((int)ex.size() > GD_MAX_EXCLUDED)
-      return fail(GD_EINVAL, "ligand %d: rotamer %d has %zu excluded pairs > %d", li, r, ex.size(), GD_MAX_EXCLUDED);
-    std::sort(ex.begin(), ex.end());
-    for (size_t e = 0, run = 0; e < ex.size(); ++e) {
-      run = (e && ex[e].first == ex[e - 1].first) ? run + 1 : 1;
+    int ne = 0;
+    for (int x = 0; x < nm; ++x)
+      for (int y = 0; y < ns; ++y)
+        if (depth[near_m[x]] + depth[near_s[y]] + 1 < min_sep) ++ne;
+    if (ne > GD_MAX_EXCLUDED)
+      return fail(GD_EINVAL, "ligand %d: rotamer %d has %d excluded pairs > %d", li, r, ne, GD_MAX_EXCLUDED);
+    ne = 0;
+    for (int x = 0; x < nm; ++x)
+      for (int y = 0; y < ns; ++y)
+        if (depth[near_m[x]] + depth[near_s[y]] + 1 < min_sep)
+          ex[ne++] = (uint16_t)((pre[near_m[x]] << 8) | pre[near_s[y]]);  // sort key (a, b)
+    std::sort(ex, ex + ne);
+    for (int e = 0, run = 0; e < ne; ++e) {
+      run = (e && (ex[e] >> 8) == (ex[e - 1] >> 8)) ? run + 1 : 1;
       if (run > GD_MAX_EXCLUDED_ATOM)
         return fail(GD_EINVAL, "ligand %d: rotamer %d has more than %d excluded pairs on one atom", li, r,
                     GD_MAX_EXCLUDED_ATOM);
     }
-    d.n_excl = (uint8_t)ex.size();
+    d.n_excl = (uint8_t)ne;
     d.excl_off = (uint32_t)excl.size();
-    for (auto& e : ex) excl.push_back((uint16_t)(e.first | (e.second << 8)));
+    for (int e = 0; e < ne; ++e) excl.push_back((uint16_t)((ex[e] >> 8) | ((ex[e] & 0xFF) << 8)));  // a | b << 8
     out_rots[r] = d;
     const int f = d.comp ? rest : sub;
     c += (double)f * (n - f) + 4.0 * f;
