@@ -245,7 +245,21 @@ class LigandBatch:
         return Ligand(xyz=self.xyz[a0:a1], bonds=self.bonds[b0:b1], rot_bond=self.rot_bond[r0:r1])
 
     def subset(self, idx) -> "LigandBatch":
-        return pack([self.ligand(int(i)) for i in idx])
+        """The ligands idx (in that order) as a new batch: one ragged gather per array."""
+        idx = np.asarray(idx, dtype=np.int64).reshape(-1)
+
+        def ragged(off, rows):
+            off = np.asarray(off, dtype=np.int64)
+            starts, lens = off[idx], off[idx + 1] - off[idx]
+            new_off = np.concatenate([[0], np.cumsum(lens)])
+            take = np.arange(new_off[-1]) - np.repeat(new_off[:-1], lens) + np.repeat(starts, lens)
+            return new_off.astype(np.int32), np.ascontiguousarray(rows[take])
+
+        atom_off, xyz = ragged(self.atom_off, np.asarray(self.xyz, np.float32).reshape(-1, 3))
+        bond_off, bonds = ragged(self.bond_off, np.asarray(self.bonds, np.int32).reshape(-1, 2))
+        rot_off, rot_bond = ragged(self.rot_off, np.asarray(self.rot_bond, np.int32))
+        return LigandBatch(atom_off=atom_off, xyz=xyz, bond_off=bond_off, bonds=bonds, rot_off=rot_off,
+                           rot_bond=rot_bond)
 
 
 def pack(ligs: list[Ligand]) -> LigandBatch:
