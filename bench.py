@@ -11,8 +11,14 @@ persistent fused search kernel.
   e2e   : the same metric through gd_dock_batch + gd_fetch_results with host buffers:
           validation/packing, the host->device copy, the search and the copy of the
           results back are all inside the timed region
-  roofline : FP32-pipe bound of the search kernel: algorithmic FP32 operations (3 per
-             pair test, 6 per atom move) over the FP32 lanes x the SM clock
+  roofline : FP32-pipe bound of the search kernel.  The algorithmic work of a launch is
+             counted by the oracle over the whole workload (table beside it): per
+             candidate 16 FP32 operations and one grid byte load per fragment atom, and
+             7 operations per pair test with the candidate stopping at its first bump
+             (32-pair tiles).  The reach filter proves most of those pair tests
+             unnecessary, so the fraction can exceed 1; ``executed`` gives the FP32
+             operations the kernel itself performs (3 per pair test it runs, 6 per
+             turned atom) against the same peak.
   cpu_baseline : the FP64 oracle on the host cores, on a bounded sample
 
 --impl reference times the oracle itself (the paper has no code to run) on the same
@@ -36,10 +42,13 @@ sys.path.insert(0, ROOT)
 from paper_1901_06229_b300 import synth  # noqa: E402
 
 METRIC = "ligands/s (pose search, 1 B300)"
-FP32_OPS_PER_PAIR = 3        # 2 FFMA (|x_a - x_b|^2 + (cos-1) P + sin Q) + FMNMX
-FP32_OPS_PER_ATOM_MOVE = 6   # turn about the bond axis (6 FFMA; coordinates are grid units)
-FP32_OPS_PER_CANDIDATE = 0   # (cos - 1, sin) come from a per-block table
+# FP32 operations the kernel executes (the "executed" roofline figure)
+EXEC_OPS_PER_PAIR = 3        # 2 FFMA (|x_a - x_b|^2 + (cos-1) P + sin Q) + FMNMX
+EXEC_OPS_PER_ATOM_MOVE = 6   # turn about the bond axis (6 FFMA; coordinates are grid units)
 FP32_LANES_PER_SM = 128
+LOADS_PER_SM_CLK = 32        # one 32-lane shared/L1 load instruction per clock per SM
+# algorithmic work of each benchmark workload, counted by the oracle (oracle/algorithmic_work.py)
+ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one search-kernel launch,
 # from one ncu capture of the full-size workload, keyed by a hash of the kernel sources
@@ -58,6 +67,19 @@ def search_kernel_hash() -> str:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def algorithmic_work(name, evals, moves):
+    """The oracle's work totals of workload ``name`` (plain data), if they describe the
+    launch that ran (same candidate and fragment-atom counts), else None."""
+    try:
+        with open(ALGORITHMIC_WORK) as f:
+            t = json.load(f).get(name)
+    except OSError:
+        return None
+    if not t or t["candidates"] != int(evals) or t["frag_atom_moves"] != int(moves):
+        return None
+    return t
 
 
 def workload_for(name, rank, ligands=None):
@@ -473,7 +495,8 @@ def main():
     evals = float(res["evals"].sum())
     pairs = float(res["pair_tests"].sum())
     moves = float(res["atom_moves"].sum())
-    ops = FP32_OPS_PER_PAIR * pairs + FP32_OPS_PER_ATOM_MOVE * moves + FP32_OPS_PER_CANDIDATE * evals
+    exec_ops = EXEC_OPS_PER_PAIR * pairs + EXEC_OPS_PER_ATOM_MOVE * moves
+    alg = algorithmic_work(w.name, evals, moves) if rank == 0 else None
     value = L * world * args.steps / dev_s
     ms_step = 1e3 * dev_s / args.steps
     clocks = clk.summary()
@@ -518,8 +541,20 @@ def main():
     peaks = measured_peaks()
     mhz = peaks.get("sm_max_mhz", 2032.0)
     peak_tops = sm_count * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
-    per_launch_ops = ops / 1.0
-    achieved = per_launch_ops / (np.mean(kernel_ms) / 1e3) / 1e12
+    peak_loads = sm_count * LOADS_PER_SM_CLK * mhz * 1e6 / 1e12
+    launch_s = np.mean(kernel_ms) / 1e3
+    executed = {"achieved": exec_ops / launch_s / 1e12, "frac": exec_ops / launch_s / 1e12 / peak_tops,
+                "ops_per_launch": exec_ops}
+    if alg:
+        achieved = alg["fp32_ops"] / launch_s / 1e12
+        loads = alg["byte_loads"] / launch_s / 1e12
+        frac = max(achieved / peak_tops, loads / peak_loads)
+        work = {"ops_per_launch": alg["fp32_ops"], "byte_loads_per_launch": alg["byte_loads"],
+                "candidates_per_launch": alg["candidates"], "pair_tests_early_per_launch": alg["pair_tests_early"],
+                "loads": {"achieved": loads, "peak": peak_loads, "unit": "Tloads/s", "frac": loads / peak_loads}}
+    else:
+        achieved = frac = None
+        work = {"note": "no oracle work table for this workload"}
     line = {
         "metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -530,12 +565,13 @@ def main():
         "pair_tests_per_s": pairs * world * args.steps / dev_s,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,  # pose setup + search per step
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tops,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s", "frac": frac,
                      "traffic": MEASURED_TRAFFIC.get(search_kernel_hash(), {}).get((w.name, tile)),
                      "peak_kind": f"FP32 pipe: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x {mhz:.0f} MHz "
                                   "(sm_max_mhz of MEASURED_PEAKS.json)",
-                     "ops_per_launch": per_launch_ops},
+                     "work": "oracle count: 16 FP32 ops + 1 byte load per fragment atom, 7 ops per "
+                             "early-exit pair test" if alg else None,
+                     **work, "executed": executed},
         "clocks": clocks,
         "wall_s_timed": wall,
     }

@@ -210,7 +210,9 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
 
     Keys: orient_score/_lo/_hi [L, O], orient_pick [sum R * O * reps] (ligand-major,
     then orientation, then rep*R + r), orient_fragile [L, O], best_xyz [N, 3],
-    best_orient/best_score/best_robust [L], pair_tests_full/evals [L]; with ``debug``
+    best_orient/best_score/best_robust [L], pair_tests_full/evals [L], pair_tests_early [L]
+    (pair tests when every candidate stops at its first bumping pair, moving atom
+    ascending then static atom ascending, charged in whole 32-pair tiles); with ``debug``
     also bump (0 free / 1 bumped / 2 uncertain) and cand_score per candidate,
     flattened per ligand as [O, reps*R, A] at offsets cand_off.
     """
@@ -228,7 +230,7 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
         best_orient=np.zeros(L, np.int32), best_score=np.zeros(L, np.int32),
         best_robust=np.zeros(L, np.int32), pair_tests_full=np.zeros(L, np.int64),
         evals=np.zeros(L, np.int64), status=np.zeros(L, np.int32), cand_off=cand_off,
-        orient_rigid=np.zeros((L, O), np.int16))
+        orient_rigid=np.zeros((L, O), np.int16), pair_tests_early=np.zeros(L, np.int64))
     if debug:
         out["bump"] = np.zeros(int(cand_off[-1]), np.uint8)
         out["cand_score"] = np.zeros(int(cand_off[-1]), np.int32)
@@ -255,7 +257,7 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
         _p(cand_off, C.c_int64), _p(out["best_xyz"], C.c_double), _p(out["best_orient"], C.c_int32),
         _p(out["best_score"], C.c_int32), _p(out["best_robust"], C.c_int32),
         _p(out["pair_tests_full"], C.c_int64), _p(out["evals"], C.c_int64), _p(out["status"], C.c_int32),
-        _p(out["orient_rigid"], C.c_int16))
+        _p(out["orient_rigid"], C.c_int16), _p(out["pair_tests_early"], C.c_int64))
     if rc:
         raise ValueError("oracle rejected a ligand: " + lib().orc_last_error().decode())
     return out

@@ -253,17 +253,25 @@ bool build_rotamer(const Topo& t, const int32_t* bonds, int nb, int rb, int min_
 }
 
 // Bump status of one candidate: 0 free, 1 bumped, 2 uncertain (a pair within eps of
-// the threshold and no pair clearly inside it).
+// the threshold and no pair clearly inside it).  *first_bump is the position of the
+// first pair closer than bump_dist in the list order (moving atom ascending, then
+// static atom ascending), -1 if there is none.
 int bump_status(const Rotamer& r, const std::vector<V3>& xmoved, const std::vector<V3>& x,
-                double bump_dist, double eps, bool* bumped_exact) {
+                double bump_dist, double eps, bool* bumped_exact, int64_t* first_bump) {
   bool any_exact = false, any_sure = false, any_near = false;
+  int64_t first = -1, idx = 0;
   for (auto& pr : r.pairs) {
     double d = norm(xmoved[pr.first] - x[pr.second]);
-    if (d < bump_dist) any_exact = true;
+    if (d < bump_dist) {
+      any_exact = true;
+      if (first < 0) first = idx;
+    }
     if (d < bump_dist - eps) any_sure = true;
     else if (d < bump_dist + eps) any_near = true;
+    ++idx;
   }
   *bumped_exact = any_exact;
+  *first_bump = first;
   if (any_sure) return 1;
   return any_near ? 2 : 0;
 }
@@ -282,6 +290,8 @@ struct LigandOut {
   int32_t* best_score;         // [1]
   int32_t* best_robust;        // [1] 1 if o* cannot flip under eps
   int64_t* pair_tests_full;    // [1] eligible pair tests of the full sweep
+  int64_t* pair_tests_early;   // [1] pair tests when each candidate stops at its first bump,
+                               //     charged in whole 32-pair tiles (at most the pair count)
   int64_t* evals;              // [1]
 };
 
@@ -318,7 +328,8 @@ bool prepare(const float* xyz_in, int n, const int32_t* bonds, int nb, const int
 // eps-interval, the first fragile step (-1: none) and the final coordinates x.
 void search_restart(const Prepared& L, const Pocket& P, const Params& prm, double eps, int o, int16_t* picks,
                     uint8_t* bump, int32_t* cand_score, int* score_out, int* lo_out, int* hi_out,
-                    int* fragile_out, std::vector<V3>& x, int16_t* rigid_out = nullptr) {
+                    int* fragile_out, std::vector<V3>& x, int16_t* rigid_out = nullptr,
+                    int64_t* early_pairs = nullptr) {
   int16_t rigid_dummy = 0;
   (void)rigid_dummy;
   const double pi = 3.14159265358979323846;
@@ -374,8 +385,13 @@ void search_restart(const Prepared& L, const Pocket& P, const Params& prm, doubl
         for (int a = 0; a < n; ++a)
           xm[a] = rot.moving[a] ? x[rot.p] + rodrigues(u, theta, x[a] - x[rot.p]) : x[a];
         bool b_exact;
-        status[k] = bump_status(rot, xm, x, prm.bump_dist, eps, &b_exact);
+        int64_t first;
+        status[k] = bump_status(rot, xm, x, prm.bump_dist, eps, &b_exact, &first);
         bumped[k] = b_exact;
+        if (early_pairs) {  // BumpCheck rejects at the first bumping pair (Sec. 3.2)
+          const int64_t P = (int64_t)rot.pairs.size();
+          *early_pairs += first < 0 ? P : std::min(P, (first / 32 + 1) * 32);
+        }
         int s = static_score, slo = 0, shi = 0;
         for (int a = 0; a < n; ++a)
           if (rot.moving[a]) {
@@ -448,11 +464,13 @@ int dock_ligand(const float* xyz_in, int n, const int32_t* bonds, int nb, const 
 
   std::vector<std::vector<V3>> final_x(O);
   const size_t per_o = (size_t)reps * R;
+  int64_t early = 0;
   for (int o = 0; o < O; ++o)
     search_restart(L, P, prm, eps, o, out.orient_pick + o * per_o, out.bump ? out.bump + o * per_o * A : nullptr,
                    out.cand_score ? out.cand_score + o * per_o * A : nullptr, &out.orient_score[o],
                    &out.orient_score_lo[o], &out.orient_score_hi[o], &out.orient_fragile[o], final_x[o],
-                   out.orient_rigid ? out.orient_rigid + o : nullptr);
+                   out.orient_rigid ? out.orient_rigid + o : nullptr, &early);
+  *out.pair_tests_early = early;
   int best = 0;
   for (int o = 1; o < O; ++o)
     if (out.orient_score[o] > out.orient_score[best]) best = o;
@@ -725,7 +743,7 @@ int orc_dock_batch(int L, const int32_t* atom_off, const float* xyz, const int32
                    int32_t* orient_fragile, uint8_t* bump, int32_t* cand_score,
                    const int64_t* cand_off, double* best_xyz, int32_t* best_orient,
                    int32_t* best_score, int32_t* best_robust, int64_t* pair_tests_full,
-                   int64_t* evals, int32_t* status, int16_t* orient_rigid) {
+                   int64_t* evals, int32_t* status, int16_t* orient_rigid, int64_t* pair_tests_early) {
   Pocket P{grid, nx, ny, nz, h, V3{origin[0], origin[1], origin[2]}};
   Params prm{p->n_alpha, p->n_beta, p->n_gamma, p->n_angles, p->bump_dist, p->min_bond_sep,
              p->repetitions, p->rigid_span, p->rigid_step};
@@ -750,6 +768,7 @@ int orc_dock_batch(int L, const int32_t* atom_off, const float* xyz, const int32
       lo.best_score = best_score + i;
       lo.best_robust = best_robust + i;
       lo.pair_tests_full = pair_tests_full + i;
+      lo.pair_tests_early = pair_tests_early + i;
       lo.evals = evals + i;
       int n = atom_off[i + 1] - atom_off[i];
       int nb = bond_off[i + 1] - bond_off[i];

@@ -391,6 +391,100 @@ def test_counters():
         assert out["pair_tests_full"][i] == pairs * w.params.n_orient * w.params.n_angles
 
 
+def early_exit_pairs(lig, pocket, params, o, picks):
+    """Pair tests of restart o's sweep when each candidate stops at its first bump.
+
+    Independent replay in numpy/scipy: the conformation of step r is the restart pose
+    with the picks of the earlier rotamers applied; each candidate turns rotamer r's
+    fragment (networkx) by 2 pi k / A; its pairs are listed moving atom ascending,
+    then static atom ascending among those at graph distance >= min_sep; the count is
+    the pair count if no pair is closer than bump_dist, else the first bumping pair's
+    position rounded up to a whole 32-pair tile (at most the pair count).
+    """
+    n = len(lig.xyz)
+    A = params.n_angles
+    spl = dict(nx.all_pairs_shortest_path_length(nx_graph(lig)))
+    nz, ny, nx_ = pocket.grid.shape
+    x0 = lig.xyz.astype(np.float64)
+    cp = pocket.origin.astype(np.float64) + 0.5 * pocket.spacing * np.array([nx_, ny, nz])
+    i, j, k = o // (params.n_beta * params.n_gamma), (o // params.n_gamma) % params.n_beta, o % params.n_gamma
+    Ro = Rotation.from_euler("ZYZ", [2 * math.pi * i / params.n_alpha, math.pi * (j + 0.5) / params.n_beta,
+                                     2 * math.pi * k / params.n_gamma])
+    x = cp + Ro.apply(x0 - x0.mean(axis=0))
+    total = 0
+    for r, rb in enumerate(lig.rot_bond):
+        mv, p, q = nx_fragment(lig, int(rb))
+        pairs = [(a, b) for a in range(n) if mv[a] for b in range(n) if not mv[b] and spl[a][b] >= params.min_bond_sep]
+        ia = np.array([a for a, _ in pairs], dtype=np.int64)
+        ib = np.array([b for _, b in pairs], dtype=np.int64)
+        u = (x[q] - x[p]) / np.linalg.norm(x[q] - x[p])
+        for kk in range(A):
+            y = x.copy()
+            y[mv] = x[p] + Rotation.from_rotvec(u * 2 * math.pi * kk / A).apply(x[mv] - x[p])
+            hit = np.nonzero(np.linalg.norm(y[ia] - y[ib], axis=1) < params.bump_dist)[0]
+            total += len(pairs) if len(hit) == 0 else min(len(pairs), 32 * (int(hit[0]) // 32 + 1))
+        if picks[r] >= 0:
+            x[mv] = x[p] + Rotation.from_rotvec(u * 2 * math.pi * picks[r] / A).apply(x[mv] - x[p])
+    return total
+
+
+def test_early_exit_pair_count_matches_replay():
+    pocket = textured_pocket()
+    params = synth.SearchParams(2, 2, 2, 16, bump_dist=3.0)
+    checked = 0
+    for lig in small_ligands():
+        b = synth.pack([lig])
+        out = oracle.dock_batch(b, pocket, params)
+        if np.any(out["orient_fragile"][0] >= 0):
+            continue
+        O, R = params.n_orient, len(lig.rot_bond)
+        # the picks (pinned by the exhaustive replay above) fix the trajectory; the count
+        # along it is recomputed independently
+        picks = out["orient_pick"].reshape(O, R)
+        want = sum(early_exit_pairs(lig, pocket, params, o, picks[o]) for o in range(O))
+        assert out["pair_tests_early"][0] == want
+        assert 0 < want <= out["pair_tests_full"][0]
+        checked += 1
+    assert checked >= 2
+
+
+def test_early_exit_pair_count_limits():
+    w = synth.workload_batched(4)
+    out = oracle.dock_batch(w.batch, w.pocket, w.params)
+    # nothing closer than 0 A: every candidate tests all its pairs
+    none = oracle.dock_batch(w.batch, w.pocket, synth.SearchParams(**{**w.params.__dict__, "bump_dist": 0.0}))
+    np.testing.assert_array_equal(none["pair_tests_early"], none["pair_tests_full"])
+    # everything bumps: the first pair of every candidate bumps, one 32-pair tile each
+    huge = oracle.dock_batch(w.batch, w.pocket, synth.SearchParams(**{**w.params.__dict__, "bump_dist": 1e6}))
+    for i in range(4):
+        lig = w.batch.ligand(i)
+        n = len(lig.xyz)
+        want = 0
+        for rb in lig.rot_bond:
+            mv, _, _, dist = oracle.fragment(n, lig.bonds, int(rb))
+            want += min(32, int(((dist >= 3) & mv[:, None] & ~mv[None, :]).sum()))
+        assert huge["pair_tests_early"][i] == want * w.params.n_orient * w.params.n_angles
+    assert np.all(out["pair_tests_early"] < out["pair_tests_full"])
+    assert np.all(out["pair_tests_early"] > 0)
+
+
+def test_algorithmic_work_table():
+    """The stored per-launch work totals are the oracle's counts of the seeded workloads."""
+    from oracle import algorithmic_work as aw
+    table = aw.load()
+    w = synth.workload_single()
+    assert table[w.name] == aw.count(w, threads=2)
+    for make in (synth.workload_batched, synth.workload_large):
+        w = make()
+        t = table[w.name]
+        p = w.params
+        assert t["ligands"] == w.batch.n_ligands
+        assert t["candidates"] == p.n_orient * p.repetitions * p.n_angles * len(w.batch.rot_bond)
+        assert t["fp32_ops"] == 16 * t["frag_atom_moves"] + 7 * t["pair_tests_early"]
+        assert t["byte_loads"] == t["frag_atom_moves"]
+        assert 0 < t["pair_tests_early"] < t["pair_tests_full"]
+
+
 # ----------------------------------------------------------------------------- rigid sweep
 
 def test_rigid_candidates_are_rotation_vectors_in_order():
