@@ -57,6 +57,8 @@ SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_
 MEASURED_TRAFFIC = {
     "7b75f97d459a37de": {("batched-4096lig-64grid", 14): 4607232 + 6483456,
                          ("large-512lig-128grid", 9): 2724864 + 4864},
+    "53ab6d0c527216f8": {("batched-4096lig-64grid", 14): 4729856 + 1325824,
+                         ("large-512lig-128grid", 9): 3045632 + 4608},
 }
 
 

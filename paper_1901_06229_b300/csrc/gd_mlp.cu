@@ -204,41 +204,133 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 // One persistent CTA per SM keeps W1 (24 KB), W2 (128 KB), b1, b2 and w3 in shared
 // memory and owns all 512 TMEM columns: layer 1 accumulates in columns [0, 256), layer 2
 // in [256, 512).  Warp 8 only issues MMAs: layer 1 of a tile once the eight epilogue
-// warps have stored its X rows in the H1 buffer, then layer 2 four K = 16 slices at a
-// time as epilogue 1 completes 32-column chunks of H1.  Epilogue warp w reads TMEM lanes
-// 32 (w % 4) and columns 128 (w / 4) .. + 128; per tile it runs epilogue 1 (bias, ReLU,
-// BF16 into H1), loads the next tile's X rows into registers while layer 2 runs, stores
-// them once layer 2 has released H1 (so the next layer 1 overlaps), then epilogue 2
-// (bias, ReLU, BF16, dot with w3).
+// warps have stored its X rows, then layer 2 four K = 16 slices at a time as epilogue 1
+// completes 32-column chunks of H1.  Epilogue warp w reads TMEM lanes 32 (w % 4) and
+// columns 128 (w / 4) .. + 128.
+//
+// The tensor pipe is kept fed across tiles:
+//   * a tile's X rows live in the H1 slots of epilogue 1's first chunk (K columns
+//     0-31 and 128-159 of H1), which layer 2 has finished reading after its first four
+//     MMAs: the next tile's X is stored then, so its layer 1 queues right behind this
+//     tile's layer 2;
+//   * when layer 2 completes, the warps copy their accumulator rows into registers and
+//     release the accumulator at once, so the next tile's layer 2 can start as soon as
+//     the first chunk of its epilogue 1 is written; bias, ReLU and BF16 rounding of those
+//     rows run while the next layer 1 does, and their dot with w3 once all of the next
+//     tile's layer 2 is queued.
 constexpr int INF_EPI = 256;                // epilogue threads (8 warps)
 constexpr int INF_THREADS = INF_EPI + 32;   // + the issuing warp
 constexpr size_t INF_W1 = 256 * 48 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2, INF_VEC = 3 * 256 * 4;
+constexpr size_t INF_BAR = 128;             // 11 mbarriers + the TMEM address
 constexpr int INF_XCH = 128 * 6 / INF_EPI;  // 16-byte X chunks per epilogue thread and tile (128 rows x 6)
 
-// This thread's X chunks of the tile at row r0 (rows past M read as zero).
-__device__ __forceinline__ void x_load(const __nv_bfloat16* X, int M, int r0, uint4 (&v)[INF_XCH]) {
+// Copy this thread's X chunks of the tile at row r0 (rows past M read as zero) into
+// layer 1's A operand (K = 48) in H1's core-matrix layout (8-row groups 4096 bytes
+// apart, 8-column K chunks 128 bytes apart), asynchronously (cp.async; complete after
+// x_wait): X's K chunks 0-3 go to H1 chunks 0-3 and X's K chunks 4-5 to H1 chunks
+// 16-17, all of them slots of epilogue 1's first 32-column chunk.
+__device__ __forceinline__ void x_copy(uint8_t* h1s, const __nv_bfloat16* X, int M, int r0) {
 #pragma unroll
   for (int j = 0; j < INF_XCH; ++j) {
     const int idx = threadIdx.x + INF_EPI * j, r = idx / 6, c = idx % 6;
-    v[j] = r0 + r < M ? __ldg(reinterpret_cast<const uint4*>(X + (size_t)(r0 + r) * 48 + c * 8))
-                      : make_uint4(0, 0, 0, 0);
+    const int kc = c < 4 ? c : c + 12;
+    const bool in = r0 + r < M;
+    const __nv_bfloat16* src = in ? X + (size_t)(r0 + r) * 48 + c * 8 : X;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     smem_addr(h1s + (size_t)(r >> 3) * 4096 + kc * 128 + (r & 7) * 16)),
+                 "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
   }
 }
 
-// The same chunks into the core-matrix layout of layer 1's A operand (K = 48).
-__device__ __forceinline__ void x_store(uint8_t* dst, const uint4 (&v)[INF_XCH]) {
-#pragma unroll
-  for (int j = 0; j < INF_XCH; ++j) {
-    const int idx = threadIdx.x + INF_EPI * j, r = idx / 6, c = idx % 6;
-    *reinterpret_cast<uint4*>(dst + (size_t)(r >> 3) * 768 + c * 128 + (r & 7) * 16) = v[j];
-  }
+// Wait for this thread's X copies and make them visible to the tensor core.
+__device__ __forceinline__ void x_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* m) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(INF_EPI) : "memory"); }
+// bf16x2 of max(round(a), 0), max(round(b), 0): a in the low half.  ReLU after rounding
+// equals rounding after ReLU (rounding keeps signs).
+__device__ __forceinline__ uint32_t relu_bf16x2(float a, float b) {
+  uint32_t r;
+  asm("{\n .reg .b32 t, z;\n cvt.rn.bf16x2.f32 t, %2, %1;\n mov.b32 z, 0;\n max.bf16x2 %0, t, z;\n}"
+      : "=r"(r)
+      : "f"(a), "f"(b));
+  return r;
+}
+
+// Bias, ReLU and BF16 rounding of 32 layer-2 accumulator columns (from column c0), packed
+// in pairs.
+__device__ __forceinline__ void e2_pack(const float (&v)[32], const float* b2s, int c0, uint32_t* hp) {
+  const float4* bb = reinterpret_cast<const float4*>(b2s + c0);
+#pragma unroll
+  for (int e4 = 0; e4 < 8; ++e4) {
+    const float4 b = bb[e4];
+    hp[2 * e4] = relu_bf16x2(v[4 * e4] + b.x, v[4 * e4 + 1] + b.y);
+    hp[2 * e4 + 1] = relu_bf16x2(v[4 * e4 + 2] + b.z, v[4 * e4 + 3] + b.w);
+  }
+}
+
+// Epilogue 1 of one 32-column chunk of this thread's row: bias, ReLU and BF16 rounding
+// into H1.
+__device__ __forceinline__ void e1_chunk(uint32_t taddr, const float* b1s, int col0, uint8_t* h1s, int row) {
+  float v[32];
+  tmem_ld32(taddr, v);
+  const float4* bb = reinterpret_cast<const float4*>(b1s + col0);
+#pragma unroll
+  for (int c8 = 0; c8 < 4; ++c8) {
+    const float4 p = bb[2 * c8], q = bb[2 * c8 + 1];
+    const float* w = v + c8 * 8;
+    const uint4 h = make_uint4(relu_bf16x2(w[0] + p.x, w[1] + p.y), relu_bf16x2(w[2] + p.z, w[3] + p.w),
+                               relu_bf16x2(w[4] + q.x, w[5] + q.y), relu_bf16x2(w[6] + q.z, w[7] + q.w));
+    const int kc = (col0 >> 3) + c8;
+    *reinterpret_cast<uint4*>(h1s + (size_t)(row >> 3) * 4096 + kc * 128 + (row & 7) * 16) = h;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // H1 for the tensor core
+  tc_fence_before();
+}
+
+// Epilogue 2 of the tile at row r0 from this thread's 128 packed layer-2 activations:
+// the dot with w3 in column order; the second half's warps hand their partial dots to
+// the first half's (through red and mbarriers 9 / 10; `handed` counts the hand-overs,
+// pr / pf are the wait parities), which write y.  False when a wait timed out.
+__device__ __forceinline__ bool e2_finish(const uint32_t (&hp)[64], const float* w3s, int col0, int half, int row,
+                                          int lane, int r0, int M, float bias3, float* red, uint64_t* mbar,
+                                          int& handed, uint32_t& pr, uint32_t& pf, float* y) {
+  const float4* ww = reinterpret_cast<const float4*>(w3s + col0);
+  float dot = 0.f;
+#pragma unroll
+  for (int e4 = 0; e4 < 32; ++e4) {
+    const float4 w = ww[e4];
+    const uint32_t f = hp[2 * e4], g = hp[2 * e4 + 1];
+    dot = fmaf(__uint_as_float(f << 16), w.x, dot);
+    dot = fmaf(__uint_as_float(f & 0xFFFF0000u), w.y, dot);
+    dot = fmaf(__uint_as_float(g << 16), w.z, dot);
+    dot = fmaf(__uint_as_float(g & 0xFFFF0000u), w.w, dot);
+  }
+  if (half == 1) {
+    if (handed > 0) {  // the previous partials have been read
+      if (!mbar_wait(mbar + 10, pf)) return false;
+      pf ^= 1;
+    }
+    ++handed;
+    red[row] = dot;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(mbar + 9);
+  } else {
+    if (!mbar_wait(mbar + 9, pr)) return false;
+    pr ^= 1;
+    const float other = red[row];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(mbar + 10);
+    if (r0 + row < M) y[r0 + row] = dot + other + bias3;
+  }
+  return true;
+}
 
 __global__ void __launch_bounds__(INF_THREADS, 1)
     mlp_infer_kernel(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
@@ -250,13 +342,16 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   float* b1s = reinterpret_cast<float*>(smem + INF_W1 + INF_W2 + INF_H1);
   float* b2s = b1s + 256;
   float* w3s = b2s + 256;
-  // mbar[0] layer 1 done, [1] layer 2 done (MMA commits); [2] X rows stored, [3 + c]
-  // chunk c of epilogue 1 written (one arrival per epilogue warp).  One barrier per
-  // chunk: a warp reaches chunk c of the next tile only after every warp has passed
-  // chunk c of this one (the next layer 1 waits for all their X stores).
+  // mbar[0] layer 1 done, [1] layer 2 done, [7] layer 2's first four MMAs done (MMA
+  // commits); [2] X rows copied in, [3 + c] chunk c of epilogue 1 written, [8] layer 2's
+  // accumulator copied out (one arrival per epilogue warp); [9] the second half's
+  // partial dots written, [10] read (four arrivals each).  Every barrier completes one
+  // phase per tile, and no warp can arrive twice on one before its phase completes:
+  // each next arrival waits, directly or through the issuing warp, for every warp's
+  // current one.
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1 + INF_VEC);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 7);
-  __shared__ float red[2][128];
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 11);
+  __shared__ float red[128];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = (M + 127) / 128;
   if ((int)blockIdx.x >= ntiles) return;
@@ -275,6 +370,10 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     mbar_init(mbar, 1);
     mbar_init(mbar + 1, 1);
     for (int b = 2; b < 7; ++b) mbar_init(mbar + b, INF_EPI / 32);
+    mbar_init(mbar + 7, 1);
+    mbar_init(mbar + 8, INF_EPI / 32);
+    mbar_init(mbar + 9, INF_EPI / 64);
+    mbar_init(mbar + 10, INF_EPI / 64);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // W1 / W2 for the tensor core
@@ -287,24 +386,29 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     // ---- issuing warp
     if (lane == 0) {
       const uint32_t idesc = make_idesc(128, 256);
-      uint32_t px = 0, pc = 0;  // pc: parity of the four chunk barriers (one phase per tile)
+      uint32_t px = 0, pc = 0, pd = 0;  // parities: X stored, epilogue-1 chunks, accumulator copied
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         ok = mbar_wait(mbar + 2, px);
         px ^= 1;
         if (!ok) break;
         tc_fence_after();
         for (int kk = 0; kk < 3; ++kk)
-          mma_bf16(acc1, make_desc(smem_addr(h1s) + kk * 256, 128, 768),
+          mma_bf16(acc1, make_desc(smem_addr(h1s) + (kk < 2 ? kk * 256 : 16 * 128), 128, 4096),
                    make_desc(smem_addr(w1s) + kk * 256, 128, 768), idesc, kk > 0);
         mma_commit(mbar);
         for (int c = 0; c < 4 && ok; ++c) {
           ok = mbar_wait(mbar + 3 + c, pc);
+          if (ok && c == 0 && tile != (int)blockIdx.x) {  // the previous layer 2 copied out
+            ok = mbar_wait(mbar + 8, pd);
+            pd ^= 1;
+          }
           if (!ok) break;
           tc_fence_after();
           const int ks[4] = {2 * c, 2 * c + 1, 8 + 2 * c, 9 + 2 * c};
           for (int t = 0; t < 4; ++t)
             mma_bf16(acc2, make_desc(smem_addr(h1s) + ks[t] * 256, 128, 4096),
                      make_desc(smem_addr(w2s) + ks[t] * 256, 128, 4096), idesc, c > 0 || t > 0);
+          if (c == 0) mma_commit(mbar + 7);
         }
         pc ^= 1;
         if (ok) mma_commit(mbar + 1);
@@ -315,68 +419,68 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     // ---- epilogue warps
     const int quad = warp & 3, half = warp >> 2;
     const uint32_t lanebase = ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
-    const int row = quad * 32 + lane;
+    const int row = quad * 32 + lane, col0 = half * 128;
     const float bias3 = *b3;
-    uint32_t ph1 = 0, ph2 = 0;
-    uint4 xv[INF_XCH];
-    x_load(X, M, (int)blockIdx.x * 128, xv);
-    x_store(h1s, xv);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    uint32_t ph1 = 0, ph2 = 0, ph7 = 0, pr = 0, pf = 0;
+    int prev_r0 = -1;   // first row of the tile whose layer-2 rows sit in acc
+    int handed = 0;     // partial dots the second half has handed over so far
+    uint32_t hp[64];    // this thread's 128 layer-2 activations of tile prev_r0 (BF16 pairs)
+    x_copy(h1s, X, M, (int)blockIdx.x * 128);
+    x_wait();
     __syncwarp();
     if (lane == 0) mbar_arrive(mbar + 2);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int r0 = tile * 128, next = tile + (int)gridDim.x;
-      ok = mbar_wait(mbar, ph1);  // layer 1 of this tile
+      ok = mbar_wait(mbar, ph1);                         // layer 1 of this tile
       ph1 ^= 1;
       tc_fence_after();
       if (!ok) break;
-      for (int c0 = 0; c0 < 128; c0 += 32) {
-        float v[32];
-        tmem_ld32(acc1 + lanebase + (uint32_t)c0, v);
-        const int col0 = half * 128 + c0;
-#pragma unroll
-        for (int c8 = 0; c8 < 4; ++c8) {
-          __align__(16) __nv_bfloat16 h[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16(fmaxf(v[c8 * 8 + e] + b1s[col0 + c8 * 8 + e], 0.f));
-          const int kc = (col0 >> 3) + c8;
-          *reinterpret_cast<uint4*>(h1s + (size_t)(row >> 3) * 4096 + kc * 128 + (row & 7) * 16) =
-              *reinterpret_cast<uint4*>(h);
-        }
-        // this chunk (and, before the first, the previous tile's reads of layer 2's
-        // columns) is done: the issuing warp may run its slices of layer 2
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
+      for (int c = 0; c < 4; ++c) {
+        e1_chunk(acc1 + lanebase + (uint32_t)(32 * c), b1s, col0 + 32 * c, h1s, row);
         __syncwarp();
-        if (lane == 0) mbar_arrive(mbar + 3 + (c0 >> 5));
+        if (lane == 0) mbar_arrive(mbar + 3 + c);
       }
-      if (next < ntiles) x_load(X, M, next * 128, xv);  // during layer 2
-      ok = mbar_wait(mbar + 1, ph2);                      // layer 2 done: H1 is free
-      ph2 ^= 1;
-      tc_fence_after();
-      if (!ok) break;
-      if (next < ntiles) {  // the next tile's layer 1 overlaps epilogue 2
-        x_store(h1s, xv);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // all of this tile's layer 2 is queued.  Once its first MMAs are done, their H1
+      // slots take the next tile's X rows (copied while the previous tile is finished)
+      if (next < ntiles) {
+        ok = mbar_wait(mbar + 7, ph7);
+        ph7 ^= 1;
+        tc_fence_after();
+        if (!ok) break;
+        x_copy(h1s, X, M, next * 128);
+      }
+      if (prev_r0 >= 0) {
+        ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y);
+        if (!ok) break;
+      }
+      if (next < ntiles) {
+        x_wait();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(mbar + 2);
       }
-      float dot = 0.f;
-      for (int c0 = 0; c0 < 128; c0 += 32) {
-        float v[32];
-        tmem_ld32(acc2 + lanebase + (uint32_t)c0, v);
-        const int col0 = half * 128 + c0;
+      ok = mbar_wait(mbar + 1, ph2);  // layer 2 done: copy its rows out, release it
+      ph2 ^= 1;
+      tc_fence_after();
+      if (!ok) break;
+      {
+        float v[2][32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e)
-          dot = fmaf(__bfloat162float(__float2bfloat16(fmaxf(v[e] + b2s[col0 + e], 0.f))), w3s[col0 + e], dot);
+        for (int k = 0; k < 2; ++k) tmem_ld32(acc2 + lanebase + (uint32_t)(32 * k), v[k]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) e2_pack(v[k], b2s, col0 + 32 * k, hp + 16 * k);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) tmem_ld32(acc2 + lanebase + (uint32_t)(64 + 32 * k), v[k]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(mbar + 8);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) e2_pack(v[k], b2s, col0 + 64 + 32 * k, hp + 32 + 16 * k);  // during the next layer 1
       }
-      red[half][row] = dot;
-      epi_sync();
-      if (threadIdx.x < 128 && r0 + (int)threadIdx.x < M)
-        y[r0 + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x] + bias3;
-      epi_sync();
+      prev_r0 = r0;
     }
+    if (ok && prev_r0 >= 0)
+      ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y);
   }
   if (!ok && err) atomicExch(err, 1);
   tc_fence_before();
@@ -396,7 +500,7 @@ cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b
                          const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
                          int num_sms, cudaStream_t st) {
   static bool attr = false;
-  const size_t smem = INF_W1 + INF_W2 + INF_H1 + INF_VEC + 64;
+  const size_t smem = INF_W1 + INF_W2 + INF_H1 + INF_VEC + INF_BAR;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -126,7 +126,7 @@ def test_training_reduces_loss():
     net.close()
 
 
-@pytest.mark.parametrize("M", [1, 127, 1000, 70000])
+@pytest.mark.parametrize("M", [1, 127, 1000, 70000, 262221])
 def test_fused_predict_matches_oracle(M):
     import torch
     from oracle import mlp as om
