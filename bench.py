@@ -59,6 +59,8 @@ MEASURED_TRAFFIC = {
                          ("large-512lig-128grid", 9): 2724864 + 4864},
     "53ab6d0c527216f8": {("batched-4096lig-64grid", 14): 4729856 + 1325824,
                          ("large-512lig-128grid", 9): 3045632 + 4608},
+    "a20fe81ae2d8391d": {("batched-4096lig-64grid", 14): 4893184 + 1409280,
+                         ("large-512lig-128grid", 9): 2731520 + 6400},
 }
 
 

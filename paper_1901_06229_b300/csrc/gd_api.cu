@@ -16,6 +16,10 @@
 #include "geodock.h"
 #include "gd_internal.h"
 
+// The search kernel packs atom ids into bytes (near pairs, the reach filter's column
+// lists, which share the 512-byte coefficient buffer of a warp).
+static_assert(GD_MAX_ATOMS <= 256, "atom ids must fit a byte");
+
 using gd::RotDesc;
 using gd::SearchArgs;
 

@@ -305,6 +305,8 @@ struct WarpMem {
   float2* W2;      // per moving atom: (u x d).y, (u x d).z
   uint16_t* NEAR;  // the step's near pairs (ia << 8 | b), at most 4 nmax (overwrites HR once dead)
   float4* PC;      // pair_coef of the 32 near pairs being swept (lane t writes entry t)
+  uint8_t* SL;     // the reach filter's columns: static atom of column k (aliases PC[0, 16))
+  uint8_t* POS;    // the reach filter's column of atom b, 0xFF if none (aliases PC[16, 32))
   uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
   RotDesc* RD;     // the current ligand's rotamer descriptors
   uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
@@ -331,6 +333,8 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int f
   w.RD = reinterpret_cast<RotDesc*>(base);
   base += 16 * rmax;
   w.PC = reinterpret_cast<float4*>(base);
+  w.SL = reinterpret_cast<uint8_t*>(base);  // GD_MAX_ATOMS = 256: 255 columns at most
+  w.POS = reinterpret_cast<uint8_t*>(base) + 256;
   w.CS = nullptr;
   return w;
 }
@@ -456,18 +460,42 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const Warp
   return __reduce_max_sync(FULL, best);
 }
 
+// Columns of a step's reach filter: the static atoms it tests, in ascending preorder.
+// Column k is static atom k (static order: [s0a, s0a + ns0) then from s1a) unless the
+// filter pruned, in which case it is SL[k].
+struct Cols {
+  int prune, ns0, s0a, s1a;
+};
+
+template <bool PRUNE>
+__device__ __forceinline__ Cols step_cols(const RotDesc& rd) {
+  return rd.comp ? Cols{PRUNE, rd.hi - rd.lo, rd.lo, 0} : Cols{PRUNE, rd.lo, 0, rd.hi};
+}
+
+__device__ __forceinline__ int col_atom(const WarpMem& w, const Cols& c, int k) {
+  return c.prune ? (int)w.SL[k] : (k < c.ns0 ? c.s0a + k : c.s1a + (k - c.ns0));
+}
+
 // Reach filter of one rotamer step.  A moving atom a sweeps a circle about the bond
 // axis: height h_a along it, radius rho_a.  For a static atom b the distance over the
 // whole turn is at least sqrt((h_a - h_b)^2 + (rho_a - rho_b)^2), so only pairs below
 // bump_dist + margin (and not excluded by graph distance) need per-angle tests.
-// Moving atoms are numbered ia in sweep order, static atoms k in static order (both
-// ascending preorder ids); lane t of chunk c tests static atom 32 c + t against every
-// moving atom and the warp's ballot is the mask word MASK[ia * nch + c].  The rotamer's
-// excluded pairs are then cleared from the masks, and the masks are compacted into the
-// step's list of near pairs (NEAR, at most 4 nmax entries: the bytes of HR).  Returns
-// the number of near pairs; above 4 nmax only the masks are usable.
+// With PRUNE (the 128-register kernels: on the 80-register ones the extra code costs
+// more than it saves), the static atoms farther than that from the box
+// [min h_a, max h_a] x [min rho_a, max rho_a] of the moving atoms are dropped first:
+// the box distance is computed with the same roundings as the pair distance, and every
+// rounding step is monotone, so no dropped atom could pass the pair test with any
+// moving atom.  The remaining static atoms, in ascending preorder, are the filter's
+// columns (SL[k] is column k's atom, POS[b] atom b's column, 0xFF if dropped); without
+// pruning every static atom is a column.  Moving atoms are numbered ia in sweep order;
+// lane t of chunk c tests column 32 c + t against every moving atom and the warp's
+// ballot is the mask word MASK[ia * nch + c], nch = *n_chunks.  The rotamer's excluded
+// pairs are then cleared from the masks, and the masks are compacted into the step's
+// list of near pairs (NEAR, at most 4 nmax entries: the bytes of HR).  Returns the
+// number of near pairs; above 4 nmax only the masks are usable.
+template <bool PRUNE>
 __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
-                          int lane, unsigned long long& reach) {
+                          int lane, unsigned long long& reach, int& nch_out) {
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
   if (rd.comp) {
     m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
@@ -478,12 +506,52 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
   }
   const int ns0 = s0b - s0a;
   const int n_moving = (m0b - m0a) + (m1b - m1a), n_static = n - n_moving;
-  const int nch = (n_static + 31) >> 5;
+  const Cols cl{PRUNE, ns0, s0a, s1a};
+  int ncol = n_static;
+  if (PRUNE) {
+    // the moving atoms' (h, rho) box
+    float hlo = 3.0e38f, hhi = -3.0e38f, rlo = 3.0e38f, rhi = -3.0e38f;
+    for (int ia = lane; ia < n_moving; ia += 32) {
+      const float2 ha = w.HR[frag_atom(rd, ia)];
+      hlo = fminf(hlo, ha.x);
+      hhi = fmaxf(hhi, ha.x);
+      rlo = fminf(rlo, ha.y);
+      rhi = fmaxf(rhi, ha.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      hlo = fminf(hlo, __shfl_xor_sync(FULL, hlo, off));
+      hhi = fmaxf(hhi, __shfl_xor_sync(FULL, hhi, off));
+      rlo = fminf(rlo, __shfl_xor_sync(FULL, rlo, off));
+      rhi = fmaxf(rhi, __shfl_xor_sync(FULL, rhi, off));
+    }
+    // columns: the static atoms within reach of the box
+    ncol = 0;
+    for (int k0 = 0; k0 < n_static; k0 += 32) {
+      const int k = k0 + lane;
+      const bool real = k < n_static;
+      const int b = k < ns0 ? s0a + k : s1a + (k - ns0);
+      bool keep = false;
+      if (real) {
+        const float2 hb = w.HR[b];
+        const float dh = fmaxf(fmaxf(__fsub_rn(hlo, hb.x), __fsub_rn(hb.x, hhi)), 0.f);
+        const float dr = fmaxf(fmaxf(__fsub_rn(rlo, hb.y), __fsub_rn(hb.y, rhi)), 0.f);
+        keep = __fmaf_rn(dh, dh, __fmul_rn(dr, dr)) < a.reach2;
+      }
+      const unsigned km = __ballot_sync(FULL, keep);
+      const int col = ncol + __popc(km & ((1u << lane) - 1u));
+      if (keep) w.SL[col] = (uint8_t)b;
+      if (real) w.POS[b] = keep ? (uint8_t)col : (uint8_t)0xFF;
+      ncol += __popc(km);
+    }
+    __syncwarp();
+  }
+  const int nch = (ncol + 31) >> 5;
+  nch_out = nch;
   for (int c = 0; c < nch; ++c) {
     const int k = (c << 5) + lane;
-    const bool real = k < n_static;
-    float2 hb = make_float2(3.0e18f, 0.f);  // lanes past the last static atom never pass
-    if (real) hb = w.HR[k < ns0 ? s0a + k : s1a + (k - ns0)];
+    float2 hb = make_float2(3.0e18f, 0.f);  // lanes past the last column never pass
+    if (k < ncol) hb = w.HR[col_atom(w, cl, k)];
     uint32_t* col = w.MASK + c;
     for (int seg = 0; seg < 2; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
@@ -507,13 +575,15 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
       ia = av - rd.lo;
       k = bv < rd.lo ? bv : bv - (rd.hi - rd.lo);
     }
-    atomicAnd(w.MASK + ia * nch + (k >> 5), ~(1u << (k & 31)));
+    if (PRUNE) k = w.POS[bv];
+    if (!PRUNE || k != 0xFF) atomicAnd(w.MASK + ia * nch + (k >> 5), ~(1u << (k & 31)));
   }
   __syncwarp();
   // compaction: lane t takes mask word w0 + t (row ia = word / nch, chunk c); an
   // exclusive scan of the words' bit counts gives each word's first NEAR slot
   const int words = n_moving * nch, cap = 4 * a.nmax;
-  const float inv_nch = __frcp_rn((float)nch);  // (wi + 1/2) / nch is >= 1/16 from an integer
+  // (wi + 1/2) / nch is >= 1/16 from an integer; nch >= 1 without pruning (static atoms exist)
+  const float inv_nch = __frcp_rn((float)(PRUNE && nch == 0 ? 1 : nch));
   int base = 0;
   for (int w0 = 0; w0 < words; w0 += 32) {
     const int wi = w0 + lane;
@@ -531,7 +601,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
     while (mk) {
       const int k = (c << 5) + __ffs(mk) - 1;
       mk &= mk - 1;
-      if (pos < cap) w.NEAR[pos] = (uint16_t)((ia << 8) | (k < ns0 ? s0a + k : s1a + (k - ns0)));
+      if (pos < cap) w.NEAR[pos] = (uint16_t)((ia << 8) | col_atom(w, cl, k));
       ++pos;
     }
     base += __shfl_sync(FULL, incl, 31);
@@ -615,21 +685,19 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 
 // Every angle of one rotamer step, bump tests restricted to the near pairs of the
 // step's masks (n_near of them); used when the near list overflowed.
-template <int S, int G>
+template <int S, int G, bool PRUNE>
 __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
                                    const RotDesc& rd, float4 xp, float ux, float uy, float uz, int cur,
-                                   int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
+                                   int n_near, int nch_pruned, int lane, unsigned long long& pairs, uint8_t* dbg) {
   const float4* X = w.X;
-  int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
+  int m0a, m0b, m1a, m1b;
   if (rd.comp) {
     m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
-    s0a = rd.lo; s0b = rd.hi; s1a = 0;
   } else {
     m0a = rd.lo; m0b = rd.hi; m1a = 0; m1b = 0;
-    s0a = 0; s0b = rd.lo; s1a = rd.hi;
   }
-  const int ns0 = s0b - s0a;
-  const int nch = (n - (m0b - m0a) - (m1b - m1a) + 31) >> 5;
+  const Cols cl = step_cols<PRUNE>(rd);
+  const int nch = PRUNE ? nch_pruned : (n - (m0b - m0a) - (m1b - m1a) + 31) >> 5;
   const int passes = (a.A + 32 * S - 1) / (32 * S);
   unsigned best = 0;
   for (int pass = 0; pass < passes; ++pass) {
@@ -665,7 +733,7 @@ __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, cons
           while (mk) {
             const int k = (c << 5) + __ffs(mk) - 1;
             mk &= mk - 1;
-            const float4 kc = pair_coef(xa, dp, w2, X[k < ns0 ? s0a + k : s1a + (k - ns0)], xp, ux, uy, uz);
+            const float4 kc = pair_coef(xa, dp, w2, X[col_atom(w, cl, k)], xp, ux, uy, uz);
 #pragma unroll
             for (int j = 0; j < S; ++j) mind[j] = fminf(mind[j], pair_d2(kc.x, kc.y, kc.z, cs[j]));
           }
@@ -816,7 +884,7 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   __syncwarp();
 }
 
-template <int S, int G>
+template <int S, int G, bool PRUNE>
 __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int e0,
                             int lane) {
   float4* X = w.X;
@@ -843,11 +911,12 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       const float4 xp = X[rd.p];
       prep_step(w, n, rd, xp, ux, uy, uz, lane);
       if (a.use_filter) {
-        const int n_near = build_near(a, w, excl, n, rd, lane, reach);
+        int nch;
+        const int n_near = build_near<PRUNE>(a, w, excl, n, rd, lane, reach, nch);
         if (n_near <= 4 * a.nmax && !a.mask_sweep)
           key = eval_step_near<S, G>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, lane, pairs, dbg);
         else
-          key = eval_step_masks<S, G>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, lane, pairs, dbg);
+          key = eval_step_masks<S, G, PRUNE>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, nch, lane, pairs, dbg);
       } else
         key = eval_step<S, G>(a, sg, w, excl, n, rd, xp, ux, uy, uz, cur, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
@@ -993,7 +1062,7 @@ __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 3 : 1) search_kernel(
         pending = 0;
         e0 = load_ligand(a, w, li, lane);
       }
-      search_pose<S, G>(a, sg, w, li, o, e0, lane);
+      search_pose<S, G, !LEAN>(a, sg, w, li, o, e0, lane);
       ++pending;
     }
   }
