@@ -171,6 +171,15 @@ gd_status gd_dock_batch(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_ba
  * gd_job_launch_subset (chosen restarts), then gd_job_download + gd_fetch_results. */
 gd_status gd_prepare_batch(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batch* batch,
                            const gd_search_params* params, void* stream, gd_job** out);
+/* gd_prepare_batch over the ligands sel[0 .. n_sel) of `batch`, in that order, without
+ * building a sub-batch: the job's ligand i is batch ligand sel[i] (a ligand may be
+ * listed more than once), and its results are laid out as for a batch of those ligands.
+ * Only the selected ligands are read and validated.  For a caller that keeps one large
+ * library on the host and docks parts of it as they are needed (a streaming screen).
+ * GD_EINVAL when an index is outside [0, n_ligands) or sel is NULL with n_sel > 0. */
+gd_status gd_prepare_batch_sel(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batch* batch,
+                               const int32_t* sel, int32_t n_sel, const gd_search_params* params, void* stream,
+                               gd_job** out);
 /* Copy a job's results into `out`.  blocking = 0 returns GD_ENOTREADY while the device
  * is still working. */
 gd_status gd_fetch_results(gd_ctx* ctx, gd_job* job, gd_result_batch* out, int blocking);

@@ -7,10 +7,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <condition_variable>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "geodock.h"
@@ -50,6 +53,78 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ---------------------------------------------------------------- context & memory
 
+namespace {
+
+// Host threads that pack batches, started once with the context (starting threads per
+// batch cost more than packing a small batch).  run(T, fn) calls fn(0 .. T-1) on the
+// caller and the workers and returns when all calls have returned; calls to run are
+// serialised.
+class HostPool {
+ public:
+  explicit HostPool(int workers) {
+    for (int i = 0; i < workers; ++i) th_.emplace_back([this] { loop(); });
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  int threads() const { return (int)th_.size() + 1; }
+  void run(int T, const std::function<void(int)>& fn) {
+    std::lock_guard<std::mutex> serial(run_mu_);
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      fn_ = &fn;
+      next_ = 1;
+      T_ = T;
+      pending_ = T - 1;
+      ++gen_;
+    }
+    if (T > 1) cv_.notify_all();
+    fn(0);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return pending_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void loop() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+      if (stop_) return;
+      seen = gen_;
+      while (next_ < T_) {
+        const int t = next_++;
+        const std::function<void(int)>* fn = fn_;
+        lk.unlock();
+        (*fn)(t);
+        lk.lock();
+        if (--pending_ == 0) done_.notify_all();
+      }
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_, run_mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int next_ = 0, T_ = 0, pending_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+// Packing threads (the caller included): the host's hardware threads, 1 to 16.  Packing
+// is compute-bound (about 2-7 us per ligand and thread, depending on the host), and on a
+// 16-thread host 16 packers beat 8 by 1.3-1.4x even with the caller's other threads
+// running.
+int pack_threads() { return std::max(1, std::min(16, (int)std::thread::hardware_concurrency())); }
+
+}  // namespace
+
 struct gd_ctx {
   int device = 0;
   int num_sms = 0;
@@ -59,13 +134,16 @@ struct gd_ctx {
   std::mutex mu;
   std::multimap<size_t, void*> dev_free;   // cached device blocks by size
   std::multimap<size_t, void*> host_free;  // cached pinned blocks by size
+  std::unordered_map<void*, size_t> dev_size, host_size;  // size of every block allocated
   std::map<std::string, int> tuned;        // autotuned tile per workload signature
+  HostPool pool{pack_threads() - 1};        // batch packing
 };
 
 namespace {
 
-// Blocks are rounded to 1 MiB (or a power of two below) so repeated jobs of the same
-// shape reuse them.
+// Blocks are rounded to 1 MiB (or a power of two below); a request takes the smallest
+// cached block of at least its size and at most twice it, so jobs of similar shapes
+// (a stream of batches of varying size) reuse blocks instead of allocating.
 size_t size_class(size_t b) {
   if (b <= (1u << 20)) {
     size_t s = 4096;
@@ -79,8 +157,8 @@ gd_status dev_alloc(gd_ctx* c, size_t bytes, void** out) {
   const size_t sz = size_class(bytes);
   {
     std::lock_guard<std::mutex> g(c->mu);
-    auto it = c->dev_free.find(sz);
-    if (it != c->dev_free.end()) {
+    auto it = c->dev_free.lower_bound(sz);
+    if (it != c->dev_free.end() && it->first <= 2 * sz) {
       *out = it->second;
       c->dev_free.erase(it);
       return GD_OK;
@@ -92,6 +170,7 @@ gd_status dev_alloc(gd_ctx* c, size_t bytes, void** out) {
     for (auto& kv : c->dev_free) {
       cudaFree(kv.second);
       c->used -= kv.first;
+      c->dev_size.erase(kv.second);
     }
     c->dev_free.clear();
     if (c->used + sz > c->budget)
@@ -105,6 +184,7 @@ gd_status dev_alloc(gd_ctx* c, size_t bytes, void** out) {
   }
   std::lock_guard<std::mutex> g(c->mu);
   c->used += sz;
+  c->dev_size[p] = sz;
   *out = p;
   return GD_OK;
 }
@@ -112,15 +192,16 @@ gd_status dev_alloc(gd_ctx* c, size_t bytes, void** out) {
 void dev_release(gd_ctx* c, void* p, size_t bytes) {
   if (!p) return;
   std::lock_guard<std::mutex> g(c->mu);
-  c->dev_free.emplace(size_class(bytes), p);
+  auto it = c->dev_size.find(p);
+  c->dev_free.emplace(it != c->dev_size.end() ? it->second : size_class(bytes), p);
 }
 
 gd_status host_alloc(gd_ctx* c, size_t bytes, void** out) {
   const size_t sz = size_class(bytes);
   {
     std::lock_guard<std::mutex> g(c->mu);
-    auto it = c->host_free.find(sz);
-    if (it != c->host_free.end()) {
+    auto it = c->host_free.lower_bound(sz);
+    if (it != c->host_free.end() && it->first <= 2 * sz) {
       *out = it->second;
       c->host_free.erase(it);
       return GD_OK;
@@ -132,6 +213,8 @@ gd_status host_alloc(gd_ctx* c, size_t bytes, void** out) {
     cudaGetLastError();
     return fail(GD_ENOMEM, "cudaMallocHost(%zu): %s", sz, cudaGetErrorString(e));
   }
+  std::lock_guard<std::mutex> g(c->mu);
+  c->host_size[p] = sz;
   *out = p;
   return GD_OK;
 }
@@ -139,7 +222,8 @@ gd_status host_alloc(gd_ctx* c, size_t bytes, void** out) {
 void host_release(gd_ctx* c, void* p, size_t bytes) {
   if (!p) return;
   std::lock_guard<std::mutex> g(c->mu);
-  c->host_free.emplace(size_class(bytes), p);
+  auto it = c->host_size.find(p);
+  c->host_free.emplace(it != c->host_size.end() ? it->second : size_class(bytes), p);
 }
 
 }  // namespace
@@ -456,18 +540,32 @@ gd_status build_graph(gd_ctx* c, gd_job* j) {
   return GD_OK;
 }
 
-gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
-                   int tile, gd_job** out) {
-  const int L = b->n_ligands;
-  if (L < 0) return fail(GD_EINVAL, "n_ligands < 0");
-  if (L > 0 && (!b->atom_off || !b->xyz || !b->bond_off || !b->bonds || !b->rot_off || !b->rot_bond))
+// The job's ligand i is batch ligand sel[i] (sel = NULL: ligand i, L = n_ligands); its
+// atoms and rotamers are packed contiguously in that order.
+gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const int32_t* sel, int n_sel,
+                   const gd_search_params* p, int tile, gd_job** out) {
+  const int LB = b->n_ligands;
+  if (LB < 0) return fail(GD_EINVAL, "n_ligands < 0");
+  if (sel && n_sel < 0) return fail(GD_EINVAL, "n_sel < 0");
+  const int L = sel ? n_sel : LB;
+  if (LB > 0 && (!b->atom_off || !b->xyz || !b->bond_off || !b->bonds || !b->rot_off || !b->rot_bond))
     return fail(GD_EINVAL, "batch has a NULL array");
-  if (L > 0 && (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0))
+  if (LB > 0 && (b->atom_off[0] != 0 || b->bond_off[0] != 0 || b->rot_off[0] != 0))
     return fail(GD_EINVAL, "CSR offsets must start at 0");
-  for (int i = 0; i < L; ++i)
-    if (b->atom_off[i + 1] < b->atom_off[i] || b->bond_off[i + 1] < b->bond_off[i] || b->rot_off[i + 1] < b->rot_off[i])
-      return fail(GD_EINVAL, "CSR offsets decrease at ligand %d", i);
-  const long long N = L ? b->atom_off[L] : 0, Rt = L ? b->rot_off[L] : 0;
+  // destination offsets of the job's ligands (atoms, rotamers)
+  std::vector<int32_t> dA(L + 1, 0), dR(L + 1, 0);
+  for (int i = 0; i < L; ++i) {
+    const int s = sel ? sel[i] : i;
+    if (s < 0 || s >= LB) return fail(GD_EINVAL, "sel[%d] = %d outside [0, %d)", i, s, LB);
+    if (b->atom_off[s + 1] < b->atom_off[s] || b->bond_off[s + 1] < b->bond_off[s] || b->rot_off[s + 1] < b->rot_off[s])
+      return fail(GD_EINVAL, "CSR offsets decrease at ligand %d", s);
+    const long long na = (long long)dA[i] + (b->atom_off[s + 1] - b->atom_off[s]);
+    const long long nr = (long long)dR[i] + (b->rot_off[s + 1] - b->rot_off[s]);
+    if (na > INT32_MAX || nr > INT32_MAX) return fail(GD_EINVAL, "batch too large");
+    dA[i + 1] = (int32_t)na;
+    dR[i + 1] = (int32_t)nr;
+  }
+  const long long N = dA[L], Rt = dR[L];
   gd_job* j = new gd_job();
   j->ctx = c;
   j->L = L;
@@ -501,10 +599,10 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   uint8_t* perm = (uint8_t*)(h + j->in.perm);
   RotDesc* rots = (RotDesc*)(h + j->in.rots);
   int32_t* order = (int32_t*)(h + j->in.order);
-  // ligands are packed by up to 16 host threads over contiguous ranges; each keeps its
+  // ligands are packed by the context's host threads over contiguous ranges; each keeps its
   // own exclusion list, concatenated afterwards in ligand order
   std::vector<double> cost(L);
-  const int T = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), L / 64}));
+  const int T = std::max(1, std::min(c->pool.threads(), L / 64));
   struct Part {
     int l0 = 0, l1 = 0, nmax = 2, bad = -1;
     gd_status st = GD_OK;
@@ -514,31 +612,27 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   std::vector<Part> parts(T);
   auto work = [&](Part& pt) {
     for (int i = pt.l0; i < pt.l1; ++i) {
-      const int a0 = b->atom_off[i], n = b->atom_off[i + 1] - a0;
-      const int b0 = b->bond_off[i], nb = b->bond_off[i + 1] - b0;
-      const int r0 = b->rot_off[i], R = b->rot_off[i + 1] - r0;
-      gd_status s2 = pack_ligand(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
-                                 p->min_bond_sep, xyz + a0, perm + a0, rots + r0, pt.excl, &cost[i]);
-      if (!s2 && R * j->reps > 32767) s2 = fail(GD_EINVAL, "ligand %d: too many steps", i);
+      const int s = sel ? sel[i] : i;
+      const int a0 = b->atom_off[s], n = b->atom_off[s + 1] - a0;
+      const int b0 = b->bond_off[s], nb = b->bond_off[s + 1] - b0;
+      const int r0 = b->rot_off[s], R = b->rot_off[s + 1] - r0;
+      gd_status s2 = pack_ligand(s, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
+                                 p->min_bond_sep, xyz + dA[i], perm + dA[i], rots + dR[i], pt.excl, &cost[i]);
+      if (!s2 && R * j->reps > 32767) s2 = fail(GD_EINVAL, "ligand %d: too many steps", s);
       if (s2) {
         pt.st = s2;
-        pt.bad = i;
+        pt.bad = s;
         pt.err = g_err;  // the message lives in this thread's g_err
         return;
       }
       pt.nmax = std::max(pt.nmax, n);
     }
   };
-  {
-    std::vector<std::thread> pool;
-    for (int t = 0; t < T; ++t) {
-      parts[t].l0 = (int)((long long)L * t / T);
-      parts[t].l1 = (int)((long long)L * (t + 1) / T);
-      if (t) pool.emplace_back(work, std::ref(parts[t]));
-    }
-    work(parts[0]);
-    for (auto& th : pool) th.join();
+  for (int t = 0; t < T; ++t) {
+    parts[t].l0 = (int)((long long)L * t / T);
+    parts[t].l1 = (int)((long long)L * (t + 1) / T);
   }
+  c->pool.run(T, [&](int t) { work(parts[t]); });
   int nmax = 2;
   size_t n_excl = 0;
   for (auto& pt : parts) {
@@ -555,15 +649,13 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
     size_t base = 0;
     for (auto& pt : parts) {
       if (base)
-        for (long long r = b->rot_off[pt.l0]; r < b->rot_off[pt.l1]; ++r) rots[r].excl_off += (uint32_t)base;
+        for (long long r = dR[pt.l0]; r < dR[pt.l1]; ++r) rots[r].excl_off += (uint32_t)base;
       if (!pt.excl.empty()) memcpy(h + j->in.excl + 2 * base, pt.excl.data(), 2 * pt.excl.size());
       base += pt.excl.size();
     }
   }
-  for (int i = 0; i <= L; ++i) {
-    atom_off[i] = L ? b->atom_off[i] : 0;
-    rot_off[i] = L ? b->rot_off[i] : 0;
-  }
+  memcpy(atom_off, dA.data(), sizeof(int32_t) * (L + 1));
+  memcpy(rot_off, dR.data(), sizeof(int32_t) * (L + 1));
   j->rot_off.assign(rot_off, rot_off + L + 1);
   for (int i = 0; i < L; ++i) order[i] = i;
   std::stable_sort(order, order + L, [&](int x, int y) { return cost[x] > cost[y]; });
@@ -640,7 +732,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   a.emax = 1;
   for (int i = 0; i < L; ++i) {
     int ne = 0;
-    const int n = b->atom_off[i + 1] - b->atom_off[i];
+    const int n = dA[i + 1] - dA[i];
     for (int r = rot_off[i]; r < rot_off[i + 1]; ++r) {
       ne += rots[r].n_excl;
       a.mask_words = std::max(a.mask_words, gd::step_mask_words(n, rots[r]));
@@ -904,7 +996,7 @@ gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, 
     gd::Tile tl = gd::tile_get(t);
     if (tl.slots > 1 && 32 * (tl.slots / 2) >= p->n_angles) continue;  // idle lanes only
     gd_job* j = nullptr;
-    if (make_job(c, pk, &sub, &q, t, &j)) continue;
+    if (make_job(c, pk, &sub, nullptr, 0, &q, t, &j)) continue;
     nmax = j->args.nmax;
     cudaMemcpyAsync(j->d_in, j->h_in, j->in.total, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync((char*)j->d_out + j->out.err, 0, 4, s);
@@ -942,9 +1034,10 @@ gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, 
 
 namespace {
 
-// Validate, pack and upload a batch on `stream`; the search is not launched.
-gd_status prepare(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p, void* stream,
-                  gd_job** out) {
+// Validate, pack and upload a batch (its ligands sel[0 .. n_sel) when sel is not NULL)
+// on `stream`; the search is not launched.
+gd_status prepare(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const int32_t* sel, int n_sel,
+                  const gd_search_params* p, void* stream, gd_job** out) {
   if (!c || !pk || !b || !out) return fail(GD_EINVAL, "NULL argument");
   gd_status st = check_params(p);
   if (st) return st;
@@ -952,7 +1045,10 @@ gd_status prepare(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, cons
   int tile = p->tile;  // 0 is resolved once the batch is packed
   if (tile == -1) {
     int nmax = 2;
-    for (int i = 0; i < b->n_ligands; ++i) nmax = std::max(nmax, b->atom_off[i + 1] - b->atom_off[i]);
+    for (int i = 0; i < (sel ? n_sel : b->n_ligands); ++i) {
+      const int s = sel ? sel[i] : i;
+      if (s >= 0 && s < b->n_ligands) nmax = std::max(nmax, b->atom_off[s + 1] - b->atom_off[s]);
+    }
     const std::string sig = signature(pk, p, nmax, pk->dev.bytes_pad <= gd::max_smem_grid_bytes());
     int found = 0;
     {
@@ -964,7 +1060,7 @@ gd_status prepare(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, cons
     tile = found;
   }
   gd_job* j = nullptr;
-  if ((st = make_job(c, pk, b, p, tile, &j))) return st;
+  if ((st = make_job(c, pk, b, sel, n_sel, p, tile, &j))) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(j->d_in, j->h_in, j->in.total, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)j->d_out + j->out.err, 0, 4, s);
@@ -981,7 +1077,16 @@ gd_status prepare(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, cons
 
 gd_status gd_prepare_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
                            void* stream, gd_job** out) {
-  gd_status st = prepare(c, pk, b, p, stream, out);
+  gd_status st = prepare(c, pk, b, nullptr, 0, p, stream, out);
+  if (!st) g_err.clear();
+  return st;
+}
+
+gd_status gd_prepare_batch_sel(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const int32_t* sel,
+                               int32_t n_sel, const gd_search_params* p, void* stream, gd_job** out) {
+  if (!sel && n_sel) return fail(GD_EINVAL, "NULL sel");
+  static const int32_t none = 0;
+  gd_status st = prepare(c, pk, b, sel ? sel : &none, n_sel, p, stream, out);
   if (!st) g_err.clear();
   return st;
 }
@@ -989,7 +1094,7 @@ gd_status gd_prepare_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch
 gd_status gd_dock_batch(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, const gd_search_params* p,
                         void* stream, gd_job** out) {
   gd_job* j = nullptr;
-  gd_status st = prepare(c, pk, b, p, stream, &j);
+  gd_status st = prepare(c, pk, b, nullptr, 0, p, stream, &j);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = enqueue_search(j, s)) || (st = enqueue_download(j, s))) {

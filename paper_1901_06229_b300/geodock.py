@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: 
 EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_free_pocket",
            "gd_dock_batch", "gd_fetch_results", "gd_job_launch", "gd_job_download", "gd_job_bytes", "gd_job_free",
            "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc",
-           "gd_prepare_batch"]
+           "gd_prepare_batch", "gd_prepare_batch_sel"]
 
 
 class GeoDockError(RuntimeError):
@@ -86,6 +86,8 @@ def load():
     L.gd_job_bytes.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint64)]
     L.gd_check_batch.argtypes = [P(LigandBatchC), P(SearchParamsC)]
     L.gd_prepare_batch.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), vp, P(vp)]
+    L.gd_prepare_batch_sel.argtypes = [vp, vp, P(LigandBatchC), P(C.c_int32), C.c_int32, P(SearchParamsC), vp,
+                                       P(vp)]
     L.gd_job_features.argtypes = [vp, vp, vp, vp, vp]
     L.gd_job_features.restype = C.c_int
     L.gd_job_launch_proposed.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.c_int, vp]
@@ -142,11 +144,16 @@ class _BatchArrays:
 
 
 class Job:
-    def __init__(self, ctx, handle, batch, params, debug, bumps=False):
+    def __init__(self, ctx, handle, batch, params, debug, bumps=False, sel=None):
         self.ctx, self.handle, self.debug, self.bumps = ctx, handle, debug or bumps, bumps
-        self.L = batch.n_ligands
-        self.N = len(batch.xyz)
-        self.rot_off = np.asarray(batch.rot_off, np.int64)
+        if sel is None:
+            self.L = batch.n_ligands
+            self.N = len(batch.xyz)
+            self.rot_off = np.asarray(batch.rot_off, np.int64)
+        else:  # the job holds ligands sel of batch, packed in that order
+            self.L = len(sel)
+            self.N = int(np.diff(batch.atom_off)[sel].sum())
+            self.rot_off = np.concatenate([[0], np.cumsum(np.diff(batch.rot_off)[sel])]).astype(np.int64)
         self.params = params
 
     def fetch(self, blocking=True, out=None):
@@ -286,14 +293,20 @@ class Context:
                                          _stream_handle(stream), C.byref(h)))
         return Job(self, h, batch, params, debug, bumps)
 
-    def prepare_batch(self, pocket: Pocket, batch, params, stream=None, debug=False, tile=0) -> Job:
-        """gd_prepare_batch: validate, pack and upload without searching."""
+    def prepare_batch(self, pocket: Pocket, batch, params, stream=None, debug=False, tile=0, sel=None) -> Job:
+        """gd_prepare_batch: validate, pack and upload without searching; with sel (ligand
+        indices into batch), gd_prepare_batch_sel: the job holds those ligands in that order."""
         arrs = _BatchArrays(batch)
         prm = params_c(params, GD_FLAG_DEBUG if debug else 0, tile)
         h = C.c_void_p()
-        self._check(load().gd_prepare_batch(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm),
-                                            _stream_handle(stream), C.byref(h)))
-        return Job(self, h, batch, params, debug)
+        if sel is None:
+            self._check(load().gd_prepare_batch(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm),
+                                                _stream_handle(stream), C.byref(h)))
+        else:
+            sel = np.ascontiguousarray(sel, np.int32)
+            self._check(load().gd_prepare_batch_sel(self.h, pocket.handle, C.byref(arrs.c), _ptr(sel, C.c_int32),
+                                                    len(sel), C.byref(prm), _stream_handle(stream), C.byref(h)))
+        return Job(self, h, batch, params, debug, sel=sel)
 
     def autotune(self, pocket: Pocket, batch, params, max_ligands=256, stream=None, no_filter=False):
         arrs = _BatchArrays(batch)

@@ -72,9 +72,10 @@ class Screen:
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
 
     def _submit(self, batch, ids, stream):
+        """Queue ligands ids of batch (packed straight from the library, no sub-batch)."""
         import torch
-        job = self.ctx.prepare_batch(self.pk, batch, self.params, stream=stream, debug=self.debug)
-        rows = batch.n_ligands * self.params.n_orient
+        job = self.ctx.prepare_batch(self.pk, batch, self.params, stream=stream, debug=self.debug, sel=ids)
+        rows = len(ids) * self.params.n_orient
         with torch.cuda.stream(stream):
             X = torch.empty((rows, 48), dtype=torch.bfloat16, device="cuda")
             y = torch.empty(rows, device="cuda")
@@ -123,7 +124,7 @@ class Screen:
                 ids = np.array(take, np.int64)
                 stream = self.streams[free[-1]]
                 try:
-                    job, X, y = self._submit(workload.batch.subset(ids), ids, stream)
+                    job, X, y = self._submit(workload.batch, ids, stream)
                 except gdk.GeoDockError as e:
                     if e.status != gdk.GD_EBUDGET:
                         raise

@@ -80,3 +80,27 @@ def test_memory_budget_admission(setup):
     np.testing.assert_array_equal(res.best_orient, free_run.best_orient)
     pk.free()
     tight.close()
+
+
+def test_selected_ligands_pack_like_a_sub_batch(setup):
+    """gd_prepare_batch_sel packs ligands straight from the library: the same results as
+    a sub-batch of those ligands (out of order and repeated indices included)."""
+    ctx, pk, w, _, _ = setup
+    rng = np.random.default_rng(11)
+    ids = rng.choice(w.batch.n_ligands, 37, replace=False)
+    ids = np.concatenate([ids, ids[:3]])  # a ligand may be listed twice
+    outs = []
+    for kw in (dict(batch=w.batch.subset(ids)), dict(batch=w.batch, sel=ids)):
+        job = ctx.prepare_batch(pk, kw["batch"], w.params, sel=kw.get("sel"))
+        job.launch()
+        job.download()
+        outs.append(job.fetch())
+        job.free()
+    for key in ("best_score", "best_orient", "best_angle", "best_xyz", "evals", "pair_tests", "atom_moves"):
+        np.testing.assert_array_equal(outs[0][key], outs[1][key], err_msg=key)
+    for bad in ([w.batch.n_ligands], [-1]):
+        with pytest.raises(gdk.GeoDockError, match="outside"):
+            ctx.prepare_batch(pk, w.batch, w.params, sel=np.array(bad))
+    empty = ctx.prepare_batch(pk, w.batch, w.params, sel=np.zeros(0, np.int64))
+    assert empty.L == 0
+    empty.free()
