@@ -160,8 +160,9 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(w, seconds=12.0):
-    """Oracle throughput on the host cores over a bounded sample of the workload."""
+def cpu_baseline(w, seconds=12.0, single_seconds=4.0):
+    """Oracle throughput on the host cores over a bounded sample of the workload: one
+    std::thread per core over ligands, and single-threaded on the first ligands."""
     import oracle
     cores = os.cpu_count() or 1
     done, t0, i = 0, time.perf_counter(), 0
@@ -171,8 +172,15 @@ def cpu_baseline(w, seconds=12.0):
         done += len(idx)
         i += len(idx)
     dt = time.perf_counter() - t0
+    one, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < single_seconds and one < w.batch.n_ligands:
+        oracle.dock_batch(w.batch.subset([one]), w.pocket, w.params, n_threads=1)
+        one += 1
+    dt1 = time.perf_counter() - t1
     return {"value": done / dt, "unit": "ligands/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {done} ligands of {w.name}, {dt:.1f} s, one std::thread per core"}
+            "sample": f"first {done} ligands of {w.name}, {dt:.1f} s, one std::thread per core",
+            "single_thread": {"value": one / dt1, "unit": "ligands/s", "cores": 1,
+                              "sample": f"first {one} ligands, {dt1:.1f} s"}}
 
 
 def dist_setup():
@@ -555,6 +563,7 @@ def main():
         frac = max(achieved / peak_tops, loads / peak_loads)
         work = {"ops_per_launch": alg["fp32_ops"], "byte_loads_per_launch": alg["byte_loads"],
                 "candidates_per_launch": alg["candidates"], "pair_tests_early_per_launch": alg["pair_tests_early"],
+                "pair_tests_full_per_launch": alg["pair_tests_full"],
                 "loads": {"achieved": loads, "peak": peak_loads, "unit": "Tloads/s", "frac": loads / peak_loads}}
     else:
         achieved = frac = None
