@@ -18,7 +18,8 @@ persistent fused search kernel.
              (32-pair tiles).  The reach filter proves most of those pair tests
              unnecessary, so the fraction can exceed 1; ``executed`` gives the FP32
              operations the kernel itself performs (3 per pair test it runs, 6 per
-             turned atom) against the same peak.
+             turned atom) against the same peak, and ``issue`` its warp-instruction
+             rate (ncu count) against the schedulers' peak: the bound it actually meets.
   cpu_baseline : the FP64 oracle on the host cores, on a bounded sample
 
 --impl reference times the oracle itself (the paper has no code to run) on the same
@@ -62,6 +63,17 @@ MEASURED_TRAFFIC = {
     "a20fe81ae2d8391d": {("batched-4096lig-64grid", 14): 4893184 + 1409280,
                          ("large-512lig-128grid", 9): 2731520 + 6400},
 }
+
+
+# Warp instructions (smsp__inst_executed.sum) of one search-kernel launch, from one ncu
+# capture of the full-size workload (one pass), keyed like MEASURED_TRAFFIC: the kernel
+# is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
+# per clock) is the roofline that binds it.
+MEASURED_INSTRUCTIONS = {
+    "a20fe81ae2d8391d": {("batched-4096lig-64grid", 14): 8538068448,
+                         ("large-512lig-128grid", 9): 14730981071},
+}
+ISSUE_PER_SM_CLK = 4
 
 
 def search_kernel_hash() -> str:
@@ -557,6 +569,12 @@ def main():
     launch_s = np.mean(kernel_ms) / 1e3
     executed = {"achieved": exec_ops / launch_s / 1e12, "frac": exec_ops / launch_s / 1e12 / peak_tops,
                 "ops_per_launch": exec_ops}
+    inst = MEASURED_INSTRUCTIONS.get(search_kernel_hash(), {}).get((w.name, tile))
+    peak_issue = sm_count * ISSUE_PER_SM_CLK * mhz * 1e6 / 1e12
+    issue = {"warp_instructions_per_launch": inst, "unit": "T warp-instructions/s", "peak": peak_issue,
+             "achieved": inst / launch_s / 1e12 if inst else None,
+             "frac": inst / launch_s / 1e12 / peak_issue if inst else None,
+             "peak_kind": f"{sm_count} SMs x {ISSUE_PER_SM_CLK} schedulers x {mhz:.0f} MHz; instructions from ncu"}
     if alg:
         achieved = alg["fp32_ops"] / launch_s / 1e12
         loads = alg["byte_loads"] / launch_s / 1e12
@@ -584,7 +602,7 @@ def main():
                                   "(sm_max_mhz of MEASURED_PEAKS.json)",
                      "work": "oracle count: 16 FP32 ops + 1 byte load per fragment atom, 7 ops per "
                              "early-exit pair test" if alg else None,
-                     **work, "executed": executed},
+                     **work, "executed": executed, "issue": issue},
         "clocks": clocks,
         "wall_s_timed": wall,
     }
