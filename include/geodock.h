@@ -115,7 +115,10 @@ typedef struct {
  *                          step = rep*R_i + r; -1 where every candidate was bumped
  *   best_xyz[3*N]          its final coordinates, atoms in input order
  *   evals[L]               candidates evaluated (O * reps * R_i * A)
- *   pair_tests[L]          moving x static pair tests performed (early exit per atom)
+ *   pair_tests[L]          moving x static pair tests performed: with the reach filter,
+ *                          each step's near pairs at every angle; without it, every
+ *                          eligible pair of each moving atom at every angle not yet
+ *                          bumped (early exit per atom)
  *   atom_moves[L]          fragment atoms rotated and scored (O * reps * A * sum_r f_r,
  *                          f_r = atoms of fragment r)
  *   best_rigid[L]          rigid-sweep candidate kept for the best restart (0 without sweep)
