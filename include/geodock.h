@@ -61,6 +61,11 @@ typedef int gd_status;
 #define GD_FLAG_MASK_SWEEP 8    /* sweep every step's angles over the reach filter's bit masks
                                    instead of its compacted near list (the path a step takes
                                    when the list overflows); results are identical */
+#define GD_FLAG_TEST_STAGE_TIMEOUT 16 /* testing only: the pocket-staging barrier of kernels that
+                                   stage the grid in shared memory expects 16 bytes more than
+                                   are copied, so its bounded wait (about 2 s) runs out; the job
+                                   then reports GD_ETIMEOUT and the context stays usable.
+                                   Ignored by autotuning; rejected by gd_dock_batch_noalloc. */
 
 typedef struct gd_ctx gd_ctx;
 typedef struct gd_pocket gd_pocket;

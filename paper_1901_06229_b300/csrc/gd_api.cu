@@ -699,6 +699,7 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
   }
   a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
   a.mask_sweep = (p->flags & GD_FLAG_MASK_SWEEP) ? 1 : 0;
+  a.stage_extra_bytes = (p->flags & GD_FLAG_TEST_STAGE_TIMEOUT) ? 16 : 0;
   char* o = (char*)j->d_out;
   a.best_score = (uint32_t*)(o + j->out.best_score);
   a.best_orient = (int32_t*)(o + j->out.best_orient);
@@ -985,7 +986,7 @@ gd_status gd_autotune(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, 
   gd_ligand_batch sub = *b;
   if (max_ligands > 0 && sub.n_ligands > max_ligands) sub.n_ligands = max_ligands;
   gd_search_params q = *p;
-  q.flags &= ~(GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS);
+  q.flags &= ~(GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS | GD_FLAG_TEST_STAGE_TIMEOUT);
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   GD_CUDA(cudaEventCreate(&e0));

@@ -100,6 +100,7 @@ struct SearchArgs {
   int rigid_n;                // (2s+1)^3 (identity first)
   int16_t* pose_rigid;        // [L*O] (scratch) chosen rigid candidate per restart
   int16_t* best_rigid;        // [L] (output) of the best restart
+  int stage_extra_bytes;      // testing: bytes the grid-staging barrier expects beyond the grid
 };
 
 // Margin of the reach filter (A).  FP32 rounding moves a rotated atom by ~1e-5 A at

@@ -233,6 +233,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   if (p->repetitions < 1 || p->repetitions > GD_MAX_REPS) return nfail(GD_EINVAL, "repetitions out of range");
   if (p->flags & (GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS))
     return nfail(GD_EINVAL, "debug outputs are not available without allocation");
+  if (p->flags & GD_FLAG_TEST_STAGE_TIMEOUT) return nfail(GD_EINVAL, "test flags are not accepted here");
   if (out->orient_score || out->orient_pick || out->bump_bits)
     return nfail(GD_EINVAL, "debug outputs are not available without allocation");
   if (p->tile < -1 || p->tile > gd::tile_count()) return nfail(GD_EINVAL, "tile out of range");
@@ -371,6 +372,7 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   }
   a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
   a.mask_sweep = (p->flags & GD_FLAG_MASK_SWEEP) ? 1 : 0;
+  a.stage_extra_bytes = 0;
   a.best_score = (uint32_t*)(d + o_score);
   a.best_orient = (int32_t*)(d + o_orient);
   a.best_angle = (int16_t*)(d + o_angle);

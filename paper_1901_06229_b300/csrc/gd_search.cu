@@ -983,7 +983,8 @@ __device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"(bytes + a.stage_extra_bytes)
                  : "memory");
     constexpr int CHUNK = 32768;
     for (int off = 0; off < bytes; off += CHUNK) {

@@ -20,6 +20,7 @@ GD_FLAG_DEBUG = 1
 GD_FLAG_DEBUG_BUMPS = 2
 GD_FLAG_NO_FILTER = 4
 GD_FLAG_MASK_SWEEP = 8
+GD_FLAG_TEST_STAGE_TIMEOUT = 16
 STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: "GD_ECUDA",
                 5: "GD_ETIMEOUT", 6: "GD_EBUSY", 7: "GD_ENOTREADY"}
 
@@ -280,13 +281,15 @@ class Context:
         return Pocket(self, h)
 
     def dock_batch(self, pocket: Pocket, batch, params, stream=None, debug=False, bumps=False, tile=0,
-                   no_filter=False, mask_sweep=False) -> Job:
+                   no_filter=False, mask_sweep=False, test_stage_timeout=False) -> Job:
         """gd_dock_batch: debug keeps per-restart scores/picks, bumps also per-candidate bump bits,
         no_filter tests every pair at every angle, mask_sweep sweeps the reach filter's bit masks
-        instead of its near list (same results either way)."""
+        instead of its near list (same results either way); test_stage_timeout makes the
+        grid-staging wait run out (testing the device-timeout report)."""
         arrs = _BatchArrays(batch)
         flags = ((GD_FLAG_DEBUG if debug else 0) | (GD_FLAG_DEBUG_BUMPS if bumps else 0)
-                 | (GD_FLAG_NO_FILTER if no_filter else 0) | (GD_FLAG_MASK_SWEEP if mask_sweep else 0))
+                 | (GD_FLAG_NO_FILTER if no_filter else 0) | (GD_FLAG_MASK_SWEEP if mask_sweep else 0)
+                 | (GD_FLAG_TEST_STAGE_TIMEOUT if test_stage_timeout else 0))
         prm = params_c(params, flags, tile)
         h = C.c_void_p()
         self._check(load().gd_dock_batch(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm),
