@@ -62,6 +62,8 @@ MEASURED_TRAFFIC = {
                          ("large-512lig-128grid", 9): 3045632 + 4608},
     "a20fe81ae2d8391d": {("batched-4096lig-64grid", 14): 4893184 + 1409280,
                          ("large-512lig-128grid", 9): 2731520 + 6400},
+    "a31acb119e6544d5": {("batched-4096lig-64grid", 14): 4559104 + 1304832,
+                         ("large-512lig-128grid", 9): 3022848 + 6400},
 }
 
 
@@ -71,6 +73,8 @@ MEASURED_TRAFFIC = {
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
     "a20fe81ae2d8391d": {("batched-4096lig-64grid", 14): 8538068448,
+                         ("large-512lig-128grid", 9): 14730981071},
+    "a31acb119e6544d5": {("batched-4096lig-64grid", 14): 8538068365,
                          ("large-512lig-128grid", 9): 14730981071},
 }
 ISSUE_PER_SM_CLK = 4
