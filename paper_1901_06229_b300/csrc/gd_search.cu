@@ -1,26 +1,35 @@
 // Fused GeoDock pose-search kernel for sm_103a.
 //
 // One warp owns one pose (ligand, restart orientation) from placement to its final
-// score; the CTA is persistent and its warps pull poses from a global counter.
+// score; the CTA is persistent and its warps pull poses from a global counter, a few
+// restarts of one ligand at a time.
 //   a1  the pocket grid is staged once per CTA into shared memory with bulk async
-//       copies completing on an mbarrier (when the cropped grid fits), else read
-//       through L1/L2;
-//   a2  the ligand (preorder-packed float4) is read into a per-warp shared buffer;
+//       copies completing on an mbarrier (when the cropped grid fits, 128-register
+//       builds), else read through a 3D texture (point sampling, border 0) or L1/L2;
+//   a2  the ligand (preorder-packed float4) and its rotamer descriptors and excluded
+//       pairs are read into per-warp shared buffers;
 //   a3  generate_starting_pose: ZYZ Euler restart about the centroid, moved to the
-//       pocket centre (Listing 1 / Sec. 3.1);
-//   a4  rigid score: sum of grid cells under the atoms (scoring function, Sec. 3.2);
+//       pocket centre (Listing 1 / Sec. 3.1); a small kernel writes every restart's
+//       rotation and the centred ligands once per launch, and pose coordinates are
+//       kept in grid units (a point's cell is the floor of its coordinates);
+//   a4  rigid score: sum of grid cells under the atoms (scoring function, Sec. 3.2),
+//       each atom's cell cached beside its coordinates;
 //   a5-a8 optimize_pose (Sec. 3.1, Sec. 4.1): for each rotamer in order, every lane
-//       evaluates its own angles k = lane + 32 j: Rodrigues rotation of the moving
-//       fragment about the current bond axis, bump test of every moving atom against
-//       every static atom (exclusions of atoms fewer than min_bond_sep bonds apart
-//       handled by parking those static atoms far away while that moving atom is
-//       tested), grid gather; a warp max-reduction over a packed (score, -k) key is
-//       the per-fragment reduction, and the winning rotation is committed;
+//       evaluates its own angles k = lane + 32 j.  An exact reach filter keeps only
+//       the moving x static pairs (not excluded by bond separation) whose closest
+//       approach over the whole turn is below bump_dist + 0.01 A; each kept pair's
+//       squared distance at angle theta is |x_a - x_b|^2 + (cos - 1) P + sin Q, two
+//       FMAs per angle (BumpCheck, Sec. 3.2; the unfiltered sweep tests every pair).
+//       The moving fragment is turned about the current bond axis (Rodrigues split
+//       into the axis frame) and its cells gathered; a warp max-reduction over a
+//       packed (score, -k) key is the per-fragment reduction, and the winning
+//       rotation is committed;
 //   a9  the rotamer loop repeats `reps` times (num_repetitions, Listing 1);
 //   a10 the last warp to finish a ligand reduces over its restarts (ties: smallest
 //       o), replays the winning pose to recover its coordinates and writes results.
 // All geometry uses explicitly rounded FP32 intrinsics, so the search and the replay
-// produce bitwise-identical coordinates and no launch tile can change a result.
+// produce bitwise-identical coordinates, and neither the launch tile nor the filter
+// path (near list, masks, none) can change a result.
 #include <cuda_bf16.h>
 
 #include <cstdint>
