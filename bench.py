@@ -72,13 +72,21 @@ MEASURED_INSTRUCTIONS = {
 ISSUE_PER_SM_CLK = 4
 
 
-def search_kernel_hash() -> str:
-    """Hash of the search kernel's sources without // comments and blank lines (an edit
-    of the documentation does not detach the measurements)."""
+# DRAM bytes of one proposer-network forward (mlp_infer_kernel, 4,194,304 rows), keyed by
+# a hash of its source like MEASURED_TRAFFIC.
+MLP_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_mlp.cu",)
+MEASURED_MLP_TRAFFIC = {
+    "707fb5b547da1113": {4194304: 402859264 + 16028672},
+}
+
+
+def search_kernel_hash(sources=SEARCH_KERNEL_SOURCES) -> str:
+    """Hash of a kernel's sources without // comments and blank lines (an edit of the
+    documentation does not detach the measurements)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in SEARCH_KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
             for line in fh:
                 code = re.sub(r"//.*", "", line).rstrip()
@@ -303,6 +311,7 @@ def run_learned(args, world, rank, local):
         job.launch_proposed(ye, k, margin, 1, stream)
 
     times = {}
+    clk = ClockSampler(dev).__enter__()
     for name, fn in (("plain", plain), ("learned", learned)):
         for _ in range(args.warmup):
             fn()
@@ -319,6 +328,7 @@ def run_learned(args, world, rank, local):
         times[name] = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, world)
         job.download(stream)
         times[name + "_res"] = job.fetch()
+    clk.__exit__(None, None, None)
     cnt, _ = job.selection()
     # each stage of a learned step alone
     def stage_time(fn):
@@ -358,12 +368,16 @@ def run_learned(args, world, rank, local):
         "plain_value": plain_v, "speedup_vs_plain": value / plain_v,
         "best_pose_recall": recall, "score_regret": regret, "fallback_fraction": float(np.mean(cnt > k)),
         "restarts_searched_per_ligand": float(cnt.mean()),
-        "gpu_launches": args.steps * 7,  # features, MLP, 3 selection kernels, pose setup, search
+        "gpu_launches": args.steps * 8,  # pose setup + features, MLP, 3 selection kernels, pose setup + search
         "roofline": {"bound": "tensor", "kernel": "mlp_infer_kernel (fused two-layer forward, 1 launch)",
-                     "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak, "traffic": None,
+                     "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                     "traffic": MEASURED_MLP_TRAFFIC.get(search_kernel_hash(MLP_KERNEL_SOURCES), {}).get(L * O),
                      "peak_kind": "bf16_tflops of MEASURED_PEAKS.json (burst)"},
         "mlp_rows_per_s": L * O / mlp_s,
         "stage_ms": {"features": 1e3 * feat_s, "network": 1e3 * mlp_s, "select_and_search": 1e3 * search_s},
+        "clocks": clk.summary(),
+        # the oracle searches every restart (the exhaustive search the learned path prunes)
+        "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline(we),
     }))
 
 
@@ -385,19 +399,30 @@ def run_mlp(args, world, rank, local):
     barrier(world)
     st = torch.cuda.current_stream()
     ev = []
-    for s in range(args.steps):
-        flush.fill_(s & 0xFF)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        net.predict(X, y)
-        b.record(st)
-        ev.append((a, b))
-    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            net.predict(X, y)
+            b.record(st)
+            ev.append((a, b))
+        torch.cuda.synchronize()
     t = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, world)
     assert net.error() == 0 and bool(torch.isfinite(y).all())
+    P = net.get_params()
+    Xs = X[:65536].float().cpu().numpy()
     net.close()
     if rank != 0:
         return
+    cpu = None
+    if not args.no_cpu_baseline:  # the FP64 numpy reference of the same forward on a sample
+        from oracle import mlp as om
+        t0 = time.perf_counter()
+        om.forward(P, Xs, rounding=True)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(Xs) / dt, "unit": "rows/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"first {len(Xs)} rows, {dt:.1f} s, numpy FP64 (BLAS threads)"}
     tflops = MLP_FLOPS_PER_ROW * rows * world * args.steps / t / 1e12
     peak = measured_peaks().get("bf16_tflops", 1787.5)
     print(json.dumps({
@@ -408,7 +433,9 @@ def run_mlp(args, world, rank, local):
         "config": {"workload": f"mlp-48-256-256-1-{rows}rows", "rows": rows, "l2": "flushed between steps"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                     "traffic": None, "peak_kind": "bf16_tflops of MEASURED_PEAKS.json (burst)"}}))
+                     "traffic": MEASURED_MLP_TRAFFIC.get(search_kernel_hash(MLP_KERNEL_SOURCES), {}).get(rows),
+                     "peak_kind": "bf16_tflops of MEASURED_PEAKS.json (burst)"},
+        "clocks": clk.summary(), "cpu_baseline": cpu}))
 
 
 def run_stream(args, world, rank, local):
