@@ -110,6 +110,11 @@ struct Pocket {
   V3 origin;
 };
 
+// Centre of the grid box, where restarts place the ligand's centroid.
+inline V3 pocket_centre(V3 origin, double h, int nx, int ny, int nz) {
+  return origin + (0.5 * h) * V3{(double)nx, (double)ny, (double)nz};
+}
+
 // Cell value at x: grid[floor((x - origin)/h)], 0 outside the box (scoring function).
 int cell_value(const Pocket& P, V3 x) {
   double u[3] = {(x.x - P.origin.x) / P.h, (x.y - P.origin.y) / P.h, (x.z - P.origin.z) / P.h};
@@ -252,6 +257,9 @@ bool build_rotamer(const Topo& t, const int32_t* bonds, int nb, int rb, int min_
   return true;
 }
 
+// BumpCheck's pair rule (Sec. 3.2): a pair bumps when strictly closer than bump_dist.
+inline bool bumps(double d, double bump_dist) { return d < bump_dist; }
+
 // Bump status of one candidate: 0 free, 1 bumped, 2 uncertain (a pair within eps of
 // the threshold and no pair clearly inside it).  *first_bump is the position of the
 // first pair closer than bump_dist in the list order (moving atom ascending, then
@@ -262,7 +270,7 @@ int bump_status(const Rotamer& r, const std::vector<V3>& xmoved, const std::vect
   int64_t first = -1, idx = 0;
   for (auto& pr : r.pairs) {
     double d = norm(xmoved[pr.first] - x[pr.second]);
-    if (d < bump_dist) {
+    if (bumps(d, bump_dist)) {
       any_exact = true;
       if (first < 0) first = idx;
     }
@@ -319,7 +327,7 @@ bool prepare(const float* xyz_in, int n, const int32_t* bonds, int nb, const int
     L.c_lig = L.c_lig + L.x0[a];
   }
   L.c_lig = (1.0 / n) * L.c_lig;
-  L.c_pocket = P.origin + (0.5 * P.h) * V3{(double)P.nx, (double)P.ny, (double)P.nz};
+  L.c_pocket = pocket_centre(P.origin, P.h, P.nx, P.ny, P.nz);
   return true;
 }
 
@@ -535,7 +543,7 @@ void orc_place(const float* xyz, int n, int o, int na, int nb, int ng, int nx, i
   V3 c_lig{0, 0, 0};
   for (int a = 0; a < n; ++a) c_lig = c_lig + V3{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]};
   c_lig = (1.0 / n) * c_lig;
-  V3 c_pocket = V3{origin[0], origin[1], origin[2]} + (0.5 * h) * V3{(double)nx, (double)ny, (double)nz};
+  V3 c_pocket = pocket_centre(V3{origin[0], origin[1], origin[2]}, h, nx, ny, nz);
   M3 R = euler_orientation(o, na, nb, ng);
   for (int a = 0; a < n; ++a) {
     V3 y = c_pocket + mul(R, V3{xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2]} - c_lig);
@@ -592,7 +600,7 @@ int orc_bumped(int n, const int32_t* bonds, int nb, int rb, int min_sep, double 
   for (auto& pr : r.pairs) {
     V3 a{xyz[3 * pr.first], xyz[3 * pr.first + 1], xyz[3 * pr.first + 2]};
     V3 b{xyz[3 * pr.second], xyz[3 * pr.second + 1], xyz[3 * pr.second + 2]};
-    if (norm(a - b) < bump_dist) return 1;
+    if (bumps(norm(a - b), bump_dist)) return 1;
   }
   return 0;
 }
@@ -683,7 +691,7 @@ int orc_features(const float* xyz, int n, int R, int o, int na, int nb, int ng, 
   }
   *fps_gap = gap;
   const M3 Ro = euler_orientation(o, na, nb, ng);
-  const V3 cp = P.origin + (0.5 * P.h) * V3{(double)P.nx, (double)P.ny, (double)P.nz};
+  const V3 cp = pocket_centre(P.origin, P.h, P.nx, P.ny, P.nz);
   for (int sidx = 0; sidx < 25; ++sidx) {
     const int a = fps[sidx % nsel];
     fps_out[sidx] = a;

@@ -377,6 +377,24 @@ def test_score_never_decreases_and_k0_feasible():
     assert out["best_orient"][0] == int(np.argmax(out["orient_score"][0]))
 
 
+def test_ties_go_to_the_first_angle_and_restart():
+    """On an all-zero pocket every candidate and every restart scores 0: the picks are
+    the smallest angle (k = 0, the identity, always free), the best restart is o = 0 and
+    the rigid sweep keeps its first candidate (the identity)."""
+    pocket = synth.Pocket(grid=np.zeros((16, 16, 16), np.uint8), spacing=0.5,
+                          origin=np.array([-4.0, -4.0, -4.0], np.float32))
+    params = synth.SearchParams(2, 2, 2, 8)
+    for lig in small_ligands()[:2]:
+        out = oracle.dock_batch(synth.pack([lig]), pocket, params)
+        assert np.all(out["orient_score"] == 0)
+        assert np.all(out["orient_pick"] == 0)
+        assert out["best_orient"][0] == 0 and out["best_score"][0] == 0
+    # the rigid sweep ties too: the identity (candidate 0) is kept
+    rigid = synth.SearchParams(2, 2, 2, 8, rigid_span=1, rigid_step=0.1)
+    out = oracle.dock_batch(synth.pack(small_ligands()[:1]), pocket, rigid)
+    assert np.all(out["orient_rigid"] == 0)
+
+
 def test_counters():
     w = synth.workload_batched(3)
     out = oracle.dock_batch(w.batch, w.pocket, w.params)
