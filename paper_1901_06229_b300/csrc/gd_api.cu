@@ -482,7 +482,8 @@ struct gd_job {
   SearchArgs args{};
   gd::LaunchCfg cfg{};
   cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;  // built at the job's second launch
+  int launches = 0;                // searches enqueued so far
   // restart selection of the learned proposer (allocated on first use)
   void* d_sel = nullptr;
   size_t sel_bytes = 0;
@@ -520,10 +521,10 @@ std::string signature(const gd_pocket* pk, const gd_search_params* p, int nmax, 
   return b;
 }
 
-// Capture [clear counters, search kernel] once; replayed by every launch of the job.
+// Capture [clear counters, search kernel] once; replayed by every later launch of the
+// job.  A job's first launch goes to the stream directly (capturing and instantiating a
+// graph costs more host time than a single launch of a small job saves).
 gd_status build_graph(gd_ctx* c, gd_job* j) {
-  cudaError_t pe = gd::plan_search(j->args, j->tile, j->grid_in_smem, c->num_sms, &j->cfg);
-  if (pe != cudaSuccess) return fail(GD_ECUDA, "search launch shape: %s", cudaGetErrorString(pe));
   cudaStream_t s = c->capture_stream;
   GD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s);
@@ -754,9 +755,12 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
     return fail(GD_EINVAL, "tile %d needs more shared memory than a block has", tile);
   }
   GD_CUDA(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
-  if (L > 0 && (st = build_graph(c, j))) {
-    job_release(c, j);
-    return st;
+  if (L > 0) {  // launch shape (kernel attributes and occupancy: queried outside any capture)
+    cudaError_t pe = gd::plan_search(j->args, j->tile, j->grid_in_smem, c->num_sms, &j->cfg);
+    if (pe != cudaSuccess) {
+      job_release(c, j);
+      return fail(GD_ECUDA, "search launch shape: %s", cudaGetErrorString(pe));
+    }
   }
   *out = j;
   return GD_OK;
@@ -764,7 +768,17 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
 
 gd_status enqueue_search(gd_job* j, cudaStream_t s) {
   if (j->L == 0) return GD_OK;
-  GD_CUDA(cudaGraphLaunch(j->exec, s));
+  if (!j->exec && j->launches == 0) {  // first launch: straight to the stream
+    GD_CUDA(cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s));
+    GD_CUDA(gd::launch_search(j->args, j->cfg, s));
+  } else {  // relaunched: capture once, replay from then on
+    if (!j->exec) {
+      gd_status st = build_graph(j->ctx, j);
+      if (st) return st;
+    }
+    GD_CUDA(cudaGraphLaunch(j->exec, s));
+  }
+  ++j->launches;
   GD_CUDA(cudaEventRecord(j->done, s));  // releasing the job waits for this launch
   return GD_OK;
 }
