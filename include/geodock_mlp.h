@@ -79,7 +79,12 @@ gd_status gd_job_features(gd_ctx* ctx, gd_job* job, void* x_bf16, float* x_f32, 
  * evals[] counts them.  Needs O <= 256.  Queue gd_job_download + gd_fetch_results. */
 gd_status gd_job_launch_proposed(gd_ctx* ctx, gd_job* job, const float* pred, int k, float margin, int rule,
                                  void* stream);
-/* Restarts searched per ligand (k or O) and the prediction spreads of the last proposed
+/* The same with a bounded fallback: a ligand that falls back searches its k_fallback
+ * best-predicted restarts (ties to the smaller restart id), k <= k_fallback <= O;
+ * k_fallback = O is gd_job_launch_proposed.  GD_EINVAL outside that range. */
+gd_status gd_job_launch_proposed_fb(gd_ctx* ctx, gd_job* job, const float* pred, int k, int k_fallback, float margin,
+                                    int rule, void* stream);
+/* Restarts searched per ligand (k, or the fallback count) and the prediction spreads of the last proposed
  * launch (host arrays of L; either may be NULL; waits for the job). */
 gd_status gd_job_selection(gd_ctx* ctx, gd_job* job, int32_t* counts, float* spreads);
 

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "geodock.h"
+#include "geodock_mlp.h"
 #include "gd_internal.h"
 
 // The search kernel packs atom ids into bytes (near pairs, the reach filter's column
@@ -1134,9 +1135,16 @@ gd_status gd_job_features(gd_ctx* c, gd_job* j, void* x_bf16, float* x_f32, void
 
 gd_status gd_job_launch_proposed(gd_ctx* c, gd_job* j, const float* pred, int k, float margin, int rule,
                                  void* stream) {
+  return gd_job_launch_proposed_fb(c, j, pred, k, j ? j->O : 0, margin, rule, stream);
+}
+
+gd_status gd_job_launch_proposed_fb(gd_ctx* c, gd_job* j, const float* pred, int k, int k_fallback, float margin,
+                                    int rule, void* stream) {
   if (!c || !j || !pred) return fail(GD_EINVAL, "NULL argument");
   if (j->O > 256) return fail(GD_EINVAL, "restart selection supports at most 256 restarts (have %d)", j->O);
   if (k < 1 || k > j->O) return fail(GD_EINVAL, "k = %d outside [1, %d]", k, j->O);
+  if (k_fallback < k || k_fallback > j->O)
+    return fail(GD_EINVAL, "k_fallback = %d outside [k = %d, %d]", k_fallback, k, j->O);
   if (j->L == 0) return GD_OK;
   cudaSetDevice(c->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1167,8 +1175,8 @@ gd_status gd_job_launch_proposed(gd_ctx* c, gd_job* j, const float* pred, int k,
   gd::LaunchCfg cfg;
   cudaError_t e = gd::plan_search(a, j->tile, j->grid_in_smem, c->num_sms, &cfg);
   if (e == cudaSuccess)
-    e = gd::launch_selection(a, pred, k, margin, rule, j->sel_cnt, j->sel_topk, j->sel_spread, j->sel_off, j->sel_items,
-                             j->sel_n, s);
+    e = gd::launch_selection(a, pred, k, k_fallback, margin, rule, j->sel_cnt, j->sel_topk, j->sel_spread, j->sel_off,
+                             j->sel_items, j->sel_n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.pose_score, 0xFF, 4 * L * O, s);
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s);
   if (e == cudaSuccess) e = gd::launch_search(a, cfg, s);

@@ -155,12 +155,12 @@ cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int nu
 // The proposer's 48 features of every (ligand, restart) of a packed batch, rows
 // li * O + o, as BF16 (Xb) and/or FP32 (Xf).
 cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, int num_sms, cudaStream_t stream);
-// Restart selection from predicted scores [L x O]: per ligand the top k (or all O when
-// the top-k spread is below (rule 0) / above (rule 1) margin), written as an item list
-// in queue order.
-cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, float margin, int rule, int32_t* cnt,
-                             uint16_t* topk, float* spread, int32_t* off, uint32_t* items, int32_t* n_items,
-                             cudaStream_t stream);
+// Restart selection from predicted scores [L x O]: per ligand the top k, or the top kf
+// (all O when kf >= O) when the top-k spread is below (rule 0) / above (rule 1) margin,
+// written as an item list in queue order.
+cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, int kf, float margin, int rule,
+                             int32_t* cnt, uint16_t* topk, float* spread, int32_t* off, uint32_t* items,
+                             int32_t* n_items, cudaStream_t stream);
 // Launch the search (kernel only; the work counter and per-ligand counters must be
 // zeroed by the caller first).
 cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t stream);

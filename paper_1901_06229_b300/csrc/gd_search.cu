@@ -1244,16 +1244,24 @@ __global__ void __launch_bounds__(256) feature_kernel(const __grid_constant__ Se
 // restart when the spread is below `margin` (rule 0: the network cannot separate its
 // top choices) or above it (rule 1: the network expects only a few restarts to be good,
 // which is where a wrong top-k loses the best pose).
-__global__ void select_kernel(const float* pred, int L, int O, int k, float margin, int rule, int32_t* cnt,
+__global__ void select_kernel(const float* pred, int L, int O, int k, int kf, float margin, int rule, int32_t* cnt,
                               uint16_t* topk, float* spread) {
   const int lane = threadIdx.x & 31;
   const int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (li >= L) return;
   const float* p = pred + (size_t)li * O;
   // orderable keys: larger prediction first, then smaller restart id
+  // rank the k best; a ligand that falls back and searches only its kf < O best is
+  // ranked on to kf (rows of topk are kt = kf < O ? kf : k long)
+  const int kt = kf < O ? kf : k;
   float first = 0.f, last = 0.f;
+  bool fallback = false;
   unsigned taken[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // bit per (lane, slot): restarts o = lane + 32 s
-  for (int r = 0; r < k; ++r) {
+  for (int r = 0; r < kt; ++r) {
+    if (r == k) {  // the k best are ranked: fall back?
+      fallback = rule ? first - last > margin : first - last < margin;
+      if (!fallback) break;
+    }
     unsigned long long best = 0;
     for (int sidx = 0; sidx * 32 + lane < O && sidx < 8; ++sidx) {
       if (taken[sidx]) continue;
@@ -1270,15 +1278,17 @@ __global__ void select_kernel(const float* pred, int L, int O, int k, float marg
     }
     const int o = (int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFu));
     if ((o & 31) == lane) taken[o >> 5] = 1;
-    if (lane == 0) topk[(size_t)li * k + r] = (uint16_t)o;
-    const float v = p[o];
-    if (r == 0) first = v;
-    last = v;
+    if (lane == 0) topk[(size_t)li * kt + r] = (uint16_t)o;
+    if (r < k) {
+      const float v = p[o];
+      if (r == 0) first = v;
+      last = v;
+    }
   }
   if (lane == 0) {
     const float sp = first - last;
     spread[li] = sp;
-    cnt[li] = (rule ? sp > margin : sp < margin) ? O : k;
+    cnt[li] = (rule ? sp > margin : sp < margin) ? (kf < O ? kf : O) : k;
   }
 }
 
@@ -1308,9 +1318,10 @@ __global__ void scan_kernel(const int32_t* order, const int32_t* cnt, int L, int
   }
 }
 
-// Items (rows li * O + o) of every ligand at its queue offset.
+// Items (rows li * O + o) of every ligand at its queue offset: its ranked restarts
+// (rows of topk are kt long), or all of them in order when it searches every restart.
 __global__ void items_kernel(const int32_t* order, const int32_t* cnt, const int32_t* off, const uint16_t* topk, int L,
-                             int O, int k, uint32_t* items) {
+                             int O, int kt, uint32_t* items) {
   const int lane = threadIdx.x & 31;
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= L) return;
@@ -1318,7 +1329,7 @@ __global__ void items_kernel(const int32_t* order, const int32_t* cnt, const int
   const int c = cnt[li];
   uint32_t* dst = items + off[p];
   for (int s = lane; s < c; s += 32) {
-    const int o = c == k ? (int)topk[(size_t)li * k + s] : s;
+    const int o = c == O && kt < O ? s : (int)topk[(size_t)li * kt + s];
     dst[s] = (uint32_t)li * (uint32_t)O + (uint32_t)o;
   }
 }
@@ -1406,14 +1417,14 @@ cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int nu
   }
 }
 
-cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, float margin, int rule, int32_t* cnt,
-                             uint16_t* topk, float* spread, int32_t* off, uint32_t* items, int32_t* n_items,
-                             cudaStream_t st) {
+cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, int kf, float margin, int rule,
+                             int32_t* cnt, uint16_t* topk, float* spread, int32_t* off, uint32_t* items,
+                             int32_t* n_items, cudaStream_t st) {
   if (a.L == 0) return cudaSuccess;
   const int blocks = (a.L * 32 + 255) / 256;
-  select_kernel<<<blocks, 256, 0, st>>>(pred, a.L, a.O, k, margin, rule, cnt, topk, spread);
+  select_kernel<<<blocks, 256, 0, st>>>(pred, a.L, a.O, k, kf, margin, rule, cnt, topk, spread);
   scan_kernel<<<1, 1024, 0, st>>>(a.order, cnt, a.L, off, n_items);
-  items_kernel<<<blocks, 256, 0, st>>>(a.order, cnt, off, topk, a.L, a.O, k, items);
+  items_kernel<<<blocks, 256, 0, st>>>(a.order, cnt, off, topk, a.L, a.O, kf < a.O ? kf : k, items);
   return cudaGetLastError();
 }
 

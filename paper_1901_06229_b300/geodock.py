@@ -93,6 +93,8 @@ def load():
     L.gd_job_features.restype = C.c_int
     L.gd_job_launch_proposed.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.c_int, vp]
     L.gd_job_launch_proposed.restype = C.c_int
+    L.gd_job_launch_proposed_fb.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_float, C.c_int, vp]
+    L.gd_job_launch_proposed_fb.restype = C.c_int
     L.gd_job_selection.argtypes = [vp, vp, vp, vp]
     L.gd_job_selection.restype = C.c_int
     L.gd_tile_count.argtypes = []
@@ -195,12 +197,17 @@ class Job:
         p = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
         self.ctx._check(load().gd_job_features(self.ctx.h, self.handle, p(x_bf16), p(x_f32), _stream_handle(stream)))
 
-    def launch_proposed(self, pred, k, margin, rule=1, stream=None):
-        """gd_job_launch_proposed: search the k best-predicted restarts per ligand, all of
-        them where the top-k spread is below (rule 0) / above (rule 1) margin; pred is a
-        CUDA float tensor [L*O]."""
-        self.ctx._check(load().gd_job_launch_proposed(self.ctx.h, self.handle, C.c_void_p(pred.data_ptr()), int(k),
-                                                      float(margin), int(rule), _stream_handle(stream)))
+    def launch_proposed(self, pred, k, margin, rule=1, stream=None, k_fallback=None):
+        """gd_job_launch_proposed(_fb): search the k best-predicted restarts per ligand, the
+        k_fallback best (all of them when None) where the top-k spread is below (rule 0) /
+        above (rule 1) margin; pred is a CUDA float tensor [L*O]."""
+        if k_fallback is None:
+            self.ctx._check(load().gd_job_launch_proposed(self.ctx.h, self.handle, C.c_void_p(pred.data_ptr()),
+                                                          int(k), float(margin), int(rule), _stream_handle(stream)))
+        else:
+            self.ctx._check(load().gd_job_launch_proposed_fb(self.ctx.h, self.handle, C.c_void_p(pred.data_ptr()),
+                                                             int(k), int(k_fallback), float(margin), int(rule),
+                                                             _stream_handle(stream)))
 
     def selection(self):
         """(restarts searched per ligand, prediction spread per ligand) of the last proposed launch."""

@@ -69,10 +69,11 @@ def predict(ctx, net, pk, w, stream=None):
     return job, y
 
 
-def evaluate(ctx, net, pk, w, k=16, margin=1e30, rule=1, exhaustive=None):
-    """Recall / regret of the pruned search against the exhaustive one on workload w."""
+def evaluate(ctx, net, pk, w, k=16, margin=1e30, rule=1, exhaustive=None, k_fallback=None):
+    """Recall / regret of the pruned search against the exhaustive one on workload w
+    (ligands that fall back search their k_fallback best restarts, all when None)."""
     job, y = predict(ctx, net, pk, w)
-    job.launch_proposed(y, k, margin, rule)
+    job.launch_proposed(y, k, margin, rule, k_fallback=k_fallback)
     job.download()
     pruned = job.fetch()
     cnt, spread = job.selection()
@@ -88,7 +89,7 @@ def evaluate(ctx, net, pk, w, k=16, margin=1e30, rule=1, exhaustive=None):
                 pruned=pruned, exhaustive=exhaustive, spread=spread)
 
 
-def tune_margin(ctx, net, pk, w, k=16, target=0.99, rule=1, margins=None):
+def tune_margin(ctx, net, pk, w, k=16, target=0.99, rule=1, margins=None, k_fallback=None):
     """The margin that reaches `target` best-pose recall on workload w with the fewest
     fallbacks: for rule 1 (fall back above the margin) the largest such margin, scanned
     downwards; for rule 0 the smallest, scanned upwards."""
@@ -97,14 +98,14 @@ def tune_margin(ctx, net, pk, w, k=16, target=0.99, rule=1, margins=None):
         margins = grid[::-1] if rule == 1 else [-1e30] + grid
     ex, r = None, None
     for m in margins:
-        r = evaluate(ctx, net, pk, w, k, m, rule, exhaustive=ex)
+        r = evaluate(ctx, net, pk, w, k, m, rule, exhaustive=ex, k_fallback=k_fallback)
         ex = r["exhaustive"]
         if r["recall"] >= target:
             return float(m), r
     return float(margins[-1]), r
 
 
-def fit(ctx, pk, n_train=12000, n_val=4000, k=16, target=0.99, seed=1):
+def fit(ctx, pk, n_train=12000, n_val=4000, k=16, target=0.99, seed=1, k_fallback=None):
     """Train on streaming-screen ligands and tune the fallback margin for `target` recall
     on a held-out split.  Returns (network, margin, training info)."""
     import torch
@@ -118,7 +119,7 @@ def fit(ctx, pk, n_train=12000, n_val=4000, k=16, target=0.99, seed=1):
     hist = train(net, X, ts)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    margin, r = tune_margin(ctx, net, pk, wv, k=k, target=target, rule=1)
+    margin, r = tune_margin(ctx, net, pk, wv, k=k, target=target, rule=1, k_fallback=k_fallback)
     del X, t, ts
     return net, margin, dict(rows=n_train * wt.params.n_orient, epochs=len(hist), seconds=secs,
                              final_loss=hist[-1], val_recall=r["recall"], val_fallback=r["fallback"])

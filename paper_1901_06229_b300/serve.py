@@ -57,17 +57,19 @@ class ScreenResult:
 
 
 class Screen:
-    """Continuous-batching screen of one pocket with a trained proposer.
+    """Continuous-batching screen of one pocket with a trained proposer (k restarts per
+    ligand, k_fallback -- all when None -- where the proposer's top-k spread falls back).
 
     Admission: a batch is admitted when a stream slot is free and gd_prepare_batch fits
     the context's device-memory budget; otherwise it waits for an in-flight batch to
     finish, and if nothing is in flight the batch size is halved."""
 
     def __init__(self, ctx, pocket, params, net, k=16, margin=1e30, rule=1, max_batch=512, max_inflight=4,
+                 k_fallback=None,
                  debug=False):
         import torch
         self.ctx, self.pk, self.params, self.net = ctx, pocket, params, net
-        self.k, self.margin, self.rule = k, margin, rule
+        self.k, self.margin, self.rule, self.k_fallback = k, margin, rule, k_fallback
         self.max_batch, self.debug = max_batch, debug
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
 
@@ -81,7 +83,7 @@ class Screen:
             y = torch.empty(rows, device="cuda")
             job.features(x_bf16=X, stream=stream)
             self.net.predict(X, y)
-            job.launch_proposed(y, self.k, self.margin, self.rule, stream)
+            job.launch_proposed(y, self.k, self.margin, self.rule, stream, k_fallback=self.k_fallback)
             job.download(stream)
         return job, X, y
 

@@ -77,6 +77,45 @@ def _topk_host(pred, k):
     return np.array(out)
 
 
+def test_bounded_fallback_searches_the_best_predicted_restarts(ctx):
+    """gd_job_launch_proposed_fb: ligands whose top-k spread exceeds the margin search
+    their k_fallback best-predicted restarts (ties to the smaller id), the others their k
+    best; each best pose is the best over exactly those restarts."""
+    import torch
+    w = synth.workload_batched(32)
+    L, O, k, kf = w.batch.n_ligands, w.params.n_orient, 16, 64
+    pk = ctx.load_pocket(w.pocket)
+    job = ctx.prepare_batch(pk, w.batch, w.params, debug=True)
+    job.launch()
+    job.download()
+    ex = job.fetch()
+    pred = np.random.default_rng(7).normal(size=(L, O)).astype(np.float32)
+    pred[:, 3] = pred[:, 200] = 9.0  # a planted tie: restart 3 ranks before 200
+    top_k = _topk_host(pred, k)
+    spread = pred[np.arange(L), top_k[:, 0]] - pred[np.arange(L), top_k[:, -1]]
+    margin = float(np.median(spread))  # about half of the ligands fall back
+    job.launch_proposed(torch.tensor(pred.ravel()).cuda(), k, margin, rule=1, k_fallback=kf)
+    job.download()
+    pr = job.fetch()
+    cnt, _ = job.selection()
+    fb = spread > margin
+    assert 0 < fb.sum() < L
+    np.testing.assert_array_equal(cnt, np.where(fb, kf, k))
+    top_f = _topk_host(pred, kf)
+    R = np.diff(w.batch.rot_off)
+    for i in range(L):
+        chosen = top_f[i] if fb[i] else top_k[i]
+        sc = ex["orient_score"][i, chosen].astype(np.int64)
+        assert pr["best_score"][i] == sc.max()
+        assert pr["best_orient"][i] == chosen[sc == sc.max()].min()
+        np.testing.assert_array_equal(pr["orient_score"][i, chosen], ex["orient_score"][i, chosen])
+        assert pr["evals"][i] == len(chosen) * R[i] * w.params.n_angles
+    with pytest.raises(gdk.GeoDockError, match="k_fallback"):
+        job.launch_proposed(torch.tensor(pred.ravel()).cuda(), k, margin, rule=1, k_fallback=k - 1)
+    job.free()
+    pk.free()
+
+
 def test_subset_search_is_the_best_of_the_chosen_restarts(ctx):
     import torch
     w = synth.workload_batched(24)
