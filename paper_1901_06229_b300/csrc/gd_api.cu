@@ -132,6 +132,7 @@ struct gd_ctx {
   size_t budget = 0;  // 0: unlimited
   size_t used = 0;    // device bytes currently held (cached blocks included)
   cudaStream_t capture_stream = nullptr;
+  std::mutex capture_mu;  // one graph capture at a time on capture_stream
   std::mutex mu;
   std::multimap<size_t, void*> dev_free;   // cached device blocks by size
   std::multimap<size_t, void*> host_free;  // cached pinned blocks by size
@@ -526,6 +527,7 @@ std::string signature(const gd_pocket* pk, const gd_search_params* p, int nmax, 
 // job.  A job's first launch goes to the stream directly (capturing and instantiating a
 // graph costs more host time than a single launch of a small job saves).
 gd_status build_graph(gd_ctx* c, gd_job* j) {
+  std::lock_guard<std::mutex> serial(c->capture_mu);  // host threads share the capture stream
   cudaStream_t s = c->capture_stream;
   GD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s);

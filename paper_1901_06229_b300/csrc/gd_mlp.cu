@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -496,16 +497,25 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
 // tensor-core CTA off its SM.)
 size_t gemm_smem_bytes() { return 128 * KC * 2 + 256 * KC * 2 + 16 + 32 * 1024; }
 
+// Dynamic shared-memory limit of a kernel, raised once per device (any host thread).
+cudaError_t smem_attr_once(const void* fn, size_t bytes, std::atomic<bool>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[dev].store(true, std::memory_order_release);
+  return e;
+}
+
 cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
                          const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
                          int num_sms, cudaStream_t st) {
-  static bool attr = false;
+  static std::atomic<bool> attr[64];
   const size_t smem = INF_W1 + INF_W2 + INF_H1 + INF_VEC + INF_BAR;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = smem_attr_once((const void*)mlp_infer_kernel, smem, attr);
+  if (e != cudaSuccess) return e;
   if (M <= 0) return cudaSuccess;
   const int tiles = (M + 127) / 128;
   mlp_infer_kernel<<<tiles < num_sms ? tiles : num_sms, INF_THREADS, smem, st>>>(X, M, W1b, W2b, b1, b2, w3r, b3, y,
@@ -514,13 +524,9 @@ cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b
 }
 
 cudaError_t gemm_launch(const GemmArgs& g, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gemm_smem_bytes());
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<bool> attr[64];
+  cudaError_t e = smem_attr_once((const void*)gemm_kernel, gemm_smem_bytes(), attr);
+  if (e != cudaSuccess) return e;
   dim3 grid((g.M + 127) / 128, (g.N + 255) / 256);
   gemm_kernel<<<grid, 128, gemm_smem_bytes(), st>>>(g);
   return cudaGetLastError();

@@ -104,3 +104,44 @@ def test_selected_ligands_pack_like_a_sub_batch(setup):
     empty = ctx.prepare_batch(pk, w.batch, w.params, sel=np.zeros(0, np.int64))
     assert empty.L == 0
     empty.free()
+
+
+def test_concurrent_jobs_on_one_context(setup):
+    """Host threads docking on one context at once (ctypes releases the GIL): packing on
+    the shared host pool, cached memory and per-job graphs give every job the result it
+    gets alone."""
+    import threading
+    import torch
+    ctx, pk, w, _, _ = setup
+    parts = [np.arange(i, w.batch.n_ligands, 4) for i in range(4)]
+    alone = []
+    for ids in parts:
+        job = ctx.prepare_batch(pk, w.batch, w.params, sel=ids)
+        job.launch()
+        job.download()
+        alone.append(job.fetch())
+        job.free()
+    got, errors = [None] * 4, []
+
+    def worker(t):
+        try:
+            s = torch.cuda.Stream()
+            for _ in range(3):  # prepare, launch, relaunch (graph), fetch
+                job = ctx.prepare_batch(pk, w.batch, w.params, sel=parts[t], stream=s)
+                job.launch(s)
+                job.launch(s)
+                job.download(s)
+                got[t] = job.fetch()
+                job.free()
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for t in range(4):
+        for key in ("best_score", "best_orient", "best_angle", "best_xyz"):
+            np.testing.assert_array_equal(got[t][key], alone[t][key], err_msg=f"{key} of part {t}")
