@@ -60,8 +60,8 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
-    "993fb87c6b7e0860": {("batched-4096lig-64grid", 14): 4565248 + 1304064,
-                         ("large-512lig-128grid", 9): 2799616 + 5632},
+    "abd01e1b241c1ff1": {("batched-4096lig-64grid", 14): 4576512 + 1309440,
+                         ("large-512lig-128grid", 9): 3059456 + 5376},
 }
 
 
@@ -70,8 +70,8 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
-    "993fb87c6b7e0860": {("batched-4096lig-64grid", 14): 8538068324,
-                         ("large-512lig-128grid", 9): 14730981071},
+    "abd01e1b241c1ff1": {("batched-4096lig-64grid", 14): 8538068346,
+                         ("large-512lig-128grid", 9): 14730981103},
 }
 ISSUE_PER_SM_CLK = 4
 
@@ -80,7 +80,7 @@ ISSUE_PER_SM_CLK = 4
 # a hash of its source like MEASURED_TRAFFIC.
 MLP_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_mlp.cu",)
 MEASURED_MLP_TRAFFIC = {
-    "707fb5b547da1113": {4194304: 402859264 + 16028672},
+    "0b6551ae97cb3c63": {4194304: 402875904 + 16060928},
 }
 
 
