@@ -105,3 +105,45 @@ def test_check_batch_excluded_pair_limit():
     l = _lig(bonds, [9])
     with pytest.raises(gdk.GeoDockError, match="excluded"):
         gdk.check_batch(synth.pack([l]), synth.SearchParams(min_bond_sep=8))
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "geodock.h"
+#include "geodock_mlp.h"
+
+int main(void) {
+  /* a 6-atom chain with its middle bond rotatable, coordinates 1.5 A apart */
+  int32_t atom_off[2] = {0, 6}, bond_off[2] = {0, 5}, rot_off[2] = {0, 1};
+  int32_t bonds[10] = {0, 1, 1, 2, 2, 3, 3, 4, 4, 5}, rot_bond[1] = {2};
+  float xyz[18];
+  for (int a = 0; a < 6; ++a) { xyz[3 * a] = 1.5f * a; xyz[3 * a + 1] = 0.3f * (a & 1); xyz[3 * a + 2] = 0.f; }
+  gd_ligand_batch b = {1, atom_off, xyz, bond_off, bonds, rot_off, rot_bond};
+  gd_search_params p = {4, 4, 4, 32, 2.0f, 3, 1, 0, 0, 0, 0.0f};
+  if (gd_check_batch(&b, &p) != GD_OK) { printf("rejected: %s\n", gd_last_error(NULL)); return 1; }
+  bonds[9] = 0; /* 4-0 instead of 4-5: a cycle */
+  if (gd_check_batch(&b, &p) != GD_EINVAL || strstr(gd_last_error(NULL), "tree") == NULL) return 2;
+  int warps = 0, slots = 0, regs = 0;
+  if (gd_tile_count() < 1 || gd_tile_info(1, &warps, &slots, &regs) != GD_OK || warps < 1) return 3;
+  printf("ok %d tiles\n", gd_tile_count());
+  return 0;
+}
+"""
+
+
+def test_headers_compile_as_c_and_link(tmp_path):
+    """The boundary is a C ABI: a C99 program includes both headers, links the library
+    and calls its host-only entry points (no device needed)."""
+    import subprocess
+    from paper_1901_06229_b300 import build
+    lib = build.build()
+    src = tmp_path / "use.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe), "-L", os.path.dirname(lib), "-lgeodock",
+                           f"-Wl,-rpath,{os.path.dirname(lib)}"])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
+    assert out.stdout.startswith("ok ")
