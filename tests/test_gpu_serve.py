@@ -9,7 +9,7 @@ from paper_1901_06229_b300 import mlp, serve, synth
 pytestmark = pytest.mark.gpu
 
 
-def _alone(ctx, pk, w, net, i, k, margin):
+def _alone(ctx, pk, w, net, i, k, margin, k_fallback=None):
     import torch
     b = w.batch.subset([i])
     job = ctx.prepare_batch(pk, b, w.params)
@@ -17,7 +17,7 @@ def _alone(ctx, pk, w, net, i, k, margin):
     y = torch.empty(w.params.n_orient, device="cuda")
     job.features(x_bf16=X)
     net.predict(X, y)
-    job.launch_proposed(y, k, margin, 1)
+    job.launch_proposed(y, k, margin, 1, k_fallback=k_fallback)
     job.download()
     out = job.fetch()
     job.free()
@@ -64,6 +64,19 @@ def test_results_are_the_same_alone_and_in_the_mix(setup):
     assert np.all(res.latency > 0)
     for i in np.random.default_rng(0).choice(w.batch.n_ligands, 40, replace=False):
         assert _alone(ctx, pk, w, net, int(i), 16, margin) == (int(res.best_score[i]), int(res.best_orient[i]))
+
+
+def test_bounded_fallback_in_the_mix(setup):
+    """The screen with a bounded fallback (ligands that fall back search their 64
+    best-predicted restarts) gives every ligand the result it gets alone."""
+    ctx, pk, w, net, margin = setup
+    arr = serve.poisson_arrivals(w.batch.n_ligands, 20000.0, seed=4)
+    scr = serve.Screen(ctx, pk, w.params, net, k=16, margin=margin, max_batch=64, max_inflight=3, k_fallback=64)
+    res = scr.run(w, arr)
+    assert set(np.unique(res.restarts)) == {16, 64}  # both pruned and fallback ligands
+    for i in np.random.default_rng(1).choice(w.batch.n_ligands, 40, replace=False):
+        got = (int(res.best_score[i]), int(res.best_orient[i]))
+        assert _alone(ctx, pk, w, net, int(i), 16, margin, k_fallback=64) == got
 
 
 def test_memory_budget_admission(setup):

@@ -77,6 +77,19 @@ MUTANTS = {
     "quaternion sign not fixed": (
         "if (q[0] < 0)", "if (q[0] > 0)",
         [feats.test_quaternion_matches_scipy]),
+    "farthest-point sampling keeps the largest distance": (
+        "mind[a] = s == 0 ? d : std::min(mind[a], d);", "mind[a] = s == 0 ? d : std::max(mind[a], d);",
+        [feats.test_farthest_point_order_on_a_line]),
+    "grid samples scaled by 1/256": (
+        "feat[23 + sidx] = cell_value(P, y) / 255.0;", "feat[23 + sidx] = cell_value(P, y) / 256.0;",
+        [feats.test_grid_samples_read_the_placed_pose]),
+    "quaternion from full angles": (
+        "const double qa[4] = {std::cos(al / 2), 0, 0, std::sin(al / 2)};",
+        "const double qa[4] = {std::cos(al), 0, 0, std::sin(al)};",
+        [feats.test_quaternion_matches_scipy]),
+    "size feature over 256 atoms": (
+        "feat[4] = n / 250.0;", "feat[4] = n / 256.0;",
+        [feats.test_size_gyration_histogram_on_hand_placed_atoms]),
     "gyration without the square root": (
         "feat[6] = std::sqrt(r2 / n) / 10.0;", "feat[6] = (r2 / n) / 10.0;",
         [feats.test_size_gyration_histogram_on_hand_placed_atoms]),
