@@ -60,8 +60,9 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
-    "abd01e1b241c1ff1": {("batched-4096lig-64grid", 14): 4576512 + 1309440,
-                         ("large-512lig-128grid", 9): 3059456 + 5376},
+    "56ba36595493e18b": {("batched-4096lig-64grid", 14): 4845312 + 1353984,
+                         ("batched-4096lig-64grid", 15): 4559104 + 1257216,
+                         ("large-512lig-128grid", 9): 3154944 + 6144},
 }
 
 
@@ -70,8 +71,9 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
-    "abd01e1b241c1ff1": {("batched-4096lig-64grid", 14): 8538068346,
-                         ("large-512lig-128grid", 9): 14730981103},
+    "56ba36595493e18b": {("batched-4096lig-64grid", 14): 8568626090,
+                         ("batched-4096lig-64grid", 15): 8568730816,
+                         ("large-512lig-128grid", 9): 14778610348},
 }
 ISSUE_PER_SM_CLK = 4
 

@@ -567,7 +567,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
     uint32_t* col = w.MASK + c;
     for (int seg = 0; seg < 2; ++seg) {
       const int ma = seg ? m1a : m0a, mb = seg ? m1b : m0b;
-#pragma unroll 4
+#pragma unroll 2
       for (int ai = ma; ai < mb; ++ai, col += nch) {
         const float2 ha = w.HR[ai];
         const float dh = __fsub_rn(ha.x, hb.x), dr = __fsub_rn(ha.y, hb.y);
