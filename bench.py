@@ -60,9 +60,9 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
-    "56ba36595493e18b": {("batched-4096lig-64grid", 14): 4845312 + 1353984,
-                         ("batched-4096lig-64grid", 15): 4559104 + 1257216,
-                         ("large-512lig-128grid", 9): 3154944 + 6144},
+    "d4fb57d5101b56b7": {("batched-4096lig-64grid", 14): 4557056 + 1316352,
+                         ("batched-4096lig-64grid", 15): 4765952 + 1353984,
+                         ("large-512lig-128grid", 9): 2984704 + 6400},
 }
 
 
@@ -71,9 +71,9 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
-    "56ba36595493e18b": {("batched-4096lig-64grid", 14): 8568626090,
-                         ("batched-4096lig-64grid", 15): 8568730816,
-                         ("large-512lig-128grid", 9): 14778610348},
+    "d4fb57d5101b56b7": {("batched-4096lig-64grid", 14): 8448360721,
+                         ("batched-4096lig-64grid", 15): 8448465530,
+                         ("large-512lig-128grid", 9): 14834383532},
 }
 ISSUE_PER_SM_CLK = 4
 

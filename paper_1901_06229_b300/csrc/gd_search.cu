@@ -168,6 +168,7 @@ __device__ void place(const SearchArgs& a, float4* X, int a0, int n, int o, int 
   const float r00 = __ldg(r + 0), r01 = __ldg(r + 1), r02 = __ldg(r + 2);
   const float r10 = __ldg(r + 3), r11 = __ldg(r + 4), r12 = __ldg(r + 5);
   const float r20 = __ldg(r + 6), r21 = __ldg(r + 7), r22 = __ldg(r + 8);
+#pragma unroll 2
   for (int i = lane; i < n; i += 32) {
     const float4 d = __ldg(a.xc + a0 + i);
     const float x = __fmaf_rn(r00, d.x, __fmaf_rn(r01, d.y, __fmul_rn(r02, d.z)));
@@ -264,6 +265,7 @@ __device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n,
   const float4 xp = X[rd.p];
   __syncwarp();
   const int f = frag_size(rd, n);
+#pragma unroll 2
   for (int i = lane; i < f; i += 32) {
     const int t = frag_atom(rd, i);
     const float4 v = X[t];
