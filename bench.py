@@ -86,6 +86,16 @@ MEASURED_MLP_TRAFFIC = {
 }
 
 
+def pipe_peaks(pipes: dict, achieved, loads, peak_tops: float, peak_loads: float) -> dict:
+    """The pipes' peaks as measured by gd_measure_peaks beside the nominal ones the
+    roofline divides by (lane FFMAs and lane shared-memory byte loads per second)."""
+    f, l = pipes["ffma_per_s"] / 1e12, pipes["lds_u8_per_s"] / 1e12
+    return {"ffma_T_per_s": f, "lds_u8_T_per_s": l, "ffma_of_nominal": f / peak_tops, "lds_u8_of_nominal": l / peak_loads,
+            "frac_fp32": achieved / f if achieved is not None else None,
+            "frac_loads": loads / l if loads is not None else None,
+            "how": "gd_measure_peaks: every SM full, best of 3 launches, run after the timed region"}
+
+
 def search_kernel_hash(sources=SEARCH_KERNEL_SOURCES) -> str:
     """Hash of a kernel's sources without // comments and blank lines (an edit of the
     documentation does not detach the measurements)."""
@@ -601,6 +611,7 @@ def main():
 
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = measured_peaks()
+    pipes = gdk.measure_peaks(torch.cuda.current_device())  # own microbenchmarks, after the timed region
     mhz = peaks.get("sm_max_mhz", 2032.0)
     peak_tops = sm_count * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
     peak_loads = sm_count * LOADS_PER_SM_CLK * mhz * 1e6 / 1e12
@@ -640,7 +651,9 @@ def main():
                                   "(sm_max_mhz of MEASURED_PEAKS.json)",
                      "work": "oracle count: 16 FP32 ops + 1 byte load per fragment atom, 7 ops per "
                              "early-exit pair test" if alg else None,
-                     **work, "executed": executed, "issue": issue},
+                     **work, "executed": executed, "issue": issue,
+                     "microbenchmark": pipe_peaks(pipes, achieved, alg["byte_loads"] / launch_s / 1e12 if alg else None,
+                                                  peak_tops, peak_loads)},
         "clocks": clocks,
         "wall_s_timed": wall,
     }

@@ -222,6 +222,16 @@ gd_status gd_autotune(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batc
                       const gd_search_params* params, int max_ligands, void* stream, int* best_tile,
                       float* best_ms);
 
+/* Peaks of the pipes that bound the search kernel, measured on `device` (made the
+ * calling thread's current device) by two microbenchmarks launched on `stream`
+ * (NULL: the legacy default stream): every SM full of 256-thread blocks, enough
+ * independent work per warp to hide latency, best of three timed launches, about 50 ms
+ * in all.  *ffma_per_s: FP32 fused multiply-adds per second, counted per lane (the unit
+ * of the search's algorithmic FP32 count); *lds_u8_per_s: shared-memory byte loads per
+ * second, counted per lane.  Either pointer may be NULL.  GD_ECUDA on a CUDA failure;
+ * no device memory stays allocated. */
+gd_status gd_measure_peaks(int device, void* stream, double* ffma_per_s, double* lds_u8_per_s);
+
 /* ---- Docking without allocation --------------------------------------------------
  * The paper has no counterpart: this serves callers that cannot allocate device memory
  * when they dock -- a process whose device memory is already fully reserved by

@@ -19,6 +19,7 @@
 #include "geodock.h"
 #include "geodock_mlp.h"
 #include "gd_internal.h"
+#include "gd_peak.h"
 
 // The search kernel packs atom ids into bytes (near pairs, the reach filter's column
 // lists, which share the 512-byte coefficient buffer of a warp).
@@ -991,6 +992,12 @@ gd_status gd_tile_info(int tile, int* warps, int* slots, int* max_regs) {
   if (warps) *warps = t.warps;
   if (slots) *slots = t.slots;
   if (max_regs) *max_regs = gd::tile_max_regs(t);
+  return GD_OK;
+}
+
+gd_status gd_measure_peaks(int device, void* stream, double* ffma_per_s, double* lds_u8_per_s) {
+  GD_CUDA(cudaSetDevice(device));
+  GD_CUDA(gd::measure_peaks(static_cast<cudaStream_t>(stream), ffma_per_s, lds_u8_per_s));
   return GD_OK;
 }
 

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: 
 EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_free_pocket",
            "gd_dock_batch", "gd_fetch_results", "gd_job_launch", "gd_job_download", "gd_job_bytes", "gd_job_free",
            "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc",
-           "gd_prepare_batch", "gd_prepare_batch_sel"]
+           "gd_prepare_batch", "gd_prepare_batch_sel", "gd_measure_peaks"]
 
 
 class GeoDockError(RuntimeError):
@@ -387,6 +387,16 @@ def tile_info(tile: int):
     if st:
         raise GeoDockError(st, load().gd_last_error(None).decode())
     return w.value, s.value, r.value
+
+
+def measure_peaks(device: int = 0, stream=None) -> dict:
+    """Measured peaks of the search kernel's pipes on one device (gd_measure_peaks):
+    FP32 FMAs per second and shared-memory byte loads per second, both per lane."""
+    f, l = C.c_double(), C.c_double()
+    st = load().gd_measure_peaks(int(device), _stream_handle(stream), C.byref(f), C.byref(l))
+    if st:
+        raise GeoDockError(st, load().gd_last_error(None).decode())
+    return {"ffma_per_s": f.value, "lds_u8_per_s": l.value}
 
 
 def dock(batch, pocket, params, device=0, debug=False, bumps=False, tile=0, stream=None) -> dict:
