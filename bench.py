@@ -47,6 +47,12 @@ METRIC = "ligands/s (pose search, 1 B300)"
 # best-predicted restarts (the fewest that still reach 99 % best-pose recall on held-out
 # streaming ligands; 32 or 64 cannot)
 K_FALLBACK = 128
+# Best-pose recall the learned path must keep, and the recall its fallback margin is
+# tuned for on the 4,000-ligand validation split: the two splits' recalls differ by
+# sampling alone with a spread of about 0.18 % (binomial, 4,000 and 16,384 ligands at
+# 99 %), so tuning 0.3 % above the target keeps the held-out recall above it.
+RECALL_TARGET = 0.99
+VAL_RECALL_TARGET = 0.993
 # FP32 operations the kernel executes (the "executed" roofline figure)
 EXEC_OPS_PER_PAIR = 3        # 2 FFMA (|x_a - x_b|^2 + (cos-1) P + sin Q) + FMNMX
 EXEC_OPS_PER_ATOM_MOVE = 6   # turn about the bond axis (6 FFMA; coordinates are grid units)
@@ -282,8 +288,8 @@ def run_learned(args, world, rank, local):
     """Learned-pruned search vs the plain exhaustive search on the same held-out ligands.
 
     Training: 12,000 streaming-screen ligands (lognormal sizes) x 256 restarts, targets
-    from the plain search; margin tuned for 99 % best-pose recall on 4,000 more; timed on
-    16,384 held-out ligands.  A learned step = features + network + selection + pruned
+    from the plain search; margin tuned for 99.3 % best-pose recall on 4,000 more, so that
+    the 16,384 held-out ligands it is timed on keep at least 99 %.  A learned step = features + network + selection + pruned
     search; a plain step = the exhaustive search.  Both device-timed with CUDA events.
     """
     import torch
@@ -310,7 +316,7 @@ def run_learned(args, world, rank, local):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     k = 16
-    margin, _ = proposer.tune_margin(ctx, net, pk, wv, k=k, rule=1, k_fallback=K_FALLBACK)
+    margin, _ = proposer.tune_margin(ctx, net, pk, wv, k=k, target=VAL_RECALL_TARGET, rule=1, k_fallback=K_FALLBACK)
     L, O = we.batch.n_ligands, we.params.n_orient
     stream = torch.cuda.current_stream()
     job = ctx.prepare_batch(pk, we.batch, we.params, stream=stream, tile=args.tile)
@@ -384,7 +390,8 @@ def run_learned(args, world, rank, local):
             "train": {"ligands": wt.batch.n_ligands, "rows": int(X.shape[0]), "epochs": len(hist), "seconds": train_s,
                       "final_loss_std_units": hist[-1]}},
         "plain_value": plain_v, "speedup_vs_plain": value / plain_v,
-        "best_pose_recall": recall, "score_regret": regret, "fallback_fraction": float(np.mean(cnt > k)),
+        "best_pose_recall": recall, "recall_target": RECALL_TARGET, "validation_recall_target": VAL_RECALL_TARGET,
+        "score_regret": regret, "fallback_fraction": float(np.mean(cnt > k)),
         "restarts_searched_per_ligand": float(cnt.mean()),
         "gpu_launches": args.steps * 8,  # pose setup + features, MLP, 3 selection kernels, pose setup + search
         "roofline": {"bound": "tensor", "kernel": "mlp_infer_kernel (fused two-layer forward, 1 launch)",
