@@ -474,7 +474,7 @@ def run_stream(args, world, rank, local):
     ctx = gdk.Context(dev, mem_budget_bytes=8 << 30)
     w = synth.workload_stream(n, seed_offset=53 + 10 * rank)
     pk = ctx.load_pocket(w.pocket)
-    net, margin, info = proposer.fit(ctx, pk, k_fallback=K_FALLBACK)
+    net, margin, info = proposer.fit(ctx, pk, target=VAL_RECALL_TARGET, k_fallback=K_FALLBACK)
     scr = serve.Screen(ctx, pk, w.params, net, k=16, margin=margin, max_batch=args.max_batch, max_inflight=4,
                        k_fallback=K_FALLBACK)
     # warm-up on the first ligands
