@@ -10,7 +10,8 @@ persistent fused search kernel.
           search; the L2 is flushed between steps, outside the timed events)
   e2e   : the same metric through gd_dock_batch + gd_fetch_results with host buffers:
           validation/packing, the host->device copy, the search and the copy of the
-          results back are all inside the timed region
+          results back are all inside the timed region (at least 20 batches, two in
+          flight)
   roofline : FP32-pipe bound of the search kernel.  The algorithmic work of a launch is
              counted by the oracle over the whole workload (table beside it): per
              candidate 16 FP32 operations and one grid byte load per fragment atom, and
@@ -581,7 +582,10 @@ def main():
     clocks = clk.summary()
 
     # ---- e2e: host buffers through the public API --------------------------------------------
-    e2e_steps = args.e2e_steps or args.steps
+    # at least 20 batches: the first batch's packing and copy, before any search runs, and
+    # the last one's result copy are paid once per run, not per batch (the line records
+    # the count it used)
+    e2e_steps = args.e2e_steps or max(args.steps, 20)
     for _ in range(2):  # warm the context's memory caches
         j = ctx.dock_batch(pk, w.batch, w.params, stream=stream, tile=tile)
         j.fetch()
