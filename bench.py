@@ -586,16 +586,17 @@ def main():
     # the last one's result copy are paid once per run, not per batch (the line records
     # the count it used)
     e2e_steps = args.e2e_steps or max(args.steps, 20)
-    for _ in range(2):  # warm the context's memory caches
-        j = ctx.dock_batch(pk, w.batch, w.params, stream=stream, tile=tile)
-        j.fetch()
-        j.free()
-    barrier(world)
-    torch.cuda.synchronize()
     # gd_dock_batch returns once the work is queued, so a streaming caller packs and
     # submits batch k+1 while batch k runs; two jobs are in flight, on two streams, so one
     # job's copies run on the copy engines while the other's search runs
     streams = [stream, torch.cuda.Stream()]
+    for _ in range(2):  # warm the context's memory caches with two jobs alive at once
+        warm = [ctx.dock_batch(pk, w.batch, w.params, stream=s, tile=tile) for s in streams]
+        for j in warm:
+            j.fetch()
+            j.free()
+    barrier(world)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     inflight = []
     for step in range(e2e_steps):
