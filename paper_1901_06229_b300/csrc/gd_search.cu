@@ -661,7 +661,8 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
       }
       __syncwarp();
       const int cnt = n_near - e0 < 32 ? n_near - e0 : 32;
-#pragma unroll 4
+      // unrolled by 8 with four angles per lane, by 4 with fewer (measured best for each)
+#pragma unroll(S >= 4 ? 8 : 4)
       for (int t = 0; t < cnt; ++t) {
         const float4 k = w.PC[t];
 #pragma unroll
