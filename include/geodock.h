@@ -251,7 +251,10 @@ gd_status gd_measure_peaks(int device, void* stream, double* ffma_per_s, double*
  * The call is synchronous on `stream` (results are in `out` on return).
  * Limits: a batch whose grid, inputs, results and scratch need more than
  * GD_NOALLOC_MAX_BYTES is rejected with GD_EINVAL (about 20*L*O + 2*O*reps*Rt +
- * 300*Rt + 48*N + 64*L bytes plus the cropped grid); all other limits as gd_dock_batch.
+ * 300*Rt + 48*N + 64*L bytes plus the cropped grid); tile -1 (autotuned) is rejected,
+ * since there is no context to keep an autotuned choice (0 = the built-in default, or a
+ * tile id); rigid_span must be 0.  Ligands and parameters are validated by the same code
+ * as gd_dock_batch and gd_check_batch, with the same messages.
  * Set-up: the first call on a device (the current device) looks up the array's device
  * address with cudaGetSymbolAddress; make that first call before any stream capture.
  * Concurrency: every call shares the one array and its contents persist between calls

@@ -20,6 +20,7 @@
 
 #include "geodock.h"
 #include "gd_internal.h"
+#include "gd_pack.h"
 
 using gd::RotDesc;
 
@@ -53,136 +54,6 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
                        const gd_ligand_batch* b, const gd_search_params* p, gd_result_batch* out, void* stream);
 
 size_t a256(size_t v) { return (v + 255) / 256 * 256; }
-
-// Validate ligand li and write its preorder atoms, permutation, rotamer descriptors and
-// excluded pairs; every temporary lives in fixed-size arrays.
-gd_status pack_one(int li, int n, const float* xyz, int nb, const int32_t* bonds, int R,
-                   const int32_t* rot_bond, int min_sep, float4* out_xyz, uint8_t* out_perm,
-                   RotDesc* out_rots, uint16_t* excl, size_t excl_cap, size_t* n_excl) {
-  constexpr int NM = GD_MAX_ATOMS;
-  if (n < 2 || n > NM) return nfail(GD_EINVAL, "ligand %d: %d atoms outside [2, %d]", li, n, NM);
-  if (nb != n - 1) return nfail(GD_EINVAL, "ligand %d: %d bonds for %d atoms (not a tree)", li, nb, n);
-  if (R < 0 || R > GD_MAX_ROTAMERS) return nfail(GD_EINVAL, "ligand %d: %d rotamers > %d", li, R, GD_MAX_ROTAMERS);
-  for (int i = 0; i < 3 * n; ++i)
-    if (!std::isfinite(xyz[i])) return nfail(GD_EINVAL, "ligand %d: non-finite coordinate", li);
-  int deg[NM], adj_off[NM + 1], adj[2 * NM], fill[NM];
-  for (int i = 0; i < n; ++i) deg[i] = 0;
-  for (int b = 0; b < nb; ++b) {
-    const int u = bonds[2 * b], v = bonds[2 * b + 1];
-    if (u < 0 || v < 0 || u >= n || v >= n || u == v) return nfail(GD_EINVAL, "ligand %d: bad bond %d", li, b);
-    deg[u]++;
-    deg[v]++;
-  }
-  adj_off[0] = 0;
-  for (int i = 0; i < n; ++i) adj_off[i + 1] = adj_off[i] + deg[i];
-  for (int i = 0; i < n; ++i) fill[i] = adj_off[i];
-  for (int b = 0; b < nb; ++b) {
-    const int u = bonds[2 * b], v = bonds[2 * b + 1];
-    adj[fill[u]++] = v;
-    adj[fill[v]++] = u;
-  }
-  // DFS preorder from atom 0 (same child order as gd_dock_batch)
-  int parent[NM], pre[NM], order[NM], stack[NM], size[NM];
-  for (int i = 0; i < n; ++i) pre[i] = -1;
-  int sp = 0, cnt = 0;
-  stack[sp++] = 0;
-  parent[0] = -1;
-  while (sp) {
-    const int v = stack[--sp];
-    if (pre[v] >= 0) return nfail(GD_EINVAL, "ligand %d: bonds contain a cycle (not a tree)", li);
-    pre[v] = cnt;
-    order[cnt++] = v;
-    for (int e = adj_off[v + 1] - 1; e >= adj_off[v]; --e) {
-      const int w = adj[e];
-      if (w == parent[v]) continue;
-      if (pre[w] >= 0 || sp >= NM) return nfail(GD_EINVAL, "ligand %d: bonds contain a cycle (not a tree)", li);
-      parent[w] = v;
-      stack[sp++] = w;
-    }
-  }
-  if (cnt != n) return nfail(GD_EINVAL, "ligand %d: bond graph is not connected", li);
-  for (int i = 0; i < n; ++i) size[i] = 1;
-  for (int t = n - 1; t > 0; --t) size[parent[order[t]]] += size[order[t]];
-  for (int t = 0; t < n; ++t) {
-    const int v = order[t];
-    out_xyz[t] = make_float4(xyz[3 * v], xyz[3 * v + 1], xyz[3 * v + 2], 0.f);
-    out_perm[t] = (uint8_t)v;
-  }
-  int depth[NM], queue[NM], near_m[NM], near_s[NM];
-  int nm_cnt, ns_cnt;
-  uint16_t ex[GD_MAX_EXCLUDED];
-  for (int r = 0; r < R; ++r) {
-    const int b = rot_bond[r];
-    if (b < 0 || b >= nb) return nfail(GD_EINVAL, "ligand %d: rotamer %d names bond %d of %d", li, r, b, nb);
-    const int u = bonds[2 * b], v = bonds[2 * b + 1];
-    const int child = parent[v] == u ? v : u;
-    const int sub = size[child], rest = n - sub;
-    if (sub == 1 || rest == 1) return nfail(GD_EINVAL, "ligand %d: rotamer %d is on a terminal bond", li, r);
-    RotDesc d{};
-    d.comp = sub > rest ? 1 : 0;
-    const int q = d.comp ? parent[child] : child;
-    const int p = d.comp ? child : parent[child];
-    d.p = (uint16_t)pre[p];
-    d.q = (uint16_t)pre[q];
-    d.lo = (uint16_t)pre[child];
-    d.hi = (uint16_t)(pre[child] + sub);
-    auto moving = [&](int atom) {
-      const bool in = pre[atom] >= d.lo && pre[atom] < d.hi;
-      return d.comp ? !in : in;
-    };
-    for (int i = 0; i < n; ++i) depth[i] = -1;
-    nm_cnt = ns_cnt = 0;
-    for (int side = 0; side < 2; ++side) {
-      const int root = side ? p : q;
-      int head = 0, tail = 0;
-      queue[tail++] = root;
-      depth[root] = 0;
-      while (head < tail) {
-        const int a = queue[head++];
-        if (side) near_s[ns_cnt++] = a;
-        else near_m[nm_cnt++] = a;
-        if (depth[a] >= min_sep - 2) continue;
-        for (int e = adj_off[a]; e < adj_off[a + 1]; ++e) {
-          const int w = adj[e];
-          if (depth[w] >= 0 || moving(w) != (side == 0)) continue;
-          depth[w] = depth[a] + 1;
-          queue[tail++] = w;
-        }
-      }
-    }
-    int ne = 0;
-    for (int i = 0; i < nm_cnt; ++i)
-      for (int k = 0; k < ns_cnt; ++k)
-        if (depth[near_m[i]] + depth[near_s[k]] + 1 < min_sep) {
-          if (ne >= GD_MAX_EXCLUDED)
-            return nfail(GD_EINVAL, "ligand %d: rotamer %d has more than %d excluded pairs", li, r, GD_MAX_EXCLUDED);
-          ex[ne++] = (uint16_t)(pre[near_m[i]] | (pre[near_s[k]] << 8));
-        }
-    // sort by (moving atom, static atom): insertion sort on (a, b)
-    for (int i = 1; i < ne; ++i) {
-      const uint16_t key = ex[i];
-      const int ka = key & 0xFF, kb = key >> 8;
-      int j = i - 1;
-      while (j >= 0 && ((ex[j] & 0xFF) > ka || ((ex[j] & 0xFF) == ka && (ex[j] >> 8) > kb))) {
-        ex[j + 1] = ex[j];
-        --j;
-      }
-      ex[j + 1] = key;
-    }
-    for (int i = 0, run = 0; i < ne; ++i) {
-      run = (i && (ex[i] & 0xFF) == (ex[i - 1] & 0xFF)) ? run + 1 : 1;
-      if (run > GD_MAX_EXCLUDED_ATOM)
-        return nfail(GD_EINVAL, "ligand %d: rotamer %d has more than %d excluded pairs on one atom", li, r,
-                     GD_MAX_EXCLUDED_ATOM);
-    }
-    if (*n_excl + ne > excl_cap) return nfail(GD_EINVAL, "excluded-pair table full");
-    d.n_excl = (uint8_t)ne;
-    d.excl_off = (uint32_t)*n_excl;
-    for (int i = 0; i < ne; ++i) excl[(*n_excl)++] = ex[i];
-    out_rots[r] = d;
-  }
-  return GD_OK;
-}
 
 // Device address of g_dev on the current device (taken once per device).
 gd_status setup_device(int dev, unsigned char** base, int* sms) {
@@ -224,19 +95,16 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1ll << 31))
     return nfail(GD_EINVAL, "grid dims %d x %d x %d", nx, ny, nz);
   if (!(spacing > 0.f) || !std::isfinite(spacing)) return nfail(GD_EINVAL, "spacing must be > 0");
-  if (p->n_alpha < 1 || p->n_beta < 1 || p->n_gamma < 1 ||
-      (long long)p->n_alpha * p->n_beta * p->n_gamma > GD_MAX_ORIENT)
-    return nfail(GD_EINVAL, "bad Euler grid");
-  if (p->n_angles < 1 || p->n_angles > GD_MAX_ANGLES) return nfail(GD_EINVAL, "n_angles out of range");
-  if (!(p->bump_dist > 0.f) || !std::isfinite(p->bump_dist)) return nfail(GD_EINVAL, "bump_dist must be > 0");
-  if (p->min_bond_sep < 1 || p->min_bond_sep > 8) return nfail(GD_EINVAL, "min_bond_sep outside [1, 8]");
-  if (p->repetitions < 1 || p->repetitions > GD_MAX_REPS) return nfail(GD_EINVAL, "repetitions out of range");
+  {
+    const gd_status st = gd::check_params_fixed(nfail, p);
+    if (st) return st;
+  }
   if (p->flags & (GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS))
     return nfail(GD_EINVAL, "debug outputs are not available without allocation");
   if (p->flags & GD_FLAG_TEST_STAGE_TIMEOUT) return nfail(GD_EINVAL, "test flags are not accepted here");
   if (out->orient_score || out->orient_pick || out->bump_bits)
     return nfail(GD_EINVAL, "debug outputs are not available without allocation");
-  if (p->tile < -1 || p->tile > gd::tile_count()) return nfail(GD_EINVAL, "tile out of range");
+  if (p->tile == -1) return nfail(GD_EINVAL, "tile -1 (autotuned) needs a context; pass 0 (default) or a tile id");
   if (p->rigid_span != 0) return nfail(GD_EINVAL, "the rigid alignment sweep is not available without allocation");
   const int L = b->n_ligands;
   if (L < 0) return nfail(GD_EINVAL, "n_ligands < 0");
@@ -315,9 +183,10 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
     const int a0 = b->atom_off[i], n = b->atom_off[i + 1] - a0;
     const int b0 = b->bond_off[i], nb = b->bond_off[i + 1] - b0;
     const int r0 = b->rot_off[i], R = b->rot_off[i + 1] - r0;
-    gd_status st = pack_one(i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R, b->rot_bond + r0,
-                            p->min_bond_sep, (float4*)(h + o_xyz) + a0, h + o_perm + a0, (RotDesc*)(h + o_rots) + r0,
-                            (uint16_t*)(h + o_excl), (size_t)Rt * GD_MAX_EXCLUDED, &n_excl);
+    gd_status st = gd::pack_ligand_fixed(nfail, i, n, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R,
+                                         b->rot_bond + r0, p->min_bond_sep, (float4*)(h + o_xyz) + a0,
+                                         h + o_perm + a0, (RotDesc*)(h + o_rots) + r0, (uint16_t*)(h + o_excl),
+                                         (size_t)Rt * GD_MAX_EXCLUDED, &n_excl, nullptr);
     if (st) return st;
     if (R * reps > 32767) return nfail(GD_EINVAL, "ligand %d: too many steps", i);
     if (n > nmax) nmax = n;

@@ -107,6 +107,44 @@ def test_check_batch_excluded_pair_limit():
         gdk.check_batch(synth.pack([l]), synth.SearchParams(min_bond_sep=8))
 
 
+def _reason(fn):
+    with pytest.raises(gdk.GeoDockError) as e:
+        fn()
+    return e.value.status, str(e.value)
+
+
+_BAD_LIGANDS = [lambda: _lig([[0, 1], [1, 2], [2, 0]], [], n=4), lambda: _lig([[0, 1], [2, 3], [1, 0]], [], n=4),
+                lambda: _lig(CHAIN, [0]), lambda: _lig(CHAIN, [7]), lambda: _lig([[0, 7]], [], n=2),
+                lambda: _lig([[0, 0]], [], n=2), lambda: _lig([[i, i + 1] for i in range(256)], [])]
+
+
+def test_noalloc_rejects_what_check_batch_rejects_with_the_same_reason():
+    """gd_dock_batch_noalloc validates ligands and parameters with the packer and checks
+    gd_dock_batch uses, before it touches a device: the same status and message."""
+    pocket = synth.workload_single().pocket
+    ok = _lig(CHAIN, [2])
+    cases = [(synth.pack([mk()]), synth.SearchParams()) for mk in _BAD_LIGANDS]
+    nan = _lig(CHAIN, [2])
+    nan.xyz[3, 1] = np.nan
+    cases.append((synth.pack([ok, nan]), synth.SearchParams()))
+    bonds = [[i, i + 1] for i in range(20)] + [[i, 21 + i] for i in range(20)] + [[i, 41 + i] for i in range(20)]
+    cases.append((synth.pack([_lig(bonds, [9])]), synth.SearchParams(min_bond_sep=8)))  # excluded-pair limit
+    for bad in (synth.SearchParams(0, 4, 4), synth.SearchParams(n_angles=0), synth.SearchParams(n_angles=2000),
+                synth.SearchParams(bump_dist=-1.0), synth.SearchParams(repetitions=0),
+                synth.SearchParams(min_bond_sep=0), synth.SearchParams(300, 300, 1)):
+        cases.append((synth.pack([ok]), bad))
+    for batch, params in cases:
+        a = _reason(lambda: gdk.check_batch(batch, params))
+        b = _reason(lambda: gdk.dock_noalloc(batch, pocket, params))
+        assert a[0] == gdk.GD_EINVAL and a == b, (a, b)
+
+
+def test_noalloc_rejects_the_autotuned_tile():
+    w = synth.workload_single()
+    st, msg = _reason(lambda: gdk.dock_noalloc(w.batch, w.pocket, w.params, tile=-1))
+    assert st == gdk.GD_EINVAL and "context" in msg
+
+
 C_PROGRAM = r"""
 #include <stdio.h>
 #include <string.h>
