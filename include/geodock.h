@@ -199,6 +199,13 @@ gd_status gd_job_download(gd_ctx* ctx, gd_job* job, void* stream);
 /* Bytes one gd_dock_batch of this job moves host->device (packed inputs) and
  * device->host (results, plus debug arrays when requested). */
 gd_status gd_job_bytes(gd_ctx* ctx, const gd_job* job, uint64_t* h2d_bytes, uint64_t* d2h_bytes);
+/* Launch shape of a job's search (the persistent launch of a3-a10): the tile it runs,
+ * whether its kernel stages the pocket grid in shared memory (1: a bulk async copy per
+ * block) or reads it through the texture / L1 path (0), and the blocks, threads per
+ * block and dynamic shared memory per block of the launch (blocks = 0 for an empty
+ * batch).  Any output pointer may be NULL. */
+gd_status gd_job_info(gd_ctx* ctx, const gd_job* job, int* tile, int* grid_in_smem, int* blocks, int* threads,
+                      size_t* smem_bytes);
 /* Wait for the job's queued work and release it. */
 gd_status gd_job_free(gd_ctx* ctx, gd_job* job);
 

@@ -174,7 +174,8 @@ def features(xyz, n_rot: int, o: int, params, pocket, eps: float = EPS) -> dict:
 # ------------------------------------------------------------------ whole search
 
 def dock_pose(lig, pocket, params, o: int, debug: bool = False, eps: float = EPS) -> dict:
-    """One restart ``o`` of one ligand: picks, score (+ eps interval), first fragile step, coords."""
+    """One restart ``o`` of one ligand: picks, score (+ eps interval), first fragile step, coords,
+    step_fragile (1 where a step's pick is fragile; bit 2 of step 0: the rigid choice)."""
     n, R = len(lig.xyz), len(lig.rot_bond)
     reps, A = params.repetitions, params.n_angles
     x = np.ascontiguousarray(lig.xyz, np.float32)
@@ -187,6 +188,7 @@ def dock_pose(lig, pocket, params, o: int, debug: bool = False, eps: float = EPS
     picks = np.zeros(reps * R, np.int16)
     slhf = np.zeros(5, np.int32)
     xyz = np.zeros((n, 3))
+    sfrag = np.zeros(reps * R, np.uint8)
     bump = np.zeros(reps * R * A, np.uint8) if debug else None
     cand = np.zeros(reps * R * A, np.int32) if debug else None
     nul = lambda ct: C.cast(None, C.POINTER(ct))
@@ -195,11 +197,11 @@ def dock_pose(lig, pocket, params, o: int, debug: bool = False, eps: float = EPS
                              C.byref(prm), C.c_double(eps), int(o), _p(picks, C.c_int16),
                              _p(bump, C.c_uint8) if debug else nul(C.c_uint8),
                              _p(cand, C.c_int32) if debug else nul(C.c_int32),
-                             _p(slhf, C.c_int32), _p(xyz, C.c_double))
+                             _p(slhf, C.c_int32), _p(xyz, C.c_double), _p(sfrag, C.c_uint8))
     if rc:
         raise ValueError(lib().orc_last_error().decode())
     out = dict(picks=picks, score=int(slhf[0]), score_lo=int(slhf[1]), score_hi=int(slhf[2]),
-               fragile=int(slhf[3]), rigid=int(slhf[4]), xyz=xyz)
+               fragile=int(slhf[3]), rigid=int(slhf[4]), xyz=xyz, step_fragile=sfrag)
     if debug:
         out["bump"], out["cand_score"] = bump, cand
     return out
@@ -209,7 +211,9 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
     """Run the search over a CSR ligand batch; returns per-ligand / per-orientation arrays.
 
     Keys: orient_score/_lo/_hi [L, O], orient_pick [sum R * O * reps] (ligand-major,
-    then orientation, then rep*R + r), orient_fragile [L, O], best_xyz [N, 3],
+    then orientation, then rep*R + r), orient_fragile [L, O] (first fragile step, -1 none),
+    orient_step_fragile (laid out as orient_pick: 1 where that step's pick is fragile, bit 2
+    of a restart's step 0 when its rigid choice is), best_xyz [N, 3],
     best_orient/best_score/best_robust [L], pair_tests_full/evals [L], pair_tests_early [L]
     (pair tests when every candidate stops at its first bumping pair, moving atom
     ascending then static atom ascending, charged in whole 32-pair tiles); with ``debug``
@@ -230,7 +234,8 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
         best_orient=np.zeros(L, np.int32), best_score=np.zeros(L, np.int32),
         best_robust=np.zeros(L, np.int32), pair_tests_full=np.zeros(L, np.int64),
         evals=np.zeros(L, np.int64), status=np.zeros(L, np.int32), cand_off=cand_off,
-        orient_rigid=np.zeros((L, O), np.int16), pair_tests_early=np.zeros(L, np.int64))
+        orient_rigid=np.zeros((L, O), np.int16), pair_tests_early=np.zeros(L, np.int64),
+        orient_step_fragile=np.zeros(int(R.sum()) * O * reps, np.uint8))
     if debug:
         out["bump"] = np.zeros(int(cand_off[-1]), np.uint8)
         out["cand_score"] = np.zeros(int(cand_off[-1]), np.int32)
@@ -257,7 +262,8 @@ def dock_batch(batch, pocket, params, n_threads: int = 1, debug: bool = False, e
         _p(cand_off, C.c_int64), _p(out["best_xyz"], C.c_double), _p(out["best_orient"], C.c_int32),
         _p(out["best_score"], C.c_int32), _p(out["best_robust"], C.c_int32),
         _p(out["pair_tests_full"], C.c_int64), _p(out["evals"], C.c_int64), _p(out["status"], C.c_int32),
-        _p(out["orient_rigid"], C.c_int16), _p(out["pair_tests_early"], C.c_int64))
+        _p(out["orient_rigid"], C.c_int16), _p(out["pair_tests_early"], C.c_int64),
+        _p(out["orient_step_fragile"], C.c_uint8))
     if rc:
         raise ValueError("oracle rejected a ligand: " + lib().orc_last_error().decode())
     return out

@@ -291,6 +291,8 @@ struct LigandOut {
   int16_t* orient_pick;        // [O * reps * R]
   int16_t* orient_rigid;       // optional [O] rigid-sweep choice per restart
   int32_t* orient_fragile;     // [O] first fragile step (rep*R + r) or -1
+  uint8_t* step_fragile;       // optional [O * reps * R]: 1 where the step's pick is fragile
+                               // (step 0 also has bit 2 when the rigid choice is)
   uint8_t* bump;               // optional [O * reps * R * A]: 0 free, 1 bumped, 2 uncertain
   int32_t* cand_score;         // optional [O * reps * R * A] exact candidate score (-1 if bumped)
   double* best_xyz;            // [n*3]
@@ -337,7 +339,7 @@ bool prepare(const float* xyz_in, int n, const int32_t* bonds, int nb, const int
 void search_restart(const Prepared& L, const Pocket& P, const Params& prm, double eps, int o, int16_t* picks,
                     uint8_t* bump, int32_t* cand_score, int* score_out, int* lo_out, int* hi_out,
                     int* fragile_out, std::vector<V3>& x, int16_t* rigid_out = nullptr,
-                    int64_t* early_pairs = nullptr) {
+                    int64_t* early_pairs = nullptr, uint8_t* step_fragile = nullptr) {
   int16_t rigid_dummy = 0;
   (void)rigid_dummy;
   const double pi = 3.14159265358979323846;
@@ -346,6 +348,7 @@ void search_restart(const Prepared& L, const Pocket& P, const Params& prm, doubl
   x.resize(n);
   for (int a = 0; a < n; ++a) x[a] = L.c_pocket + mul(Ro, L.x0[a] - L.c_lig);
   int fragile_step = -1;
+  bool rigid_fragile = false;
   if (rigid_out) *rigid_out = 0;
   if (prm.rigid_span > 0) {  // align_ligand: best rigid rotation about the pocket centre
     const int W = 2 * prm.rigid_span + 1, M = W * W * W;
@@ -370,8 +373,9 @@ void search_restart(const Prepared& L, const Pocket& P, const Params& prm, doubl
       if (sc[m] > sc[best]) best = m;
     for (int m = 0; m < M; ++m) {  // can an eps move change the choice?
       if (m == best) continue;
-      if ((m < best && !(hi[m] < lo[best])) || (m > best && !(hi[m] <= lo[best]))) fragile_step = 0;
+      if ((m < best && !(hi[m] < lo[best])) || (m > best && !(hi[m] <= lo[best]))) rigid_fragile = true;
     }
+    if (rigid_fragile) fragile_step = 0;
     const M3 Rb = rigid_candidate(best, prm.rigid_span, prm.rigid_step);
     for (int a = 0; a < n; ++a) x[a] = L.c_pocket + mul(Rb, x[a] - L.c_pocket);
     if (rigid_out) *rigid_out = best;
@@ -419,8 +423,11 @@ void search_restart(const Prepared& L, const Pocket& P, const Params& prm, doubl
       for (int k = 0; k < A; ++k)
         if (!bumped[k] && (kstar < 0 || score[k] > score[kstar])) kstar = k;
       picks[step] = (int16_t)kstar;
-      // Can an eps perturbation change the pick?
-      if (fragile_step < 0) {  // (0 marks a fragile rigid choice: nothing after it compares)
+      // Can an eps perturbation change the pick?  fragile_step keeps the first such step
+      // (0 also marks a fragile rigid choice); step_fragile, when asked for, flags every
+      // such step along this trajectory, so that an implementation which made the same
+      // picks so far can still be compared after a fragile step.
+      if (fragile_step < 0 || step_fragile) {
         bool robust;
         if (kstar < 0) {  // every candidate bumped: robust only if every bump is sure
           robust = true;
@@ -434,7 +441,8 @@ void search_restart(const Prepared& L, const Pocket& P, const Params& prm, doubl
             if (k > kstar && !(hi[k] <= lo[kstar])) robust = false;
           }
         }
-        if (!robust) fragile_step = step;
+        if (!robust && fragile_step < 0) fragile_step = step;
+        if (step_fragile) step_fragile[step] = robust ? 0 : 1;
       }
       if (kstar >= 0) {  // commit the chosen rotation
         double theta = 2.0 * pi * kstar / A;
@@ -451,6 +459,7 @@ void search_restart(const Prepared& L, const Pocket& P, const Params& prm, doubl
     slo += l;
     shi += h;
   }
+  if (step_fragile && rigid_fragile && reps * R > 0) step_fragile[0] |= 2;  // bit 1: fragile rigid choice
   *score_out = s;
   *lo_out = slo;
   *hi_out = shi;
@@ -477,7 +486,8 @@ int dock_ligand(const float* xyz_in, int n, const int32_t* bonds, int nb, const 
     search_restart(L, P, prm, eps, o, out.orient_pick + o * per_o, out.bump ? out.bump + o * per_o * A : nullptr,
                    out.cand_score ? out.cand_score + o * per_o * A : nullptr, &out.orient_score[o],
                    &out.orient_score_lo[o], &out.orient_score_hi[o], &out.orient_fragile[o], final_x[o],
-                   out.orient_rigid ? out.orient_rigid + o : nullptr, &early);
+                   out.orient_rigid ? out.orient_rigid + o : nullptr, &early,
+                   out.step_fragile ? out.step_fragile + o * per_o : nullptr);
   *out.pair_tests_early = early;
   int best = 0;
   for (int o = 1; o < O; ++o)
@@ -715,11 +725,13 @@ struct orc_params {
 };
 
 // One restart o of one ligand: picks[reps*R], optional bump/cand_score[reps*R*A],
-// score / interval / first fragile step, final coordinates xyz_out[3n].
+// score / interval / first fragile step, final coordinates xyz_out[3n], optional
+// step_fragile[reps*R] (1 where the step's pick is fragile; bit 2 of step 0: the rigid
+// choice is).
 int orc_dock_pose(int n, const float* xyz, int nb, const int32_t* bonds, int R, const int32_t* rot_bond,
                   const uint8_t* grid, int nx, int ny, int nz, double h, const double* origin,
                   const orc_params* p, double eps, int o, int16_t* picks, uint8_t* bump, int32_t* cand_score,
-                  int32_t* score_lo_hi_fragile, double* xyz_out) {
+                  int32_t* score_lo_hi_fragile, double* xyz_out, uint8_t* step_fragile) {
   Pocket P{grid, nx, ny, nz, h, V3{origin[0], origin[1], origin[2]}};
   Params prm{p->n_alpha, p->n_beta, p->n_gamma, p->n_angles, p->bump_dist, p->min_bond_sep, p->repetitions,
              p->rigid_span, p->rigid_step};
@@ -728,7 +740,7 @@ int orc_dock_pose(int n, const float* xyz, int nb, const int32_t* bonds, int R, 
   std::vector<V3> x;
   int16_t rigid = 0;
   search_restart(L, P, prm, eps, o, picks, bump, cand_score, &score_lo_hi_fragile[0], &score_lo_hi_fragile[1],
-                 &score_lo_hi_fragile[2], &score_lo_hi_fragile[3], x, &rigid);
+                 &score_lo_hi_fragile[2], &score_lo_hi_fragile[3], x, &rigid, nullptr, step_fragile);
   score_lo_hi_fragile[4] = rigid;
   for (int a = 0; a < n; ++a) {
     xyz_out[3 * a] = x[a].x;
@@ -751,7 +763,8 @@ int orc_dock_batch(int L, const int32_t* atom_off, const float* xyz, const int32
                    int32_t* orient_fragile, uint8_t* bump, int32_t* cand_score,
                    const int64_t* cand_off, double* best_xyz, int32_t* best_orient,
                    int32_t* best_score, int32_t* best_robust, int64_t* pair_tests_full,
-                   int64_t* evals, int32_t* status, int16_t* orient_rigid, int64_t* pair_tests_early) {
+                   int64_t* evals, int32_t* status, int16_t* orient_rigid, int64_t* pair_tests_early,
+                   uint8_t* step_fragile) {
   Pocket P{grid, nx, ny, nz, h, V3{origin[0], origin[1], origin[2]}};
   Params prm{p->n_alpha, p->n_beta, p->n_gamma, p->n_angles, p->bump_dist, p->min_bond_sep,
              p->repetitions, p->rigid_span, p->rigid_step};
@@ -769,6 +782,7 @@ int orc_dock_batch(int L, const int32_t* atom_off, const float* xyz, const int32
       lo.orient_pick = orient_pick + (size_t)rot_off[i] * O * prm.repetitions;
       lo.orient_rigid = orient_rigid ? orient_rigid + (size_t)i * O : nullptr;
       lo.orient_fragile = orient_fragile + (size_t)i * O;
+      lo.step_fragile = step_fragile ? step_fragile + (size_t)rot_off[i] * O * prm.repetitions : nullptr;
       lo.bump = bump ? bump + cand_off[i] : nullptr;
       lo.cand_score = cand_score ? cand_score + cand_off[i] : nullptr;
       lo.best_xyz = best_xyz + 3 * (size_t)atom_off[i];

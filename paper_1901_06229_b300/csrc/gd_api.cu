@@ -1128,6 +1128,17 @@ gd_status gd_job_bytes(gd_ctx* c, const gd_job* j, uint64_t* h2d, uint64_t* d2h)
   return GD_OK;
 }
 
+gd_status gd_job_info(gd_ctx* c, const gd_job* j, int* tile, int* grid_in_smem, int* blocks, int* threads,
+                      size_t* smem_bytes) {
+  if (!c || !j) return fail(GD_EINVAL, "NULL argument");
+  if (tile) *tile = j->tile;
+  if (grid_in_smem) *grid_in_smem = j->grid_in_smem ? 1 : 0;
+  if (blocks) *blocks = (int)j->cfg.blocks;
+  if (threads) *threads = (int)j->cfg.threads;
+  if (smem_bytes) *smem_bytes = j->cfg.smem;
+  return GD_OK;
+}
+
 gd_status gd_job_free(gd_ctx* c, gd_job* j) {
   if (!c || !j) return GD_OK;
   cudaSetDevice(c->device);

@@ -167,12 +167,17 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
       }
       mma_commit(mbar);
     }
-    ok = mbar_wait(mbar, phase);
+    // one outcome for the whole block: every thread takes the same branch and barriers
+    ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;
+    if (!ok) break;  // phase stays that of the commit that did not arrive
     phase ^= 1;
     tc_fence_after();
   }
   if (!ok) {
-    if (threadIdx.x == 0 && g.err) atomicExch(g.err, 1);
+    if (threadIdx.x == 0) {
+      if (g.err) atomicExch(g.err, 1);
+      mbar_wait(mbar, phase);  // give the queued MMAs another bounded wait before TMEM is freed
+    }
   } else {
     // epilogue: warp w owns rows 32w .. 32w + 31 (TMEM lanes)
     const int row = m0 + warp * 32 + lane;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 constexpr int INF_EPI = 256;                // epilogue threads (8 warps)
 constexpr int INF_THREADS = INF_EPI + 32;   // + the issuing warp
 constexpr size_t INF_W1 = 256 * 48 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2, INF_VEC = 3 * 256 * 4;
-constexpr size_t INF_BAR = 128;             // 11 mbarriers + the TMEM address
+constexpr size_t INF_BAR = 128;             // 12 mbarriers + the TMEM address
 constexpr int INF_XCH = 128 * 6 / INF_EPI;  // 16-byte X chunks per epilogue thread and tile (128 rows x 6)
 
 // Copy this thread's X chunks of the tile at row r0 (rows past M read as zero) into
@@ -315,7 +320,7 @@ __device__ __forceinline__ bool e2_finish(const uint32_t (&hp)[64], const float*
   }
   if (half == 1) {
     if (handed > 0) {  // the previous partials have been read
-      if (!mbar_wait(mbar + 10, pf)) return false;
+      if (!__all_sync(0xffffffffu, mbar_wait(mbar + 10, pf))) return false;
       pf ^= 1;
     }
     ++handed;
@@ -323,7 +328,7 @@ __device__ __forceinline__ bool e2_finish(const uint32_t (&hp)[64], const float*
     __syncwarp();
     if (lane == 0) mbar_arrive(mbar + 9);
   } else {
-    if (!mbar_wait(mbar + 9, pr)) return false;
+    if (!__all_sync(0xffffffffu, mbar_wait(mbar + 9, pr))) return false;
     pr ^= 1;
     const float other = red[row];
     __syncwarp();
@@ -346,12 +351,13 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   // mbar[0] layer 1 done, [1] layer 2 done, [7] layer 2's first four MMAs done (MMA
   // commits); [2] X rows copied in, [3 + c] chunk c of epilogue 1 written, [8] layer 2's
   // accumulator copied out (one arrival per epilogue warp); [9] the second half's
-  // partial dots written, [10] read (four arrivals each).  Every barrier completes one
+  // partial dots written, [10] read (four arrivals each); [11] the final commit after a
+  // wait ran out (see the end of the kernel).  Every barrier completes one
   // phase per tile, and no warp can arrive twice on one before its phase completes:
   // each next arrival waits, directly or through the issuing warp, for every warp's
   // current one.
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1 + INF_VEC);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 11);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 12);
   __shared__ float red[128];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = (M + 127) / 128;
@@ -375,6 +381,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     mbar_init(mbar + 8, INF_EPI / 32);
     mbar_init(mbar + 9, INF_EPI / 64);
     mbar_init(mbar + 10, INF_EPI / 64);
+    mbar_init(mbar + 11, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // W1 / W2 for the tensor core
@@ -432,7 +439,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     if (lane == 0) mbar_arrive(mbar + 2);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int r0 = tile * 128, next = tile + (int)gridDim.x;
-      ok = mbar_wait(mbar, ph1);                         // layer 1 of this tile
+      ok = __all_sync(0xffffffffu, mbar_wait(mbar, ph1));  // layer 1 of this tile
       ph1 ^= 1;
       tc_fence_after();
       if (!ok) break;
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
       // all of this tile's layer 2 is queued.  Once its first MMAs are done, their H1
       // slots take the next tile's X rows (copied while the previous tile is finished)
       if (next < ntiles) {
-        ok = mbar_wait(mbar + 7, ph7);
+        ok = __all_sync(0xffffffffu, mbar_wait(mbar + 7, ph7));
         ph7 ^= 1;
         tc_fence_after();
         if (!ok) break;
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(mbar + 2);
       }
-      ok = mbar_wait(mbar + 1, ph2);  // layer 2 done: copy its rows out, release it
+      ok = __all_sync(0xffffffffu, mbar_wait(mbar + 1, ph2));  // layer 2 done: copy its rows out, release it
       ph2 ^= 1;
       tc_fence_after();
       if (!ok) break;
@@ -483,7 +490,16 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     if (ok && prev_r0 >= 0)
       ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y);
   }
-  if (!ok && err) atomicExch(err, 1);
+  // A wait that ran out anywhere in the block: before the tensor memory is freed, the
+  // issuing thread commits once more and waits (bounded) for that commit, which arrives
+  // when every MMA it has queued is complete.
+  if (__syncthreads_or(!ok)) {
+    if (warp == INF_EPI / 32 && lane == 0) {
+      mma_commit(mbar + 11);
+      mbar_wait(mbar + 11, 0);
+    }
+    if (threadIdx.x == 0 && err) atomicExch(err, 1);
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));

@@ -1011,7 +1011,11 @@ __device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
           : "memory");
     }
   }
-  // bounded wait on phase 0 (about two seconds at the maximum clock)
+  // bounded wait on phase 0 (about two seconds at the maximum clock).  The outcome is
+  // decided once for the block, so every thread returns or goes on together.  A timeout
+  // whose copies never land leaves them in flight into this block's shared memory when it
+  // exits; the test hook (stage_extra_bytes) only makes the barrier expect more bytes
+  // than are copied, so there every copy has landed.
   const long long t0 = clock64();
   uint32_t ok = 0;
   while (!ok) {
@@ -1020,9 +1024,9 @@ __device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
         : "=r"(ok)
         : "r"(smem_u32(mbar))
         : "memory");
-    if (!ok && clock64() - t0 > 4000000000LL) return false;
+    if (!ok && clock64() - t0 > 4000000000LL) break;
   }
-  return true;
+  return __syncthreads_and((int)ok) != 0;
 }
 
 template <int S, int G, bool LEAN>

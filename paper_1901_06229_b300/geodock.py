@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: 
 EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_free_pocket",
            "gd_dock_batch", "gd_fetch_results", "gd_job_launch", "gd_job_download", "gd_job_bytes", "gd_job_free",
            "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc",
-           "gd_prepare_batch", "gd_prepare_batch_sel", "gd_measure_peaks"]
+           "gd_prepare_batch", "gd_prepare_batch_sel", "gd_measure_peaks", "gd_job_info"]
 
 
 class GeoDockError(RuntimeError):
@@ -85,6 +85,7 @@ def load():
     L.gd_job_download.argtypes = [vp, vp, vp]
     L.gd_job_free.argtypes = [vp, vp]
     L.gd_job_bytes.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint64)]
+    L.gd_job_info.argtypes = [vp, vp, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_size_t)]
     L.gd_check_batch.argtypes = [P(LigandBatchC), P(SearchParamsC)]
     L.gd_prepare_batch.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), vp, P(vp)]
     L.gd_prepare_batch_sel.argtypes = [vp, vp, P(LigandBatchC), P(C.c_int32), C.c_int32, P(SearchParamsC), vp,
@@ -229,6 +230,13 @@ class Job:
         i, o = C.c_uint64(), C.c_uint64()
         self.ctx._check(load().gd_job_bytes(self.ctx.h, self.handle, C.byref(i), C.byref(o)))
         return i.value, o.value
+
+    def info(self):
+        """gd_job_info: the search launch's tile, grid staging mode and shape."""
+        t, g, b, th, sm = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_size_t()
+        self.ctx._check(load().gd_job_info(self.ctx.h, self.handle, C.byref(t), C.byref(g), C.byref(b), C.byref(th),
+                                           C.byref(sm)))
+        return dict(tile=t.value, grid_in_smem=bool(g.value), blocks=b.value, threads=th.value, smem=sm.value)
 
     def free(self):
         if self.handle:

@@ -56,13 +56,24 @@ class ScreenResult:
                     restarts_per_ligand=float(np.mean(self.restarts)))
 
 
+def slot_bytes(max_batch, n_orient):
+    """Device bytes of one in-flight slot's proposer buffers: a BF16 feature row (48 x 2
+    bytes) and an FP32 prediction per (ligand, restart) of a full batch."""
+    return max_batch * n_orient * (48 * 2 + 4)
+
+
 class Screen:
     """Continuous-batching screen of one pocket with a trained proposer (k restarts per
     ligand, k_fallback -- all when None -- where the proposer's top-k spread falls back).
 
-    Admission: a batch is admitted when a stream slot is free and gd_prepare_batch fits
-    the context's device-memory budget; otherwise it waits for an in-flight batch to
-    finish, and if nothing is in flight the batch size is halved."""
+    Memory: every in-flight slot owns its proposer buffers (features and predictions of a
+    full batch, slot_bytes), allocated once here; the search's own memory comes from the
+    context and counts against its budget, so a screen under a total budget B runs on a
+    context created with B - max_inflight * slot_bytes (Screen.context_budget).
+    Admission: a batch is admitted when a slot is free and gd_prepare_batch fits the
+    context's budget; otherwise it waits for an in-flight batch to finish, and if nothing
+    is in flight the batch size is halved.  Each completed batch lets the size grow back
+    (doubling, up to max_batch)."""
 
     def __init__(self, ctx, pocket, params, net, k=16, margin=1e30, rule=1, max_batch=512, max_inflight=4,
                  k_fallback=None,
@@ -72,25 +83,35 @@ class Screen:
         self.k, self.margin, self.rule, self.k_fallback = k, margin, rule, k_fallback
         self.max_batch, self.debug = max_batch, debug
         self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
+        rows = max_batch * params.n_orient
+        self.X = [torch.empty((rows, 48), dtype=torch.bfloat16, device="cuda") for _ in range(max_inflight)]
+        self.y = [torch.empty(rows, device="cuda") for _ in range(max_inflight)]
 
-    def _submit(self, batch, ids, stream):
-        """Queue ligands ids of batch (packed straight from the library, no sub-batch)."""
+    @staticmethod
+    def context_budget(total_bytes, max_batch, n_orient, max_inflight=4):
+        """Budget of the context of a screen that may hold total_bytes of device memory."""
+        return total_bytes - max_inflight * slot_bytes(max_batch, n_orient)
+
+    def _submit(self, batch, ids, slot):
+        """Queue ligands ids of the library batch (packed straight from it, no sub-batch)."""
         import torch
+        stream = self.streams[slot]
         job = self.ctx.prepare_batch(self.pk, batch, self.params, stream=stream, debug=self.debug, sel=ids)
         rows = len(ids) * self.params.n_orient
         with torch.cuda.stream(stream):
-            X = torch.empty((rows, 48), dtype=torch.bfloat16, device="cuda")
-            y = torch.empty(rows, device="cuda")
+            X, y = self.X[slot][:rows], self.y[slot][:rows]
             job.features(x_bf16=X, stream=stream)
             self.net.predict(X, y)
             job.launch_proposed(y, self.k, self.margin, self.rule, stream, k_fallback=self.k_fallback)
             job.download(stream)
         return job, X, y
 
-    def run(self, workload, arrival_times, clock=time.perf_counter):
-        """Serve every ligand of `workload`; ligand i becomes available at arrival_times[i]
-        seconds after the start.  Returns per-ligand results and timings."""
-        N = workload.batch.n_ligands
+    def run(self, workload, arrival_times, clock=time.perf_counter, ligand_of=None):
+        """Serve one request per arrival time: request i asks for ligand ligand_of[i] of
+        `workload`'s library (default: ligand i) and becomes available arrival_times[i]
+        seconds after the start.  Returns per-request results and timings."""
+        N = len(arrival_times)
+        ligand_of = np.arange(N) if ligand_of is None else np.asarray(ligand_of, np.int64)
         order = np.argsort(arrival_times, kind="stable")
         res = ScreenResult(best_score=np.zeros(N, np.uint32), best_orient=np.zeros(N, np.int32),
                            arrival=np.asarray(arrival_times, np.float64).copy(), done=np.zeros(N),
@@ -120,13 +141,15 @@ class Screen:
                 free.append(self.streams.index(b.stream))
                 inflight.remove(b)
                 finished += len(b.ids)
+                cap = min(self.max_batch, 2 * cap)  # memory came back: let the batch size recover
                 progressed = True
             if pending and free:
                 take = [pending.popleft() for _ in range(min(cap, len(pending)))]
                 ids = np.array(take, np.int64)
-                stream = self.streams[free[-1]]
+                slot = free[-1]
+                stream = self.streams[slot]
                 try:
-                    job, X, y = self._submit(workload.batch, ids, stream)
+                    job, X, y = self._submit(workload.batch, ligand_of[ids], slot)
                 except gdk.GeoDockError as e:
                     if e.status != gdk.GD_EBUDGET:
                         raise

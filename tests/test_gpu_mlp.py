@@ -66,6 +66,28 @@ def _net_case(seed, B):
     return P, X, t
 
 
+STEPS = 4  # BF16 steps (2^-7 relative) of an element's absolute mass the device may differ by
+
+
+def grad_mass(P, X, t):
+    """Each gradient element's absolute mass: its sum over the batch with every factor
+    replaced by its absolute value (|G2|^T |H1| for dW2, and so on down the backward
+    pass).  The device and the oracle round the same operands (H1, H2, G2, G1) to BF16;
+    where an FP32 and an FP64 value straddle a BF16 rounding boundary the operand moves by
+    one BF16 step (at most 2^-7 of it), and through y such a move shifts every later
+    factor of its row by a comparable share.  An element's difference is therefore a
+    small number of BF16 steps of its mass -- not of the (often cancelling) gradient."""
+    from oracle import mlp as om
+    f = om.forward(P, X, rounding=True)
+    B = len(t)
+    dy = np.abs(2.0 * (f["y"] - np.asarray(t, np.float64)) / B)
+    aw3, aH1, aH2, aX = np.abs(f["w3"]), np.abs(f["H1"]), np.abs(f["H2"]), np.abs(f["X"])
+    G2 = np.outer(dy, aw3) * (f["H2"] > 0)
+    G1 = (G2 @ np.abs(f["W2"])) * (f["H1"] > 0)
+    return om.pack(dict(W1=G1.T @ aX, b1=G1.sum(0), W2=G2.T @ aH1, b2=G2.sum(0), w3=aH2.T @ dy,
+                        b3=np.array([dy.sum()])))
+
+
 def test_network_forward_and_gradients_match_oracle():
     import torch
     from oracle import mlp as om
@@ -88,15 +110,17 @@ def test_network_forward_and_gradients_match_oracle():
     np.testing.assert_allclose(y.cpu().numpy(), f["y"], rtol=1e-3, atol=2e-3)
     ref_loss, ref = om.gradients(P, Xr, t, rounding=True)
     assert abs(loss.item() - ref_loss) <= 1e-3 * ref_loss + 1e-6
-    g = grad.cpu().numpy()
+    g = grad.cpu().numpy().astype(np.float64)
+    mass = grad_mass(P, Xr, t)
     o = 0
     for name, shape in om.SIZES:
         n = int(np.prod(shape))
-        a, b = g[o:o + n], ref[o:o + n]
-        scale = np.abs(b).max() + 1e-12
-        # BF16 rounding points agree except where FP32 and FP64 sums straddle a BF16
-        # rounding boundary (a few elements, one BF16 ulp): compare on the tensor's scale
-        assert np.abs(a - b).max() <= 2e-2 * scale, (name, np.abs(a - b).max(), scale)
+        a, b, lim = g[o:o + n], ref[o:o + n], STEPS * 2.0 ** -7 * mass[o:o + n] + 1e-7
+        err = np.abs(a - b)
+        worst = int(np.argmax(err / lim))
+        print(name, "largest error in BF16 steps of the element's mass:",
+              float(err[worst] / (2.0 ** -7 * mass[o + worst] + 1e-30)))
+        assert np.all(err <= lim), (name, worst, a[worst], b[worst], lim[worst])
         assert np.corrcoef(a, b)[0, 1] > 0.9999 if n > 1 else True
         o += n
     net.close()

@@ -79,6 +79,25 @@ def test_bounded_fallback_in_the_mix(setup):
         assert _alone(ctx, pk, w, net, int(i), 16, margin, k_fallback=64) == got
 
 
+def test_requests_cycling_over_the_library(setup):
+    """Requests that name library ligands (each ligand asked for twice, the second time
+    while other batches run) get the same result as the ligand's first request."""
+    ctx, pk, w, net, margin = setup
+    n = w.batch.n_ligands
+    lig = np.concatenate([np.arange(n), np.random.default_rng(5).permutation(n)])
+    arr = serve.poisson_arrivals(2 * n, 40000.0, seed=6)
+    res = serve.Screen(ctx, pk, w.params, net, k=16, margin=margin, max_batch=64, max_inflight=3).run(
+        w, arr, ligand_of=lig)
+    first = np.full(n, -1)
+    for r in range(2 * n):
+        if first[lig[r]] < 0:
+            first[lig[r]] = r
+        else:
+            q = first[lig[r]]
+            assert (res.best_score[r], res.best_orient[r]) == (res.best_score[q], res.best_orient[q])
+    assert res.batches > 3
+
+
 def test_memory_budget_admission(setup):
     ctx0, pk0, w, net, margin = setup
     arr = np.zeros(w.batch.n_ligands)  # everything arrives at once
