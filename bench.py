@@ -71,6 +71,9 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
+    "ad511480c64b7604": {("batched-4096lig-64grid", 14): 4564992 + 1341440,
+                         ("batched-4096lig-64grid", 15): 4736256 + 1323008,
+                         ("large-512lig-128grid", 9): 3233280 + 5632},
     "089efa26c3e7fd61": {("batched-4096lig-64grid", 14): 4551680 + 1316352,
                          ("batched-4096lig-64grid", 15): 4552960 + 1300992,
                          ("large-512lig-128grid", 9): 3128832 + 5120},
@@ -82,6 +85,9 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
+    "ad511480c64b7604": {("batched-4096lig-64grid", 14): 8448360711,
+                         ("batched-4096lig-64grid", 15): 8448465499,
+                         ("large-512lig-128grid", 9): 14709211994},
     "089efa26c3e7fd61": {("batched-4096lig-64grid", 14): 8448360733,
                          ("batched-4096lig-64grid", 15): 8448465523,
                          ("large-512lig-128grid", 9): 14709211960},
