@@ -140,6 +140,7 @@ struct gd_ctx {
   std::multimap<size_t, void*> host_free;  // cached pinned blocks by size
   std::unordered_map<void*, size_t> dev_size, host_size;  // size of every block allocated
   std::map<std::string, int> tuned;        // autotuned tile per workload signature
+  std::vector<cudaEvent_t> events;         // completion events of released jobs, for reuse
   HostPool pool{pack_threads() - 1};        // batch packing
 };
 
@@ -372,7 +373,10 @@ gd_status job_release(gd_ctx* c, gd_job* j) {
   if (j->done) cudaEventSynchronize(j->done);
   if (j->exec) cudaGraphExecDestroy(j->exec);
   if (j->graph) cudaGraphDestroy(j->graph);
-  if (j->done) cudaEventDestroy(j->done);
+  if (j->done) {  // completed (synchronised above): kept for the context's next job
+    std::lock_guard<std::mutex> g(c->mu);
+    c->events.push_back(j->done);
+  }
   dev_release(c, j->d_in, j->in.total);
   dev_release(c, j->d_out, j->out.total);
   dev_release(c, j->d_scr, j->scr.total);
@@ -392,14 +396,13 @@ std::string signature(const gd_pocket* pk, const gd_search_params* p, int nmax, 
   return b;
 }
 
-// Capture [clear counters, search kernel] once; replayed by every later launch of the
-// job.  A job's first launch goes to the stream directly (capturing and instantiating a
+// Capture [pose setup (which also clears the search's counters), search kernel] once;
+// replayed by every later launch of the job.  A job's first launch goes to the stream directly (capturing and instantiating a
 // graph costs more host time than a single launch of a small job saves).
 gd_status build_graph(gd_ctx* c, gd_job* j) {
   std::lock_guard<std::mutex> serial(c->capture_mu);  // host threads share the capture stream
   cudaStream_t s = c->capture_stream;
   GD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s);
   cudaError_t le = gd::launch_search(j->args, j->cfg, s);
   cudaGraph_t g = nullptr;
   cudaError_t ee = cudaStreamEndCapture(s, &g);
@@ -615,18 +618,24 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
     a.rmax = std::max(a.rmax, rot_off[i + 1] - rot_off[i]);
     a.emax = std::max(a.emax, ne);
   }
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax);
   // tile (0: chosen from the batch's buffer sizes) and grid staging mode
   const size_t smem_cap = 227 * 1024;
   if (tile == 0) tile = gd::default_tile(a);
   j->tile = tile;
-  j->grid_in_smem = !gd::tile_get(tile).lean && pk->dev.bytes_pad <= gd::max_smem_grid_bytes() &&
+  j->grid_in_smem = gd::tile_stages_grid(gd::tile_get(tile)) && pk->dev.bytes_pad <= gd::max_smem_grid_bytes() &&
                     gd::search_smem_bytes(a, tile, true) <= smem_cap;
   if (!j->grid_in_smem && gd::search_smem_bytes(a, tile, false) > smem_cap) {
     job_release(c, j);
     return fail(GD_EINVAL, "tile %d needs more shared memory than a block has", tile);
   }
-  GD_CUDA(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (!c->events.empty()) {
+      j->done = c->events.back();
+      c->events.pop_back();
+    }
+  }
+  if (!j->done) GD_CUDA(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
   if (L > 0) {  // launch shape (kernel attributes and occupancy: queried outside any capture)
     cudaError_t pe = gd::plan_search(j->args, j->tile, j->grid_in_smem, c->num_sms, &j->cfg);
     if (pe != cudaSuccess) {
@@ -641,7 +650,6 @@ gd_status make_job(gd_ctx* c, const gd_pocket* pk, const gd_ligand_batch* b, con
 gd_status enqueue_search(gd_job* j, cudaStream_t s) {
   if (j->L == 0) return GD_OK;
   if (!j->exec && j->launches == 0) {  // first launch: straight to the stream
-    GD_CUDA(cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s));
     GD_CUDA(gd::launch_search(j->args, j->cfg, s));
   } else {  // relaunched: capture once, replay from then on
     if (!j->exec) {
@@ -696,6 +704,7 @@ gd_status gd_destroy(gd_ctx* c) {
   cudaDeviceSynchronize();
   for (auto& kv : c->dev_free) cudaFree(kv.second);
   for (auto& kv : c->host_free) cudaFreeHost(kv.second);
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   delete c;
   return GD_OK;
@@ -1055,7 +1064,6 @@ gd_status gd_job_launch_proposed_fb(gd_ctx* c, gd_job* j, const float* pred, int
     e = gd::launch_selection(a, pred, k, k_fallback, margin, rule, j->sel_cnt, j->sel_topk, j->sel_spread, j->sel_off,
                              j->sel_items, j->sel_n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.pose_score, 0xFF, 4 * L * O, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync((char*)j->d_scr + j->scr.done, 0, j->scr.work + 8 - j->scr.done, s);
   if (e == cudaSuccess) e = gd::launch_search(a, cfg, s);
   if (e == cudaSuccess) e = cudaEventRecord(j->done, s);
   if (e != cudaSuccess) return fail(GD_ECUDA, "proposed search: %s", cudaGetErrorString(e));

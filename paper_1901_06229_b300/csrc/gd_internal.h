@@ -79,8 +79,8 @@ struct SearchArgs {
   uint32_t* pose_score;       // [L*O]
   int16_t* pose_pick;         // [O * reps * Rt]
   unsigned long long* pose_pairs;  // [L*O]
-  int32_t* done;              // [L]   zeroed before every launch
-  unsigned long long* work;   // [1]   zeroed before every launch
+  int32_t* done;              // [L]   zeroed by the pose-setup kernel before every search
+  unsigned long long* work;   // [1]   zeroed by the pose-setup kernel before every search
   int32_t* err;               // [1]   0 = fine, else error code (output block; zeroed at setup)
   // debug (may be null)
   uint8_t* bump_bits;         // [O * reps * A * Rt]
@@ -91,7 +91,6 @@ struct SearchArgs {
   float4* quat;               // [O] (scratch) restart unit quaternions (w >= 0)
   int fmax;                   // largest rotating fragment of the batch (>= 1)
   int rmax, emax;             // largest rotamer / excluded-pair count of one ligand (>= 1)
-  int warp_bytes;             // shared memory per warp (see warp_smem_bytes)
   unsigned long long* reach_tests;  // [L] (output) moving x static pairs checked by the reach filter
   unsigned long long* pose_reach;   // [L*O] (scratch)
   // rigid alignment sweep (off when rigid_n <= 1)
@@ -113,8 +112,12 @@ constexpr float REACH_MARGIN = 0.01f;
 // MASK uint32[mask_words] | EXL uint16[emax] | RD RotDesc[rmax] | PC float4[32] (the
 // coefficients of the near pairs being swept).  fmax / rmax / emax: the largest
 // fragment, rotamer count and excluded-pair count of one ligand in the batch (>= 1).
-__host__ __device__ inline int warp_smem_bytes(int nmax, int fmax, int mask_words, int rmax, int emax) {
+// compact (the 96-register builds): no W2 (rebuilt from DP) and no EXL / RD (the
+// descriptors and excluded pairs are read through L1).
+__host__ __device__ inline int warp_smem_bytes(int nmax, int fmax, int mask_words, int rmax, int emax,
+                                               bool compact = false) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
+  if (compact) return a16(16 * nmax) + a16(8 * nmax) + a16(16 * fmax) + a16(4 * mask_words) + 32 * 16;
   return a16(16 * nmax) + a16(8 * nmax) + a16(16 * fmax) + a16(8 * fmax) + a16(4 * mask_words) + a16(2 * emax) +
          16 * rmax + 32 * 16;
 }
@@ -134,12 +137,22 @@ inline int work_chunk(long long n_items) { return n_items >= 8LL * 148 * 32 ? 4 
 // pose_score of a restart that a subset launch leaves out (buffers are filled with it)
 constexpr uint32_t NOT_SEARCHED = 0xFFFFFFFFu;
 
+// Builds of the search kernel.
+//   BUILD_WIDE:    <= 128 registers, one block of up to 16 warps per SM; the pocket grid
+//                  is staged in shared memory when its crop fits; the reach filter prunes
+//                  its static columns first.
+//   BUILD_LEAN:    <= 80 registers (a little state spills) for up to 24 warps per SM; the
+//                  grid is read through the texture path; no column pruning.
+//   BUILD_COMPACT: <= 96 registers and smaller per-warp buffers (compact warp_smem_bytes)
+//                  for about 20 warps per SM with the buffers of 250-atom ligands; texture
+//                  path; column pruning.
+enum : int { BUILD_WIDE = 0, BUILD_LEAN = 1, BUILD_COMPACT = 2 };
+
 // Launch configuration of one tile.
 struct Tile {
   int warps;        // warps (poses in flight) per block
   int slots;        // angles per lane evaluated together
-  int lean;         // 1: kernel built for <= 80 registers (up to 24 resident warps per SM);
-                    //    the grid is then read through the texture path, never staged
+  int build;        // BUILD_*
 };
 int tile_count();
 Tile tile_get(int id);  // id in [1, tile_count()]
@@ -161,14 +174,18 @@ cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, i
 cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, int kf, float margin, int rule,
                              int32_t* cnt, uint16_t* topk, float* spread, int32_t* off, uint32_t* items,
                              int32_t* n_items, cudaStream_t stream);
-// Launch the search (kernel only; the work counter and per-ligand counters must be
-// zeroed by the caller first).
+// Launch the search: the pose-setup kernel (which also zeroes the work counter and the
+// per-ligand completion counters) and the search kernel, on `stream`.
 cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t stream);
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem);
 int max_smem_grid_bytes();
 // Tile used for tile 0 (the built-in default) given the batch's buffer sizes.
 int default_tile(const SearchArgs& a);
 // Register budget per thread of a tile's kernel.
-inline int tile_max_regs(const Tile& t) { return t.lean ? 80 : 128; }
+inline int tile_max_regs(const Tile& t) {
+  return t.build == BUILD_LEAN ? 80 : (t.build == BUILD_COMPACT ? 96 : 128);
+}
+// Whether a tile's kernel can stage the pocket grid in shared memory.
+inline bool tile_stages_grid(const Tile& t) { return t.build == BUILD_WIDE; }
 
 }  // namespace gd

@@ -280,11 +280,10 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
     a.rmax = rot_off[i + 1] - rot_off[i] > a.rmax ? rot_off[i + 1] - rot_off[i] : a.rmax;
     a.emax = ne > a.emax ? ne : a.emax;
   }
-  a.warp_bytes = gd::warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax);
 
   const int tile = p->tile > 0 ? p->tile : gd::default_tile(a);
   const size_t smem_cap = 227 * 1024;
-  bool smem_grid = !gd::tile_get(tile).lean && (int)grid_pad <= gd::max_smem_grid_bytes() &&
+  bool smem_grid = gd::tile_stages_grid(gd::tile_get(tile)) && (int)grid_pad <= gd::max_smem_grid_bytes() &&
                    gd::search_smem_bytes(a, tile, true) <= smem_cap;
   if (!smem_grid && gd::search_smem_bytes(a, tile, false) > smem_cap)
     return nfail(GD_EINVAL, "tile %d needs more shared memory than a block has", tile);
@@ -297,7 +296,6 @@ gd_status dock_noalloc(const uint8_t* grid, int nx, int ny, int nz, float spacin
   int32_t err = 0;
   if ((e = cudaMemcpyAsync(d, g_stage, in_used, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(d + o_err, 0, 4, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(d + o_done, 0, o_work + 8 - o_done, s)) != cudaSuccess ||
       (e = gd::launch_search(a, cfg, s)) != cudaSuccess)
     return nfail(GD_ECUDA, "launch: %s", cudaGetErrorString(e));
   struct Copy {

@@ -35,6 +35,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "gd_internal.h"
@@ -92,7 +93,14 @@ __device__ __forceinline__ float2 angle_entry(int k, int A) {
 // about the axis): with d = x - p, h = d.u, d_perp = d - h u and w = u x d, the point
 // turned by theta is x + (cos theta - 1) d_perp + sin theta w.  axis_frame gives
 // (d_perp, w.x) in dp and (w.y, w.z) in w2, once per atom and rotamer step; turn is then
-// six FMAs per angle.  The search and the commit of a step share both functions.
+// six FMAs per angle.  frame_w2 is (w.y, w.z) alone, with the same roundings, for the
+// compact builds that keep dp but not w2.  The search and the commit of a step share
+// these functions.
+__device__ __forceinline__ float2 frame_w2(float4 x, float4 p, float ux, float uy, float uz) {
+  const float dx = __fsub_rn(x.x, p.x), dy = __fsub_rn(x.y, p.y), dz = __fsub_rn(x.z, p.z);
+  return make_float2(__fmaf_rn(uz, dx, -__fmul_rn(ux, dz)), __fmaf_rn(ux, dy, -__fmul_rn(uy, dx)));
+}
+
 __device__ __forceinline__ void axis_frame(float x, float y, float z, float4 p, float ux, float uy, float uz,
                                            float4& dp, float2& w2, float& h) {
   const float dx = __fsub_rn(x, p.x), dy = __fsub_rn(y, p.y), dz = __fsub_rn(z, p.z);
@@ -181,9 +189,13 @@ __device__ void place(const SearchArgs& a, float4* X, int a0, int n, int o, int 
 }
 
 // Per launch, before the search: R_o of every restart (ZYZ Euler angles, Listing 1:
-// R = Rz(alpha) Ry(beta) Rz(gamma)) and every ligand's coordinates minus its centroid.
+// R = Rz(alpha) Ry(beta) Rz(gamma)) and every ligand's coordinates minus its centroid;
+// the work counter and the per-ligand completion counters of the search that follows on
+// the same stream are cleared here too.
 __global__ void __launch_bounds__(256) pose_setup_kernel(const __grid_constant__ SearchArgs a) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  if (tid == 0) *a.work = 0ull;
+  for (int i = tid; i < a.L; i += nth) a.done[i] = 0;
   for (int o = tid; o < a.O; o += nth) {
     const int ia = o / (a.nb * a.ng), jb = (o / a.ng) % a.nb, kg = o % a.ng;
     float sa, ca, sb, cb, sg, cg;
@@ -258,7 +270,8 @@ __device__ __forceinline__ int frag_size(const RotDesc& rd, int n) {
 
 // Commit the winning rotation to the fragment (same arithmetic as the candidate); the
 // w component of each moved atom caches its new grid cell.  DP / W2: the step's axis
-// frames in sweep order when the search has them, else (replay) NULL and recomputed.
+// frames in sweep order when the search has them (W2 NULL in the compact builds: rebuilt
+// from the atom and p), else (replay) NULL and recomputed.
 template <int G>
 __device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n, const RotDesc& rd, float ux,
                        float uy, float uz, float2 cs, int lane, const float4* DP, const float2* W2) {
@@ -274,7 +287,7 @@ __device__ void commit(const PocketDev& pk, const uint8_t* sg, float4* X, int n,
     float h, x, y, z;
     if (DP) {
       dp = DP[i];
-      w2 = W2[i];
+      w2 = W2 ? W2[i] : frame_w2(v, xp, ux, uy, uz);
     } else {
       axis_frame(v.x, v.y, v.z, xp, ux, uy, uz, dp, w2, h);
     }
@@ -322,13 +335,17 @@ struct WarpMem {
   uint8_t* SL;     // the reach filter's columns: static atom of column k (aliases PC[0, 16))
   uint8_t* POS;    // the reach filter's column of atom b, 0xFF if none (aliases PC[16, 32))
   uint32_t* MASK;  // near-pair masks: word ia * nch + c, bit t <-> static atom 32 c + t
-  RotDesc* RD;     // the current ligand's rotamer descriptors
-  uint16_t* EXL;   // the current ligand's excluded pairs (all rotamers)
+  RotDesc* RDs;    // per-warp copies of the ligand's rotamer descriptors / excluded pairs
+  uint16_t* EXLs;  //   (NULL in the compact builds)
+  const RotDesc* RD;    // the current ligand's rotamer descriptors: RDs, or global memory
+  const uint16_t* EXL;  // its excluded pairs (all rotamers), from the first one's offset on
   const float2* CS;  // (cos, sin) of every angle, shared by the block
 };
 
+// Per-warp buffers (see warp_smem_bytes).  compact: no W2 (rebuilt from DP) and no copies
+// of the descriptors and excluded pairs (read through L1 instead).
 __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int fmax, int mask_words, int rmax,
-                                            int emax) {
+                                            int emax, bool compact) {
   auto a16 = [](int v) { return (v + 15) / 16 * 16; };
   WarpMem w;
   w.X = reinterpret_cast<float4*>(base);
@@ -338,14 +355,23 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int f
   base += a16(8 * nmax);
   w.DP = reinterpret_cast<float4*>(base);
   base += a16(16 * fmax);
-  w.W2 = reinterpret_cast<float2*>(base);
-  base += a16(8 * fmax);
+  w.W2 = nullptr;
+  if (!compact) {
+    w.W2 = reinterpret_cast<float2*>(base);
+    base += a16(8 * fmax);
+  }
   w.MASK = reinterpret_cast<uint32_t*>(base);
   base += a16(4 * mask_words);
-  w.EXL = reinterpret_cast<uint16_t*>(base);
-  base += a16(2 * emax);
-  w.RD = reinterpret_cast<RotDesc*>(base);
-  base += 16 * rmax;
+  w.EXLs = nullptr;
+  w.RDs = nullptr;
+  if (!compact) {
+    w.EXLs = reinterpret_cast<uint16_t*>(base);
+    base += a16(2 * emax);
+    w.RDs = reinterpret_cast<RotDesc*>(base);
+    base += 16 * rmax;
+  }
+  w.RD = w.RDs;
+  w.EXL = w.EXLs;
   w.PC = reinterpret_cast<float4*>(base);
   w.SL = reinterpret_cast<uint8_t*>(base);  // GD_MAX_ATOMS = 256: 255 columns at most
   w.POS = reinterpret_cast<uint8_t*>(base) + 256;
@@ -353,8 +379,17 @@ __device__ __forceinline__ WarpMem warp_mem(unsigned char* base, int nmax, int f
   return w;
 }
 
+// (u x d).y, (u x d).z of moving atom ia (sweep order) at x (its coordinates this step):
+// stored, or rebuilt from x and p in the compact builds (bitwise the same values).
+template <bool COMPACT>
+__device__ __forceinline__ float2 w2_at(const WarpMem& w, int ia, float4 x, float4 p, float ux, float uy, float uz) {
+  if (COMPACT) return frame_w2(x, p, ux, uy, uz);
+  return w.W2[ia];
+}
+
 // Per rotamer step: (h, rho) of every atom about the bond axis for the reach filter, and
 // the axis frame of every moving atom (sweep order) for the candidate rotations.
+template <bool COMPACT>
 __device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp, float ux, float uy, float uz,
                           int lane) {
   for (int i = lane; i < n; i += 32) {
@@ -371,7 +406,7 @@ __device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp,
     if (in != (rd.comp != 0)) {
       const int ia = rd.comp ? (i < rd.lo ? i : i - (rd.hi - rd.lo)) : i - rd.lo;
       w.DP[ia] = dp;
-      w.W2[ia] = w2;
+      if (!COMPACT) w.W2[ia] = w2;
     }
   }
   __syncwarp();
@@ -379,7 +414,7 @@ __device__ void prep_step(const WarpMem& w, int n, const RotDesc& rd, float4 xp,
 
 // Evaluate every angle of one rotamer step; returns the warp-wide best key
 // ((score + 1) << 16 | (0xFFFF - k)), 0 if every candidate is bumped.
-template <int S, int G>
+template <int S, int G, bool COMPACT>
 __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, const uint16_t* excl,
                               int n, const RotDesc& rd, float4 xp, float ux, float uy, float uz, int cur,
                               int lane, unsigned long long& pairs, uint8_t* dbg) {
@@ -418,7 +453,7 @@ __device__ unsigned eval_step(const SearchArgs& a, const uint8_t* sg, const Warp
         const float4 xa = X[ai];
         stat -= __float_as_int(xa.w);
         const float4 dp = w.DP[ia];
-        const float2 w2 = w.W2[ia];
+        const float2 w2 = w2_at<COMPACT>(w, ia, xa, xp, ux, uy, uz);
         // park the static atoms this moving atom must not be tested against
         int ex_end = ex;
         float4 saved = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -628,7 +663,7 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
 // Every angle of one rotamer step: bump tests over the step's near pairs (chunks of 32:
 // lane t computes pair t's coefficients, shuffles hand them to every lane), then the grid
 // gathers of the moving atoms.
-template <int S, int G>
+template <int S, int G, bool COMPACT>
 __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
                                    const RotDesc& rd, float4 xp, float ux, float uy, float uz, int cur,
                                    int n_near, int lane, unsigned long long& pairs, uint8_t* dbg) {
@@ -657,7 +692,8 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
       __syncwarp();
       if (e0 + lane < n_near) {
         const int ent = w.NEAR[e0 + lane], ia = ent >> 8;
-        w.PC[lane] = pair_coef(X[frag_atom(rd, ia)], w.DP[ia], w.W2[ia], X[ent & 0xFF], xp, ux, uy, uz);
+        const float4 xa = X[frag_atom(rd, ia)], dpa = w.DP[ia];
+        w.PC[lane] = pair_coef(xa, dpa, w2_at<COMPACT>(w, ia, xa, xp, ux, uy, uz), X[ent & 0xFF], xp, ux, uy, uz);
       }
       __syncwarp();
       const int cnt = n_near - e0 < 32 ? n_near - e0 : 32;
@@ -677,7 +713,7 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
         const float4 xa = X[ai];
         stat -= __float_as_int(xa.w);
         const float4 dp = w.DP[ia];
-        const float2 w2 = w.W2[ia];
+        const float2 w2 = w2_at<COMPACT>(w, ia, xa, xp, ux, uy, uz);
 #pragma unroll
         for (int j = 0; j < S; ++j) {
           float x, y, z;
@@ -700,7 +736,7 @@ __device__ unsigned eval_step_near(const SearchArgs& a, const uint8_t* sg, const
 
 // Every angle of one rotamer step, bump tests restricted to the near pairs of the
 // step's masks (n_near of them); used when the near list overflowed.
-template <int S, int G, bool PRUNE>
+template <int S, int G, bool PRUNE, bool COMPACT>
 __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int n,
                                    const RotDesc& rd, float4 xp, float ux, float uy, float uz, int cur,
                                    int n_near, int nch_pruned, int lane, unsigned long long& pairs, uint8_t* dbg) {
@@ -736,7 +772,7 @@ __device__ unsigned eval_step_masks(const SearchArgs& a, const uint8_t* sg, cons
         const float4 xa = X[ai];
         stat -= __float_as_int(xa.w);
         const float4 dp = w.DP[ia];
-        const float2 w2 = w.W2[ia];
+        const float2 w2 = w2_at<COMPACT>(w, ia, xa, xp, ux, uy, uz);
         float xr[S][3];
 #pragma unroll
         for (int j = 0; j < S; ++j) {
@@ -899,7 +935,7 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   __syncwarp();
 }
 
-template <int S, int G, bool PRUNE>
+template <int S, int G, bool PRUNE, bool COMPACT>
 __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int e0,
                             int lane) {
   float4* X = w.X;
@@ -924,19 +960,20 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
         dbg = a.bump_bits + (size_t)r0 * a.reps * a.O * a.A + ((size_t)o * a.reps * R + rep * R + r) * a.A;
       unsigned key;
       const float4 xp = X[rd.p];
-      prep_step(w, n, rd, xp, ux, uy, uz, lane);
+      prep_step<COMPACT>(w, n, rd, xp, ux, uy, uz, lane);
       if (a.use_filter) {
         int nch;
         const int n_near = build_near<PRUNE>(a, w, excl, n, rd, lane, reach, nch);
         if (n_near <= 4 * a.nmax && !a.mask_sweep)
-          key = eval_step_near<S, G>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, lane, pairs, dbg);
+          key = eval_step_near<S, G, COMPACT>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, lane, pairs, dbg);
         else
-          key = eval_step_masks<S, G, PRUNE>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, nch, lane, pairs, dbg);
+          key = eval_step_masks<S, G, PRUNE, COMPACT>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, nch, lane, pairs,
+                                                      dbg);
       } else
-        key = eval_step<S, G>(a, sg, w, excl, n, rd, xp, ux, uy, uz, cur, lane, pairs, dbg);
+        key = eval_step<S, G, COMPACT>(a, sg, w, excl, n, rd, xp, ux, uy, uz, cur, lane, pairs, dbg);
       const int k = key ? (int)(0xFFFFu - (key & 0xFFFFu)) : -1;
       if (k >= 0) {
-        commit<G>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, w.DP, w.W2);
+        commit<G>(a.pk, sg, X, n, rd, ux, uy, uz, w.CS[k], lane, w.DP, COMPACT ? nullptr : w.W2);
         cur = (int)(key >> 16) - 1;
       }
       if (lane == 0) a.pose_pick[pick_base + rep * R + r] = (int16_t)k;
@@ -952,19 +989,27 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
   __syncwarp();
 }
 
-// A ligand's rotamer descriptors and excluded pairs into the warp's buffers; returns the
-// offset of its first excluded pair.
-__device__ int load_ligand(const SearchArgs& a, const WarpMem& w, int li, int lane) {
+// A ligand's rotamer descriptors and excluded pairs into the warp's buffers (compact
+// builds: pointed at in global memory, read through L1); returns the offset of its first
+// excluded pair.
+template <bool COMPACT>
+__device__ int load_ligand(const SearchArgs& a, WarpMem& w, int li, int lane) {
   const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
   int e0 = 0;
+  if (COMPACT) {
+    w.RD = a.rots + r0;
+    if (R > 0) e0 = (int)__ldg(&a.rots[r0].excl_off);
+    w.EXL = a.excl + e0;
+    return e0;
+  }
   __syncwarp();
   if (R > 0) {
     for (int i = lane; i < 4 * R; i += 32)
-      reinterpret_cast<uint32_t*>(w.RD)[i] = __ldg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i);
+      reinterpret_cast<uint32_t*>(w.RDs)[i] = __ldg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i);
     __syncwarp();
-    e0 = (int)w.RD[0].excl_off;
-    const int ne = (int)w.RD[R - 1].excl_off + w.RD[R - 1].n_excl - e0;
-    for (int i = lane; i < ne; i += 32) w.EXL[i] = __ldg(a.excl + e0 + i);
+    e0 = (int)w.RDs[0].excl_off;
+    const int ne = (int)w.RDs[R - 1].excl_off + w.RDs[R - 1].n_excl - e0;
+    for (int i = lane; i < ne; i += 32) w.EXLs[i] = __ldg(a.excl + e0 + i);
   }
   __syncwarp();
   return e0;
@@ -1029,8 +1074,10 @@ __device__ bool stage_grid(const SearchArgs& a, uint8_t* sg, uint64_t* mbar) {
   return __syncthreads_and((int)ok) != 0;
 }
 
-template <int S, int G, bool LEAN>
-__global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 3 : 1) search_kernel(const __grid_constant__ SearchArgs a) {
+template <int S, int G, int B>
+__global__ void __launch_bounds__(B == BUILD_LEAN ? 256 : (B == BUILD_COMPACT ? 640 : 512), B == BUILD_LEAN ? 3 : 1)
+    search_kernel(const __grid_constant__ SearchArgs a) {
+  constexpr bool PRUNE = B != BUILD_LEAN, COMPACT = B == BUILD_COMPACT;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* sg = nullptr;
@@ -1050,7 +1097,8 @@ __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 3 : 1) search_kernel(
   for (int k = threadIdx.x; k < a.A; k += blockDim.x) cs[k] = angle_entry(k, a.A);
   off += ((size_t)a.A * 8 + 15) / 16 * 16;
   __syncthreads();
-  WarpMem w = warp_mem(smem + off + (size_t)warp * a.warp_bytes, a.nmax, a.fmax, a.mask_words, a.rmax, a.emax);
+  const int warp_bytes = warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax, COMPACT);
+  WarpMem w = warp_mem(smem + off + (size_t)warp * warp_bytes, a.nmax, a.fmax, a.mask_words, a.rmax, a.emax, COMPACT);
   w.CS = cs;
   // items: every (ligand, restart) in queue order, or an explicit list of rows li*O + o;
   // a warp takes a.chunk consecutive items at a time (mostly restarts of one ligand), loads
@@ -1080,9 +1128,9 @@ __global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 3 : 1) search_kernel(
         if (pending) complete<G>(a, sg, w, cur, pending, lane);
         cur = li;
         pending = 0;
-        e0 = load_ligand(a, w, li, lane);
+        e0 = load_ligand<COMPACT>(a, w, li, lane);
       }
-      search_pose<S, G, !LEAN>(a, sg, w, li, o, e0, lane);
+      search_pose<S, G, PRUNE, COMPACT>(a, sg, w, li, o, e0, lane);
       ++pending;
     }
   }
@@ -1264,13 +1312,38 @@ cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
   return e;
 }
 
-template <int S, int G, bool LEAN>
+// Resident blocks per SM of a kernel at a block size and dynamic shared memory, queried
+// once per (kernel, device, shape) and remembered: jobs are planned per call, and the
+// query costs more host time than the search of a single ligand's restarts.
+cudaError_t blocks_per_sm(const void* fn, int threads, size_t smem, int* per_sm) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int, size_t>, int> known;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const auto key = std::make_tuple(fn, dev, threads, smem);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = known.find(key);
+    if (it != known.end()) {
+      *per_sm = it->second;
+      return cudaSuccess;
+    }
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  known[key] = *per_sm;
+  return cudaSuccess;
+}
+
+template <int S, int G, int B>
 cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, LaunchCfg* cfg) {
-  auto k = search_kernel<S, G, LEAN>;
+  auto k = search_kernel<S, G, B>;
   cudaError_t e = raise_smem_limit((const void*)k, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, warps * 32, smem);
+  e = blocks_per_sm((const void*)k, warps * 32, smem, &per_sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long blocks = (long long)per_sm * num_sms;
@@ -1284,12 +1357,29 @@ cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, Lau
   return cudaSuccess;
 }
 
-// ids 1..12: <= 128 registers, one block of up to 16 warps per SM with the grid staged;
-// ids 13..15: <= 80 registers (a little spilled) for up to 24 warps per SM, grid not staged.
-constexpr Tile kTiles[] = {{8, 1, 0}, {8, 2, 0},  {8, 4, 0},  {4, 1, 0}, {4, 2, 0}, {4, 4, 0},
-                           {16, 1, 0}, {16, 2, 0}, {16, 4, 0}, {2, 1, 0}, {2, 2, 0}, {2, 4, 0},
-                           {8, 1, 1}, {8, 2, 1},  {4, 2, 1}};
+// ids 1..12: wide builds (<= 128 registers), one block of up to 16 warps per SM, the grid
+// staged when it fits; ids 13..15: lean builds (<= 80 registers) for up to 24 warps per
+// SM; ids 16..18: compact builds (<= 96 registers, compact per-warp buffers) for about 20
+// warps per SM with large ligands.
+constexpr Tile kTiles[] = {{8, 1, BUILD_WIDE},     {8, 2, BUILD_WIDE},     {8, 4, BUILD_WIDE},
+                           {4, 1, BUILD_WIDE},     {4, 2, BUILD_WIDE},     {4, 4, BUILD_WIDE},
+                           {16, 1, BUILD_WIDE},    {16, 2, BUILD_WIDE},    {16, 4, BUILD_WIDE},
+                           {2, 1, BUILD_WIDE},     {2, 2, BUILD_WIDE},     {2, 4, BUILD_WIDE},
+                           {8, 1, BUILD_LEAN},     {8, 2, BUILD_LEAN},     {4, 2, BUILD_LEAN},
+                           {20, 4, BUILD_COMPACT}, {20, 2, BUILD_COMPACT}, {10, 4, BUILD_COMPACT}};
 constexpr int kLean8x1 = 13;
+
+template <int B>
+cudaError_t plan_build(const SearchArgs& a, const Tile& t, bool tex, size_t smem, int num_sms, LaunchCfg* cfg) {
+  switch (t.slots * 2 + (tex ? 1 : 0)) {
+    case 2: return plan_t<1, GRID_LDG, B>(a, t.warps, smem, num_sms, cfg);
+    case 3: return plan_t<1, GRID_TEX, B>(a, t.warps, smem, num_sms, cfg);
+    case 4: return plan_t<2, GRID_LDG, B>(a, t.warps, smem, num_sms, cfg);
+    case 5: return plan_t<2, GRID_TEX, B>(a, t.warps, smem, num_sms, cfg);
+    case 8: return plan_t<4, GRID_LDG, B>(a, t.warps, smem, num_sms, cfg);
+    default: return plan_t<4, GRID_TEX, B>(a, t.warps, smem, num_sms, cfg);
+  }
+}
 
 }  // namespace
 
@@ -1299,7 +1389,8 @@ int max_smem_grid_bytes() { return 200 * 1024; }
 
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem) {
   const Tile t = tile_get(tile);
-  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax) +
+  const bool compact = t.build == BUILD_COMPACT;
+  size_t s = (size_t)t.warps * (size_t)warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax, compact) +
              ((size_t)a.A * 8 + 15) / 16 * 16;
   if (grid_in_smem) s += (size_t)a.pk.bytes_pad + 16;
   return s;
@@ -1319,31 +1410,18 @@ cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int nu
   const Tile t = tile_get(tile);
   const size_t smem = search_smem_bytes(a, tile, grid_in_smem);
   const bool tex = !grid_in_smem && a.pk.tex != 0;
-  if (t.lean) {
-    if (grid_in_smem) return cudaErrorInvalidConfiguration;
-    switch (t.slots * 2 + (tex ? 1 : 0)) {
-      case 2: return plan_t<1, GRID_LDG, true>(a, t.warps, smem, num_sms, cfg);
-      case 3: return plan_t<1, GRID_TEX, true>(a, t.warps, smem, num_sms, cfg);
-      case 4: return plan_t<2, GRID_LDG, true>(a, t.warps, smem, num_sms, cfg);
-      case 5: return plan_t<2, GRID_TEX, true>(a, t.warps, smem, num_sms, cfg);
-      case 8: return plan_t<4, GRID_LDG, true>(a, t.warps, smem, num_sms, cfg);
-      default: return plan_t<4, GRID_TEX, true>(a, t.warps, smem, num_sms, cfg);
-    }
-  }
   if (grid_in_smem) {
+    if (!tile_stages_grid(t)) return cudaErrorInvalidConfiguration;
     switch (t.slots) {
-      case 1: return plan_t<1, GRID_SMEM, false>(a, t.warps, smem, num_sms, cfg);
-      case 2: return plan_t<2, GRID_SMEM, false>(a, t.warps, smem, num_sms, cfg);
-      default: return plan_t<4, GRID_SMEM, false>(a, t.warps, smem, num_sms, cfg);
+      case 1: return plan_t<1, GRID_SMEM, BUILD_WIDE>(a, t.warps, smem, num_sms, cfg);
+      case 2: return plan_t<2, GRID_SMEM, BUILD_WIDE>(a, t.warps, smem, num_sms, cfg);
+      default: return plan_t<4, GRID_SMEM, BUILD_WIDE>(a, t.warps, smem, num_sms, cfg);
     }
   }
-  switch (t.slots * 2 + (tex ? 1 : 0)) {
-    case 2: return plan_t<1, GRID_LDG, false>(a, t.warps, smem, num_sms, cfg);
-    case 3: return plan_t<1, GRID_TEX, false>(a, t.warps, smem, num_sms, cfg);
-    case 4: return plan_t<2, GRID_LDG, false>(a, t.warps, smem, num_sms, cfg);
-    case 5: return plan_t<2, GRID_TEX, false>(a, t.warps, smem, num_sms, cfg);
-    case 8: return plan_t<4, GRID_LDG, false>(a, t.warps, smem, num_sms, cfg);
-    default: return plan_t<4, GRID_TEX, false>(a, t.warps, smem, num_sms, cfg);
+  switch (t.build) {
+    case BUILD_LEAN: return plan_build<BUILD_LEAN>(a, t, tex, smem, num_sms, cfg);
+    case BUILD_COMPACT: return plan_build<BUILD_COMPACT>(a, t, tex, smem, num_sms, cfg);
+    default: return plan_build<BUILD_WIDE>(a, t, tex, smem, num_sms, cfg);
   }
 }
 

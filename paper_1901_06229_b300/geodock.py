@@ -37,10 +37,12 @@ class GeoDockError(RuntimeError):
         self.status = status
 
 
+# Pointer fields are c_void_p filled with plain addresses (the C side sees the same
+# pointers): building a typed ctypes pointer per array costs more than the search of a
+# single ligand.
 class LigandBatchC(C.Structure):
-    _fields_ = [("n_ligands", C.c_int32), ("atom_off", C.POINTER(C.c_int32)), ("xyz", C.POINTER(C.c_float)),
-                ("bond_off", C.POINTER(C.c_int32)), ("bonds", C.POINTER(C.c_int32)),
-                ("rot_off", C.POINTER(C.c_int32)), ("rot_bond", C.POINTER(C.c_int32))]
+    _fields_ = [("n_ligands", C.c_int32), ("atom_off", C.c_void_p), ("xyz", C.c_void_p),
+                ("bond_off", C.c_void_p), ("bonds", C.c_void_p), ("rot_off", C.c_void_p), ("rot_bond", C.c_void_p)]
 
 
 class SearchParamsC(C.Structure):
@@ -50,14 +52,12 @@ class SearchParamsC(C.Structure):
                 ("rigid_span", C.c_int32), ("rigid_step", C.c_float)]
 
 
+RESULT_FIELDS = ("best_score", "best_orient", "best_angle", "best_xyz", "evals", "pair_tests", "atom_moves",
+                 "reach_tests", "orient_score", "orient_pick", "bump_bits", "best_rigid", "orient_rigid")
+
+
 class ResultBatchC(C.Structure):
-    _fields_ = [("best_score", C.POINTER(C.c_uint32)), ("best_orient", C.POINTER(C.c_int32)),
-                ("best_angle", C.POINTER(C.c_int16)), ("best_xyz", C.POINTER(C.c_float)),
-                ("evals", C.POINTER(C.c_uint64)), ("pair_tests", C.POINTER(C.c_uint64)),
-                ("atom_moves", C.POINTER(C.c_uint64)), ("reach_tests", C.POINTER(C.c_uint64)),
-                ("orient_score", C.POINTER(C.c_uint32)), ("orient_pick", C.POINTER(C.c_int16)),
-                ("bump_bits", C.POINTER(C.c_uint8)), ("best_rigid", C.POINTER(C.c_int16)),
-                ("orient_rigid", C.POINTER(C.c_int16))]
+    _fields_ = [(name, C.c_void_p) for name in RESULT_FIELDS]
 
 
 _lib = None
@@ -112,6 +112,69 @@ def _ptr(a, ct):
     return a.ctypes.data_as(C.POINTER(ct))
 
 
+def _addr(a):
+    """Address of a numpy array's first element."""
+    return a.ctypes.data
+
+
+class Results(dict):
+    """Result arrays by name (see gd_result_batch); .addrs holds their addresses."""
+    addrs = None
+
+
+def result_arrays(L, N, Rt, reps, O, A, debug=False, bumps=False, rigid=True):
+    """Host arrays of one result batch (gd_result_batch), views of one buffer; with debug
+    the per-restart arrays, with bumps the per-candidate bump bits.  Every element is
+    written by gd_fetch_results."""
+    key = (L, N, Rt, reps, O, A, debug, bumps, rigid)
+    lay = _LAYOUTS.get(key)
+    if lay is None:
+        spec = [("best_score", _U32, L, None), ("best_orient", _I32, L, None), ("best_angle", _I16, Rt * reps, None),
+                ("best_xyz", _F32, 3 * N, (N, 3)), ("evals", _U64, L, None), ("pair_tests", _U64, L, None),
+                ("atom_moves", _U64, L, None), ("reach_tests", _U64, L, None)]
+        if rigid:
+            spec.append(("best_rigid", _I16, L, None))
+        if debug:
+            spec += [("orient_score", _U32, L * O, (L, O)), ("orient_pick", _I16, Rt * reps * O, None),
+                     ("orient_rigid", _I16, L * O, (L, O))]
+        if bumps:
+            spec.append(("bump_bits", _U8, Rt * reps * O * A, None))
+        rows, o = [], 0
+        for name, t, n, shape in spec:
+            rows.append((name, t, o, o + n * t.itemsize, shape))
+            o = (o + n * t.itemsize + 15) & ~15
+        lay = (rows, max(o, 16))
+        if len(_LAYOUTS) > 64:
+            _LAYOUTS.clear()
+        _LAYOUTS[key] = lay
+    rows, total = lay
+    buf = np.empty(total, np.uint8)
+    base = buf.ctypes.data
+    out = Results()
+    addrs = out.addrs = {}
+    for name, t, o0, o1, shape in rows:
+        a = buf[o0:o1].view(t)
+        out[name] = a if shape is None else a.reshape(shape)
+        addrs[name] = base + o0
+    return out
+
+
+_LAYOUTS = {}
+_U8, _I16, _I32, _U32, _U64, _F32 = (np.dtype(t) for t in (np.uint8, np.int16, np.int32, np.uint32, np.uint64,
+                                                            np.float32))
+
+
+def result_c(r):
+    """gd_result_batch pointing at the arrays of r (NULL for absent ones)."""
+    addrs = getattr(r, "addrs", None)
+    if addrs is None:  # a caller's own dict of arrays
+        for name in RESULT_FIELDS:
+            if name in r and not r[name].flags.c_contiguous:
+                raise ValueError(f"result array {name} must be C-contiguous")
+        addrs = {name: _addr(r[name]) for name in RESULT_FIELDS if name in r}
+    return ResultBatchC(*(addrs.get(name) for name in RESULT_FIELDS))
+
+
 def _stream_handle(stream):
     if stream is None:
         try:
@@ -133,18 +196,31 @@ def params_c(params, flags=0, tile=0) -> SearchParamsC:
 
 
 class _BatchArrays:
-    """Keeps the contiguous numpy arrays alive while C holds pointers to them."""
+    """Keeps the contiguous numpy arrays alive while C holds pointers to them.  When the
+    batch's arrays are already contiguous in the right types they are used in place, and
+    the view is kept on the batch for the next call while its arrays are the same objects
+    (the library reads their contents at every call)."""
 
-    def __init__(self, batch):
-        self.atom_off = np.ascontiguousarray(batch.atom_off, np.int32)
-        self.xyz = np.ascontiguousarray(batch.xyz, np.float32)
-        self.bond_off = np.ascontiguousarray(batch.bond_off, np.int32)
-        self.bonds = np.ascontiguousarray(batch.bonds, np.int32)
-        self.rot_off = np.ascontiguousarray(batch.rot_off, np.int32)
-        self.rot_bond = np.ascontiguousarray(batch.rot_bond, np.int32)
-        self.c = LigandBatchC(len(self.atom_off) - 1, _ptr(self.atom_off, C.c_int32), _ptr(self.xyz, C.c_float),
-                              _ptr(self.bond_off, C.c_int32), _ptr(self.bonds, C.c_int32),
-                              _ptr(self.rot_off, C.c_int32), _ptr(self.rot_bond, C.c_int32))
+    _TYPES = (("atom_off", np.int32), ("xyz", np.float32), ("bond_off", np.int32), ("bonds", np.int32),
+              ("rot_off", np.int32), ("rot_bond", np.int32))
+
+    def __new__(cls, batch):
+        src = tuple(getattr(batch, name) for name, _ in cls._TYPES)
+        cached = getattr(batch, "_gd_arrays", None)
+        if cached is not None and all(a is b for a, b in zip(cached._src, src)):
+            return cached
+        self = super().__new__(cls)
+        arrs = [np.ascontiguousarray(a, t) for a, (_, t) in zip(src, cls._TYPES)]
+        for (name, _), a in zip(cls._TYPES, arrs):
+            setattr(self, name, a)
+        self._src = src
+        self.c = LigandBatchC(len(self.atom_off) - 1, *(_addr(a) for a in arrs))
+        if all(a is b for a, b in zip(arrs, src)):  # in place: safe to reuse while the arrays stay
+            try:
+                batch._gd_arrays = self
+            except AttributeError:
+                pass
+        return self
 
 
 class Job:
@@ -165,29 +241,8 @@ class Job:
         p = self.params
         O, reps, A = p.n_alpha * p.n_beta * p.n_gamma, p.repetitions, p.n_angles
         Rt = int(self.rot_off[-1]) if len(self.rot_off) else 0
-        r = out if out is not None else dict(
-            best_score=np.zeros(self.L, np.uint32), best_orient=np.zeros(self.L, np.int32),
-            best_angle=np.zeros(Rt * reps, np.int16), best_xyz=np.zeros((self.N, 3), np.float32),
-            evals=np.zeros(self.L, np.uint64), pair_tests=np.zeros(self.L, np.uint64),
-            atom_moves=np.zeros(self.L, np.uint64), reach_tests=np.zeros(self.L, np.uint64),
-            best_rigid=np.zeros(self.L, np.int16))
-        if self.debug and out is None:
-            r["orient_score"] = np.zeros((self.L, O), np.uint32)
-            r["orient_pick"] = np.zeros(Rt * reps * O, np.int16)
-            r["orient_rigid"] = np.zeros((self.L, O), np.int16)
-        if self.bumps and out is None:
-            r["bump_bits"] = np.zeros(Rt * reps * O * A, np.uint8)
-        nul = lambda ct: C.cast(None, C.POINTER(ct))
-        rb = ResultBatchC(_ptr(r["best_score"], C.c_uint32), _ptr(r["best_orient"], C.c_int32),
-                          _ptr(r["best_angle"], C.c_int16), _ptr(r["best_xyz"], C.c_float),
-                          _ptr(r["evals"], C.c_uint64), _ptr(r["pair_tests"], C.c_uint64),
-                          _ptr(r["atom_moves"], C.c_uint64), _ptr(r["reach_tests"], C.c_uint64),
-                          _ptr(r["orient_score"], C.c_uint32) if "orient_score" in r else nul(C.c_uint32),
-                          _ptr(r["orient_pick"], C.c_int16) if "orient_pick" in r else nul(C.c_int16),
-                          _ptr(r["bump_bits"], C.c_uint8) if "bump_bits" in r else nul(C.c_uint8),
-                          _ptr(r["best_rigid"], C.c_int16) if "best_rigid" in r else nul(C.c_int16),
-                          _ptr(r["orient_rigid"], C.c_int16) if "orient_rigid" in r else nul(C.c_int16))
-        st = load().gd_fetch_results(self.ctx.h, self.handle, C.byref(rb), 1 if blocking else 0)
+        r = out if out is not None else result_arrays(self.L, self.N, Rt, reps, O, A, self.debug, self.bumps)
+        st = load().gd_fetch_results(self.ctx.h, self.handle, C.byref(result_c(r)), 1 if blocking else 0)
         if st == GD_ENOTREADY:
             return None
         self.ctx._check(st)
@@ -366,16 +421,8 @@ def dock_noalloc(batch, pocket, params, stream=None, tile=0) -> dict:
     nz, ny, nx = g.shape
     org = np.ascontiguousarray(pocket.origin, np.float32)
     n_lig, n_atoms, Rt = batch.n_ligands, len(batch.xyz), int(batch.rot_off[-1]) if len(batch.rot_off) else 0
-    r = dict(best_score=np.zeros(n_lig, np.uint32), best_orient=np.zeros(n_lig, np.int32),
-             best_angle=np.zeros(Rt * params.repetitions, np.int16), best_xyz=np.zeros((n_atoms, 3), np.float32),
-             evals=np.zeros(n_lig, np.uint64), pair_tests=np.zeros(n_lig, np.uint64),
-             atom_moves=np.zeros(n_lig, np.uint64), reach_tests=np.zeros(n_lig, np.uint64))
-    nul = lambda ct: C.cast(None, C.POINTER(ct))
-    rb = ResultBatchC(_ptr(r["best_score"], C.c_uint32), _ptr(r["best_orient"], C.c_int32),
-                      _ptr(r["best_angle"], C.c_int16), _ptr(r["best_xyz"], C.c_float),
-                      _ptr(r["evals"], C.c_uint64), _ptr(r["pair_tests"], C.c_uint64),
-                      _ptr(r["atom_moves"], C.c_uint64), _ptr(r["reach_tests"], C.c_uint64),
-                      nul(C.c_uint32), nul(C.c_int16), nul(C.c_uint8))
+    r = result_arrays(n_lig, n_atoms, Rt, params.repetitions, params.n_orient, params.n_angles, rigid=False)
+    rb = result_c(r)
     msg = C.create_string_buffer(512)
     st = L.gd_dock_batch_noalloc(_ptr(g, C.c_uint8), nx, ny, nz, float(pocket.spacing), _ptr(org, C.c_float),
                                  C.byref(arrs.c), C.byref(prm), C.byref(rb), _stream_handle(stream), msg, 512)

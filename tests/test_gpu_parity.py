@@ -78,10 +78,13 @@ def test_batched_subset_elementwise(ctx):
     assert st["restarts"] == 24 * 256
 
 
-def test_large_ligands_reduced_restarts(ctx):
+@pytest.mark.parametrize("tile", [0, 16, 17])
+def test_large_ligands_reduced_restarts(ctx, tile):
+    """Large ligands against the oracle with the default tile and the compact builds
+    (96 registers, descriptors read through L1, (u x d) rebuilt from the axis frame)."""
     w = synth.workload_large(6)
     params = synth.SearchParams(2, 2, 2, 128)
-    _, _, st = full_compare(ctx, w.pocket, w.batch, params, min_exact=40)
+    _, _, st = full_compare(ctx, w.pocket, w.batch, params, min_exact=40, tile=tile)
     assert st["restarts"] == 48
 
 
@@ -214,7 +217,7 @@ def test_reach_filter_is_exact(ctx, which):
     assert b["reach_tests"].sum() == 0 and a["reach_tests"].sum() > 0
 
 
-@pytest.mark.parametrize("tile", [9, 14])
+@pytest.mark.parametrize("tile", [9, 14, 16])
 def test_mask_sweep_matches_oracle(ctx, tile):
     """The overflow path of the reach filter (sweeping its bit masks) against the oracle,
     on ligands whose static side spans several 32-atom mask words."""
