@@ -529,13 +529,89 @@ def run_stream(args, world, rank, local):
         "ligands_per_s": thr, "latency_ms": {"p50": p50, "p99": p99}, "runs": runs, "clocks": clk.summary()}))
 
 
+def run_serve(args, world, rank, local):
+    """Streaming screen on the device queue: Poisson arrivals submitted to one running
+    search launch (gd_server: continuous batching on the device, plain exhaustive search
+    of every restart), results collected as they finish; ligands/s and per-ligand latency
+    (finish seen on the host minus arrival) over repeated runs, median and range."""
+    import torch
+    from paper_1901_06229_b300 import geodock as gdk, serve
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    n = args.ligands or 100000
+    w = synth.workload_stream(n, seed_offset=53 + 10 * rank)
+    ctx = gdk.Context(dev, mem_budget_bytes=8 << 30)
+    pk = ctx.load_pocket(w.pocket)
+    R = np.diff(w.batch.rot_off)
+    srv = gdk.Server(ctx, pk, w.params, capacity=args.max_batch * 4, max_atoms=256, max_rotamers=int(R.max()),
+                     idle_ms=200, tile=max(args.tile, 0))
+    # warm-up: the first ligands at once
+    warm = min(2048, n)
+    srv.submit(w.batch, np.arange(warm))
+    got = 0
+    while got < warm:
+        got += len(srv.collect()[0])
+    n_req = max(n, int(np.ceil(args.rate * args.stream_seconds)))
+    runs = []
+    with ClockSampler(dev) as clk:
+        for rep in range(args.stream_repeats):
+            arr = serve.poisson_arrivals(n_req, args.rate, seed=rank + 1000 * rep)
+            lig = np.arange(n_req) % n
+            done_t = np.zeros(n_req)
+            seq0 = None
+            nxt = finished = 0
+            t0 = time.perf_counter()
+            while finished < n_req:
+                now = time.perf_counter() - t0
+                hi = int(np.searchsorted(arr, now, side="right"))
+                if hi > nxt:
+                    take = min(hi, nxt + srv.capacity // 2)
+                    try:
+                        q = srv.submit(w.batch, lig[nxt:take])
+                        seq0 = q - nxt if seq0 is None else seq0
+                        nxt = take
+                    except gdk.GeoDockError as e:
+                        if e.status != gdk.GD_EBUSY:
+                            raise
+                seqs, _, _ = srv.collect(8192)
+                if len(seqs):
+                    done_t[seqs.astype(np.int64) - seq0] = time.perf_counter() - t0
+                    finished += len(seqs)
+                elif hi == nxt:
+                    time.sleep(5e-5)
+            lat = done_t - arr
+            span = float(done_t.max() - arr.min())
+            runs.append({"ligands_per_s": n_req / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "ligands": n_req})
+    st = srv.stats()
+    srv.close()
+    pk.free()
+    ctx.close()
+    if rank != 0:
+        return
+
+    def stat(key):
+        v = np.array([r[key] for r in runs])
+        return {"median": float(np.median(v)), "min": float(v.min()), "max": float(v.max())}
+    print(json.dumps({
+        "metric": "ligands/s and per-ligand latency (device-queue screen, 1 B300)",
+        "value": stat("ligands_per_s")["median"], "unit": "ligands/s", "n_gpus": world,
+        "steps": args.stream_repeats, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators)",
+        "config": workload_config(w, "resident pocket; no flush (serving)") | {
+            "arrivals": f"Poisson, {args.rate:g} ligands/s", "requests_per_run": n_req, "runs": args.stream_repeats,
+            "search": "every restart (plain method)", "capacity": srv.capacity, "budget_bytes": 8 << 30},
+        "ligands_per_s": stat("ligands_per_s"), "latency_ms": {"p50": stat("p50_ms"), "p99": stat("p99_ms")},
+        "server": st, "runs": runs, "clocks": clk.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned", "learned24", "stream", "mlp"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned", "learned24", "stream", "serve", "mlp"])
     ap.add_argument("--rate", type=float, default=100000.0, help="stream: Poisson arrival rate (ligands/s)")
     ap.add_argument("--max-batch", type=int, default=2048, help="stream: largest admitted batch")
     ap.add_argument("--stream-seconds", type=float, default=3.0, help="stream: least offered duration of a run")
@@ -558,6 +634,9 @@ def main():
         return
     if args.workload == "stream":
         run_stream(args, world, rank, local)
+        return
+    if args.workload == "serve":
+        run_serve(args, world, rank, local)
         return
     if args.workload == "mlp":
         run_mlp(args, world, rank, local)

@@ -239,6 +239,63 @@ gd_status gd_autotune(gd_ctx* ctx, const gd_pocket* pocket, const gd_ligand_batc
  * no device memory stays allocated. */
 gd_status gd_measure_peaks(int device, void* stream, double* ffma_per_s, double* lds_u8_per_s);
 
+/* ---- Streaming server: continuous batching into one persistent launch -------------
+ * The paper's hybrid version hands each ligand to whichever thread becomes free (Sec. 4.2,
+ * Listing 3: one task per ligand), and its MPI master sends a node new ligands as soon as
+ * it finishes the last ones (Sec. 5); here ligands that arrive over time join a search
+ * launch that is already running.  A server owns `capacity` slots
+ * for ligands of at most max_atoms atoms, max_rotamers rotamers and max_excluded excluded
+ * pairs in all (0: 16 per rotamer), in device memory counted against the context's
+ * budget, plus mapped (zero-copy) host memory for its ligand records, results and
+ * control words.  gd_server_submit validates and packs ligands into free slots on the
+ * host and publishes them; a persistent launch on the server's own stream takes work,
+ * 4 restarts of one ligand at a time, as soon as it is published, copies each ligand's record into
+ * its slot when it starts it, searches every restart exactly as gd_dock_batch does (same
+ * results, bit for bit) and writes each ligand's results to host memory as soon as its
+ * last restart is done.  An idle launch ends after `idle_ms`; any later call that finds
+ * published work unclaimed launches it again.  Waits on the device are bounded by the SM
+ * clock: a warp that waits longer than about 0.5 s for a slot being staged sets an error,
+ * which the next gd_server_poll / gd_server_collect reports as GD_ETIMEOUT (the server
+ * must then be destroyed; the context stays usable); a blocking gd_server_poll gives up
+ * with GD_ETIMEOUT after 30 s without the result.  tile: 0 = the wide tile with the most warps
+ * whose buffers, sized for the server's largest ligand, fit a block; > 0 a lean or wide
+ * tile (compact tiles, 16-18, are rejected).  Destroy a server before its pocket and its
+ * context.  Not thread-safe: one host thread per
+ * server, or external locking.
+ * Results of ligand seq (numbered from 0 in submission order): gd_server_poll copies them
+ * into a one-ligand gd_result_batch (best_score[1], best_orient[1], best_angle[reps*R],
+ * best_xyz[3*n], counters[1]; debug arrays must be NULL) and frees the slot;
+ * gd_server_collect returns the score and best restart of every finished ligand not
+ * yet returned, oldest first, and frees their slots.  A slot is reused only after its
+ * ligand's results were returned; gd_server_submit answers GD_EBUSY when fewer than
+ * n_sel slots are free. */
+typedef struct gd_server gd_server;
+gd_status gd_server_create(gd_ctx* ctx, const gd_pocket* pocket, const gd_search_params* params, int capacity,
+                           int max_atoms, int max_rotamers, int max_excluded, int idle_ms, gd_server** out);
+/* Submit ligands sel[0 .. n_sel) of `batch` (sel NULL: all of it, in order); the first gets
+ * sequence number *first_seq, the others the following ones. */
+gd_status gd_server_submit(gd_server* srv, const gd_ligand_batch* batch, const int32_t* sel, int32_t n_sel,
+                           uint64_t* first_seq);
+/* Results of ligand seq; blocking = 0 returns GD_ENOTREADY while it is searched. */
+gd_status gd_server_poll(gd_server* srv, uint64_t seq, gd_result_batch* out, int blocking);
+/* Up to max finished ligands: their sequence numbers, best scores and best restarts (any
+ * output pointer may be NULL); *n_out of them. */
+gd_status gd_server_collect(gd_server* srv, uint64_t* seq, uint32_t* best_score, int32_t* best_orient, int max,
+                            int* n_out);
+/* Counters: launches started, launches that ended idle, ligands published, ligands whose
+ * results were returned, work-item tickets taken on the device (4 restarts each; up to
+ * one per warp runs ahead of the published work) and reads of the mapped control words by
+ * the device.  Any pointer may be NULL. */
+gd_status gd_server_stats(gd_server* srv, uint64_t* launches, uint64_t* idle_exits, uint64_t* published,
+                          uint64_t* finished, uint64_t* claimed_items, uint64_t* control_reads);
+/* Testing only: the slot of ligand hold_seq is never released to the warps that wait
+ * for it, so their bounded waits run out (0.2 s here) and the server reports GD_ETIMEOUT;
+ * -1 turns it off.  Takes effect for ligands submitted afterwards. */
+gd_status gd_server_test_hold(gd_server* srv, int64_t hold_seq);
+/* Stop the launch once every published ligand has been claimed, wait for it and free
+ * everything. */
+gd_status gd_server_destroy(gd_server* srv);
+
 /* ---- Docking without allocation --------------------------------------------------
  * The paper has no counterpart: this serves callers that cannot allocate device memory
  * when they dock -- a process whose device memory is already fully reserved by

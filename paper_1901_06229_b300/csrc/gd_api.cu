@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1151,6 +1153,497 @@ gd_status gd_job_free(gd_ctx* c, gd_job* j) {
   if (!c || !j) return GD_OK;
   cudaSetDevice(c->device);
   return job_release(c, j);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- streaming server
+//
+// Host side of the persistent search launch that ligands join while it runs (declared
+// with gd_server_create).  Mapped (zero-copy) host memory holds the control words the
+// launch polls, one packed record per slot and one result row per slot; the device holds
+// the slots' search data and per-restart scratch.  Ligand seq lives in slot seq % cap;
+// a slot is reused only once its ligand's results were returned to the caller.
+
+struct gd_server {
+  gd_ctx* ctx = nullptr;
+  int O = 0, reps = 0, A = 0, cap = 0, amax = 0, rmax = 0, emax = 0, tile = 0, min_sep = 3;
+  bool grid_in_smem = false;
+  SearchArgs args{};
+  gd::ServeArgs sv{};
+  gd::LaunchCfg cfg{};
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ended = nullptr;
+  bool running = false;
+  // mapped host memory: control words | records | result rows
+  char* h_map = nullptr;
+  volatile unsigned long long* h_published = nullptr;
+  volatile int* h_stop = nullptr;
+  volatile int* h_status = nullptr;
+  volatile unsigned long long* h_result_seq = nullptr;
+  char* h_rec = nullptr;
+  uint32_t* h_score = nullptr;
+  int32_t* h_orient = nullptr;
+  uint64_t *h_evals = nullptr, *h_pairs = nullptr, *h_moves = nullptr, *h_reach = nullptr;
+  int16_t* h_rigid = nullptr;
+  int16_t* h_angle = nullptr;
+  float* h_xyz = nullptr;
+  // device memory
+  void* d_mem = nullptr;
+  size_t dev_bytes = 0;
+  unsigned long long* d_work = nullptr;
+  // bookkeeping
+  unsigned long long next_seq = 0;      // ligands published
+  unsigned long long oldest = 0;        // no ligand before this one is still outstanding
+  unsigned long long launches = 0, idle_exits = 0, finished = 0;
+  std::vector<unsigned long long> owner;  // per slot: seq + 1 of the ligand in it, 0 if free
+  std::vector<int32_t> nat, nrot;         // per slot: atoms and rotamers of that ligand
+};
+
+namespace {
+
+// Device-side bounds are counted in SM cycles (the clock every SM has); at the maximum
+// clock of 2.032 GHz these are the times named, at lower clocks longer.
+constexpr double SERVE_CYCLES_PER_NS = 2.032;
+constexpr long long SERVE_WAIT_CYCLES = (long long)(0.5e9 * SERVE_CYCLES_PER_NS);       // a slot being staged
+constexpr long long SERVE_TEST_WAIT_CYCLES = (long long)(0.2e9 * SERVE_CYCLES_PER_NS);  // ... held by a test
+constexpr double SERVE_POLL_LIMIT_S = 30.0;  // a blocking gd_server_poll gives up after this long
+
+// Whether some published ligand has no results yet.
+bool server_unfinished(const gd_server* s) {
+  for (unsigned long long q = s->oldest; q < s->next_seq; ++q) {
+    const int slot = (int)(q % (unsigned long long)s->cap);
+    if (s->owner[slot] == q + 1 && s->h_result_seq[slot] != q + 1) return true;
+  }
+  return false;
+}
+
+// Notice a launch that ended; launch again if a published ligand has no results yet (its
+// items, or tickets parked for them, wait for a launch).
+gd_status server_pump(gd_server* s) {
+  if (s->running) {
+    const cudaError_t e = cudaEventQuery(s->ended);
+    if (e == cudaErrorNotReady) return GD_OK;
+    if (e != cudaSuccess) return fail(GD_ECUDA, "server launch: %s", cudaGetErrorString(e));
+    s->running = false;
+    if (!*s->h_stop && *s->h_status == gd::ERR_NONE) ++s->idle_exits;
+  }
+  if (*s->h_status != gd::ERR_NONE)
+    return fail(GD_ETIMEOUT, *s->h_status == gd::ERR_SLOT_TIMEOUT ? "a server wait for a staged slot timed out"
+                                                                   : "the server's pocket staging wait timed out");
+  if (*s->h_stop || !server_unfinished(s)) return GD_OK;
+  GD_CUDA(gd::launch_serve(s->args, s->sv, s->cfg, s->stream));
+  GD_CUDA(cudaEventRecord(s->ended, s->stream));
+  s->running = true;
+  ++s->launches;
+  return GD_OK;
+}
+
+void server_free(gd_server* s) {
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->ended) cudaEventDestroy(s->ended);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->h_map) cudaFreeHost(s->h_map);
+  dev_release(s->ctx, s->d_mem, s->dev_bytes);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_params* p, int capacity, int max_atoms,
+                           int max_rotamers, int max_excluded, int idle_ms, gd_server** out) {
+  if (!c || !pk || !p || !out) return fail(GD_EINVAL, "NULL argument");
+  gd_status st = check_params(p);
+  if (st) return st;
+  if (p->flags & (GD_FLAG_DEBUG | GD_FLAG_DEBUG_BUMPS | GD_FLAG_TEST_STAGE_TIMEOUT))
+    return fail(GD_EINVAL, "the server keeps no debug outputs and takes no test flags");
+  if (capacity < 1 || capacity > (1 << 20)) return fail(GD_EINVAL, "capacity %d outside [1, 2^20]", capacity);
+  if (max_atoms < 2 || max_atoms > GD_MAX_ATOMS) return fail(GD_EINVAL, "max_atoms %d outside [2, %d]", max_atoms,
+                                                             GD_MAX_ATOMS);
+  if (max_rotamers < 0 || max_rotamers > GD_MAX_ROTAMERS)
+    return fail(GD_EINVAL, "max_rotamers %d outside [0, %d]", max_rotamers, GD_MAX_ROTAMERS);
+  if (max_excluded == 0) max_excluded = 16 * std::max(1, max_rotamers);
+  if (max_excluded < 1 || max_excluded > GD_MAX_EXCLUDED * std::max(1, max_rotamers))
+    return fail(GD_EINVAL, "max_excluded %d outside [1, %d]", max_excluded, GD_MAX_EXCLUDED * std::max(1, max_rotamers));
+  if (idle_ms < 1 || idle_ms > 60000) return fail(GD_EINVAL, "idle_ms %d outside [1, 60000]", idle_ms);
+  const int O = p->n_alpha * p->n_beta * p->n_gamma;
+  if (max_rotamers * p->repetitions > 32767) return fail(GD_EINVAL, "too many steps per ligand");
+  cudaSetDevice(c->device);
+  gd_server* s = new gd_server();
+  s->ctx = c;
+  s->O = O;
+  s->reps = p->repetitions;
+  s->A = p->n_angles;
+  s->cap = capacity;
+  s->amax = (max_atoms + 3) / 4 * 4;  // 4-byte aligned per-slot permutation rows
+  s->rmax = std::max(1, max_rotamers);
+  s->emax = max_excluded;
+  s->min_sep = p->min_bond_sep;
+  s->owner.assign(capacity, 0);
+  s->nat.assign(capacity, 0);
+  s->nrot.assign(capacity, 0);
+  const long long cap = capacity, amax = s->amax, rmax = s->rmax, emax = s->emax;
+  const long long rec_stride = gd::serve_rec_bytes(s->amax, s->rmax, s->emax);
+  // mapped host memory
+  size_t o = 0;
+  const size_t o_ctrl = o;   o = align_up(o + 256, 256);
+  const size_t o_rec = o;    o = align_up(o + (size_t)(cap * rec_stride), 256);
+  const size_t o_rseq = o;   o = align_up(o + 8 * cap, 256);
+  const size_t o_score = o;  o = align_up(o + 4 * cap, 256);
+  const size_t o_orient = o; o = align_up(o + 4 * cap, 256);
+  const size_t o_evals = o;  o = align_up(o + 8 * cap, 256);
+  const size_t o_pairs = o;  o = align_up(o + 8 * cap, 256);
+  const size_t o_moves = o;  o = align_up(o + 8 * cap, 256);
+  const size_t o_reach = o;  o = align_up(o + 8 * cap, 256);
+  const size_t o_rigid = o;  o = align_up(o + 2 * cap, 256);
+  const size_t o_angle = o;  o = align_up(o + 2 * (size_t)(cap * rmax * s->reps), 256);
+  const size_t o_xyz = o;    o = align_up(o + 12 * (size_t)(cap * amax), 256);
+  const size_t map_bytes = o;
+  cudaError_t e = cudaHostAlloc((void**)&s->h_map, map_bytes, cudaHostAllocMapped);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->h_map = nullptr;
+    server_free(s);
+    return fail(GD_ENOMEM, "cudaHostAlloc(%zu, mapped): %s", map_bytes, cudaGetErrorString(e));
+  }
+  memset(s->h_map, 0, map_bytes);
+  char* h = s->h_map;
+  s->h_published = (volatile unsigned long long*)(h + o_ctrl);
+  s->h_stop = (volatile int*)(h + o_ctrl + 8);
+  s->h_status = (volatile int*)(h + o_ctrl + 12);
+  s->h_rec = h + o_rec;
+  s->h_result_seq = (volatile unsigned long long*)(h + o_rseq);
+  s->h_score = (uint32_t*)(h + o_score);
+  s->h_orient = (int32_t*)(h + o_orient);
+  s->h_evals = (uint64_t*)(h + o_evals);
+  s->h_pairs = (uint64_t*)(h + o_pairs);
+  s->h_moves = (uint64_t*)(h + o_moves);
+  s->h_reach = (uint64_t*)(h + o_reach);
+  s->h_rigid = (int16_t*)(h + o_rigid);
+  s->h_angle = (int16_t*)(h + o_angle);
+  s->h_xyz = (float*)(h + o_xyz);
+  char* hd = nullptr;  // the same memory as the device addresses it
+  e = cudaHostGetDevicePointer((void**)&hd, s->h_map, 0);
+  if (e != cudaSuccess) {
+    server_free(s);
+    return fail(GD_ECUDA, "cudaHostGetDevicePointer: %s", cudaGetErrorString(e));
+  }
+  // device memory
+  o = 0;
+  const size_t d_work = o;    o += 8;
+  const size_t d_pub = o;     o += 8;
+  const size_t d_stop = o;    o += 8;
+  const size_t d_poll = o;    o += 8;
+  const size_t d_polls = o;   o += 8;
+  const size_t d_dummy = o;   o = align_up(o + 8, 256);
+  const size_t d_parked = o;  o = align_up(o + 8 * (size_t)c->num_sms * 64, 256);  // every resident warp
+  const size_t d_ready = o;   o = align_up(o + 8 * cap, 256);
+  const size_t d_done = o;    o = align_up(o + 4 * cap, 256);
+  const size_t d_n = o;       o = align_up(o + 4 * cap, 256);
+  const size_t d_r = o;       o = align_up(o + 4 * cap, 256);
+  const size_t d_err = o;     o = align_up(o + 4, 256);
+  const size_t d_xc = o;      o = align_up(o + 16 * (size_t)(cap * amax), 256);
+  const size_t d_perm = o;    o = align_up(o + (size_t)(cap * amax), 256);
+  const size_t d_rots = o;    o = align_up(o + 16 * (size_t)(cap * rmax), 256);
+  const size_t d_excl = o;    o = align_up(o + 2 * (size_t)(cap * emax), 256);
+  const size_t d_pscore = o;  o = align_up(o + 4 * (size_t)(cap * O), 256);
+  const size_t d_ppick = o;   o = align_up(o + 2 * (size_t)(cap * rmax * s->reps * O), 256);
+  const size_t d_ppairs = o;  o = align_up(o + 8 * (size_t)(cap * O), 256);
+  const size_t d_preach = o;  o = align_up(o + 8 * (size_t)(cap * O), 256);
+  const size_t d_prigid = o;  o = align_up(o + 2 * (size_t)(cap * O), 256);
+  const size_t d_rmat = o;    o = align_up(o + 36 * (size_t)O, 256);
+  const size_t d_quat = o;    o = align_up(o + 16 * (size_t)O, 256);
+  s->dev_bytes = o;
+  if ((st = dev_alloc(c, s->dev_bytes, &s->d_mem))) {
+    s->d_mem = nullptr;
+    server_free(s);
+    return st;
+  }
+  char* d = (char*)s->d_mem;
+  s->d_work = (unsigned long long*)(d + d_work);
+  e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ended, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, d_xc, s->stream);  // counters, slot words
+  if (e != cudaSuccess) {
+    server_free(s);
+    return fail(GD_ECUDA, "server set-up: %s", cudaGetErrorString(e));
+  }
+  // search arguments in the slot layout
+  SearchArgs& a = s->args;
+  a.pk = pk->dev;
+  a.L = capacity;
+  a.xc = (float4*)(d + d_xc);
+  a.perm = (const uint8_t*)(d + d_perm);
+  a.rots = (const RotDesc*)(d + d_rots);
+  a.excl = (const uint16_t*)(d + d_excl);
+  a.slot_n = (const int32_t*)(d + d_n);
+  a.slot_r = (const int32_t*)(d + d_r);
+  a.slot_amax = s->amax;
+  a.slot_rmax = s->rmax;
+  a.na = p->n_alpha;
+  a.nb = p->n_beta;
+  a.ng = p->n_gamma;
+  a.O = O;
+  a.A = p->n_angles;
+  a.reps = p->repetitions;
+  {
+    const float ih = a.pk.inv_h, bd = p->bump_dist * ih, rd = (p->bump_dist + gd::REACH_MARGIN) * ih;
+    a.thr2 = bd * bd;
+    a.reach2 = rd * rd;
+  }
+  a.use_filter = (p->flags & GD_FLAG_NO_FILTER) ? 0 : 1;
+  a.mask_sweep = (p->flags & GD_FLAG_MASK_SWEEP) ? 1 : 0;
+  a.rigid_span = p->rigid_span;
+  a.rigid_step = p->rigid_step;
+  a.rigid_n = p->rigid_span > 0 ? (2 * p->rigid_span + 1) * (2 * p->rigid_span + 1) * (2 * p->rigid_span + 1) : 0;
+  a.best_score = (uint32_t*)(hd + o_score);
+  a.best_orient = (int32_t*)(hd + o_orient);
+  a.best_angle = (int16_t*)(hd + o_angle);
+  a.best_xyz = (float*)(hd + o_xyz);
+  a.evals = (unsigned long long*)(hd + o_evals);
+  a.pair_tests = (unsigned long long*)(hd + o_pairs);
+  a.atom_moves = (unsigned long long*)(hd + o_moves);
+  a.reach_tests = (unsigned long long*)(hd + o_reach);
+  a.best_rigid = (int16_t*)(hd + o_rigid);
+  a.pose_score = (uint32_t*)(d + d_pscore);
+  a.pose_pick = (int16_t*)(d + d_ppick);
+  a.pose_pairs = (unsigned long long*)(d + d_ppairs);
+  a.pose_reach = (unsigned long long*)(d + d_preach);
+  a.pose_rigid = (int16_t*)(d + d_prigid);
+  a.rmat = (float*)(d + d_rmat);
+  a.quat = (float4*)(d + d_quat);
+  a.done = (int32_t*)(d + d_done);
+  a.work = (unsigned long long*)(d + d_dummy);  // written by the restart-table launch only
+  a.err = (int32_t*)(d + d_err);
+  a.bump_bits = nullptr;
+  // per-warp buffers sized for the largest ligand the server accepts: the fragment is the
+  // smaller side of its bond (at most half the atoms)
+  a.nmax = s->amax;
+  a.fmax = std::max(1, s->amax / 2);
+  a.mask_words = 1;
+  for (int f = 1; f <= s->amax / 2; ++f) a.mask_words = std::max(a.mask_words, f * ((s->amax - f + 31) / 32));
+  a.rmax = s->rmax;
+  a.emax = s->emax;
+  // tile: the built-in default (never a compact one) unless the caller named one
+  int tile = p->tile;
+  if (tile < 0) {
+    server_free(s);
+    return fail(GD_EINVAL, "the server takes tile 0 (default) or a lean or wide tile id");
+  }
+  if (tile == 0) {  // the wide tile with the most warps whose buffers fit a block (16, 8, 4, 2)
+    const int two = a.A >= 64 ? 1 : 0;
+    const int ids[4] = {7 + two, 1 + two, 4 + two, 10 + two};
+    tile = ids[3];
+    for (int id : ids)
+      if (gd::search_smem_bytes(a, id, false) <= 227 * 1024) {
+        tile = id;
+        break;
+      }
+  }
+  if (gd::tile_get(tile).build == gd::BUILD_COMPACT) {
+    server_free(s);
+    return fail(GD_EINVAL, "tile %d is a compact build: the server needs a lean or wide tile", tile);
+  }
+  const size_t smem_cap = 227 * 1024;
+  s->tile = tile;
+  s->grid_in_smem = gd::tile_stages_grid(gd::tile_get(tile)) && pk->dev.bytes_pad <= gd::max_smem_grid_bytes() &&
+                    gd::search_smem_bytes(a, tile, true) <= smem_cap;
+  if (!s->grid_in_smem && gd::search_smem_bytes(a, tile, false) > smem_cap) {
+    server_free(s);
+    return fail(GD_EINVAL, "tile %d needs more shared memory than a block has for %d-atom ligands", tile, max_atoms);
+  }
+  e = gd::plan_serve(a, tile, s->grid_in_smem, c->num_sms, &s->cfg);
+  if (e != cudaSuccess) {
+    server_free(s);
+    return fail(GD_ECUDA, "server launch shape: %s", cudaGetErrorString(e));
+  }
+  gd::ServeArgs& v = s->sv;
+  v.published = (const unsigned long long*)(hd + o_ctrl);
+  v.stop = (const int*)(hd + o_ctrl + 8);
+  v.status = (int*)(hd + o_ctrl + 12);
+  v.work = s->d_work;
+  v.pub_dev = (unsigned long long*)(d + d_pub);
+  v.stop_dev = (unsigned long long*)(d + d_stop);
+  v.last_poll = (unsigned long long*)(d + d_poll);
+  v.slot_ready = (unsigned long long*)(d + d_ready);
+  v.result_seq = (unsigned long long*)(hd + o_rseq);
+  v.rec = (const unsigned char*)(hd + o_rec);
+  v.rec_stride = rec_stride;
+  v.cap = capacity;
+  v.emax = s->emax;
+  v.chunk = 4;
+  v.chunks = (O + 3) / 4;
+  v.idle_cycles = (long long)((double)idle_ms * 1e6 * SERVE_CYCLES_PER_NS);
+  v.wait_cycles = SERVE_WAIT_CYCLES;
+  v.polls = (unsigned long long*)(d + d_polls);
+  v.parked = (unsigned long long*)(d + d_parked);
+  v.hold_seq = -1;
+  e = gd::launch_restart_tables(a, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    server_free(s);
+    return fail(GD_ECUDA, "restart tables: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  g_err.clear();
+  return GD_OK;
+}
+
+gd_status gd_server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t* sel, int32_t n_sel,
+                           uint64_t* first_seq) {
+  if (!s || !b) return fail(GD_EINVAL, "NULL argument");
+  cudaSetDevice(s->ctx->device);
+  const int LB = b->n_ligands;
+  const int n = sel ? n_sel : LB;
+  if (LB < 0 || n < 0) return fail(GD_EINVAL, "negative ligand count");
+  if (n > 0 && (!b->atom_off || !b->xyz || !b->bond_off || !b->bonds || !b->rot_off || !b->rot_bond))
+    return fail(GD_EINVAL, "batch has a NULL array");
+  if (n > s->cap) return fail(GD_EINVAL, "%d ligands for %d slots", n, s->cap);
+  if (*s->h_status != gd::ERR_NONE) return fail(GD_ETIMEOUT, "a server wait for a staged slot timed out");
+  for (int i = 0; i < n; ++i)
+    if (s->owner[(s->next_seq + i) % s->cap]) return fail(GD_EBUSY, "no free slot: return finished results first");
+  const long long stride = s->sv.rec_stride;
+  for (int i = 0; i < n; ++i) {
+    const int li = sel ? sel[i] : i;
+    if (li < 0 || li >= LB) return fail(GD_EINVAL, "sel[%d] = %d outside [0, %d)", i, li, LB);
+    const int a0 = b->atom_off[li], na = b->atom_off[li + 1] - a0;
+    const int b0 = b->bond_off[li], nb = b->bond_off[li + 1] - b0;
+    const int r0 = b->rot_off[li], R = b->rot_off[li + 1] - r0;
+    if (na > s->amax || na < 0) return fail(GD_EINVAL, "ligand %d: %d atoms > the server's %d", li, na, s->amax);
+    if (R > s->rmax || R < 0) return fail(GD_EINVAL, "ligand %d: %d rotamers > the server's %d", li, R, s->rmax);
+    const int slot = (int)((s->next_seq + i) % s->cap);
+    char* rec = s->h_rec + (size_t)slot * (size_t)stride;
+    size_t ne = 0;
+    gd_status st = gd::pack_ligand_fixed(fail, li, na, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R,
+                                         b->rot_bond + r0, s->min_sep, (float4*)(rec + 16),
+                                         (uint8_t*)(rec + gd::serve_rec_perm_dev(s->amax)),
+                                         (RotDesc*)(rec + gd::serve_rec_rots_dev(s->amax)),
+                                         (uint16_t*)(rec + gd::serve_rec_excl_dev(s->amax, s->rmax)), (size_t)s->emax,
+                                         &ne, nullptr);
+    if (st) return st;  // nothing of this call is published: the slots stay free
+    const gd::ServeRecHeader hdr{na, R, (int32_t)ne, 0};
+    memcpy(rec, &hdr, sizeof hdr);
+    s->nat[slot] = na;
+    s->nrot[slot] = R;
+  }
+  for (int i = 0; i < n; ++i) s->owner[(s->next_seq + i) % s->cap] = s->next_seq + i + 1;
+  if (first_seq) *first_seq = s->next_seq;
+  s->next_seq += n;
+  std::atomic_thread_fence(std::memory_order_seq_cst);  // the records before the count
+  *s->h_published = s->next_seq;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  return server_pump(s);
+}
+
+gd_status gd_server_poll(gd_server* s, uint64_t seq, gd_result_batch* r, int blocking) {
+  if (!s || !r) return fail(GD_EINVAL, "NULL argument");
+  if (r->orient_score || r->orient_pick || r->bump_bits || r->orient_rigid)
+    return fail(GD_EINVAL, "the server keeps no debug outputs");
+  cudaSetDevice(s->ctx->device);
+  const int slot = (int)(seq % (uint64_t)s->cap);
+  if (seq >= s->next_seq || s->owner[slot] != seq + 1) return fail(GD_EINVAL, "ligand %llu is not outstanding",
+                                                                   (unsigned long long)seq);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    gd_status st = server_pump(s);
+    if (st) return st;
+    if (s->h_result_seq[slot] == seq + 1) break;
+    if (!blocking) return GD_ENOTREADY;
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > SERVE_POLL_LIMIT_S)
+      return fail(GD_ETIMEOUT, "no result for ligand %llu within %.0f s", (unsigned long long)seq, SERVE_POLL_LIMIT_S);
+    std::this_thread::yield();
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  const int na = s->nat[slot], R = s->nrot[slot];
+  if (r->best_score) r->best_score[0] = s->h_score[slot];
+  if (r->best_orient) r->best_orient[0] = s->h_orient[slot];
+  if (r->best_angle) memcpy(r->best_angle, s->h_angle + (size_t)slot * s->rmax * s->reps, 2 * (size_t)R * s->reps);
+  if (r->best_xyz) memcpy(r->best_xyz, s->h_xyz + 3 * (size_t)slot * s->amax, 12 * (size_t)na);
+  if (r->evals) r->evals[0] = s->h_evals[slot];
+  if (r->pair_tests) r->pair_tests[0] = s->h_pairs[slot];
+  if (r->atom_moves) r->atom_moves[0] = s->h_moves[slot];
+  if (r->reach_tests) r->reach_tests[0] = s->h_reach[slot];
+  if (r->best_rigid) r->best_rigid[0] = s->h_rigid[slot];
+  s->owner[slot] = 0;
+  ++s->finished;
+  return GD_OK;
+}
+
+gd_status gd_server_collect(gd_server* s, uint64_t* seqs, uint32_t* score, int32_t* orient, int max, int* n_out) {
+  if (!s || !n_out || max < 0) return fail(GD_EINVAL, "bad argument");
+  cudaSetDevice(s->ctx->device);
+  *n_out = 0;
+  gd_status st = server_pump(s);
+  if (st) return st;
+  int k = 0;
+  for (unsigned long long q = s->oldest; q < s->next_seq && k < max; ++q) {
+    const int slot = (int)(q % (unsigned long long)s->cap);
+    if (s->owner[slot] != q + 1) {  // returned already
+      if (q == s->oldest) ++s->oldest;
+      continue;
+    }
+    if (s->h_result_seq[slot] != q + 1) continue;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    if (seqs) seqs[k] = q;
+    if (score) score[k] = s->h_score[slot];
+    if (orient) orient[k] = s->h_orient[slot];
+    s->owner[slot] = 0;
+    ++s->finished;
+    ++k;
+    if (q == s->oldest) ++s->oldest;
+  }
+  *n_out = k;
+  return GD_OK;
+}
+
+gd_status gd_server_stats(gd_server* s, uint64_t* launches, uint64_t* idle_exits, uint64_t* published,
+                          uint64_t* finished, uint64_t* claimed_items, uint64_t* control_reads) {
+  if (!s) return fail(GD_EINVAL, "NULL argument");
+  cudaSetDevice(s->ctx->device);
+  if (s->running && cudaEventQuery(s->ended) == cudaSuccess) server_pump(s);
+  if (launches) *launches = s->launches;
+  if (idle_exits) *idle_exits = s->idle_exits;
+  if (published) *published = s->next_seq;
+  if (finished) *finished = s->finished;
+  if (claimed_items || control_reads) {  // device counters, read on a stream of their own (the launch may run)
+    unsigned long long v[2] = {0, 0};
+    cudaStream_t st = nullptr;
+    GD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaError_t e = cudaMemcpyAsync(&v[0], s->sv.work, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v[1], s->sv.polls, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess) return fail(GD_ECUDA, "server counters: %s", cudaGetErrorString(e));
+    if (claimed_items) *claimed_items = v[0];
+    if (control_reads) *control_reads = v[1];
+  }
+  return GD_OK;
+}
+
+gd_status gd_server_test_hold(gd_server* s, int64_t hold_seq) {
+  if (!s) return fail(GD_EINVAL, "NULL argument");
+  cudaSetDevice(s->ctx->device);
+  // the hold and the wait bound travel with the launch parameters: a running launch is
+  // left to end (it does once idle), and the next one takes them
+  s->sv.hold_seq = hold_seq;
+  s->sv.wait_cycles = hold_seq >= 0 ? SERVE_TEST_WAIT_CYCLES : SERVE_WAIT_CYCLES;
+  if (s->running) {
+    GD_CUDA(cudaEventSynchronize(s->ended));
+    s->running = false;
+    if (!*s->h_stop && *s->h_status == gd::ERR_NONE) ++s->idle_exits;
+  }
+  return GD_OK;
+}
+
+gd_status gd_server_destroy(gd_server* s) {
+  if (!s) return GD_OK;
+  cudaSetDevice(s->ctx->device);
+  *s->h_stop = 1;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  server_free(s);
+  return GD_OK;
 }
 
 }  // extern "C"

@@ -100,7 +100,53 @@ struct SearchArgs {
   int16_t* pose_rigid;        // [L*O] (scratch) chosen rigid candidate per restart
   int16_t* best_rigid;        // [L] (output) of the best restart
   int stage_extra_bytes;      // testing: bytes the grid-staging barrier expects beyond the grid
+  // slot layout (the streaming server): ligand li's atoms start at li * slot_amax and its
+  // rotamers at li * slot_rmax, with counts slot_n[li] / slot_r[li]; NULL: the CSR offsets
+  const int32_t* slot_n;
+  const int32_t* slot_r;
+  int slot_amax, slot_rmax;
 };
+
+// The streaming server's persistent launch (see gd_server_create).  Ligand seq lives in
+// slot seq % cap.  The host publishes ligands by raising *published (mapped host memory)
+// after writing their records; warps take tickets for work items (item t: ligand
+// t / chunks, restarts [4 (t % chunks), ...)) and start on one once it is published; a
+// launch that ends idle parks its warps' unpublished tickets for the next launch.
+struct ServeArgs {
+  const unsigned long long* published;  // (mapped) ligands published so far
+  const int* stop;                      // (mapped) 1: exit once every published item is claimed
+  int* status;                          // (mapped) 0 fine, ERR_SLOT_TIMEOUT after a wait ran out
+  unsigned long long* work;             // items claimed so far (device; persists across launches)
+  unsigned long long* pub_dev;          // device copy of *published
+  unsigned long long* stop_dev;         // device copy of *stop
+  unsigned long long* last_poll;        // globaltimer of the last read of the mapped words
+  unsigned long long* slot_ready;       // [cap] seq + 1 once the slot holds ligand seq
+  unsigned long long* result_seq;       // (mapped) [cap] seq + 1 once ligand seq's results are written
+  const unsigned char* rec;             // (mapped) [cap] ligand records of rec_stride bytes
+  long long rec_stride;
+  int cap, emax;                        // slots; excluded pairs per slot
+  int chunk, chunks;                    // restarts per item; items per ligand
+  long long idle_cycles;                // an idle warp exits after this many SM cycles without work
+  long long wait_cycles;                // bound (SM cycles) of a wait for a slot being staged
+  long long hold_seq;                   // testing: the ligand whose slot is never released (-1)
+  unsigned long long* polls;            // reads of the mapped control words (device counter)
+  unsigned long long* parked;           // [warps of the launch] ticket + 1 a warp held when its launch ended idle
+};
+
+// A ligand record in the server's mapped host memory (slot s at rec + s * rec_stride):
+// header, then xyz float4[amax] (preorder, w unused), perm uint8[amax], RotDesc[rmax]
+// (excl_off relative to the record's excluded pairs), excl uint16[emax].
+struct ServeRecHeader {
+  int32_t n, R, n_excl, pad;
+};
+__host__ __device__ inline long long serve_rec_perm_dev(int amax) { return 16 + 16LL * amax; }
+__host__ __device__ inline long long serve_rec_rots_dev(int amax) { return (16 + 17LL * amax + 15) / 16 * 16; }
+__host__ __device__ inline long long serve_rec_excl_dev(int amax, int rmax) {
+  return serve_rec_rots_dev(amax) + 16LL * rmax;
+}
+__host__ __device__ inline long long serve_rec_bytes(int amax, int rmax, int emax) {
+  return (serve_rec_excl_dev(amax, rmax) + 2LL * emax + 127) / 128 * 128;
+}
 
 // Margin of the reach filter (A).  FP32 rounding moves a rotated atom by ~1e-5 A at
 // most, so a pair whose closest approach over the whole turn exceeds bump_dist by
@@ -128,7 +174,7 @@ __host__ __device__ inline int frag_atoms(int n, const RotDesc& d) {
   return d.comp ? n - sub : sub;
 }
 
-enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1 };
+enum : int { ERR_NONE = 0, ERR_STAGE_TIMEOUT = 1, ERR_SLOT_TIMEOUT = 2 };
 
 // Items per work-queue grab: 4 once there are at least 8 per warp a full GPU holds
 // (148 SMs x 32 warps), so chunking never idles warps on small batches.
@@ -177,6 +223,11 @@ cudaError_t launch_selection(const SearchArgs& a, const float* pred, int k, int 
 // Launch the search: the pose-setup kernel (which also zeroes the work counter and the
 // per-ligand completion counters) and the search kernel, on `stream`.
 cudaError_t launch_search(const SearchArgs& a, const LaunchCfg& cfg, cudaStream_t stream);
+// The streaming server's persistent launch (every SM full; lean and wide builds only) and
+// the restart tables it reads (pose-setup kernel without ligands; a.work is written).
+cudaError_t plan_serve(const SearchArgs& a, int tile, bool grid_in_smem, int num_sms, LaunchCfg* cfg);
+cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& sv, const LaunchCfg& cfg, cudaStream_t stream);
+cudaError_t launch_restart_tables(const SearchArgs& a, cudaStream_t stream);
 size_t search_smem_bytes(const SearchArgs& a, int tile, bool grid_in_smem);
 int max_smem_grid_bytes();
 // Tile used for tile 0 (the built-in default) given the batch's buffer sizes.

@@ -32,6 +32,7 @@
 // path (near list, masks, none) can change a result.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -171,6 +172,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // a3: x <- R_o (x0 - c_lig), coordinates relative to the pocket centre, kept in grid
 // units (x inv_h + shift).  The centred coordinates x0 - c_lig and the restart
 // rotations R_o come from pose_setup_kernel.
+template <bool SRV>
 __device__ void place(const SearchArgs& a, float4* X, int a0, int n, int o, int lane) {
   const float* r = a.rmat + 9 * (size_t)o;
   const float r00 = __ldg(r + 0), r01 = __ldg(r + 1), r02 = __ldg(r + 2);
@@ -178,7 +180,9 @@ __device__ void place(const SearchArgs& a, float4* X, int a0, int n, int o, int 
   const float r20 = __ldg(r + 6), r21 = __ldg(r + 7), r22 = __ldg(r + 8);
 #pragma unroll 2
   for (int i = lane; i < n; i += 32) {
-    const float4 d = __ldg(a.xc + a0 + i);
+    // the server's slots are rewritten while it runs: read them coherently (L2), not
+    // through the read-only path
+    const float4 d = SRV ? __ldcg(a.xc + a0 + i) : __ldg(a.xc + a0 + i);
     const float x = __fmaf_rn(r00, d.x, __fmaf_rn(r01, d.y, __fmul_rn(r02, d.z)));
     const float y = __fmaf_rn(r10, d.x, __fmaf_rn(r11, d.y, __fmul_rn(r12, d.z)));
     const float z = __fmaf_rn(r20, d.x, __fmaf_rn(r21, d.y, __fmul_rn(r22, d.z)));
@@ -244,6 +248,23 @@ __global__ void __launch_bounds__(256) pose_setup_kernel(const __grid_constant__
       const float4 v = x0[i];
       a.xc[a0 + i] = make_float4(__fsub_rn(v.x, cx), __fsub_rn(v.y, cy), __fsub_rn(v.z, cz), 0.f);
     }
+  }
+}
+
+// Ligand li's first atom a0 / atom count n and first rotamer r0 / rotamer count R: from the
+// CSR offsets of a batch, or (SRV, the streaming server) from its slot.
+template <bool SRV>
+__device__ __forceinline__ void lig_span(const SearchArgs& a, int li, int& a0, int& n, int& r0, int& R) {
+  if (SRV) {
+    a0 = li * a.slot_amax;
+    n = __ldcg(a.slot_n + li);
+    r0 = li * a.slot_rmax;
+    R = __ldcg(a.slot_r + li);
+  } else {
+    a0 = a.atom_off[li];
+    n = a.atom_off[li + 1] - a0;
+    r0 = a.rot_off[li];
+    R = a.rot_off[li + 1] - r0;
   }
 }
 
@@ -864,9 +885,13 @@ __device__ int rigid_align(const SearchArgs& a, const uint8_t* sg, float4* X, in
   return m;
 }
 
-// a10: reduce over the ligand's restarts, replay the winner, write the results.
-template <int G>
-__device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int lane) {
+// a10: reduce over the ligand's restarts, replay the winner, write the results.  SRV (the
+// streaming server): the results go to the slot's row of the mapped result arrays, then
+// the slot's completion counter is cleared and result_seq raised (system scope) so the
+// host sees them.
+template <int G, bool SRV>
+__device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int lane,
+                         const ServeArgs* sv) {
   float4* X = w.X;
   const int O = a.O;
   unsigned best = 0;
@@ -887,14 +912,14 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   }
   const int ob = (int)(0xFFFFu - (best & 0xFFFFu));
   const unsigned sb = (best >> 16) - 1u;
-  const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
-  const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
+  int a0, n, r0, R;
+  lig_span<SRV>(a, li, a0, n, r0, R);
   const size_t pick_base = (size_t)r0 * a.reps * O + (size_t)ob * a.reps * R;
   unsigned long long fsum = 0;  // sum of fragment sizes over the rotamers
   for (int r = lane; r < R; r += 32) {
-    const RotDesc* d = a.rots + r0 + r;
-    const int sub = (int)__ldg(&d->hi) - (int)__ldg(&d->lo);
-    fsum += (unsigned long long)(__ldg(&d->comp) ? n - sub : sub);
+    const RotDesc d = w.RD[r];  // the ligand's descriptors (this warp's copy, or global memory)
+    const int sub = (int)d.hi - (int)d.lo;
+    fsum += (unsigned long long)(d.comp ? n - sub : sub);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(FULL, fsum, off);
@@ -909,7 +934,7 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   }
   for (int s = lane; s < a.reps * R; s += 32)
     a.best_angle[(size_t)r0 * a.reps + s] = __ldcg(a.pose_pick + pick_base + s);
-  place(a, X, a0, n, ob, lane);
+  place<SRV>(a, X, a0, n, ob, lane);
   int rig = 0;
   if (a.rigid_n > 1) {
     rig = __ldcg(a.pose_rigid + (size_t)li * O + ob);
@@ -927,21 +952,33 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
     }
   for (int i = lane; i < n; i += 32) {
     const float4 v = X[i];
-    float* dst = a.best_xyz + 3 * ((size_t)a0 + a.perm[a0 + i]);
+    float* dst = a.best_xyz + 3 * ((size_t)a0 + (SRV ? __ldcg(a.perm + a0 + i) : a.perm[a0 + i]));
     dst[0] = __fadd_rn(__fmul_rn(__fsub_rn(v.x, a.pk.shift[0]), a.pk.h), a.pk.centre[0]);
     dst[1] = __fadd_rn(__fmul_rn(__fsub_rn(v.y, a.pk.shift[1]), a.pk.h), a.pk.centre[1]);
     dst[2] = __fadd_rn(__fmul_rn(__fsub_rn(v.z, a.pk.shift[2]), a.pk.h), a.pk.centre[2]);
   }
   __syncwarp();
+  if (SRV) {
+    // every lane's result stores before the flag the host polls
+    __threadfence_system();
+    __syncwarp();
+    if (lane == 0) {
+      a.done[li] = 0;  // the slot's next ligand starts its count from zero
+      const unsigned long long seq1 = __ldcg(sv->slot_ready + li);  // seq + 1
+      __threadfence_system();
+      asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(sv->result_seq + li), "l"(seq1) : "memory");
+    }
+    __syncwarp();
+  }
 }
 
-template <int S, int G, bool PRUNE, bool COMPACT>
+template <int S, int G, bool PRUNE, bool COMPACT, bool SRV>
 __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int o, int e0,
                             int lane) {
   float4* X = w.X;
-  const int a0 = a.atom_off[li], n = a.atom_off[li + 1] - a0;
-  const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
-  place(a, X, a0, n, o, lane);
+  int a0, n, r0, R;
+  lig_span<SRV>(a, li, a0, n, r0, R);
+  place<SRV>(a, X, a0, n, o, lane);
   {
     const int m = a.rigid_n > 1 ? rigid_align<G>(a, sg, X, n, lane) : 0;
     if (lane == 0 && a.pose_rigid) a.pose_rigid[(size_t)li * a.O + o] = (int16_t)m;
@@ -992,9 +1029,11 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
 // A ligand's rotamer descriptors and excluded pairs into the warp's buffers (compact
 // builds: pointed at in global memory, read through L1); returns the offset of its first
 // excluded pair.
-template <bool COMPACT>
+template <bool COMPACT, bool SRV>
 __device__ int load_ligand(const SearchArgs& a, WarpMem& w, int li, int lane) {
-  const int r0 = a.rot_off[li], R = a.rot_off[li + 1] - r0;
+  static_assert(!(COMPACT && SRV), "the server's slots are copied into each warp's buffers");
+  int a0, n, r0, R;
+  lig_span<SRV>(a, li, a0, n, r0, R);
   int e0 = 0;
   if (COMPACT) {
     w.RD = a.rots + r0;
@@ -1005,11 +1044,12 @@ __device__ int load_ligand(const SearchArgs& a, WarpMem& w, int li, int lane) {
   __syncwarp();
   if (R > 0) {
     for (int i = lane; i < 4 * R; i += 32)
-      reinterpret_cast<uint32_t*>(w.RDs)[i] = __ldg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i);
+      reinterpret_cast<uint32_t*>(w.RDs)[i] = SRV ? __ldcg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i)
+                                                  : __ldg(reinterpret_cast<const uint32_t*>(a.rots + r0) + i);
     __syncwarp();
     e0 = (int)w.RDs[0].excl_off;
     const int ne = (int)w.RDs[R - 1].excl_off + w.RDs[R - 1].n_excl - e0;
-    for (int i = lane; i < ne; i += 32) w.EXLs[i] = __ldg(a.excl + e0 + i);
+    for (int i = lane; i < ne; i += 32) w.EXLs[i] = SRV ? __ldcg(a.excl + e0 + i) : __ldg(a.excl + e0 + i);
   }
   __syncwarp();
   return e0;
@@ -1017,15 +1057,16 @@ __device__ int load_ligand(const SearchArgs& a, WarpMem& w, int li, int lane) {
 
 // Completion of `done` poses of ligand li by this warp: the warp that completes the
 // ligand's count reduces its restarts (a10); the fence orders the poses' results first.
-template <int G>
-__device__ void complete(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int done, int lane) {
+template <int G, bool SRV>
+__device__ void complete(const SearchArgs& a, const uint8_t* sg, const WarpMem& w, int li, int done, int lane,
+                         const ServeArgs* sv = nullptr) {
   __threadfence();
   int prev = 0;
   if (lane == 0) prev = atomicAdd(a.done + li, done);
   prev = __shfl_sync(FULL, prev, 0);
   if (prev + done == (a.item_cnt ? a.item_cnt[li] : a.O)) {
     __threadfence();
-    finalize<G>(a, sg, w, li, lane);
+    finalize<G, SRV>(a, sg, w, li, lane, sv);
   }
 }
 
@@ -1125,16 +1166,238 @@ __global__ void __launch_bounds__(B == BUILD_LEAN ? 256 : (B == BUILD_COMPACT ? 
         o = (int)(q % (unsigned long long)a.O);
       }
       if (li != cur) {
-        if (pending) complete<G>(a, sg, w, cur, pending, lane);
+        if (pending) complete<G, false>(a, sg, w, cur, pending, lane);
         cur = li;
         pending = 0;
-        e0 = load_ligand<COMPACT>(a, w, li, lane);
+        e0 = load_ligand<COMPACT, false>(a, w, li, lane);
       }
-      search_pose<S, G, PRUNE, COMPACT>(a, sg, w, li, o, e0, lane);
+      search_pose<S, G, PRUNE, COMPACT, false>(a, sg, w, li, o, e0, lane);
       ++pending;
     }
   }
-  if (pending) complete<G>(a, sg, w, cur, pending, lane);
+  if (pending) complete<G, false>(a, sg, w, cur, pending, lane);
+}
+
+// ---- the streaming server's persistent launch ---------------------------------------
+//
+// Continuous batching into one running launch: the host writes each arriving ligand's
+// record into its slot of mapped host memory and raises a published count; each warp
+// takes a ticket for the next work item (4 restarts of one ligand) and starts on it once
+// it is published; a ticket still unpublished when the launch ends idle is parked for the
+// same warp of the next launch, which goes on from the same device-side counter.  The warp that claims a ligand's first item copies its record into
+// the slot's device arrays (centred coordinates computed as the pose-setup kernel does)
+// and releases the slot; warps with the ligand's later items wait for that (bounded).
+// The warp that completes a ligand's restarts writes its results into the slot's row of
+// the mapped result arrays and raises the slot's result sequence.  Every wait is bounded
+// by the SM clock: an idle launch exits after idle_cycles, a slot wait that runs out sets
+// ERR_SLOT_TIMEOUT in the mapped status word and ends the warp.
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// A word of mapped host memory: fetched again over the bus (cached copies of system
+// memory count as stale), then a system-scope fence orders the reads after it.
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+  const unsigned long long v = __ldcv(p);
+  asm volatile("fence.acq_rel.sys;" ::: "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Lane 0 of warp gw (its position in the grid, the same in every launch): take the next
+// work item and wait until it is published (0, *t set); 1 when the host asked the launch
+// to stop (the ticket is dropped: nothing more is published); 2 when the item was not
+// published within idle_cycles SM cycles -- the ticket is then parked in parked[gw] and
+// taken up again by the same grid position of the next launch, so no item is lost.
+// Tickets come from one atomicAdd each, so warps never retry against each other.  The
+// mapped control words are read by one warp at a time, at most every 2 us of the global
+// timer, and in any case by a warp whose own last read is about 0.5 ms of its SM clock
+// old (so no timer can keep the launch from seeing new work); between checks a waiting
+// warp sleeps 64 ns doubling up to 4 us.
+__device__ int serve_claim(const ServeArgs& s, int gw, unsigned long long* t, long long& my_poll) {
+  unsigned long long tk = s.parked[gw];
+  if (tk) {
+    s.parked[gw] = 0ull;
+    tk -= 1ull;
+  } else {
+    tk = atomicAdd(s.work, 1ull);
+  }
+  const long long c0 = clock64();
+  unsigned sleep_ns = 64;
+  for (;;) {
+    if (tk < ld_acquire_gpu(s.pub_dev) * (unsigned long long)s.chunks) {
+      *t = tk;
+      return 0;
+    }
+    const long long c = clock64();
+    const unsigned long long now = globaltimer_ns();
+    const unsigned long long last = ld_relaxed_gpu(s.last_poll);
+    const bool due = now - last > 2000ull && now >= last && atomicCAS(s.last_poll, last, now) == last;
+    if (due || c - my_poll > 1000000LL) {
+      my_poll = c;
+      const unsigned long long ph = ld_acquire_sys(s.published);
+      const int stop = __ldcv(s.stop);
+      asm volatile("red.release.gpu.global.max.u64 [%0], %1;" ::"l"(s.pub_dev), "l"(ph) : "memory");
+      if (stop) atomicExch(s.stop_dev, 1ull);
+      atomicAdd(s.polls, 1ull);
+      if (tk < ph * (unsigned long long)s.chunks) continue;
+    }
+    if (ld_relaxed_gpu(s.stop_dev)) return 1;
+    if (c - c0 > s.idle_cycles) {
+      s.parked[gw] = tk + 1ull;
+      return 2;
+    }
+    __nanosleep(sleep_ns);
+    sleep_ns = sleep_ns < 4096u ? 2u * sleep_ns : 4096u;
+  }
+}
+
+// The warp that claimed ligand seq's first item: its record (mapped host memory, read
+// with cache-bypassing loads) into slot `slot`, then the slot released to the other items.
+__device__ void serve_stage(const SearchArgs& a, const ServeArgs& s, int slot, unsigned long long seq, int lane) {
+  const unsigned char* rec = s.rec + (size_t)slot * (size_t)s.rec_stride;
+  const int4 h = __ldcv(reinterpret_cast<const int4*>(rec));
+  const int amax = a.slot_amax, rmax = a.slot_rmax;
+  // the host validated these against the slot sizes; clamped again so that no record can
+  // make this warp write outside its slot
+  const int n = min(max(h.x, 1), amax), R = min(max(h.y, 0), rmax), ne = min(max(h.z, 0), s.emax);
+  const float4* x0 = reinterpret_cast<const float4*>(rec + 16);
+  // centroid and centred coordinates with the pose-setup kernel's arithmetic and order
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = __ldcv(x0 + i);
+    sx = __fadd_rn(sx, v.x);
+    sy = __fadd_rn(sy, v.y);
+    sz = __fadd_rn(sz, v.z);
+  }
+  sx = warp_sum_f(sx);
+  sy = warp_sum_f(sy);
+  sz = warp_sum_f(sz);
+  const float cx = __fdiv_rn(sx, (float)n), cy = __fdiv_rn(sy, (float)n), cz = __fdiv_rn(sz, (float)n);
+  float4* xc = a.xc + (size_t)slot * amax;
+  for (int i = lane; i < n; i += 32) {
+    const float4 v = __ldcv(x0 + i);
+    xc[i] = make_float4(__fsub_rn(v.x, cx), __fsub_rn(v.y, cy), __fsub_rn(v.z, cz), 0.f);
+  }
+  const unsigned char* perm = rec + serve_rec_perm_dev(amax);
+  uint8_t* dperm = const_cast<uint8_t*>(a.perm) + (size_t)slot * amax;
+  for (int i = lane; i < n; i += 32) dperm[i] = __ldcv(perm + i);
+  const uint4* rots = reinterpret_cast<const uint4*>(rec + serve_rec_rots_dev(amax));
+  uint4* drots = reinterpret_cast<uint4*>(const_cast<RotDesc*>(a.rots) + (size_t)slot * rmax);
+  for (int r = lane; r < R; r += 32) {
+    uint4 d = __ldcv(rots + r);
+    d.w += (unsigned)(slot * s.emax);  // excl_off: into the slot's excluded pairs
+    drots[r] = d;
+  }
+  const unsigned short* ex = reinterpret_cast<const unsigned short*>(rec + serve_rec_excl_dev(amax, rmax));
+  uint16_t* dex = const_cast<uint16_t*>(a.excl) + (size_t)slot * s.emax;
+  for (int i = lane; i < ne; i += 32) dex[i] = __ldcv(ex + i);
+  if (lane == 0) {
+    const_cast<int32_t*>(a.slot_n)[slot] = n;
+    const_cast<int32_t*>(a.slot_r)[slot] = R;
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0 && (long long)seq != s.hold_seq)
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(s.slot_ready + slot), "l"(seq + 1ull) : "memory");
+  __syncwarp();
+}
+
+// Wait (bounded) until ligand seq's slot is staged; false when the wait ran out.
+__device__ bool serve_wait(const ServeArgs& s, int slot, unsigned long long seq, int lane) {
+  int ok = 0;
+  if (lane == 0) {
+    const long long c0 = clock64();
+    for (;;) {
+      if (ld_acquire_gpu(s.slot_ready + slot) == seq + 1ull) {
+        ok = 1;
+        break;
+      }
+      if (clock64() - c0 > s.wait_cycles) break;
+      __nanosleep(128);
+    }
+  }
+  ok = __shfl_sync(FULL, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+template <int S, int G, int B>
+__global__ void __launch_bounds__(B == BUILD_LEAN ? 256 : 512, B == BUILD_LEAN ? 3 : 1)
+    serve_kernel(const __grid_constant__ SearchArgs a, const __grid_constant__ ServeArgs sv) {
+  static_assert(B != BUILD_COMPACT, "the server copies descriptors into each warp's buffers");
+  constexpr bool PRUNE = B != BUILD_LEAN;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* sg = nullptr;
+  size_t off = 0;
+  if (G == GRID_SMEM) {
+    sg = smem;
+    off = (size_t)a.pk.bytes_pad;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + off);
+    off += 16;
+    if (!stage_grid(a, sg, mbar)) {
+      if (threadIdx.x == 0) {
+        atomicExch(a.err, ERR_STAGE_TIMEOUT);
+        *reinterpret_cast<volatile int*>(sv.status) = ERR_STAGE_TIMEOUT;
+        __threadfence_system();
+      }
+      return;
+    }
+  }
+  float2* cs = reinterpret_cast<float2*>(smem + off);
+  for (int k = threadIdx.x; k < a.A; k += blockDim.x) cs[k] = angle_entry(k, a.A);
+  off += ((size_t)a.A * 8 + 15) / 16 * 16;
+  __syncthreads();
+  const int warp_bytes = warp_smem_bytes(a.nmax, a.fmax, a.mask_words, a.rmax, a.emax, false);
+  WarpMem w = warp_mem(smem + off + (size_t)warp * warp_bytes, a.nmax, a.fmax, a.mask_words, a.rmax, a.emax, false);
+  w.CS = cs;
+  unsigned long long cur_seq = ~0ull;
+  int e0 = 0;
+  long long my_poll = clock64();
+  const int gw = (int)(blockIdx.x * (blockDim.x >> 5)) + warp;
+  for (;;) {
+    unsigned long long t = 0;
+    int st = 0;
+    if (lane == 0) st = serve_claim(sv, gw, &t, my_poll);
+    st = __shfl_sync(FULL, st, 0);
+    t = __shfl_sync(FULL, t, 0);
+    if (st) break;
+    const unsigned long long seq = t / (unsigned long long)sv.chunks;
+    const int c = (int)(t % (unsigned long long)sv.chunks);
+    const int slot = (int)(seq % (unsigned long long)sv.cap);
+    if (c == 0) {
+      serve_stage(a, sv, slot, seq, lane);
+    } else if (!serve_wait(sv, slot, seq, lane)) {
+      if (lane == 0) {
+        *reinterpret_cast<volatile int*>(sv.status) = ERR_SLOT_TIMEOUT;
+        __threadfence_system();
+      }
+      break;
+    }
+    if (seq != cur_seq) {
+      cur_seq = seq;
+      e0 = load_ligand<false, true>(a, w, slot, lane);
+    }
+    const int o0 = c * sv.chunk, o1 = o0 + sv.chunk < a.O ? o0 + sv.chunk : a.O;
+    for (int o = o0; o < o1; ++o) search_pose<S, G, PRUNE, false, true>(a, sg, w, slot, o, e0, lane);
+    // completed right away: a ligand's result must not wait for this warp's next item
+    complete<G, true>(a, sg, w, slot, o1 - o0, lane, &sv);
+  }
 }
 
 // ---- features of the learned orientation proposer -----------------------------------
@@ -1423,6 +1686,64 @@ cudaError_t plan_search(const SearchArgs& a, int tile, bool grid_in_smem, int nu
     case BUILD_COMPACT: return plan_build<BUILD_COMPACT>(a, t, tex, smem, num_sms, cfg);
     default: return plan_build<BUILD_WIDE>(a, t, tex, smem, num_sms, cfg);
   }
+}
+
+namespace {
+
+template <int S, int G, int B>
+cudaError_t plan_serve_t(int warps, size_t smem, int num_sms, LaunchCfg* cfg) {
+  auto k = serve_kernel<S, G, B>;
+  cudaError_t e = raise_smem_limit((const void*)k, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = blocks_per_sm((const void*)k, warps * 32, smem, &per_sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cfg->fn = (const void*)k;
+  cfg->blocks = (unsigned)(per_sm * num_sms);  // persistent: every SM full
+  cfg->threads = (unsigned)(warps * 32);
+  cfg->smem = smem;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t plan_serve(const SearchArgs& a, int tile, bool grid_in_smem, int num_sms, LaunchCfg* cfg) {
+  const Tile t = tile_get(tile);
+  if (t.build == BUILD_COMPACT) return cudaErrorInvalidConfiguration;
+  const size_t smem = search_smem_bytes(a, tile, grid_in_smem);
+  if (grid_in_smem) {
+    if (!tile_stages_grid(t)) return cudaErrorInvalidConfiguration;
+    switch (t.slots) {
+      case 1: return plan_serve_t<1, GRID_SMEM, BUILD_WIDE>(t.warps, smem, num_sms, cfg);
+      case 2: return plan_serve_t<2, GRID_SMEM, BUILD_WIDE>(t.warps, smem, num_sms, cfg);
+      default: return plan_serve_t<4, GRID_SMEM, BUILD_WIDE>(t.warps, smem, num_sms, cfg);
+    }
+  }
+  if (!a.pk.tex) return cudaErrorInvalidConfiguration;  // the server reads the grid through the texture
+  if (t.build == BUILD_LEAN) {
+    if (t.slots == 1) return plan_serve_t<1, GRID_TEX, BUILD_LEAN>(t.warps, smem, num_sms, cfg);
+    if (t.slots == 2) return plan_serve_t<2, GRID_TEX, BUILD_LEAN>(t.warps, smem, num_sms, cfg);
+    return cudaErrorInvalidConfiguration;
+  }
+  switch (t.slots) {
+    case 1: return plan_serve_t<1, GRID_TEX, BUILD_WIDE>(t.warps, smem, num_sms, cfg);
+    case 2: return plan_serve_t<2, GRID_TEX, BUILD_WIDE>(t.warps, smem, num_sms, cfg);
+    default: return plan_serve_t<4, GRID_TEX, BUILD_WIDE>(t.warps, smem, num_sms, cfg);
+  }
+}
+
+cudaError_t launch_serve(const SearchArgs& a, const ServeArgs& sv, const LaunchCfg& cfg, cudaStream_t st) {
+  void* args[] = {const_cast<SearchArgs*>(&a), const_cast<ServeArgs*>(&sv)};
+  return cudaLaunchKernel(cfg.fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+cudaError_t launch_restart_tables(const SearchArgs& a, cudaStream_t st) {
+  SearchArgs t = a;  // rotations and quaternions of every restart only: no ligands
+  t.L = 0;
+  const int blocks = (int)std::min(1024LL, std::max(1LL, ((long long)a.O + 255) / 256));
+  pose_setup_kernel<<<blocks, 256, 0, st>>>(t);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_features(const SearchArgs& a, __nv_bfloat16* Xb, float* Xf, int num_sms, cudaStream_t st) {

@@ -8,6 +8,7 @@ fails loudly: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 import os
 
 import numpy as np
@@ -28,7 +29,9 @@ STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_EBUDGET", 4: 
 EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_free_pocket",
            "gd_dock_batch", "gd_fetch_results", "gd_job_launch", "gd_job_download", "gd_job_bytes", "gd_job_free",
            "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc",
-           "gd_prepare_batch", "gd_prepare_batch_sel", "gd_measure_peaks", "gd_job_info"]
+           "gd_prepare_batch", "gd_prepare_batch_sel", "gd_measure_peaks", "gd_job_info",
+           "gd_server_create", "gd_server_submit", "gd_server_poll", "gd_server_collect", "gd_server_stats",
+           "gd_server_test_hold", "gd_server_destroy"]
 
 
 class GeoDockError(RuntimeError):
@@ -86,6 +89,13 @@ def load():
     L.gd_job_free.argtypes = [vp, vp]
     L.gd_job_bytes.argtypes = [vp, vp, P(C.c_uint64), P(C.c_uint64)]
     L.gd_job_info.argtypes = [vp, vp, P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_int), P(C.c_size_t)]
+    L.gd_server_create.argtypes = [vp, vp, P(SearchParamsC), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(vp)]
+    L.gd_server_submit.argtypes = [vp, P(LigandBatchC), vp, C.c_int32, P(C.c_uint64)]
+    L.gd_server_poll.argtypes = [vp, C.c_uint64, P(ResultBatchC), C.c_int]
+    L.gd_server_collect.argtypes = [vp, vp, vp, vp, C.c_int, P(C.c_int)]
+    L.gd_server_stats.argtypes = [vp] + [P(C.c_uint64)] * 6
+    L.gd_server_test_hold.argtypes = [vp, C.c_int64]
+    L.gd_server_destroy.argtypes = [vp]
     L.gd_check_batch.argtypes = [P(LigandBatchC), P(SearchParamsC)]
     L.gd_prepare_batch.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), vp, P(vp)]
     L.gd_prepare_batch_sel.argtypes = [vp, vp, P(LigandBatchC), P(C.c_int32), C.c_int32, P(SearchParamsC), vp,
@@ -308,10 +318,14 @@ class Job:
 class Pocket:
     def __init__(self, ctx, handle):
         self.ctx, self.handle = ctx, handle
+        self._servers = weakref.WeakSet()  # servers searching this pocket: closed before it is freed
 
     def free(self):
         if self.handle:
-            load().gd_free_pocket(self.ctx.h, self.handle)
+            for srv in list(self._servers):
+                srv.close()
+            if self.ctx.h:
+                load().gd_free_pocket(self.ctx.h, self.handle)
             self.handle = None
 
 
@@ -325,6 +339,7 @@ class Context:
         if st:
             raise GeoDockError(st, L.gd_last_error(None).decode())
         self.h = h
+        self._servers = weakref.WeakSet()  # closed before the context is
 
     def _check(self, st):
         if st:
@@ -332,6 +347,8 @@ class Context:
 
     def close(self):
         if self.h:
+            for srv in list(self._servers):
+                srv.close()
             load().gd_destroy(self.h)
             self.h = None
 
@@ -388,6 +405,93 @@ class Context:
         self._check(load().gd_autotune(self.h, pocket.handle, C.byref(arrs.c), C.byref(prm), int(max_ligands),
                                        _stream_handle(stream), C.byref(t), C.byref(ms)))
         return t.value, ms.value
+
+
+class Server:
+    """gd_server: ligands submitted over time join one running search launch (continuous
+    batching on the device); results come back per ligand, numbered in submission order.
+    The pocket must stay loaded while the server exists."""
+
+    def __init__(self, ctx, pocket, params, capacity=4096, max_atoms=256, max_rotamers=64, max_excluded=0,
+                 idle_ms=200, tile=0):
+        self.ctx, self.params = ctx, params
+        self.h = None
+        h = C.c_void_p()
+        prm = params_c(params, 0, tile)
+        ctx._check(load().gd_server_create(ctx.h, pocket.handle, C.byref(prm), int(capacity), int(max_atoms),
+                                           int(max_rotamers), int(max_excluded), int(idle_ms), C.byref(h)))
+        self.h = h
+        ctx._servers.add(self)
+        pocket._servers.add(self)
+        self.capacity = capacity
+        self._sizes = {}  # seq -> (atoms, rotamers) of ligands not yet returned in full
+
+    def submit(self, batch, sel=None) -> int:
+        """Submit ligands sel of batch (all when None); returns the first sequence number
+        (GeoDockError GD_EBUSY when there are not enough free slots)."""
+        arrs = _BatchArrays(batch)
+        first = C.c_uint64()
+        if sel is None:
+            n = batch.n_ligands
+            self.ctx._check(load().gd_server_submit(self.h, C.byref(arrs.c), None, n, C.byref(first)))
+            idx = range(n)
+        else:
+            sel = np.ascontiguousarray(sel, np.int32)
+            n = len(sel)
+            self.ctx._check(load().gd_server_submit(self.h, C.byref(arrs.c), C.c_void_p(_addr(sel)), n,
+                                                    C.byref(first)))
+            idx = sel
+        na, nr = np.diff(batch.atom_off), np.diff(batch.rot_off)
+        for k, i in enumerate(idx):
+            self._sizes[first.value + k] = (int(na[i]), int(nr[i]))
+        return first.value
+
+    def poll(self, seq, blocking=True):
+        """Full results of ligand seq (one-ligand result arrays), or None if not ready."""
+        n, R = self._sizes[seq]
+        r = result_arrays(1, n, R, self.params.repetitions, 1, 1)
+        st = load().gd_server_poll(self.h, int(seq), C.byref(result_c(r)), 1 if blocking else 0)
+        if st == GD_ENOTREADY:
+            return None
+        self.ctx._check(st)
+        del self._sizes[seq]
+        return r
+
+    def collect(self, max_n=4096):
+        """(seqs, best scores, best restarts) of the finished ligands not returned yet."""
+        seq = np.empty(max_n, np.uint64)
+        sc = np.empty(max_n, np.uint32)
+        ob = np.empty(max_n, np.int32)
+        k = C.c_int()
+        self.ctx._check(load().gd_server_collect(self.h, C.c_void_p(_addr(seq)), C.c_void_p(_addr(sc)),
+                                                 C.c_void_p(_addr(ob)), int(max_n), C.byref(k)))
+        n = k.value
+        for q in seq[:n].tolist():
+            self._sizes.pop(q, None)
+        return seq[:n], sc[:n], ob[:n]
+
+    def stats(self):
+        v = [C.c_uint64() for _ in range(6)]
+        self.ctx._check(load().gd_server_stats(self.h, *(C.byref(x) for x in v)))
+        return dict(zip(("launches", "idle_exits", "published", "finished", "claimed_items", "control_reads"),
+                        (x.value for x in v)))
+
+    def test_hold(self, seq):
+        """Testing only: the slot of ligand seq is never released on the device (-1: off)."""
+        self.ctx._check(load().gd_server_test_hold(self.h, int(seq)))
+
+    def close(self):
+        """Destroy the server (before its context and pocket go; they close it otherwise)."""
+        if self.h:
+            if self.ctx.h:
+                load().gd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def check_batch(batch, params) -> None:

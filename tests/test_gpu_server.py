@@ -1,0 +1,126 @@
+"""The streaming server: ligands submitted over time join one running search launch.
+
+Each result must be bit-for-bit what gd_dock_batch gives the same ligand (the server runs
+the same search on its slots), whether the ligand is submitted alone or while others are
+being searched, when slots are reused, and across launches that end idle and start
+again.  A slot held back on the device (test hook) makes the bounded waits run out: the
+server then reports GD_ETIMEOUT and the context stays usable.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1901_06229_b300 import geodock as gdk
+from paper_1901_06229_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("best_score", "best_orient", "best_angle", "best_xyz", "evals", "pair_tests", "atom_moves", "reach_tests",
+        "best_rigid")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gdk.Context(0)
+    yield c
+    c.close()
+
+
+def _alone(ctx, pk, batch, params, i):
+    job = ctx.dock_batch(pk, batch.subset([i]), params)
+    out = job.fetch()
+    job.free()
+    return out
+
+
+def _same(got, ref, what):
+    for k in KEYS:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{what}: {k}")
+
+
+def test_results_equal_dock_batch_alone_and_in_the_mix(ctx):
+    w = synth.workload_stream(96, seed_offset=70)
+    pk = ctx.load_pocket(w.pocket)
+    srv = gdk.Server(ctx, pk, w.params, capacity=256, max_atoms=256, max_rotamers=48)
+    # one ligand alone, then the rest in waves that arrive while earlier ones are searched
+    s0 = srv.submit(w.batch, [0])
+    alone = srv.poll(s0)
+    seqs = {}
+    order = np.random.default_rng(3).permutation(np.arange(1, 96))
+    for wave in np.array_split(order, 6):
+        first = srv.submit(w.batch, wave)
+        for k, i in enumerate(wave):
+            seqs[first + k] = int(i)
+        time.sleep(0.002)
+    got = {q: srv.poll(q) for q in sorted(seqs)}
+    print(srv.stats())
+    ref = ctx.dock_batch(pk, w.batch, w.params).fetch()
+    ao, ro = np.asarray(w.batch.atom_off), np.asarray(w.batch.rot_off)
+    view = lambda r, i: dict(best_score=r["best_score"][i:i + 1], best_orient=r["best_orient"][i:i + 1],
+                             best_angle=r["best_angle"][ro[i]:ro[i + 1]], best_xyz=r["best_xyz"][ao[i]:ao[i + 1]],
+                             evals=r["evals"][i:i + 1], pair_tests=r["pair_tests"][i:i + 1],
+                             atom_moves=r["atom_moves"][i:i + 1], reach_tests=r["reach_tests"][i:i + 1],
+                             best_rigid=r["best_rigid"][i:i + 1])
+    _same(alone, view(ref, 0), "ligand 0 alone")
+    _same(alone, _alone(ctx, pk, w.batch, w.params, 0), "ligand 0 as a one-ligand batch")
+    for q, i in seqs.items():
+        _same(got[q], view(ref, i), f"ligand {i} in the mix")
+    srv.close()
+    pk.free()
+
+
+def test_slots_are_reused_and_idle_launches_restart(ctx):
+    w = synth.workload_stream(80, seed_offset=71)
+    pk = ctx.load_pocket(w.pocket)
+    srv = gdk.Server(ctx, pk, w.params, capacity=16, max_atoms=256, max_rotamers=48, idle_ms=20)
+    ref = ctx.dock_batch(pk, w.batch, w.params).fetch()
+    got_s, got_o, first_of = {}, {}, {}
+    nxt = done = 0
+    t_end = time.time() + 60
+    for phase_end in (40, 80):  # between the phases the launch runs out of work and ends
+        while done < phase_end:
+            assert time.time() < t_end, (done, nxt, srv.stats())
+            while nxt < phase_end:
+                try:
+                    q = srv.submit(w.batch, [nxt])
+                except gdk.GeoDockError as e:
+                    assert e.status == gdk.GD_EBUSY  # all 16 slots hold unreturned ligands
+                    break
+                first_of[q] = nxt
+                nxt += 1
+            seq, sc, ob = srv.collect()
+            for q, a, b in zip(seq.tolist(), sc.tolist(), ob.tolist()):
+                got_s[first_of[q]], got_o[first_of[q]] = a, b
+            done += len(seq)
+        time.sleep(0.1)
+    st = srv.stats()
+    print(st)
+    assert st["launches"] >= 2 and st["idle_exits"] >= 1 and st["finished"] == 80
+    np.testing.assert_array_equal([got_s[i] for i in range(80)], ref["best_score"])
+    np.testing.assert_array_equal([got_o[i] for i in range(80)], ref["best_orient"])
+    small = gdk.Server(ctx, pk, w.params, capacity=4, max_atoms=20, max_rotamers=8)
+    with pytest.raises(gdk.GeoDockError) as e:  # a ligand larger than the server's slots
+        small.submit(w.batch, [int(np.argmax(np.diff(w.batch.atom_off)))])
+    assert e.value.status == gdk.GD_EINVAL
+    small.close()
+    srv.close()
+    pk.free()
+
+
+def test_a_held_slot_times_out_and_the_context_stays_usable(ctx):
+    w = synth.workload_stream(8, seed_offset=72)
+    pk = ctx.load_pocket(w.pocket)
+    srv = gdk.Server(ctx, pk, w.params, capacity=8, max_atoms=256, max_rotamers=48, idle_ms=50)
+    srv.test_hold(2)  # ligand 2's slot is never released to its later work items
+    first = srv.submit(w.batch)
+    t0 = time.time()
+    with pytest.raises(gdk.GeoDockError) as e:
+        for q in range(first, first + 8):
+            srv.poll(q)
+    print(f"timed out after {time.time() - t0:.2f} s: {e.value}")
+    assert e.value.status == gdk.GD_ETIMEOUT
+    srv.close()
+    out = ctx.dock_batch(pk, w.batch, w.params).fetch()  # the context still docks
+    assert len(out["best_score"]) == 8 and np.all(out["best_score"] > 0)
+    pk.free()
