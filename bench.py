@@ -71,6 +71,10 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
+    "8849191a14128210": {("batched-4096lig-64grid", 14): 4568832 + 1177856,
+                         ("batched-4096lig-64grid", 15): 4556544 + 1146880,
+                         ("large-512lig-128grid", 16): 2858752 + 9216,
+                         ("large-512lig-128grid", 18): 2807040 + 11264},
     "ad511480c64b7604": {("batched-4096lig-64grid", 14): 4564992 + 1341440,
                          ("batched-4096lig-64grid", 15): 4736256 + 1323008,
                          ("large-512lig-128grid", 9): 3233280 + 5632},
@@ -85,6 +89,10 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
+    "8849191a14128210": {("batched-4096lig-64grid", 14): 8469406720,
+                         ("batched-4096lig-64grid", 15): 8469510627,
+                         ("large-512lig-128grid", 16): 15486849117,
+                         ("large-512lig-128grid", 18): 15486908104},
     "ad511480c64b7604": {("batched-4096lig-64grid", 14): 8448360711,
                          ("batched-4096lig-64grid", 15): 8448465499,
                          ("large-512lig-128grid", 9): 14709211994},

@@ -219,8 +219,9 @@ gd_status gd_check_batch(const gd_ligand_batch* batch, const gd_search_params* p
  * angles per lane and the register budget per thread of its kernel (128: the pocket
  * grid is staged in shared memory when it fits; 80: a little state spills to local
  * memory, but up to 24 warps stay resident per SM and the grid is read through the
- * texture path).  Any
- * output pointer may be NULL. */
+ * texture path; 96: smaller per-warp buffers -- the rotamer descriptors and excluded pairs
+ * read through L1, the turn's u x d term rebuilt per use -- so that about 20 warps with
+ * the buffers of 250-atom ligands fit an SM).  Any output pointer may be NULL. */
 int gd_tile_count(void);
 gd_status gd_tile_info(int tile, int* warps_per_block, int* angles_per_lane, int* max_registers);
 /* Time every tile on the batch (or its first max_ligands ligands) and return the
@@ -259,7 +260,7 @@ gd_status gd_measure_peaks(int device, void* stream, double* ffma_per_s, double*
  * must then be destroyed; the context stays usable); a blocking gd_server_poll gives up
  * with GD_ETIMEOUT after 30 s without the result.  tile: 0 = the wide tile with the most warps
  * whose buffers, sized for the server's largest ligand, fit a block; > 0 a lean or wide
- * tile (compact tiles, 16-18, are rejected).  Destroy a server before its pocket and its
+ * tile (compact tiles, 16-20, are rejected).  Destroy a server before its pocket and its
  * context.  Not thread-safe: one host thread per
  * server, or external locking.
  * Results of ligand seq (numbered from 0 in submission order): gd_server_poll copies them

@@ -1622,14 +1622,16 @@ cudaError_t plan_t(const SearchArgs& a, int warps, size_t smem, int num_sms, Lau
 
 // ids 1..12: wide builds (<= 128 registers), one block of up to 16 warps per SM, the grid
 // staged when it fits; ids 13..15: lean builds (<= 80 registers) for up to 24 warps per
-// SM; ids 16..18: compact builds (<= 96 registers, compact per-warp buffers) for about 20
-// warps per SM with large ligands.
+// SM; ids 16..20: compact builds (<= 96 registers, compact per-warp buffers) for about 20
+// warps per SM with large ligands, or fewer warps (12, 16) that leave more of the SM's
+// L1 to the texture path.
 constexpr Tile kTiles[] = {{8, 1, BUILD_WIDE},     {8, 2, BUILD_WIDE},     {8, 4, BUILD_WIDE},
                            {4, 1, BUILD_WIDE},     {4, 2, BUILD_WIDE},     {4, 4, BUILD_WIDE},
                            {16, 1, BUILD_WIDE},    {16, 2, BUILD_WIDE},    {16, 4, BUILD_WIDE},
                            {2, 1, BUILD_WIDE},     {2, 2, BUILD_WIDE},     {2, 4, BUILD_WIDE},
                            {8, 1, BUILD_LEAN},     {8, 2, BUILD_LEAN},     {4, 2, BUILD_LEAN},
-                           {20, 4, BUILD_COMPACT}, {20, 2, BUILD_COMPACT}, {10, 4, BUILD_COMPACT}};
+                           {20, 4, BUILD_COMPACT}, {20, 2, BUILD_COMPACT}, {10, 4, BUILD_COMPACT},
+                           {16, 4, BUILD_COMPACT}, {12, 4, BUILD_COMPACT}};
 constexpr int kLean8x1 = 13;
 
 template <int B>

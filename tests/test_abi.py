@@ -39,9 +39,9 @@ def test_library_exports_every_declared_function():
 
 
 def test_tiles():
-    assert gdk.tile_count() == 18
-    seen = {gdk.tile_info(t) for t in range(1, 19)}
-    assert len(seen) == 18
+    assert gdk.tile_count() == 20
+    seen = {gdk.tile_info(t) for t in range(1, 21)}
+    assert len(seen) == 20
     assert {r for _, _, r in seen} == {80, 96, 128}
     with pytest.raises(gdk.GeoDockError):
         gdk.tile_info(0)
