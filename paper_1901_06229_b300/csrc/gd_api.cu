@@ -1508,26 +1508,58 @@ gd_status gd_server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t
   for (int i = 0; i < n; ++i) {
     const int li = sel ? sel[i] : i;
     if (li < 0 || li >= LB) return fail(GD_EINVAL, "sel[%d] = %d outside [0, %d)", i, li, LB);
-    const int a0 = b->atom_off[li], na = b->atom_off[li + 1] - a0;
-    const int b0 = b->bond_off[li], nb = b->bond_off[li + 1] - b0;
-    const int r0 = b->rot_off[li], R = b->rot_off[li + 1] - r0;
-    if (na > s->amax || na < 0) return fail(GD_EINVAL, "ligand %d: %d atoms > the server's %d", li, na, s->amax);
-    if (R > s->rmax || R < 0) return fail(GD_EINVAL, "ligand %d: %d rotamers > the server's %d", li, R, s->rmax);
-    const int slot = (int)((s->next_seq + i) % s->cap);
-    char* rec = s->h_rec + (size_t)slot * (size_t)stride;
-    size_t ne = 0;
-    gd_status st = gd::pack_ligand_fixed(fail, li, na, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R,
-                                         b->rot_bond + r0, s->min_sep, (float4*)(rec + 16),
-                                         (uint8_t*)(rec + gd::serve_rec_perm_dev(s->amax)),
-                                         (RotDesc*)(rec + gd::serve_rec_rots_dev(s->amax)),
-                                         (uint16_t*)(rec + gd::serve_rec_excl_dev(s->amax, s->rmax)), (size_t)s->emax,
-                                         &ne, nullptr);
-    if (st) return st;  // nothing of this call is published: the slots stay free
-    const gd::ServeRecHeader hdr{na, R, (int32_t)ne, 0};
-    memcpy(rec, &hdr, sizeof hdr);
-    s->nat[slot] = na;
-    s->nrot[slot] = R;
   }
+  // pack each ligand into its slot's record, on the context's packing threads for large
+  // submissions (contiguous ranges; the first failure in submission order is reported)
+  struct Part {
+    int i0 = 0, i1 = 0, bad = -1;
+    gd_status st = GD_OK;
+    std::string err;
+  };
+  const int T = std::max(1, std::min(s->ctx->pool.threads(), n / 32));
+  std::vector<Part> parts(T);
+  for (int t = 0; t < T; ++t) {
+    parts[t].i0 = (int)((long long)n * t / T);
+    parts[t].i1 = (int)((long long)n * (t + 1) / T);
+  }
+  auto work = [&](Part& pt) {
+    for (int i = pt.i0; i < pt.i1; ++i) {
+      const int li = sel ? sel[i] : i;
+      const int a0 = b->atom_off[li], na = b->atom_off[li + 1] - a0;
+      const int b0 = b->bond_off[li], nb = b->bond_off[li + 1] - b0;
+      const int r0 = b->rot_off[li], R = b->rot_off[li + 1] - r0;
+      gd_status st = GD_OK;
+      if (na > s->amax || na < 0) st = fail(GD_EINVAL, "ligand %d: %d atoms > the server's %d", li, na, s->amax);
+      else if (R > s->rmax || R < 0) st = fail(GD_EINVAL, "ligand %d: %d rotamers > the server's %d", li, R, s->rmax);
+      const int slot = (int)((s->next_seq + i) % s->cap);
+      char* rec = s->h_rec + (size_t)slot * (size_t)stride;
+      size_t ne = 0;
+      if (!st)
+        st = gd::pack_ligand_fixed(fail, li, na, b->xyz + 3 * (size_t)a0, nb, b->bonds + 2 * (size_t)b0, R,
+                                   b->rot_bond + r0, s->min_sep, (float4*)(rec + 16),
+                                   (uint8_t*)(rec + gd::serve_rec_perm_dev(s->amax)),
+                                   (RotDesc*)(rec + gd::serve_rec_rots_dev(s->amax)),
+                                   (uint16_t*)(rec + gd::serve_rec_excl_dev(s->amax, s->rmax)), (size_t)s->emax, &ne,
+                                   nullptr);
+      if (st) {
+        pt.st = st;
+        pt.bad = i;
+        pt.err = g_err;  // the message lives in this thread's g_err
+        return;
+      }
+      const gd::ServeRecHeader hdr{na, R, (int32_t)ne, 0};
+      memcpy(rec, &hdr, sizeof hdr);
+      s->nat[slot] = na;
+      s->nrot[slot] = R;
+    }
+  };
+  if (T == 1) work(parts[0]);
+  else s->ctx->pool.run(T, [&](int t) { work(parts[t]); });
+  for (auto& pt : parts)
+    if (pt.st) {  // nothing of this call is published: the slots stay free
+      g_err = pt.err;
+      return pt.st;
+    }
   for (int i = 0; i < n; ++i) s->owner[(s->next_seq + i) % s->cap] = s->next_seq + i + 1;
   if (first_seq) *first_seq = s->next_seq;
   s->next_seq += n;
