@@ -71,6 +71,10 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
+    "c9a7dbf8340ec2f4": {("batched-4096lig-64grid", 14): 4557056 + 1204736,
+                         ("batched-4096lig-64grid", 15): 4556032 + 1150464,
+                         ("large-512lig-128grid", 16): 3102208 + 9216,
+                         ("large-512lig-128grid", 18): 3362560 + 8960},
     "8849191a14128210": {("batched-4096lig-64grid", 14): 4568832 + 1177856,
                          ("batched-4096lig-64grid", 15): 4556544 + 1146880,
                          ("large-512lig-128grid", 16): 2858752 + 9216,
@@ -89,6 +93,10 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
+    "c9a7dbf8340ec2f4": {("batched-4096lig-64grid", 14): 8469406704,
+                         ("batched-4096lig-64grid", 15): 8469510617,
+                         ("large-512lig-128grid", 16): 15486849117,
+                         ("large-512lig-128grid", 18): 15486908155},
     "8849191a14128210": {("batched-4096lig-64grid", 14): 8469406720,
                          ("batched-4096lig-64grid", 15): 8469510627,
                          ("large-512lig-128grid", 16): 15486849117,
