@@ -303,10 +303,12 @@ __device__ __forceinline__ void e1_chunk(uint32_t taddr, const float* b1s, int c
 // Epilogue 2 of the tile at row r0 from this thread's 128 packed layer-2 activations:
 // the dot with w3 in column order; the second half's warps hand their partial dots to
 // the first half's (through red and mbarriers 9 / 10; `handed` counts the hand-overs,
-// pr / pf are the wait parities), which write y.  False when a wait timed out.
+// pr / pf are the wait parities), which write y.  Returns ok && every wait completed; a
+// lane that comes in with ok false skips the waits, and the warp still runs every other
+// step together, so that it stays converged.
 __device__ __forceinline__ bool e2_finish(const uint32_t (&hp)[64], const float* w3s, int col0, int half, int row,
                                           int lane, int r0, int M, float bias3, float* red, uint64_t* mbar,
-                                          int& handed, uint32_t& pr, uint32_t& pf, float* y) {
+                                          int& handed, uint32_t& pr, uint32_t& pf, float* y, bool ok) {
   const float4* ww = reinterpret_cast<const float4*>(w3s + col0);
   float dot = 0.f;
 #pragma unroll
@@ -320,7 +322,7 @@ __device__ __forceinline__ bool e2_finish(const uint32_t (&hp)[64], const float*
   }
   if (half == 1) {
     if (handed > 0) {  // the previous partials have been read
-      if (!__all_sync(0xffffffffu, mbar_wait(mbar + 10, pf))) return false;
+      if (ok) ok = mbar_wait(mbar + 10, pf);
       pf ^= 1;
     }
     ++handed;
@@ -328,14 +330,15 @@ __device__ __forceinline__ bool e2_finish(const uint32_t (&hp)[64], const float*
     __syncwarp();
     if (lane == 0) mbar_arrive(mbar + 9);
   } else {
-    if (!__all_sync(0xffffffffu, mbar_wait(mbar + 9, pr))) return false;
+    if (ok) ok = mbar_wait(mbar + 9, pr);
     pr ^= 1;
+    __syncwarp();
     const float other = red[row];
     __syncwarp();
     if (lane == 0) mbar_arrive(mbar + 10);
     if (r0 + row < M) y[r0 + row] = dot + other + bias3;
   }
-  return true;
+  return ok;
 }
 
 __global__ void __launch_bounds__(INF_THREADS, 1)
@@ -439,10 +442,14 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     if (lane == 0) mbar_arrive(mbar + 2);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int r0 = tile * 128, next = tile + (int)gridDim.x;
-      ok = __all_sync(0xffffffffu, mbar_wait(mbar, ph1));  // layer 1 of this tile
+      // Waits inside a tile: each lane records its outcome and the warp goes on together
+      // (no branch on it before the vote after the layer-2 wait), so the warp reaches
+      // every .sync.aligned instruction converged; a timed-out lane skips the tile's
+      // later waits.
+      ok = mbar_wait(mbar, ph1);  // layer 1 of this tile
       ph1 ^= 1;
+      __syncwarp();
       tc_fence_after();
-      if (!ok) break;
       for (int c = 0; c < 4; ++c) {
         e1_chunk(acc1 + lanebase + (uint32_t)(32 * c), b1s, col0 + 32 * c, h1s, row);
         __syncwarp();
@@ -451,26 +458,26 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
       // all of this tile's layer 2 is queued.  Once its first MMAs are done, their H1
       // slots take the next tile's X rows (copied while the previous tile is finished)
       if (next < ntiles) {
-        ok = __all_sync(0xffffffffu, mbar_wait(mbar + 7, ph7));
+        if (ok) ok = mbar_wait(mbar + 7, ph7);
         ph7 ^= 1;
+        __syncwarp();
         tc_fence_after();
-        if (!ok) break;
         x_copy(h1s, X, M, next * 128);
       }
-      if (prev_r0 >= 0) {
-        ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y);
-        if (!ok) break;
-      }
+      if (prev_r0 >= 0) ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y, ok);
       if (next < ntiles) {
         x_wait();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(mbar + 2);
       }
-      ok = __all_sync(0xffffffffu, mbar_wait(mbar + 1, ph2));  // layer 2 done: copy its rows out, release it
+      if (ok) ok = mbar_wait(mbar + 1, ph2);  // layer 2 done: copy its rows out, release it
       ph2 ^= 1;
+      if (!__all_sync(0xffffffffu, ok)) {  // the warp's one outcome for this tile
+        ok = false;
+        break;
+      }
       tc_fence_after();
-      if (!ok) break;
       {
         float v[2][32];
 #pragma unroll
@@ -488,7 +495,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
       prev_r0 = r0;
     }
     if (ok && prev_r0 >= 0)
-      ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y);
+      ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y, ok);
   }
   // A wait that ran out anywhere in the block: before the tensor memory is freed, the
   // issuing thread commits once more and waits (bounded) for that commit, which arrives
