@@ -51,15 +51,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* m, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count));
 }
 
-// Bounded wait for phase `parity`; false after ~2 s at the maximum clock.
+// Bounded wait for phase `parity`; false after ~2 s at the maximum clock.  Each try_wait
+// may suspend the thread for up to 20 us (a hint) until the phase completes, so waiting
+// warps poll the barrier's shared-memory word less often.
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(smem_addr(m)), "r"(parity)
+        : "r"(smem_addr(m)), "r"(parity), "r"(20000u)
         : "memory");
     if (ok) return true;
     if (clock64() - t0 > 4000000000LL) return false;
@@ -207,12 +209,18 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 }
 
 // Fused inference: y = relu(relu(X W1^T + b1) W2^T + b2) . w3 + b3 for 128-row tiles.
-// One persistent CTA per SM keeps W1 (24 KB), W2 (128 KB), b1, b2 and w3 in shared
-// memory and owns all 512 TMEM columns: layer 1 accumulates in columns [0, 256), layer 2
+// One persistent CTA per SM keeps W1 (28 KB, b1 folded in), W2 (128 KB), b2 and w3 in
+// shared memory and owns all 512 TMEM columns: layer 1 accumulates in columns [0, 256), layer 2
 // in [256, 512).  Warp 8 only issues MMAs: layer 1 of a tile once the eight epilogue
 // warps have stored its X rows, then layer 2 four K = 16 slices at a time as epilogue 1
 // completes 32-column chunks of H1.  Epilogue warp w reads TMEM lanes 32 (w % 4) and
 // columns 128 (w / 4) .. + 128.
+//
+// b1 is added by the layer-1 MMAs: layer 1 runs over K = 64, X's 48 features, three
+// columns of ones and 13 of zeros, against W1's rows extended by b1 = hi + mid + lo
+// (the BF16 rounding of b1, of what it leaves, and of the rest: the three sum to the
+// FP32 b1 exactly) and five zeros (K columns 56-63 meet H1's zero columns).  Epilogue 1 is then ReLU and BF16 rounding alone, with no
+// loads of b1 competing with the tensor core for shared memory.
 //
 // The tensor pipe is kept fed across tiles:
 //   * a tile's X rows live in the H1 slots of epilogue 1's first chunk (K columns
@@ -226,16 +234,28 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 //     tile's layer 2 is queued.
 constexpr int INF_EPI = 256;                // epilogue threads (8 warps)
 constexpr int INF_THREADS = INF_EPI + 32;   // + the issuing warp
-constexpr size_t INF_W1 = 256 * 48 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2, INF_VEC = 3 * 256 * 4;
-constexpr size_t INF_BAR = 128;             // 12 mbarriers + the TMEM address
+// W1 holds 7 K chunks per row (X's 6 and b1's), 896 bytes per 8-row group: the last
+// layer-1 MMA reads K chunks 6 and 7, and "chunk 7" of a row group is the first chunk of
+// the next one (of W2 for the last group), finite weights that meet the zeros of H1's
+// chunk 19 and so add exactly nothing.
+constexpr size_t INF_W1 = 256 * 56 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2, INF_VEC = 2 * 256 * 4;
+constexpr size_t INF_BAR = 128;  // 12 mbarriers + the TMEM address
+constexpr size_t INF_SMEM = INF_W1 + INF_W2 + INF_H1 + INF_VEC + INF_BAR;
 constexpr int INF_XCH = 128 * 6 / INF_EPI;  // 16-byte X chunks per epilogue thread and tile (128 rows x 6)
 
 // Copy this thread's X chunks of the tile at row r0 (rows past M read as zero) into
 // layer 1's A operand (K = 48) in H1's core-matrix layout (8-row groups 4096 bytes
 // apart, 8-column K chunks 128 bytes apart), asynchronously (cp.async; complete after
 // x_wait): X's K chunks 0-3 go to H1 chunks 0-3 and X's K chunks 4-5 to H1 chunks
-// 16-17, all of them slots of epilogue 1's first 32-column chunk.
+// 16-17, all of them slots of epilogue 1's first 32-column chunk; H1 chunks 18 (ones in
+// K columns 48-50, which multiply b1's three parts) and 19 (zeros) complete K = 64.
 __device__ __forceinline__ void x_copy(uint8_t* h1s, const __nv_bfloat16* X, int M, int r0) {
+  {
+    const int r = threadIdx.x & 127, kc = 18 + (threadIdx.x >> 7);
+    const uint32_t one = 0x3F80u;  // BF16 1.0
+    const uint4 v = kc == 18 ? make_uint4(one | (one << 16), one, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(h1s + (size_t)(r >> 3) * 4096 + kc * 128 + (r & 7) * 16) = v;
+  }
 #pragma unroll
   for (int j = 0; j < INF_XCH; ++j) {
     const int idx = threadIdx.x + INF_EPI * j, r = idx / 6, c = idx % 6;
@@ -281,18 +301,16 @@ __device__ __forceinline__ void e2_pack(const float (&v)[32], const float* b2s, 
   }
 }
 
-// Epilogue 1 of one 32-column chunk of this thread's row: bias, ReLU and BF16 rounding
-// into H1.
-__device__ __forceinline__ void e1_chunk(uint32_t taddr, const float* b1s, int col0, uint8_t* h1s, int row) {
+// Epilogue 1 of one 32-column chunk of this thread's row (b1 already in the
+// accumulator): ReLU and BF16 rounding into H1.
+__device__ __forceinline__ void e1_chunk(uint32_t taddr, int col0, uint8_t* h1s, int row) {
   float v[32];
   tmem_ld32(taddr, v);
-  const float4* bb = reinterpret_cast<const float4*>(b1s + col0);
 #pragma unroll
   for (int c8 = 0; c8 < 4; ++c8) {
-    const float4 p = bb[2 * c8], q = bb[2 * c8 + 1];
     const float* w = v + c8 * 8;
-    const uint4 h = make_uint4(relu_bf16x2(w[0] + p.x, w[1] + p.y), relu_bf16x2(w[2] + p.z, w[3] + p.w),
-                               relu_bf16x2(w[4] + q.x, w[5] + q.y), relu_bf16x2(w[6] + q.z, w[7] + q.w));
+    const uint4 h = make_uint4(relu_bf16x2(w[0], w[1]), relu_bf16x2(w[2], w[3]), relu_bf16x2(w[4], w[5]),
+                               relu_bf16x2(w[6], w[7]));
     const int kc = (col0 >> 3) + c8;
     *reinterpret_cast<uint4*>(h1s + (size_t)(row >> 3) * 4096 + kc * 128 + (row & 7) * 16) = h;
   }
@@ -348,8 +366,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   uint8_t* w1s = smem;
   uint8_t* w2s = smem + INF_W1;
   uint8_t* h1s = smem + INF_W1 + INF_W2;
-  float* b1s = reinterpret_cast<float*>(smem + INF_W1 + INF_W2 + INF_H1);
-  float* b2s = b1s + 256;
+  float* b2s = reinterpret_cast<float*>(smem + INF_W1 + INF_W2 + INF_H1);
   float* w3s = b2s + 256;
   // mbar[0] layer 1 done, [1] layer 2 done, [7] layer 2's first four MMAs done (MMA
   // commits); [2] X rows copied in, [3 + c] chunk c of epilogue 1 written, [8] layer 2's
@@ -365,12 +382,23 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = (M + 127) / 128;
   if ((int)blockIdx.x >= ntiles) return;
-  stage(w1s, W1b, 48, 256, 48, 0, 256, 0, 48, false);
+  stage(w1s, W1b, 48, 256, 48, 0, 256, 0, 56, false);  // K columns 48-55 zero
   stage(w2s, W2b, 256, 256, 256, 0, 256, 0, 256, false);
+  __syncthreads();
   for (int i = threadIdx.x; i < 256; i += INF_THREADS) {
-    b1s[i] = b1[i];
     b2s[i] = b2[i];
     w3s[i] = w3r[i];
+    // W1 row i, K columns 48-50: b1[i] = hi + mid + lo exactly (each remainder is exact
+    // in FP32 and the last has at most 8 significant bits)
+    const float b = b1[i];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+    const float r1 = b - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    __nv_bfloat16* k48 = reinterpret_cast<__nv_bfloat16*>(w1s + (size_t)(i >> 3) * 896 + 6 * 128 + (i & 7) * 16);
+    k48[0] = hi;
+    k48[1] = mid;
+    k48[2] = lo;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(tslot)));
@@ -397,17 +425,25 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     // ---- issuing warp
     if (lane == 0) {
       const uint32_t idesc = make_idesc(128, 256);
+      // Every operand sits at a fixed shared-memory address, so each MMA's descriptors are
+      // these bases with the start-address field (the low 14 bits, in 16-byte units)
+      // advanced by a compile-time offset: a few integer adds per MMA, which keeps the
+      // single issuing thread ahead of the tensor pipe.
+      const uint64_t dh = make_desc(smem_addr(h1s), 128, 4096), dw1 = make_desc(smem_addr(w1s), 128, 896),
+                     dw2 = make_desc(smem_addr(w2s), 128, 4096);
       uint32_t px = 0, pc = 0, pd = 0;  // parities: X stored, epilogue-1 chunks, accumulator copied
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         ok = mbar_wait(mbar + 2, px);
         px ^= 1;
         if (!ok) break;
         tc_fence_after();
-        for (int kk = 0; kk < 3; ++kk)
-          mma_bf16(acc1, make_desc(smem_addr(h1s) + (kk < 2 ? kk * 256 : 16 * 128), 128, 4096),
-                   make_desc(smem_addr(w1s) + kk * 256, 128, 768), idesc, kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)  // X's K chunks 0-3 and 16-17, then the ones (18-19), of H1's slots
+          mma_bf16(acc1, dh + (uint64_t)((kk < 2 ? kk * 256 : (16 + 2 * (kk - 2)) * 128) >> 4),
+                   dw1 + (uint64_t)((kk * 256) >> 4), idesc, kk > 0);
         mma_commit(mbar);
-        for (int c = 0; c < 4 && ok; ++c) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
           ok = mbar_wait(mbar + 3 + c, pc);
           if (ok && c == 0 && tile != (int)blockIdx.x) {  // the previous layer 2 copied out
             ok = mbar_wait(mbar + 8, pd);
@@ -415,10 +451,11 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
           }
           if (!ok) break;
           tc_fence_after();
-          const int ks[4] = {2 * c, 2 * c + 1, 8 + 2 * c, 9 + 2 * c};
-          for (int t = 0; t < 4; ++t)
-            mma_bf16(acc2, make_desc(smem_addr(h1s) + ks[t] * 256, 128, 4096),
-                     make_desc(smem_addr(w2s) + ks[t] * 256, 128, 4096), idesc, c > 0 || t > 0);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int k = t < 2 ? 2 * c + t : 8 + 2 * c + (t - 2);  // K slices of chunk c
+            mma_bf16(acc2, dh + (uint64_t)((k * 256) >> 4), dw2 + (uint64_t)((k * 256) >> 4), idesc, c > 0 || t > 0);
+          }
           if (c == 0) mma_commit(mbar + 7);
         }
         pc ^= 1;
@@ -451,7 +488,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
       __syncwarp();
       tc_fence_after();
       for (int c = 0; c < 4; ++c) {
-        e1_chunk(acc1 + lanebase + (uint32_t)(32 * c), b1s, col0 + 32 * c, h1s, row);
+        e1_chunk(acc1 + lanebase + (uint32_t)(32 * c), col0 + 32 * c, h1s, row);
         __syncwarp();
         if (lane == 0) mbar_arrive(mbar + 3 + c);
       }
@@ -536,7 +573,7 @@ cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b
                          const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
                          int num_sms, cudaStream_t st) {
   static std::atomic<bool> attr[64];
-  const size_t smem = INF_W1 + INF_W2 + INF_H1 + INF_VEC + INF_BAR;
+  const size_t smem = INF_SMEM;
   cudaError_t e = smem_attr_once((const void*)mlp_infer_kernel, smem, attr);
   if (e != cudaSuccess) return e;
   if (M <= 0) return cudaSuccess;
