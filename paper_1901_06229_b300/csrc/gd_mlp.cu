@@ -209,18 +209,20 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 }
 
 // Fused inference: y = relu(relu(X W1^T + b1) W2^T + b2) . w3 + b3 for 128-row tiles.
-// One persistent CTA per SM keeps W1 (28 KB, b1 folded in), W2 (128 KB), b2 and w3 in
-// shared memory and owns all 512 TMEM columns: layer 1 accumulates in columns [0, 256), layer 2
-// in [256, 512).  Warp 8 only issues MMAs: layer 1 of a tile once the eight epilogue
-// warps have stored its X rows, then layer 2 four K = 16 slices at a time as epilogue 1
-// completes 32-column chunks of H1.  Epilogue warp w reads TMEM lanes 32 (w % 4) and
-// columns 128 (w / 4) .. + 128.
+// One persistent CTA per SM keeps W1 (28 KB, b1 folded in), W2 (128 KB), b2's MMA
+// operands and w3 in shared memory and owns all 512 TMEM columns: layer 1 accumulates in
+// columns [0, 256), layer 2 in [256, 512).  Warp 8 only issues MMAs: layer 1 of a tile
+// once the eight epilogue warps have stored its X rows, then layer 2 four K = 16 slices
+// at a time as epilogue 1 completes 32-column chunks of H1.  Epilogue warp w reads TMEM
+// lanes 32 (w % 4) and columns 128 (w / 4) .. + 128.
 //
-// b1 is added by the layer-1 MMAs: layer 1 runs over K = 64, X's 48 features, three
-// columns of ones and 13 of zeros, against W1's rows extended by b1 = hi + mid + lo
-// (the BF16 rounding of b1, of what it leaves, and of the rest: the three sum to the
-// FP32 b1 exactly) and five zeros (K columns 56-63 meet H1's zero columns).  Epilogue 1 is then ReLU and BF16 rounding alone, with no
-// loads of b1 competing with the tensor core for shared memory.
+// Both biases are added by MMAs, so that neither epilogue loads them from shared memory,
+// where those loads waited behind the tensor core's operand reads:
+//   * layer 1 runs over K = 64: X's 48 features, three columns of ones and 13 of zeros,
+//     against W1's rows extended by b1 = hi + mid + lo (the BF16 rounding of b1, of
+//     what it leaves, and of the rest: the three sum to the FP32 b1 exactly) and zeros;
+//   * layer 2 starts with one more MMA, ones against b2 split the same way, which
+//     writes b2 into the accumulator before the 16 slices of H1 W2^T add to it.
 //
 // The tensor pipe is kept fed across tiles:
 //   * a tile's X rows live in the H1 slots of epilogue 1's first chunk (K columns
@@ -229,18 +231,23 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 //     tile's layer 2;
 //   * when layer 2 completes, the warps copy their accumulator rows into registers and
 //     release the accumulator at once, so the next tile's layer 2 can start as soon as
-//     the first chunk of its epilogue 1 is written; bias, ReLU and BF16 rounding of those
-//     rows run while the next layer 1 does, and their dot with w3 once all of the next
-//     tile's layer 2 is queued.
+//     the first chunk of its epilogue 1 is written; ReLU and BF16 rounding of those rows
+//     run while the next layer 1 does, and their dot with w3 once all of the next tile's
+//     layer 2 is queued.
 constexpr int INF_EPI = 256;                // epilogue threads (8 warps)
 constexpr int INF_THREADS = INF_EPI + 32;   // + the issuing warp
 // W1 holds 7 K chunks per row (X's 6 and b1's), 896 bytes per 8-row group: the last
 // layer-1 MMA reads K chunks 6 and 7, and "chunk 7" of a row group is the first chunk of
 // the next one (of W2 for the last group), finite weights that meet the zeros of H1's
 // chunk 19 and so add exactly nothing.
-constexpr size_t INF_W1 = 256 * 56 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2, INF_VEC = 2 * 256 * 4;
+constexpr size_t INF_W1 = 256 * 56 * 2, INF_W2 = 256 * 256 * 2, INF_H1 = 128 * 256 * 2;
+// b2's operands for the first layer-2 MMA: B2 (b2 = hi + mid + lo per row, one K chunk
+// per 8-row group, 128 bytes apart, "chunk 1" again the next group's and zeros after the
+// last) and ONE (8 rows of ones in K columns 0-2 and zeros, read by every 8-row group
+// of the tile: stride 0)
+constexpr size_t INF_B2 = 256 * 16 + 128, INF_ONE = 256, INF_VEC = 256 * 4;  // + w3
 constexpr size_t INF_BAR = 128;  // 12 mbarriers + the TMEM address
-constexpr size_t INF_SMEM = INF_W1 + INF_W2 + INF_H1 + INF_VEC + INF_BAR;
+constexpr size_t INF_SMEM = INF_W1 + INF_W2 + INF_H1 + INF_B2 + INF_ONE + INF_VEC + INF_BAR;
 constexpr int INF_XCH = 128 * 6 / INF_EPI;  // 16-byte X chunks per epilogue thread and tile (128 rows x 6)
 
 // Copy this thread's X chunks of the tile at row r0 (rows past M read as zero) into
@@ -289,16 +296,11 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float a, float b) {
   return r;
 }
 
-// Bias, ReLU and BF16 rounding of 32 layer-2 accumulator columns (from column c0), packed
+// ReLU and BF16 rounding of 32 layer-2 accumulator columns (b2 already in them), packed
 // in pairs.
-__device__ __forceinline__ void e2_pack(const float (&v)[32], const float* b2s, int c0, uint32_t* hp) {
-  const float4* bb = reinterpret_cast<const float4*>(b2s + c0);
+__device__ __forceinline__ void e2_pack(const float (&v)[32], uint32_t* hp) {
 #pragma unroll
-  for (int e4 = 0; e4 < 8; ++e4) {
-    const float4 b = bb[e4];
-    hp[2 * e4] = relu_bf16x2(v[4 * e4] + b.x, v[4 * e4 + 1] + b.y);
-    hp[2 * e4 + 1] = relu_bf16x2(v[4 * e4 + 2] + b.z, v[4 * e4 + 3] + b.w);
-  }
+  for (int e2 = 0; e2 < 16; ++e2) hp[e2] = relu_bf16x2(v[2 * e2], v[2 * e2 + 1]);
 }
 
 // Epilogue 1 of one 32-column chunk of this thread's row (b1 already in the
@@ -359,6 +361,21 @@ __device__ __forceinline__ bool e2_finish(const uint32_t (&hp)[64], const float*
   return ok;
 }
 
+// A bias as one 16-byte K chunk of BF16: (hi, mid, lo, 0, 0, 0, 0, 0) with hi + mid + lo
+// equal to b exactly (each remainder is exact in FP32 and the last has at most 8
+// significant bits), for an MMA against ones.
+__device__ __forceinline__ void split_bias(float b, uint8_t* dst) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+  const float r1 = b - __bfloat162float(hi);
+  const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+  __nv_bfloat16* k = reinterpret_cast<__nv_bfloat16*>(dst);
+  k[0] = hi;
+  k[1] = mid;
+  k[2] = lo;
+  for (int e = 3; e < 8; ++e) k[e] = __float2bfloat16_rn(0.f);
+}
+
 __global__ void __launch_bounds__(INF_THREADS, 1)
     mlp_infer_kernel(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
                      const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err) {
@@ -366,8 +383,9 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   uint8_t* w1s = smem;
   uint8_t* w2s = smem + INF_W1;
   uint8_t* h1s = smem + INF_W1 + INF_W2;
-  float* b2s = reinterpret_cast<float*>(smem + INF_W1 + INF_W2 + INF_H1);
-  float* w3s = b2s + 256;
+  uint8_t* b2o = smem + INF_W1 + INF_W2 + INF_H1;
+  uint8_t* one = b2o + INF_B2;
+  float* w3s = reinterpret_cast<float*>(one + INF_ONE);
   // mbar[0] layer 1 done, [1] layer 2 done, [7] layer 2's first four MMAs done (MMA
   // commits); [2] X rows copied in, [3 + c] chunk c of epilogue 1 written, [8] layer 2's
   // accumulator copied out (one arrival per epilogue warp); [9] the second half's
@@ -376,7 +394,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   // phase per tile, and no warp can arrive twice on one before its phase completes:
   // each next arrival waits, directly or through the issuing warp, for every warp's
   // current one.
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + INF_W1 + INF_W2 + INF_H1 + INF_VEC);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(w3s) + INF_VEC);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 12);
   __shared__ float red[128];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -386,19 +404,15 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
   stage(w2s, W2b, 256, 256, 256, 0, 256, 0, 256, false);
   __syncthreads();
   for (int i = threadIdx.x; i < 256; i += INF_THREADS) {
-    b2s[i] = b2[i];
     w3s[i] = w3r[i];
-    // W1 row i, K columns 48-50: b1[i] = hi + mid + lo exactly (each remainder is exact
-    // in FP32 and the last has at most 8 significant bits)
-    const float b = b1[i];
-    const __nv_bfloat16 hi = __float2bfloat16_rn(b);
-    const float r1 = b - __bfloat162float(hi);
-    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-    __nv_bfloat16* k48 = reinterpret_cast<__nv_bfloat16*>(w1s + (size_t)(i >> 3) * 896 + 6 * 128 + (i & 7) * 16);
-    k48[0] = hi;
-    k48[1] = mid;
-    k48[2] = lo;
+    split_bias(b2[i], b2o + (size_t)(i >> 3) * 128 + (i & 7) * 16);
+    split_bias(b1[i], w1s + (size_t)(i >> 3) * 896 + 6 * 128 + (i & 7) * 16);  // W1 row i, K columns 48-55
+  }
+  if (threadIdx.x < 24) {  // ONE: 8 rows of (1, 1, 1, 0, 0, 0, 0, 0), then 8 of zeros; B2's trailing zeros
+    const uint32_t o = 0x3F80u;  // BF16 1.0
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x < 16) reinterpret_cast<uint4*>(one)[threadIdx.x] = threadIdx.x < 8 ? make_uint4(o | (o << 16), o, 0u, 0u) : z;
+    else reinterpret_cast<uint4*>(b2o + 4096)[threadIdx.x - 16] = z;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(tslot)));
@@ -430,7 +444,8 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
       // advanced by a compile-time offset: a few integer adds per MMA, which keeps the
       // single issuing thread ahead of the tensor pipe.
       const uint64_t dh = make_desc(smem_addr(h1s), 128, 4096), dw1 = make_desc(smem_addr(w1s), 128, 896),
-                     dw2 = make_desc(smem_addr(w2s), 128, 4096);
+                     dw2 = make_desc(smem_addr(w2s), 128, 4096), db2 = make_desc(smem_addr(b2o), 128, 128),
+                     done = make_desc(smem_addr(one), 128, 0);
       uint32_t px = 0, pc = 0, pd = 0;  // parities: X stored, epilogue-1 chunks, accumulator copied
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         ok = mbar_wait(mbar + 2, px);
@@ -442,19 +457,22 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
           mma_bf16(acc1, dh + (uint64_t)((kk < 2 ? kk * 256 : (16 + 2 * (kk - 2)) * 128) >> 4),
                    dw1 + (uint64_t)((kk * 256) >> 4), idesc, kk > 0);
         mma_commit(mbar);
+        if (tile != (int)blockIdx.x) {  // the previous layer 2 copied out
+          ok = mbar_wait(mbar + 8, pd);
+          pd ^= 1;
+          if (!ok) break;
+          tc_fence_after();
+        }
+        mma_bf16(acc2, done, db2, idesc, false);  // layer 2 starts from b2
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           ok = mbar_wait(mbar + 3 + c, pc);
-          if (ok && c == 0 && tile != (int)blockIdx.x) {  // the previous layer 2 copied out
-            ok = mbar_wait(mbar + 8, pd);
-            pd ^= 1;
-          }
           if (!ok) break;
           tc_fence_after();
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             const int k = t < 2 ? 2 * c + t : 8 + 2 * c + (t - 2);  // K slices of chunk c
-            mma_bf16(acc2, dh + (uint64_t)((k * 256) >> 4), dw2 + (uint64_t)((k * 256) >> 4), idesc, c > 0 || t > 0);
+            mma_bf16(acc2, dh + (uint64_t)((k * 256) >> 4), dw2 + (uint64_t)((k * 256) >> 4), idesc, true);
           }
           if (c == 0) mma_commit(mbar + 7);
         }
@@ -520,14 +538,14 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
 #pragma unroll
         for (int k = 0; k < 2; ++k) tmem_ld32(acc2 + lanebase + (uint32_t)(32 * k), v[k]);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) e2_pack(v[k], b2s, col0 + 32 * k, hp + 16 * k);
+        for (int k = 0; k < 2; ++k) e2_pack(v[k], hp + 16 * k);
 #pragma unroll
         for (int k = 0; k < 2; ++k) tmem_ld32(acc2 + lanebase + (uint32_t)(64 + 32 * k), v[k]);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(mbar + 8);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) e2_pack(v[k], b2s, col0 + 64 + 32 * k, hp + 32 + 16 * k);  // during the next layer 1
+        for (int k = 0; k < 2; ++k) e2_pack(v[k], hp + 32 + 16 * k);  // during the next layer 1
       }
       prev_r0 = r0;
     }
@@ -553,7 +571,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
 
 // Operand staging (48 KB) plus 32 KB of headroom: at most two CTAs share an SM, so the
 // two 256-column TMEM allocations always fit the SM's 512 columns.  (The inference
-// kernel takes all 512 columns, but its 225 KB of shared memory keeps any other
+// kernel takes all 512 columns, but its 226 KB of shared memory keeps any other
 // tensor-core CTA off its SM.)
 size_t gemm_smem_bytes() { return 128 * KC * 2 + 256 * KC * 2 + 16 + 32 * 1024; }
 
