@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
 // The tensor pipe is kept fed across tiles:
 //   * a tile's X rows live in the H1 slots of epilogue 1's first chunk (K columns
 //     0-31 and 128-159 of H1), which layer 2 has finished reading after its first four
-//     MMAs: the next tile's X is stored then, so its layer 1 queues right behind this
-//     tile's layer 2;
+//     MMAs: the next tile's X, loaded into registers during epilogue 1, is stored then,
+//     so its layer 1 queues right behind this tile's layer 2;
 //   * when layer 2 completes, the warps copy their accumulator rows into registers and
 //     release the accumulator at once, so the next tile's layer 2 can start as soon as
 //     the first chunk of its epilogue 1 is written; ReLU and BF16 rounding of those rows
@@ -250,13 +250,26 @@ constexpr size_t INF_BAR = 128;  // 12 mbarriers + the TMEM address
 constexpr size_t INF_SMEM = INF_W1 + INF_W2 + INF_H1 + INF_B2 + INF_ONE + INF_VEC + INF_BAR;
 constexpr int INF_XCH = 128 * 6 / INF_EPI;  // 16-byte X chunks per epilogue thread and tile (128 rows x 6)
 
-// Copy this thread's X chunks of the tile at row r0 (rows past M read as zero) into
-// layer 1's A operand (K = 48) in H1's core-matrix layout (8-row groups 4096 bytes
-// apart, 8-column K chunks 128 bytes apart), asynchronously (cp.async; complete after
-// x_wait): X's K chunks 0-3 go to H1 chunks 0-3 and X's K chunks 4-5 to H1 chunks
+// This thread's share of a tile's X rows, loaded into registers ahead of time (rows
+// past M read as zero): chunk j is X row idx / 6, K chunk idx % 6 with idx = t + 256 j.
+struct XRegs {
+  uint4 v[INF_XCH];
+};
+__device__ __forceinline__ void x_load(XRegs& xr, const __nv_bfloat16* X, int M, int r0) {
+#pragma unroll
+  for (int j = 0; j < INF_XCH; ++j) {
+    const int idx = threadIdx.x + INF_EPI * j, r = idx / 6, c = idx % 6;
+    xr.v[j] = r0 + r < M ? __ldg(reinterpret_cast<const uint4*>(X + (size_t)(r0 + r) * 48 + c * 8))
+                         : make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// Store them into layer 1's A operand (K = 64) in H1's core-matrix layout (8-row groups
+// 4096 bytes apart, 8-column K chunks 128 bytes apart) and make the stores visible to the
+// tensor core: X's K chunks 0-3 go to H1 chunks 0-3 and X's K chunks 4-5 to H1 chunks
 // 16-17, all of them slots of epilogue 1's first 32-column chunk; H1 chunks 18 (ones in
 // K columns 48-50, which multiply b1's three parts) and 19 (zeros) complete K = 64.
-__device__ __forceinline__ void x_copy(uint8_t* h1s, const __nv_bfloat16* X, int M, int r0) {
+__device__ __forceinline__ void x_store(uint8_t* h1s, const XRegs& xr) {
   {
     const int r = threadIdx.x & 127, kc = 18 + (threadIdx.x >> 7);
     const uint32_t one = 0x3F80u;  // BF16 1.0
@@ -267,18 +280,8 @@ __device__ __forceinline__ void x_copy(uint8_t* h1s, const __nv_bfloat16* X, int
   for (int j = 0; j < INF_XCH; ++j) {
     const int idx = threadIdx.x + INF_EPI * j, r = idx / 6, c = idx % 6;
     const int kc = c < 4 ? c : c + 12;
-    const bool in = r0 + r < M;
-    const __nv_bfloat16* src = in ? X + (size_t)(r0 + r) * 48 + c * 8 : X;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
-                     smem_addr(h1s + (size_t)(r >> 3) * 4096 + kc * 128 + (r & 7) * 16)),
-                 "l"(src), "r"(in ? 16 : 0)
-                 : "memory");
+    *reinterpret_cast<uint4*>(h1s + (size_t)(r >> 3) * 4096 + kc * 128 + (r & 7) * 16) = xr.v[j];
   }
-}
-
-// Wait for this thread's X copies and make them visible to the tensor core.
-__device__ __forceinline__ void x_wait() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
@@ -491,12 +494,14 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
     int prev_r0 = -1;   // first row of the tile whose layer-2 rows sit in acc
     int handed = 0;     // partial dots the second half has handed over so far
     uint32_t hp[64];    // this thread's 128 layer-2 activations of tile prev_r0 (BF16 pairs)
-    x_copy(h1s, X, M, (int)blockIdx.x * 128);
-    x_wait();
+    XRegs xr;           // the next tile's X rows, in flight during epilogue 1
+    x_load(xr, X, M, (int)blockIdx.x * 128);
+    x_store(h1s, xr);
     __syncwarp();
     if (lane == 0) mbar_arrive(mbar + 2);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int r0 = tile * 128, next = tile + (int)gridDim.x;
+      if (next < ntiles) x_load(xr, X, M, next * 128);
       // Waits inside a tile: each lane records its outcome and the warp goes on together
       // (no branch on it before the vote after the layer-2 wait), so the warp reaches
       // every .sync.aligned instruction converged; a timed-out lane skips the tile's
@@ -511,21 +516,19 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
         if (lane == 0) mbar_arrive(mbar + 3 + c);
       }
       // all of this tile's layer 2 is queued.  Once its first MMAs are done, their H1
-      // slots take the next tile's X rows (copied while the previous tile is finished)
+      // slots take the next tile's X rows (loaded during epilogue 1), so the next layer 1
+      // queues behind this layer 2 before the previous tile is finished
       if (next < ntiles) {
         if (ok) ok = mbar_wait(mbar + 7, ph7);
         ph7 ^= 1;
         __syncwarp();
         tc_fence_after();
-        x_copy(h1s, X, M, next * 128);
-      }
-      if (prev_r0 >= 0) ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y, ok);
-      if (next < ntiles) {
-        x_wait();
+        x_store(h1s, xr);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(mbar + 2);
       }
+      if (prev_r0 >= 0) ok = e2_finish(hp, w3s, col0, half, row, lane, prev_r0, M, bias3, red, mbar, handed, pr, pf, y, ok);
       if (ok) ok = mbar_wait(mbar + 1, ph2);  // layer 2 done: copy its rows out, release it
       ph2 ^= 1;
       if (!__all_sync(0xffffffffu, ok)) {  // the warp's one outcome for this tile
