@@ -562,10 +562,13 @@ __device__ __forceinline__ int col_atom(const WarpMem& w, const Cols& c, int k) 
 // ballot is the mask word MASK[ia * nch + c], nch = *n_chunks.  The rotamer's excluded
 // pairs are then cleared from the masks, and the masks are compacted into the step's
 // list of near pairs (NEAR, at most 4 nmax entries: the bytes of HR).  Returns the
-// number of near pairs; above 4 nmax only the masks are usable.
-template <bool PRUNE>
-__device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, int n, const RotDesc& rd,
-                          int lane, unsigned long long& reach, int& nch_out) {
+// number of near pairs; above 4 nmax only the masks are usable.  HOIST (the compact
+// builds, which read the excluded pairs through L1): ex0 is excluded pair `lane`, read by
+// the caller at the start of the step so that the load is in flight during the axis
+// frames and the ballots.
+template <bool PRUNE, bool HOIST>
+__device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t* excl, uint32_t ex0, int n,
+                          const RotDesc& rd, int lane, unsigned long long& reach, int& nch_out) {
   int m0a, m0b, m1a, m1b, s0a, s0b, s1a;
   if (rd.comp) {
     m0a = 0; m0b = rd.lo; m1a = rd.hi; m1b = n;
@@ -636,7 +639,8 @@ __device__ int build_near(const SearchArgs& a, const WarpMem& w, const uint16_t*
   }
   __syncwarp();
   for (int e = lane; e < rd.n_excl; e += 32) {
-    const int av = excl[e] & 0xFF, bv = excl[e] >> 8;
+    const uint32_t x = HOIST && e == lane ? ex0 : excl[e];
+    const int av = x & 0xFF, bv = x >> 8;
     int ia, k;
     if (rd.comp) {
       ia = av < rd.lo ? av : av - (rd.hi - rd.lo);
@@ -990,6 +994,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
     for (int r = 0; r < R; ++r) {
       const RotDesc rd = w.RD[r];  // registers: the loops below also write shared memory
       const uint16_t* excl = w.EXL + ((int)rd.excl_off - e0);
+      const uint32_t ex0 = COMPACT && a.use_filter && lane < rd.n_excl ? excl[lane] : 0u;
       float ux, uy, uz;
       bond_axis(X, rd, ux, uy, uz);
       uint8_t* dbg = nullptr;
@@ -1000,7 +1005,7 @@ __device__ void search_pose(const SearchArgs& a, const uint8_t* sg, const WarpMe
       prep_step<COMPACT>(w, n, rd, xp, ux, uy, uz, lane);
       if (a.use_filter) {
         int nch;
-        const int n_near = build_near<PRUNE>(a, w, excl, n, rd, lane, reach, nch);
+        const int n_near = build_near<PRUNE, COMPACT>(a, w, excl, ex0, n, rd, lane, reach, nch);
         if (n_near <= 4 * a.nmax && !a.mask_sweep)
           key = eval_step_near<S, G, COMPACT>(a, sg, w, n, rd, xp, ux, uy, uz, cur, n_near, lane, pairs, dbg);
         else
