@@ -71,6 +71,10 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
+    "6f657c070d65f73e": {("batched-4096lig-64grid", 14): 4555520 + 1185024,
+                         ("batched-4096lig-64grid", 15): 4555264 + 1213184,
+                         ("large-512lig-128grid", 16): 3054080 + 9728,
+                         ("large-512lig-128grid", 18): 2749440 + 9728},
     "c9a7dbf8340ec2f4": {("batched-4096lig-64grid", 14): 4557056 + 1204736,
                          ("batched-4096lig-64grid", 15): 4556032 + 1150464,
                          ("large-512lig-128grid", 16): 3102208 + 9216,
@@ -93,6 +97,10 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
+    "6f657c070d65f73e": {("batched-4096lig-64grid", 14): 8462969359,
+                         ("batched-4096lig-64grid", 15): 8463073244,
+                         ("large-512lig-128grid", 16): 15525958491,
+                         ("large-512lig-128grid", 18): 15526017496},
     "c9a7dbf8340ec2f4": {("batched-4096lig-64grid", 14): 8469406704,
                          ("batched-4096lig-64grid", 15): 8469510617,
                          ("large-512lig-128grid", 16): 15486849117,
