@@ -1266,8 +1266,11 @@ __device__ int serve_claim(const ServeArgs& s, int gw, unsigned long long* t, lo
       s.parked[gw] = tk + 1ull;
       return 2;
     }
+    // backoff to 32 us: with every warp of the GPU idle here, shorter sleeps put ~1e9
+    // loads/s of these words on one L2 slice and starved the warps still searching
+    // (their items ran 200x slower at the end of a stream)
     __nanosleep(sleep_ns);
-    sleep_ns = sleep_ns < 4096u ? 2u * sleep_ns : 4096u;
+    sleep_ns = sleep_ns < 32768u ? 2u * sleep_ns : 32768u;
   }
 }
 
@@ -1327,13 +1330,15 @@ __device__ bool serve_wait(const ServeArgs& s, int slot, unsigned long long seq,
   int ok = 0;
   if (lane == 0) {
     const long long c0 = clock64();
+    unsigned sleep_ns = 128;
     for (;;) {
       if (ld_acquire_gpu(s.slot_ready + slot) == seq + 1ull) {
         ok = 1;
         break;
       }
       if (clock64() - c0 > s.wait_cycles) break;
-      __nanosleep(128);
+      __nanosleep(sleep_ns);
+      sleep_ns = sleep_ns < 2048u ? 2u * sleep_ns : 2048u;
     }
   }
   ok = __shfl_sync(FULL, ok, 0);
