@@ -57,6 +57,13 @@ gd_status gd_mlp_train_step(gd_mlp* model, const void* x_bf16, const float* t, c
                             float lr, float* loss, void* stream);
 /* 1 if a bounded device wait of the model's kernels ran out since creation. */
 gd_status gd_mlp_error(gd_mlp* model, int* host_err);
+/* Test of the bounded waits (no fault, no hang): on = 1 makes the model's next
+ * tensor-core launch (the predict's fused kernel, or the first GEMM of gradients /
+ * train_step) withhold its first MMA commit, so that the wait on it runs out after about
+ * two seconds; the kernel then drains its MMAs with one more commit before it frees its
+ * tensor memory, sets the error flag and returns (its outputs are undefined).  on = 0
+ * clears a hold not yet taken and the error flag (synchronises the device). */
+gd_status gd_mlp_test_hold(gd_mlp* model, int on);
 
 /* Features of every (ligand, restart) of a prepared job: 48 numbers per row, row
  * li * O + o (input ligand order), written as BF16 (x_bf16, the network's input) and/or

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
         const uint64_t db = make_desc(smem_addr(sb) + kk * 256, 128, sbo);
         mma_bf16(tmem, da, db, idesc, k0 > 0 || kk > 0);
       }
-      mma_commit(mbar);
+      if (!(g.hold && k0 == 0)) mma_commit(mbar);
     }
     // one outcome for the whole block: every thread takes the same branch and barriers
     ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;
@@ -178,7 +178,10 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
   if (!ok) {
     if (threadIdx.x == 0) {
       if (g.err) atomicExch(g.err, 1);
-      mbar_wait(mbar, phase);  // give the queued MMAs another bounded wait before TMEM is freed
+      // before TMEM is freed: one more commit, which arrives once every MMA queued so far
+      // is complete (or the late one does), and a bounded wait for it
+      mma_commit(mbar);
+      mbar_wait(mbar, phase);
     }
   } else {
     // epilogue: warp w owns rows 32w .. 32w + 31 (TMEM lanes)
@@ -381,7 +384,8 @@ __device__ __forceinline__ void split_bias(float b, uint8_t* dst) {
 
 __global__ void __launch_bounds__(INF_THREADS, 1)
     mlp_infer_kernel(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
-                     const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err) {
+                     const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
+                     int hold) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* w1s = smem;
   uint8_t* w2s = smem + INF_W1;
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(INF_THREADS, 1)
         for (int kk = 0; kk < 4; ++kk)  // X's K chunks 0-3 and 16-17, then the ones (18-19), of H1's slots
           mma_bf16(acc1, dh + (uint64_t)((kk < 2 ? kk * 256 : (16 + 2 * (kk - 2)) * 128) >> 4),
                    dw1 + (uint64_t)((kk * 256) >> 4), idesc, kk > 0);
-        mma_commit(mbar);
+        if (!(hold && tile == (int)blockIdx.x)) mma_commit(mbar);  // hold (a test): the wait on it runs out
         if (tile != (int)blockIdx.x) {  // the previous layer 2 copied out
           ok = mbar_wait(mbar + 8, pd);
           pd ^= 1;
@@ -592,7 +596,7 @@ cudaError_t smem_attr_once(const void* fn, size_t bytes, std::atomic<bool>* done
 
 cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
                          const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
-                         int num_sms, cudaStream_t st) {
+                         int hold, int num_sms, cudaStream_t st) {
   static std::atomic<bool> attr[64];
   const size_t smem = INF_SMEM;
   cudaError_t e = smem_attr_once((const void*)mlp_infer_kernel, smem, attr);
@@ -600,7 +604,7 @@ cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b
   if (M <= 0) return cudaSuccess;
   const int tiles = (M + 127) / 128;
   mlp_infer_kernel<<<tiles < num_sms ? tiles : num_sms, INF_THREADS, smem, st>>>(X, M, W1b, W2b, b1, b2, w3r, b3, y,
-                                                                                 err);
+                                                                                 err, hold);
   return cudaGetLastError();
 }
 
@@ -761,12 +765,20 @@ struct gd_mlp {
         *loss = nullptr;
   int* err = nullptr;
   __nv_bfloat16* H1p = nullptr;  // prediction chunk activations
+  int hold = 0;                  // test: the next tensor-core launch withholds its first commit
 };
 
 namespace {
 
 using gd::HID;
 using gd::F_IN;
+
+// The test hold, for the one launch that takes it.
+int take_hold(gd_mlp* m) {
+  const int h = m->hold;
+  m->hold = 0;
+  return h;
+}
 
 gd_status mlp_forward(gd_mlp* m, const __nv_bfloat16* X, int M, __nv_bfloat16* H1, __nv_bfloat16* H2, float* y,
                       cudaStream_t s) {
@@ -783,6 +795,7 @@ gd_status mlp_forward(gd_mlp* m, const __nv_bfloat16* X, int M, __nv_bfloat16* H
   g.relu = true;
   g.Cb = H1;
   g.err = m->err;
+  g.hold = take_hold(m);
   if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
   g = gd::GemmArgs{};
   g.A = H1;
@@ -800,6 +813,7 @@ gd_status mlp_forward(gd_mlp* m, const __nv_bfloat16* X, int M, __nv_bfloat16* H
   g.dot_bias_dev = m->P + gd::OFF_B3;
   g.dot_out = y;
   g.err = m->err;
+  g.hold = take_hold(m);
   return gd::gemm_launch(g, s) == cudaSuccess ? GD_OK : GD_ECUDA;
 }
 
@@ -829,6 +843,7 @@ gd_status mlp_backward(gd_mlp* m, const void* X, const float* t, const int32_t* 
   g.C = m->G + gd::OFF_W2;
   g.ldc = HID;
   g.err = m->err;
+  g.hold = take_hold(m);
   if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
   // dH1 = G2 W2
   g = gd::GemmArgs{};
@@ -843,6 +858,7 @@ gd_status mlp_backward(gd_mlp* m, const void* X, const float* t, const int32_t* 
   g.C = m->dH1;
   g.ldc = HID;
   g.err = m->err;
+  g.hold = take_hold(m);
   if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
   gd::k_grad_rows<<<nblk, HID, 0, s>>>(1, nullptr, nullptr, m->dH1, m->H1, B, m->G1b, m->partial, nullptr);
   gd::k_sum_partials<<<1, HID, 0, s>>>(m->partial, nblk, HID, m->G + gd::OFF_B1);
@@ -860,6 +876,7 @@ gd_status mlp_backward(gd_mlp* m, const void* X, const float* t, const int32_t* 
   g.C = m->G + gd::OFF_W1;
   g.ldc = F_IN;
   g.err = m->err;
+  g.hold = take_hold(m);
   if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
   return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ECUDA;
 }
@@ -953,8 +970,9 @@ gd_status gd_mlp_predict(gd_mlp* m, const void* X, long long M, float* y, void* 
   cudaSetDevice(m->device);
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  const int hold = M > 0 ? take_hold(m) : 0;
   return gd::infer_launch((const __nv_bfloat16*)X, (int)M, m->W1b, m->W2b, m->P + gd::OFF_B1, m->P + gd::OFF_B2,
-                          m->w3r, m->P + gd::OFF_B3, y, m->err, sms, (cudaStream_t)stream) == cudaSuccess
+                          m->w3r, m->P + gd::OFF_B3, y, m->err, hold, sms, (cudaStream_t)stream) == cudaSuccess
              ? GD_OK
              : GD_ECUDA;
 }
@@ -992,6 +1010,15 @@ gd_status gd_mlp_error(gd_mlp* m, int* host_err) {
   if (!m || !host_err) return GD_EINVAL;
   cudaSetDevice(m->device);
   return cudaMemcpy(host_err, m->err, 4, cudaMemcpyDeviceToHost) == cudaSuccess ? GD_OK : GD_ECUDA;
+}
+
+gd_status gd_mlp_test_hold(gd_mlp* m, int on) {
+  if (!m) return GD_EINVAL;
+  cudaSetDevice(m->device);
+  m->hold = on ? 1 : 0;
+  if (on) return GD_OK;
+  if (cudaMemset(m->err, 0, 4) != cudaSuccess) return GD_ECUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? GD_OK : GD_ECUDA;
 }
 
 }  // extern "C"

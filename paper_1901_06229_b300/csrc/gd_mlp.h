@@ -25,13 +25,14 @@ struct GemmArgs {
   const float* dot_bias_dev;  // added to dot_bias when non-null (device scalar)
   float* dot_out;
   int* err;  // set to 1 if a bounded wait ran out (may be null)
+  int hold;  // test: the first MMA commit is withheld, so that the wait on it runs out
 };
 
 size_t gemm_smem_bytes();
 // Fused two-layer forward of the proposer network (persistent, one CTA per SM).
 cudaError_t infer_launch(const __nv_bfloat16* X, int M, const __nv_bfloat16* W1b, const __nv_bfloat16* W2b,
                          const float* b1, const float* b2, const float* w3r, const float* b3, float* y, int* err,
-                         int num_sms, cudaStream_t stream);
+                         int hold, int num_sms, cudaStream_t stream);
 cudaError_t gemm_launch(const GemmArgs& g, cudaStream_t stream);
 
 }  // namespace gd

@@ -58,8 +58,9 @@ def _lib2():
         L.gd_mlp_gradients.argtypes = [vp, vp, vp, vp, i, vp, vp, vp]
         L.gd_mlp_train_step.argtypes = [vp, vp, vp, vp, i, f, vp, vp]
         L.gd_mlp_error.argtypes = [vp, C.POINTER(C.c_int)]
+        L.gd_mlp_test_hold.argtypes = [vp, i]
         for n in ("gd_mlp_create", "gd_mlp_destroy", "gd_mlp_set_params", "gd_mlp_get_params", "gd_mlp_predict",
-                  "gd_mlp_gradients", "gd_mlp_train_step", "gd_mlp_error"):
+                  "gd_mlp_gradients", "gd_mlp_train_step", "gd_mlp_error", "gd_mlp_test_hold"):
             getattr(L, n).restype = C.c_int
         L._model_ready = True
     return L
@@ -119,3 +120,8 @@ class MLP:
         e = C.c_int()
         _check(_lib2().gd_mlp_error(self.h, C.byref(e)), "gd_mlp_error")
         return e.value
+
+    def test_hold(self, on):
+        """Test only: the next tensor-core launch withholds its first MMA commit, so its
+        bounded wait runs out (on=True); on=False clears the hold and the error flag."""
+        _check(_lib2().gd_mlp_test_hold(self.h, int(bool(on))), "gd_mlp_test_hold")
