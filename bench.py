@@ -71,6 +71,10 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
+    "e95d5b061be765f4": {("batched-4096lig-64grid", 14): 4684032 + 1184256,
+                         ("batched-4096lig-64grid", 15): 4559104 + 1190912,
+                         ("large-512lig-128grid", 16): 3100672 + 11520,
+                         ("large-512lig-128grid", 18): 2902528 + 10496},
     "6f657c070d65f73e": {("batched-4096lig-64grid", 14): 4555520 + 1185024,
                          ("batched-4096lig-64grid", 15): 4555264 + 1213184,
                          ("large-512lig-128grid", 16): 3054080 + 9728,
@@ -97,6 +101,10 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
+    "e95d5b061be765f4": {("batched-4096lig-64grid", 14): 8462969330,
+                         ("batched-4096lig-64grid", 15): 8463073267,
+                         ("large-512lig-128grid", 16): 15525958491,
+                         ("large-512lig-128grid", 18): 15526017451},
     "6f657c070d65f73e": {("batched-4096lig-64grid", 14): 8462969359,
                          ("batched-4096lig-64grid", 15): 8463073244,
                          ("large-512lig-128grid", 16): 15525958491,
@@ -123,6 +131,7 @@ ISSUE_PER_SM_CLK = 4
 # a hash of its source like MEASURED_TRAFFIC.
 MLP_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_mlp.cu",)
 MEASURED_MLP_TRAFFIC = {
+    "80d6c3c81be0ce7b": {4194304: 402857216 + 15846144},
     "5869ebdabcb3ead0": {4194304: 402904064 + 15991808},
     "0b6551ae97cb3c63": {4194304: 402875904 + 16060928},
 }
