@@ -103,12 +103,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // Stage rows [r0, r0 + rows) x K chunk [k0, k0 + kc) of an operand into the core-matrix
 // layout at `dst` (row group g, K chunk c at g * (kc/8) * 128 + c * 128, row r % 8 at
 // 16 bytes each).  trans: the operand is stored [K][rows] (element (r, k) at src[k * ld + r]).
-// Rows or K beyond the matrix are zero-filled.
+// Rows or K beyond the matrix are zero-filled.  Consecutive threads take consecutive K
+// chunks of a row (one 16-byte load each), or with trans consecutive rows of a K chunk
+// (so that each of the eight element loads is coalesced across the warp).
 __device__ void stage(uint8_t* dst, const __nv_bfloat16* src, int ld, int nrows_total, int ktotal, int r0, int rows,
                       int k0, int kc, bool trans) {
   const int chunks = kc / 8;
   for (int idx = threadIdx.x; idx < rows * chunks; idx += blockDim.x) {
-    const int r = idx / chunks, c = idx % chunks;
+    const int r = trans ? idx % rows : idx / chunks, c = trans ? idx / rows : idx % chunks;
     const int gr = r0 + r, gk = k0 + c * 8;
     uint4 v = make_uint4(0, 0, 0, 0);
     if (gr < nrows_total) {
@@ -153,10 +155,13 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
   const uint32_t idesc = make_idesc(128, nt);
   bool ok = true;
   uint32_t phase = 0;
-  for (int k0 = 0; k0 < g.K && ok; k0 += KC) {
-    const int kc = g.K - k0 < KC ? g.K - k0 : KC;  // multiple of 16 by contract
-    stage(sa, g.A, g.lda, g.M, g.K, m0, 128, k0, kc, g.transA);
-    stage(sb, g.B, g.ldb, g.N, g.K, n0, nt, k0, kc, g.transB);
+  // this CTA's K range (all of K unless split)
+  const int kb = g.partial ? (int)blockIdx.z * g.kslice : 0;
+  const int ke = g.partial ? min(g.K, kb + g.kslice) : g.K;
+  for (int k0 = kb; k0 < ke && ok; k0 += KC) {
+    const int kc = ke - k0 < KC ? ke - k0 : KC;  // multiple of 16 by contract
+    stage(sa, g.A, g.lda, g.M, ke, m0, 128, k0, kc, g.transA);
+    stage(sb, g.B, g.ldb, g.N, ke, n0, nt, k0, kc, g.transB);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -165,9 +170,9 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
       for (int kk = 0; kk < kc / 16; ++kk) {
         const uint64_t da = make_desc(smem_addr(sa) + kk * 256, 128, sbo);
         const uint64_t db = make_desc(smem_addr(sb) + kk * 256, 128, sbo);
-        mma_bf16(tmem, da, db, idesc, k0 > 0 || kk > 0);
+        mma_bf16(tmem, da, db, idesc, k0 > kb || kk > 0);
       }
-      if (!(g.hold && k0 == 0)) mma_commit(mbar);
+      if (!(g.hold && k0 == kb)) mma_commit(mbar);
     }
     // one outcome for the whole block: every thread takes the same branch and barriers
     ok = __syncthreads_and(mbar_wait(mbar, phase)) != 0;
@@ -182,6 +187,26 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ GemmA
       // is complete (or the late one does), and a bounded wait for it
       mma_commit(mbar);
       mbar_wait(mbar, phase);
+    }
+  } else if (g.partial) {
+    // this K range's raw sums (zeros if the range is empty) for reduce_splits
+    const int row = m0 + warp * 32 + lane;
+    float* out = g.partial + ((size_t)blockIdx.z * g.M + row) * g.N;
+    for (int c0 = 0; c0 < nt; c0 += 32) {
+      float v[32];
+      if (kb < ke) {
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      if (row < g.M) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          if (c0 + i >= nt) break;
+          out[n0 + c0 + i] = v[i];
+        }
+      }
     }
   } else {
     // epilogue: warp w owns rows 32w .. 32w + 31 (TMEM lanes)
@@ -612,8 +637,21 @@ cudaError_t gemm_launch(const GemmArgs& g, cudaStream_t st) {
   static std::atomic<bool> attr[64];
   cudaError_t e = smem_attr_once((const void*)gemm_kernel, gemm_smem_bytes(), attr);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.M + 127) / 128, (g.N + 255) / 256);
+  dim3 grid((g.M + 127) / 128, (g.N + 255) / 256, g.partial ? g.ksplit : 1);
   gemm_kernel<<<grid, 128, gemm_smem_bytes(), st>>>(g);
+  return cudaGetLastError();
+}
+
+__global__ void k_reduce_splits(const float* partial, int S, int M, int N, float* C, int ldc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  float s = 0.f;
+  for (int z = 0; z < S; ++z) s += partial[(size_t)z * M * N + i];
+  C[(size_t)(i / N) * ldc + i % N] = s;
+}
+
+cudaError_t reduce_splits(const float* partial, int S, int M, int N, float* C, int ldc, cudaStream_t st) {
+  k_reduce_splits<<<(M * N + 255) / 256, 256, 0, st>>>(partial, S, M, N, C, ldc);
   return cudaGetLastError();
 }
 
@@ -666,7 +704,8 @@ namespace {
 constexpr int F_IN = 48, HID = 256;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + HID * F_IN, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID * HID,
               OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID, NPARAM = OFF_B3 + 1;
-constexpr int COLSUM_ROWS = 256;  // rows per block of the column-sum kernels
+constexpr int COLSUM_ROWS = 32;  // rows per block of the column-sum kernels
+constexpr int MAX_SPLITS = 64;    // K splits of the weight-gradient GEMMs (K = batch rows)
 constexpr int PREDICT_CHUNK = 1 << 18;
 
 __global__ void k_gather(const __nv_bfloat16* X, const float* t, const int32_t* idx, int B, __nv_bfloat16* Xg,
@@ -766,12 +805,28 @@ struct gd_mlp {
   int* err = nullptr;
   __nv_bfloat16* H1p = nullptr;  // prediction chunk activations
   int hold = 0;                  // test: the next tensor-core launch withholds its first commit
+  float* ws = nullptr;           // split-K partial sums (MAX_SPLITS x 256 x 256)
 };
 
 namespace {
 
 using gd::HID;
 using gd::F_IN;
+
+// The weight gradients' GEMMs sum over the batch (K = B rows): split K into ranges of a
+// multiple of 64 rows, at most MAX_SPLITS of them, one CTA each (so that a 4,096-row batch
+// takes 64 x 2 CTAs instead of 2), and add the partial sums in order.
+gd_status gemm_split_k(gd_mlp* m, gd::GemmArgs g, cudaStream_t s) {
+  const int per = (g.K + gd::MAX_SPLITS - 1) / gd::MAX_SPLITS;
+  g.kslice = (per + 63) / 64 * 64;
+  g.ksplit = (g.K + g.kslice - 1) / g.kslice;
+  float* C = g.C;
+  const int ldc = g.ldc;
+  g.C = nullptr;
+  g.partial = m->ws;
+  if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  return gd::reduce_splits(m->ws, g.ksplit, g.M, g.N, C, ldc, s) == cudaSuccess ? GD_OK : GD_ECUDA;
+}
 
 // The test hold, for the one launch that takes it.
 int take_hold(gd_mlp* m) {
@@ -844,7 +899,7 @@ gd_status mlp_backward(gd_mlp* m, const void* X, const float* t, const int32_t* 
   g.ldc = HID;
   g.err = m->err;
   g.hold = take_hold(m);
-  if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  if (gemm_split_k(m, g, s) != GD_OK) return GD_ECUDA;
   // dH1 = G2 W2
   g = gd::GemmArgs{};
   g.A = m->G2b;
@@ -877,7 +932,7 @@ gd_status mlp_backward(gd_mlp* m, const void* X, const float* t, const int32_t* 
   g.ldc = F_IN;
   g.err = m->err;
   g.hold = take_hold(m);
-  if (gd::gemm_launch(g, s) != cudaSuccess) return GD_ECUDA;
+  if (gemm_split_k(m, g, s) != GD_OK) return GD_ECUDA;
   return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ECUDA;
 }
 
@@ -909,7 +964,8 @@ gd_status gd_mlp_create(int device, uint64_t seed, int max_batch, gd_mlp** out) 
             cudaMalloc(&m->partial, 4 * nblk * (HID + 1)) == cudaSuccess &&
             cudaMalloc(&m->partial2, 4 * nblk * (HID + 1)) == cudaSuccess &&
             cudaMalloc(&m->loss, 4) == cudaSuccess && cudaMalloc(&m->err, 4) == cudaSuccess &&
-            cudaMalloc(&m->H1p, 2 * (size_t)gd::PREDICT_CHUNK * HID) == cudaSuccess;
+            cudaMalloc(&m->H1p, 2 * (size_t)gd::PREDICT_CHUNK * HID) == cudaSuccess &&
+            cudaMalloc(&m->ws, 4 * (size_t)gd::MAX_SPLITS * HID * HID) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     gd_mlp_destroy(m);
@@ -941,7 +997,7 @@ gd_status gd_mlp_destroy(gd_mlp* m) {
   for (void* p : {(void*)m->P, (void*)m->Mo, (void*)m->Vo, (void*)m->G, (void*)m->w3r, (void*)m->W1b,
                   (void*)m->W2b, (void*)m->Xg, (void*)m->H1, (void*)m->H2, (void*)m->G2b, (void*)m->G1b,
                   (void*)m->tg, (void*)m->y, (void*)m->dy, (void*)m->dH1, (void*)m->partial, (void*)m->partial2,
-                  (void*)m->loss, (void*)m->err, (void*)m->H1p})
+                  (void*)m->loss, (void*)m->err, (void*)m->H1p, (void*)m->ws})
     if (p) cudaFree(p);
   delete m;
   return GD_OK;

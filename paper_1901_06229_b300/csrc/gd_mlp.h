@@ -26,7 +26,14 @@ struct GemmArgs {
   float* dot_out;
   int* err;  // set to 1 if a bounded wait ran out (may be null)
   int hold;  // test: the first MMA commit is withheld, so that the wait on it runs out
+  // split K (partial set): CTA z < ksplit of the grid's third dimension sums K range
+  // [z kslice, min(K, (z + 1) kslice)) into partial[z][M][N] (raw FP32, no epilogue);
+  // reduce_splits then adds the ranges in order into C
+  int ksplit, kslice;
+  float* partial;
 };
+// C[m][n] (row stride ldc) = sum over z < S of partial[z][m][n], in order of z.
+cudaError_t reduce_splits(const float* partial, int S, int M, int N, float* C, int ldc, cudaStream_t stream);
 
 size_t gemm_smem_bytes();
 // Fused two-layer forward of the proposer network (persistent, one CTA per SM).
