@@ -88,13 +88,15 @@ def grad_mass(P, X, t):
                         b3=np.array([dy.sum()])))
 
 
-def test_network_forward_and_gradients_match_oracle():
+# 512 rows: 8 K ranges of the weight-gradient GEMMs; 1,008: 16, the last one 48 rows;
+# 4,096: the 64-range maximum
+@pytest.mark.parametrize("B", [512, 1008, 4096])
+def test_network_forward_and_gradients_match_oracle(B):
     import torch
     from oracle import mlp as om
     from paper_1901_06229_b300 import mlp
-    B = 512
     P, X, t = _net_case(7, B)
-    net = mlp.MLP(0, seed=1, max_batch=1024)
+    net = mlp.MLP(0, seed=1, max_batch=4096)
     net.set_params(P)
     Xb = torch.tensor(X).to(torch.bfloat16).cuda()
     tt = torch.tensor(t).cuda()
