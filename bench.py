@@ -58,6 +58,9 @@ K_FALLBACK = 128
 # 99 %), so tuning 0.3 % above the target keeps the held-out recall above it.
 RECALL_TARGET = 0.99
 VAL_RECALL_TARGET = 0.993
+# the serving sub-record of the default line: runs x seconds of Poisson arrivals at --rate
+SERVE_SUB_REPEATS = 3
+SERVE_SUB_SECONDS = 2.0
 # FP32 operations the kernel executes (the "executed" roofline figure)
 EXEC_OPS_PER_PAIR = 3        # 2 FFMA (|x_a - x_b|^2 + (cos-1) P + sin Q) + FMNMX
 EXEC_OPS_PER_ATOM_MOVE = 6   # turn about the bond axis (6 FFMA; coordinates are grid units)
@@ -565,10 +568,17 @@ def run_stream(args, world, rank, local):
 
 
 def run_serve(args, world, rank, local):
+    rec = serve_record(args, world, rank, local, args.stream_repeats, args.stream_seconds)
+    if rec is not None:
+        print(json.dumps(rec))
+
+
+def serve_record(args, world, rank, local, repeats, seconds):
     """Streaming screen on the device queue: Poisson arrivals submitted to one running
     search launch (gd_server: continuous batching on the device, plain exhaustive search
     of every restart), results collected as they finish; ligands/s and per-ligand latency
-    (finish seen on the host minus arrival) over repeated runs, median and range."""
+    (finish seen on the host minus arrival) over `repeats` runs of at least `seconds` of
+    arrivals each, median and range."""
     import torch
     from paper_1901_06229_b300 import geodock as gdk, serve
     torch.cuda.set_device(local)
@@ -586,10 +596,10 @@ def run_serve(args, world, rank, local):
     got = 0
     while got < warm:
         got += len(srv.collect()[0])
-    n_req = max(n, int(np.ceil(args.rate * args.stream_seconds)))
+    n_req = max(n, int(np.ceil(args.rate * seconds)))
     runs = []
     with ClockSampler(dev) as clk:
-        for rep in range(args.stream_repeats):
+        for rep in range(repeats):
             arr = serve.poisson_arrivals(n_req, args.rate, seed=rank + 1000 * rep)
             lig = np.arange(n_req) % n
             done_t = np.zeros(n_req)
@@ -623,21 +633,21 @@ def run_serve(args, world, rank, local):
     pk.free()
     ctx.close()
     if rank != 0:
-        return
+        return None
 
     def stat(key):
         v = np.array([r[key] for r in runs])
         return {"median": float(np.median(v)), "min": float(v.min()), "max": float(v.max())}
-    print(json.dumps({
+    return {
         "metric": "ligands/s and per-ligand latency (device-queue screen, 1 B300)",
         "value": stat("ligands_per_s")["median"], "unit": "ligands/s", "n_gpus": world,
-        "steps": args.stream_repeats, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "steps": repeats, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators)",
         "config": workload_config(w, "resident pocket; no flush (serving)") | {
-            "arrivals": f"Poisson, {args.rate:g} ligands/s", "requests_per_run": n_req, "runs": args.stream_repeats,
+            "arrivals": f"Poisson, {args.rate:g} ligands/s", "requests_per_run": n_req, "runs": repeats,
             "search": "every restart (plain method)", "capacity": srv.capacity, "budget_bytes": 8 << 30},
         "ligands_per_s": stat("ligands_per_s"), "latency_ms": {"p50": stat("p50_ms"), "p99": stat("p99_ms")},
-        "server": st, "runs": runs, "clocks": clk.summary()}))
+        "server": st, "runs": runs, "clocks": clk.summary()}
 
 
 def main():
@@ -655,8 +665,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ligands", type=int, default=None, help="smaller batch (profiling runs only)")
-    ap.add_argument("--sub", default="large,learned24",
-                    help="batched line: other workloads measured after it (large, learned24, learned)")
+    ap.add_argument("--sub", default="large,learned24,serve",
+                    help="batched line: other workloads measured after it (large, learned24, learned, serve)")
     ap.add_argument("--no-sub", action="store_true", help="batched line only")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -766,6 +776,10 @@ def main():
         if name in ("learned", "learned24"):
             rec = learned_record(args, world, rank, local, name, min(args.steps, 20), args.warmup, cpu=False)
             line[name] = learned_summary(rec)
+        if name == "serve":
+            # the device-queue screen at the offered rate, shorter runs than --workload serve
+            rec = serve_record(args, world, rank, local, SERVE_SUB_REPEATS, SERVE_SUB_SECONDS)
+            line[name] = {k: rec[k] for k in rec if k != "runs"}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line))
