@@ -5,8 +5,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("gd_api.cu", "gd_search.cu", "gd_select.cu", "gd_noalloc.cu",
-                                                "gd_mlp.cu", "gd_peak.cu")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("gd_api.cu", "gd_search.cu", "gd_select.cu", "gd_features.cu",
+                                                "gd_noalloc.cu", "gd_mlp.cu", "gd_peak.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("gd_internal.h", "gd_mlp.h", "gd_pack.h", "gd_peak.h")] + \
     [os.path.join(ROOT, "include", f) for f in ("geodock.h", "geodock_mlp.h")]
 LIB = os.path.join(HERE, "libgeodock.so")
