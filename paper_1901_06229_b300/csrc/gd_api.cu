@@ -1232,6 +1232,7 @@ gd_status server_pump(gd_server* s) {
     return fail(GD_ETIMEOUT, *s->h_status == gd::ERR_SLOT_TIMEOUT ? "a server wait for a staged slot timed out"
                                                                    : "the server's pocket staging wait timed out");
   if (*s->h_stop || !server_unfinished(s)) return GD_OK;
+  GD_CUDA(cudaMemsetAsync(s->sv.idle_state, 0, sizeof(unsigned long long), s->stream));
   GD_CUDA(gd::launch_serve(s->args, s->sv, s->cfg, s->stream));
   GD_CUDA(cudaEventRecord(s->ended, s->stream));
   s->running = true;
@@ -1337,9 +1338,11 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   const size_t d_stop = o;    o += 8;
   const size_t d_poll = o;    o += 8;
   const size_t d_polls = o;   o += 8;
+  const size_t d_idle = o;    o += 8;
   const size_t d_dummy = o;   o = align_up(o + 8, 256);
   const size_t d_parked = o;  o = align_up(o + 8 * (size_t)c->num_sms * 64, 256);  // every resident warp
   const size_t d_ready = o;   o = align_up(o + 8 * cap, 256);
+  const size_t d_claim = o;   o = align_up(o + 8 * cap, 256);
   const size_t d_done = o;    o = align_up(o + 4 * cap, 256);
   const size_t d_n = o;       o = align_up(o + 4 * cap, 256);
   const size_t d_r = o;       o = align_up(o + 4 * cap, 256);
@@ -1468,6 +1471,7 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   v.stop_dev = (unsigned long long*)(d + d_stop);
   v.last_poll = (unsigned long long*)(d + d_poll);
   v.slot_ready = (unsigned long long*)(d + d_ready);
+  v.slot_claim = (unsigned long long*)(d + d_claim);
   v.result_seq = (unsigned long long*)(hd + o_rseq);
   v.rec = (const unsigned char*)(hd + o_rec);
   v.rec_stride = rec_stride;
@@ -1479,6 +1483,7 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   v.wait_cycles = SERVE_WAIT_CYCLES;
   v.polls = (unsigned long long*)(d + d_polls);
   v.parked = (unsigned long long*)(d + d_parked);
+  v.idle_state = (unsigned long long*)(d + d_idle);
   v.hold_seq = -1;
   e = gd::launch_restart_tables(a, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

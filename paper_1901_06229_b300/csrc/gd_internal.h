@@ -121,6 +121,7 @@ struct ServeArgs {
   unsigned long long* stop_dev;         // device copy of *stop
   unsigned long long* last_poll;        // globaltimer of the last read of the mapped words
   unsigned long long* slot_ready;       // [cap] seq + 1 once the slot holds ligand seq
+  unsigned long long* slot_claim;       // [cap] seq + 1 once a warp has taken the staging of ligand seq
   unsigned long long* result_seq;       // (mapped) [cap] seq + 1 once ligand seq's results are written
   const unsigned char* rec;             // (mapped) [cap] ligand records of rec_stride bytes
   long long rec_stride;
@@ -131,7 +132,11 @@ struct ServeArgs {
   long long hold_seq;                   // testing: the ligand whose slot is never released (-1)
   unsigned long long* polls;            // reads of the mapped control words (device counter)
   unsigned long long* parked;           // [warps of the launch] ticket + 1 a warp held when its launch ended idle
+  unsigned long long* idle_state;       // this launch's warps: started << 31 | idle or gone | SERVE_CLOSING
+                                        // (zeroed before every launch)
 };
+constexpr unsigned long long SERVE_CLOSING = 1ull << 62;
+constexpr unsigned long long SERVE_STARTED_ONE = 1ull << 31;
 
 // A ligand record in the server's mapped host memory (slot s at rec + s * rec_stride):
 // header, then xyz float4[amax] (preorder, w unused), perm uint8[amax], RotDesc[rmax]

@@ -1189,13 +1189,16 @@ __global__ void __launch_bounds__(B == BUILD_LEAN ? 256 : (B == BUILD_COMPACT ? 
 // record into its slot of mapped host memory and raises a published count; each warp
 // takes a ticket for the next work item (4 restarts of one ligand) and starts on it once
 // it is published; a ticket still unpublished when the launch ends idle is parked for the
-// same warp of the next launch, which goes on from the same device-side counter.  The warp that claims a ligand's first item copies its record into
-// the slot's device arrays (centred coordinates computed as the pose-setup kernel does)
-// and releases the slot; warps with the ligand's later items wait for that (bounded).
+// same warp of the next launch, which goes on from the same device-side counter.  The
+// first warp to start on any of a ligand's items (an atomic per slot decides) copies its
+// record into the slot's device arrays (centred coordinates computed as the pose-setup
+// kernel does) and releases the slot; warps with the ligand's other items wait for that
+// (bounded).
 // The warp that completes a ligand's restarts writes its results into the slot's row of
 // the mapped result arrays and raises the slot's result sequence.  Every wait is bounded
-// by the SM clock: an idle launch exits after idle_cycles, a slot wait that runs out sets
-// ERR_SLOT_TIMEOUT in the mapped status word and ends the warp.
+// by the SM clock: a launch closes once every warp has waited idle_cycles without work
+// (or is gone), a slot wait that runs out sets ERR_SLOT_TIMEOUT in the mapped status word
+// and ends the warp.
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -1223,16 +1226,39 @@ __device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long
   return v;
 }
 
+// The launch's warp counts -- warps started (bits 31..61), warps idle or gone (bits
+// 0..30) -- and its closing flag, changed together by compare-and-swap.  step +1: this
+// warp is idle or gone (the warp that makes every started warp idle or gone sets
+// SERVE_CLOSING); -1: it has work again; 0: it starts (a warp scheduled late, after the
+// others, joins the count).  Each returns false, changing nothing, once the launch is
+// closing.
+__device__ bool serve_idle_step(const ServeArgs& s, int step) {
+  unsigned long long v = ld_relaxed_gpu(s.idle_state);
+  for (;;) {
+    if (v & SERVE_CLOSING) return false;
+    unsigned long long nv = step > 0 ? v + 1ull : (step < 0 ? v - 1ull : v + SERVE_STARTED_ONE);
+    if (step > 0 && (nv & (SERVE_STARTED_ONE - 1ull)) == (nv >> 31)) nv |= SERVE_CLOSING;
+    const unsigned long long w = atomicCAS(s.idle_state, v, nv);
+    if (w == v) return true;
+    v = w;
+  }
+}
+
 // Lane 0 of warp gw (its position in the grid, the same in every launch): take the next
 // work item and wait until it is published (0, *t set); 1 when the host asked the launch
-// to stop (the ticket is dropped: nothing more is published); 2 when the item was not
-// published within idle_cycles SM cycles -- the ticket is then parked in parked[gw] and
-// taken up again by the same grid position of the next launch, so no item is lost.
-// Tickets come from one atomicAdd each, so warps never retry against each other.  The
-// mapped control words are read by one warp at a time, at most every 2 us of the global
-// timer, and in any case by a warp whose own last read is about 0.5 ms of its SM clock
-// old (so no timer can keep the launch from seeing new work); between checks a waiting
-// warp sleeps 64 ns doubling up to 4 us.
+// to stop (the ticket is dropped: nothing more is published); 2 when the launch closes
+// idle -- the ticket is then parked in parked[gw] and taken up again by the same grid
+// position of the next launch, so no item is lost.  A warp whose item is not published
+// within idle_cycles SM cycles counts itself idle; the launch closes when every warp is
+// idle or gone (one compare-and-swap decides it), so no warp leaves while others run:
+// a parked item is never one that a running launch's warps wait for; a warp that starts
+// after the launch closed leaves without a ticket.  (Past 64
+// idle_cycles a warp leaves regardless, which only bounds the wait.)  Tickets come from
+// one atomicAdd each, so warps never retry against each other.  The mapped control words
+// are read by one warp at a time, at most every 2 us of the global timer, and in any
+// case by a warp whose own last read is about 0.5 ms of its SM clock old (so no timer
+// can keep the launch from seeing new work); between checks a waiting warp sleeps 64 ns
+// doubling up to 32 us.
 __device__ int serve_claim(const ServeArgs& s, int gw, unsigned long long* t, long long& my_poll) {
   unsigned long long tk = s.parked[gw];
   if (tk) {
@@ -1243,8 +1269,10 @@ __device__ int serve_claim(const ServeArgs& s, int gw, unsigned long long* t, lo
   }
   const long long c0 = clock64();
   unsigned sleep_ns = 64;
+  bool idle = false;
   for (;;) {
     if (tk < ld_acquire_gpu(s.pub_dev) * (unsigned long long)s.chunks) {
+      if (idle && !serve_idle_step(s, -1)) break;  // published as the launch closed
       *t = tk;
       return 0;
     }
@@ -1262,16 +1290,20 @@ __device__ int serve_claim(const ServeArgs& s, int gw, unsigned long long* t, lo
       if (tk < ph * (unsigned long long)s.chunks) continue;
     }
     if (ld_relaxed_gpu(s.stop_dev)) return 1;
-    if (c - c0 > s.idle_cycles) {
-      s.parked[gw] = tk + 1ull;
-      return 2;
+    if (!idle && c - c0 > s.idle_cycles) {
+      idle = true;
+      serve_idle_step(s, +1);
     }
+    if (idle && (ld_relaxed_gpu(s.idle_state) & SERVE_CLOSING)) break;
+    if (c - c0 > 64 * s.idle_cycles) break;
     // backoff to 32 us: with every warp of the GPU idle here, shorter sleeps put ~1e9
     // loads/s of these words on one L2 slice and starved the warps still searching
     // (their items ran 200x slower at the end of a stream)
     __nanosleep(sleep_ns);
     sleep_ns = sleep_ns < 32768u ? 2u * sleep_ns : 32768u;
   }
+  s.parked[gw] = tk + 1ull;
+  return 2;
 }
 
 // The warp that claimed ligand seq's first item: its record (mapped host memory, read
@@ -1380,6 +1412,11 @@ __global__ void __launch_bounds__(B == BUILD_LEAN ? 256 : 512, B == BUILD_LEAN ?
   int e0 = 0;
   long long my_poll = clock64();
   const int gw = (int)(blockIdx.x * (blockDim.x >> 5)) + warp;
+  // join the launch's warp count; a launch that closed before this warp was scheduled has
+  // nothing left for it (a ticket it parked earlier waits for the next launch)
+  int joined = 0;
+  if (lane == 0) joined = serve_idle_step(sv, 0) ? 1 : 0;
+  if (!__shfl_sync(FULL, joined, 0)) return;
   for (;;) {
     unsigned long long t = 0;
     int st = 0;
@@ -1390,12 +1427,19 @@ __global__ void __launch_bounds__(B == BUILD_LEAN ? 256 : 512, B == BUILD_LEAN ?
     const unsigned long long seq = t / (unsigned long long)sv.chunks;
     const int c = (int)(t % (unsigned long long)sv.chunks);
     const int slot = (int)(seq % (unsigned long long)sv.cap);
-    if (c == 0) {
+    // the first warp to reach ligand seq, whichever of its items it holds, stages the
+    // slot: the warp holding the first item may have parked it and left an idle launch
+    // while live warps took the later items once they were published
+    unsigned long long prev = 0;
+    if (lane == 0) prev = atomicMax(sv.slot_claim + slot, seq + 1ull);
+    prev = __shfl_sync(FULL, prev, 0);
+    if (prev < seq + 1ull) {
       serve_stage(a, sv, slot, seq, lane);
     } else if (!serve_wait(sv, slot, seq, lane)) {
       if (lane == 0) {
         *reinterpret_cast<volatile int*>(sv.status) = ERR_SLOT_TIMEOUT;
         __threadfence_system();
+        serve_idle_step(sv, +1);  // gone: the idle warps need not wait for this one
       }
       break;
     }

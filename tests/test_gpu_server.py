@@ -108,6 +108,46 @@ def test_slots_are_reused_and_idle_launches_restart(ctx):
     pk.free()
 
 
+def test_ligands_published_while_idle_warps_park_their_tickets(ctx):
+    """Batches arriving just as the idle launch's warps give up: warps claimed their
+    tickets at different times (some at once, some after their last item), so they run
+    out of idle time one after another, and a batch published in between must neither
+    find a ligand's first item parked by a warp that has left while live warps hold its
+    later items (the launch closes only when every warp is idle, and the first warp to
+    reach a ligand stages it), nor lose the items of a batch published as the launch
+    closes (parked, taken up by the next launch).  No wait runs out and every result is
+    gd_dock_batch's.  The arrival time sweeps from half an idle timeout after a batch's
+    last result to past the launch's close."""
+    w = synth.workload_stream(48, seed_offset=73)
+    pk = ctx.load_pocket(w.pocket)
+    idle_ms = 10
+    srv = gdk.Server(ctx, pk, w.params, capacity=64, max_atoms=256, max_rotamers=48, idle_ms=idle_ms)
+    ref = ctx.dock_batch(pk, w.batch, w.params).fetch()
+    cycles = 30
+    t_batch = 0.0
+    for c in range(cycles):
+        t_sub = time.perf_counter()
+        first = srv.submit(w.batch)
+        got = {}
+        while len(got) < 48:
+            assert time.perf_counter() < t_sub + 30, (c, len(got), srv.stats())
+            seq, sc, ob = srv.collect()
+            for q, a, b in zip(seq.tolist(), sc.tolist(), ob.tolist()):
+                got[q - first] = (a, b)
+        t_batch += time.perf_counter() - t_sub
+        np.testing.assert_array_equal([got[i][0] for i in range(48)], ref["best_score"], err_msg=f"cycle {c}")
+        np.testing.assert_array_equal([got[i][1] for i in range(48)], ref["best_orient"], err_msg=f"cycle {c}")
+        # the next batch lands between 0.5 and 2 idle timeouts after this one's last result
+        wake = time.perf_counter() + 1e-3 * idle_ms * (0.5 + 1.5 * c / (cycles - 1))
+        while time.perf_counter() < wake:
+            pass
+    st = srv.stats()
+    print(st, "batch ms", round(1e3 * t_batch / cycles, 2))
+    assert st["finished"] == 48 * cycles and st["launches"] >= 2
+    srv.close()
+    pk.free()
+
+
 def test_a_held_slot_times_out_and_the_context_stays_usable(ctx):
     w = synth.workload_stream(8, seed_offset=72)
     pk = ctx.load_pocket(w.pocket)
