@@ -74,6 +74,14 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
+    "0dd17a1cd3e68422": {("batched-4096lig-64grid", 14): 4561408 + 1121024,
+                         ("batched-4096lig-64grid", 15): 4743424 + 1152512,
+                         ("large-512lig-128grid", 16): 2742528 + 8960,
+                         ("large-512lig-128grid", 18): 3049216 + 12800},
+    "250345eb4db4aed3": {("batched-4096lig-64grid", 14): 4553472 + 1180160,
+                         ("batched-4096lig-64grid", 15): 4556544 + 1187072,
+                         ("large-512lig-128grid", 16): 2849536 + 9728,
+                         ("large-512lig-128grid", 18): 3107840 + 10240},
     "e95d5b061be765f4": {("batched-4096lig-64grid", 14): 4684032 + 1184256,
                          ("batched-4096lig-64grid", 15): 4559104 + 1190912,
                          ("large-512lig-128grid", 16): 3100672 + 11520,
@@ -104,6 +112,14 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
+    "0dd17a1cd3e68422": {("batched-4096lig-64grid", 14): 8462969337,
+                         ("batched-4096lig-64grid", 15): 8463073215,
+                         ("large-512lig-128grid", 16): 15525958569,
+                         ("large-512lig-128grid", 18): 15526017496},
+    "250345eb4db4aed3": {("batched-4096lig-64grid", 14): 8462969343,
+                         ("batched-4096lig-64grid", 15): 8463073238,
+                         ("large-512lig-128grid", 16): 15525958491,
+                         ("large-512lig-128grid", 18): 15526017496},
     "e95d5b061be765f4": {("batched-4096lig-64grid", 14): 8462969330,
                          ("batched-4096lig-64grid", 15): 8463073267,
                          ("large-512lig-128grid", 16): 15525958491,
