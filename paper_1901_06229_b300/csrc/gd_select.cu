@@ -26,37 +26,44 @@ __global__ void select_kernel(const float* pred, int L, int O, int k, int kf, fl
   const int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (li >= L) return;
   const float* p = pred + (size_t)li * O;
-  // orderable keys: larger prediction first, then smaller restart id
+  // orderable keys of the lane's restarts o = lane + 32 s (larger prediction first),
+  // loaded once; the ranking takes the largest key, ties to the smaller restart id
+  unsigned ord[8];
+  unsigned avail = 0u;  // bit s: restart lane + 32 s not ranked yet
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int o = s * 32 + lane;
+    ord[s] = 0u;
+    if (o < O) {
+      const unsigned u = __float_as_uint(p[o]);
+      ord[s] = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+      avail |= 1u << s;
+    }
+  }
   // rank the k best; a ligand that falls back and searches only its kf < O best is
   // ranked on to kf (rows of topk are kt = kf < O ? kf : k long)
   const int kt = kf < O ? kf : k;
   float first = 0.f, last = 0.f;
   bool fallback = false;
-  unsigned taken[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // bit per (lane, slot): restarts o = lane + 32 s
   for (int r = 0; r < kt; ++r) {
     if (r == k) {  // the k best are ranked: fall back?
       fallback = rule ? first - last > margin : first - last < margin;
       if (!fallback) break;
     }
-    unsigned long long best = 0;
-    for (int sidx = 0; sidx * 32 + lane < O && sidx < 8; ++sidx) {
-      if (taken[sidx]) continue;
-      const int o = sidx * 32 + lane;
-      const unsigned u = __float_as_uint(p[o]);
-      const unsigned ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-      const unsigned long long key = ((unsigned long long)ord << 32) | (0xFFFFFFFFu - (unsigned)o);
-      best = key > best ? key : best;
-    }
+    unsigned mx = 0u;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long q = __shfl_xor_sync(FULL, best, off);
-      best = q > best ? q : best;
-    }
-    const int o = (int)(0xFFFFFFFFu - (unsigned)(best & 0xFFFFFFFFu));
-    if ((o & 31) == lane) taken[o >> 5] = 1;
+    for (int s = 0; s < 8; ++s)
+      if ((avail >> s) & 1u) mx = ord[s] > mx ? ord[s] : mx;
+    mx = __reduce_max_sync(FULL, mx);
+    unsigned mine = 0xFFFFu;  // this lane's smallest restart holding the maximum
+#pragma unroll
+    for (int s = 7; s >= 0; --s)
+      if (((avail >> s) & 1u) && ord[s] == mx) mine = (unsigned)(s * 32 + lane);
+    const int o = (int)__reduce_min_sync(FULL, mine);
+    if ((o & 31) == lane) avail &= ~(1u << (o >> 5));
     if (lane == 0) topk[(size_t)li * kt + r] = (uint16_t)o;
-    if (r < k) {
-      const float v = p[o];
+    if (r < k) {  // the prediction itself, back from its key
+      const float v = __uint_as_float((mx & 0x80000000u) ? (mx & 0x7FFFFFFFu) : ~mx);
       if (r == 0) first = v;
       last = v;
     }
@@ -68,30 +75,54 @@ __global__ void select_kernel(const float* pred, int L, int O, int k, int kf, fl
   }
 }
 
-// Exclusive scan of the counts in queue order (one block): off[p] for position p.
+// Exclusive scan of the counts in queue order (one block of 1024 threads, 1024 positions
+// at a time: warp shuffles, then the warps' totals): off[p] for position p.  The counts
+// of up to 16 chunks are loaded before any is scanned, so their loads overlap.
 __global__ void scan_kernel(const int32_t* order, const int32_t* cnt, int L, int32_t* off, int32_t* total) {
-  __shared__ int32_t part[1024];
-  const int per = (L + blockDim.x - 1) / blockDim.x;
-  const int p0 = threadIdx.x * per, p1 = min(L, p0 + per);
-  int32_t s = 0;
-  for (int p = p0; p < p1; ++p) s += cnt[order[p]];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int32_t run = 0;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      const int32_t v = part[t];
-      part[t] = run;
-      run += v;
+  __shared__ int32_t wsum[32];
+  __shared__ int32_t chunk_total;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t carry = 0;
+  int32_t pre[16];
+  for (int base = 0; base < L; base += 1024) {
+    const int c = (base >> 10) & 15;
+    if (c == 0) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int p = base + 1024 * q + (int)threadIdx.x;
+        pre[q] = p < L ? cnt[order[p]] : 0;
+      }
     }
-    *total = run;
+    int32_t v = pre[0];
+#pragma unroll
+    for (int q = 1; q < 16; ++q)
+      if (q == c) v = pre[q];
+    const int p = base + (int)threadIdx.x;
+    int32_t x = v;  // inclusive scan within the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t y = __shfl_up_sync(FULL, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const int32_t t = wsum[lane];
+      int32_t y = t;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t z = __shfl_up_sync(FULL, y, d);
+        if (lane >= d) y += z;
+      }
+      wsum[lane] = y - t;  // exclusive: the warps before this one
+      if (lane == 31) chunk_total = y;
+    }
+    __syncthreads();
+    if (p < L) off[p] = carry + wsum[warp] + x - v;
+    carry += chunk_total;
+    __syncthreads();
   }
-  __syncthreads();
-  s = part[threadIdx.x];
-  for (int p = p0; p < p1; ++p) {
-    off[p] = s;
-    s += cnt[order[p]];
-  }
+  if (threadIdx.x == 0) *total = carry;
 }
 
 // Items (rows li * O + o) of every ligand at its queue offset: its ranked restarts
