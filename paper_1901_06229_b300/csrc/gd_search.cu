@@ -1249,16 +1249,15 @@ __device__ bool serve_idle_step(const ServeArgs& s, int step) {
 // to stop (the ticket is dropped: nothing more is published); 2 when the launch closes
 // idle -- the ticket is then parked in parked[gw] and taken up again by the same grid
 // position of the next launch, so no item is lost.  A warp whose item is not published
-// within idle_cycles SM cycles counts itself idle; the launch closes when every warp is
-// idle or gone (one compare-and-swap decides it), so no warp leaves while others run:
-// a parked item is never one that a running launch's warps wait for; a warp that starts
-// after the launch closed leaves without a ticket.  (Past 64
-// idle_cycles a warp leaves regardless, which only bounds the wait.)  Tickets come from
-// one atomicAdd each, so warps never retry against each other.  The mapped control words
-// are read by one warp at a time, at most every 2 us of the global timer, and in any
-// case by a warp whose own last read is about 0.5 ms of its SM clock old (so no timer
-// can keep the launch from seeing new work); between checks a waiting warp sleeps 64 ns
-// doubling up to 32 us.
+// within idle_cycles SM cycles counts itself idle; the launch closes when every started
+// warp is idle or gone (one compare-and-swap decides it), so no warp leaves while others
+// run: a parked item is never one that a running launch's warps wait for, and a warp that
+// starts after the launch closed leaves without a ticket.  (Past 64 idle_cycles a warp
+// leaves regardless, which only bounds the wait.)  Tickets come from one atomicAdd each,
+// so warps never retry against each other.  The mapped control words are read by one
+// warp at a time, at most every 2 us of the global timer, and in any case by a warp whose
+// own last read is about 0.5 ms of its SM clock old (so no timer can keep the launch from
+// seeing new work); between checks a waiting warp sleeps 64 ns doubling up to 32 us.
 __device__ int serve_claim(const ServeArgs& s, int gw, unsigned long long* t, long long& my_poll) {
   unsigned long long tk = s.parked[gw];
   if (tk) {
