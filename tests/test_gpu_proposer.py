@@ -30,10 +30,20 @@ def gpu_features(ctx, w):
     return xf.cpu().numpy(), xb.float().cpu().numpy()
 
 
-@pytest.mark.parametrize("which", ["batched", "single", "large"])
+def _slot_boundary_workload():
+    """Ligands on both sides of the feature kernel's atom-slot variants (1, 2, 4 or 8 atoms
+    per lane: at most 32, 64, 128 or 256 atoms), and the largest the generator builds."""
+    ligs = []
+    for i, n in enumerate((25, 32, 33, 64, 65, 128, 129, 250)):
+        rng = synth.SplitMix64(synth.ligand_seed(synth.BASE_SEED + 77, i))
+        ligs.append(synth.gen_ligand(rng, n, max(1, n // 6)))
+    return synth.Workload("slot-boundaries", synth.pocket_64(), synth.pack(ligs), synth.SearchParams(2, 2, 2, 64))
+
+
+@pytest.mark.parametrize("which", ["batched", "single", "large", "slot_boundaries"])
 def test_features_match_oracle(ctx, which):
     w = {"batched": lambda: synth.workload_batched(12), "single": synth.workload_single,
-         "large": lambda: synth.workload_large(2)}[which]()
+         "large": lambda: synth.workload_large(2), "slot_boundaries": _slot_boundary_workload}[which]()
     xf, xb = gpu_features(ctx, w)
     O = w.params.n_orient
     rng = np.random.default_rng(3)
