@@ -251,10 +251,11 @@ gd_status gd_measure_peaks(int device, void* stream, double* ffma_per_s, double*
  * control words.  gd_server_submit validates and packs ligands into free slots on the
  * host and publishes them; a persistent launch on the server's own stream takes work,
  * 4 restarts of one ligand at a time, as soon as it is published, copies each ligand's record into
- * its slot when it starts it, searches every restart exactly as gd_dock_batch does (same
- * results, bit for bit) and writes each ligand's results to host memory as soon as its
- * last restart is done.  An idle launch ends after `idle_ms`; any later call that finds
- * published work unclaimed launches it again.  Waits on the device are bounded by the SM
+ * its slot when it starts the first of them, searches every restart exactly as gd_dock_batch
+ * does (same results, bit for bit) and writes each ligand's results to host memory as soon
+ * as its last restart is done.  A launch ends once every one of its warps has waited
+ * `idle_ms` without work (work that arrives as it ends waits for the next launch); any
+ * later call that finds published work unfinished launches it again.  Waits on the device are bounded by the SM
  * clock: a warp that waits longer than about 0.5 s for a slot being staged sets an error,
  * which the next gd_server_poll / gd_server_collect reports as GD_ETIMEOUT (the server
  * must then be destroyed; the context stays usable); a blocking gd_server_poll gives up
