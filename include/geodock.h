@@ -278,6 +278,22 @@ gd_status gd_server_create(gd_ctx* ctx, const gd_pocket* pocket, const gd_search
  * sequence number *first_seq, the others the following ones. */
 gd_status gd_server_submit(gd_server* srv, const gd_ligand_batch* batch, const int32_t* sel, int32_t n_sel,
                            uint64_t* first_seq);
+/* As gd_server_submit, but ligand i of the submission searches only the restarts
+ * restarts[i * stride .. + n_restarts[i]) (host memory, copied before the call returns;
+ * distinct ids in [0, O), 1 <= n_restarts[i] <= min(O, stride)), as gd_job_launch_proposed
+ * does for the restarts a selection chose: its results are the best over those restarts
+ * (ties to the smaller restart), bit for bit what the proposed search gives for the same
+ * restarts, and its counters count those restarts.  This is the learned screen's path
+ * into the running launch (Sec. 3.1's restart loop over a subset of the restarts). */
+gd_status gd_server_submit_restarts(gd_server* srv, const gd_ligand_batch* batch, const int32_t* sel, int32_t n_sel,
+                                    const uint16_t* restarts, const int32_t* n_restarts, int32_t stride,
+                                    uint64_t* first_seq);
+/* Leave free_sms of the device's SMs out of the server's launch, for other kernels that
+ * run beside it (e.g. the proposer's features and network for the next arrivals).  They
+ * stay free when the server's tile holds one block per SM (a wide tile whose buffers need
+ * most of an SM's shared memory); with smaller blocks it only shrinks the launch.  Call it
+ * before the first submission (GD_EBUSY afterwards); GD_EINVAL unless 0 <= free_sms < SMs. */
+gd_status gd_server_reserve_sms(gd_server* srv, int free_sms);
 /* Results of ligand seq; blocking = 0 returns GD_ENOTREADY while it is searched. */
 gd_status gd_server_poll(gd_server* srv, uint64_t seq, gd_result_batch* out, int blocking);
 /* Up to max finished ligands: their sequence numbers, best scores and best restarts (any

@@ -1286,7 +1286,7 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   s->nat.assign(capacity, 0);
   s->nrot.assign(capacity, 0);
   const long long cap = capacity, amax = s->amax, rmax = s->rmax, emax = s->emax;
-  const long long rec_stride = gd::serve_rec_bytes(s->amax, s->rmax, s->emax);
+  const long long rec_stride = gd::serve_rec_bytes(s->amax, s->rmax, s->emax, O);
   // mapped host memory
   size_t o = 0;
   const size_t o_ctrl = o;   o = align_up(o + 256, 256);
@@ -1343,6 +1343,7 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   const size_t d_parked = o;  o = align_up(o + 8 * (size_t)c->num_sms * 64, 256);  // every resident warp
   const size_t d_ready = o;   o = align_up(o + 8 * cap, 256);
   const size_t d_claim = o;   o = align_up(o + 8 * cap, 256);
+  const size_t d_nres = o;    o = align_up(o + 4 * cap, 256);
   const size_t d_done = o;    o = align_up(o + 4 * cap, 256);
   const size_t d_n = o;       o = align_up(o + 4 * cap, 256);
   const size_t d_r = o;       o = align_up(o + 4 * cap, 256);
@@ -1358,6 +1359,7 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   const size_t d_prigid = o;  o = align_up(o + 2 * (size_t)(cap * O), 256);
   const size_t d_rmat = o;    o = align_up(o + 36 * (size_t)O, 256);
   const size_t d_quat = o;    o = align_up(o + 16 * (size_t)O, 256);
+  const size_t d_res = o;     o = align_up(o + 2 * (size_t)cap * O, 256);
   s->dev_bytes = o;
   if ((st = dev_alloc(c, s->dev_bytes, &s->d_mem))) {
     s->d_mem = nullptr;
@@ -1472,6 +1474,8 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   v.last_poll = (unsigned long long*)(d + d_poll);
   v.slot_ready = (unsigned long long*)(d + d_ready);
   v.slot_claim = (unsigned long long*)(d + d_claim);
+  v.slot_nres = (int32_t*)(d + d_nres);
+  v.slot_res = (uint16_t*)(d + d_res);
   v.result_seq = (unsigned long long*)(hd + o_rseq);
   v.rec = (const unsigned char*)(hd + o_rec);
   v.rec_stride = rec_stride;
@@ -1496,8 +1500,12 @@ gd_status gd_server_create(gd_ctx* c, const gd_pocket* pk, const gd_search_param
   return GD_OK;
 }
 
-gd_status gd_server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t* sel, int32_t n_sel,
-                           uint64_t* first_seq) {
+namespace {
+
+// gd_server_submit(_restarts): restarts NULL searches every restart of each ligand; else
+// ligand i of the submission searches restarts[i * res_stride .. + n_restarts[i]).
+gd_status server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t* sel, int32_t n_sel,
+                        const uint16_t* restarts, const int32_t* n_restarts, int32_t res_stride, uint64_t* first_seq) {
   if (!s || !b) return fail(GD_EINVAL, "NULL argument");
   cudaSetDevice(s->ctx->device);
   const int LB = b->n_ligands;
@@ -1513,6 +1521,23 @@ gd_status gd_server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t
   for (int i = 0; i < n; ++i) {
     const int li = sel ? sel[i] : i;
     if (li < 0 || li >= LB) return fail(GD_EINVAL, "sel[%d] = %d outside [0, %d)", i, li, LB);
+  }
+  if (restarts) {
+    if (!n_restarts) return fail(GD_EINVAL, "restart lists without their lengths");
+    std::vector<unsigned char> seen((size_t)s->O);
+    for (int i = 0; i < n; ++i) {
+      const int k = n_restarts[i];
+      if (k < 1 || k > s->O || k > res_stride)
+        return fail(GD_EINVAL, "ligand %d of the submission: %d restarts outside [1, min(%d, stride %d)]", i, k, s->O,
+                    res_stride);
+      std::fill(seen.begin(), seen.end(), 0);
+      for (int q = 0; q < k; ++q) {
+        const int o = restarts[(size_t)i * res_stride + q];
+        if (o >= s->O) return fail(GD_EINVAL, "ligand %d of the submission: restart %d outside [0, %d)", i, o, s->O);
+        if (seen[o]) return fail(GD_EINVAL, "ligand %d of the submission: restart %d listed twice", i, o);
+        seen[o] = 1;
+      }
+    }
   }
   // pack each ligand into its slot's record, on the context's packing threads for large
   // submissions (contiguous ranges; the first failure in submission order is reported)
@@ -1552,7 +1577,12 @@ gd_status gd_server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t
         pt.err = g_err;  // the message lives in this thread's g_err
         return;
       }
-      const gd::ServeRecHeader hdr{na, R, (int32_t)ne, 0};
+      // every restart listed is the same as none listed: all of them, in order
+      const int32_t nres = restarts && n_restarts[i] < s->O ? n_restarts[i] : 0;
+      if (nres)
+        memcpy(rec + gd::serve_rec_res_dev(s->amax, s->rmax, s->emax), restarts + (size_t)i * res_stride,
+               2 * (size_t)nres);
+      const gd::ServeRecHeader hdr{na, R, (int32_t)ne, nres};
       memcpy(rec, &hdr, sizeof hdr);
       s->nat[slot] = na;
       s->nrot[slot] = R;
@@ -1572,6 +1602,32 @@ gd_status gd_server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t
   *s->h_published = s->next_seq;
   std::atomic_thread_fence(std::memory_order_seq_cst);
   return server_pump(s);
+}
+
+}  // namespace
+
+gd_status gd_server_submit(gd_server* s, const gd_ligand_batch* b, const int32_t* sel, int32_t n_sel,
+                           uint64_t* first_seq) {
+  return server_submit(s, b, sel, n_sel, nullptr, nullptr, 0, first_seq);
+}
+
+gd_status gd_server_submit_restarts(gd_server* s, const gd_ligand_batch* b, const int32_t* sel, int32_t n_sel,
+                                    const uint16_t* restarts, const int32_t* n_restarts, int32_t stride,
+                                    uint64_t* first_seq) {
+  if (!restarts) return fail(GD_EINVAL, "NULL restart lists");
+  return server_submit(s, b, sel, n_sel, restarts, n_restarts, stride, first_seq);
+}
+
+gd_status gd_server_reserve_sms(gd_server* s, int free_sms) {
+  if (!s) return fail(GD_EINVAL, "NULL argument");
+  if (s->launches) return fail(GD_EBUSY, "the server has launched already: reserve SMs before the first submission");
+  if (free_sms < 0 || free_sms >= s->ctx->num_sms)
+    return fail(GD_EINVAL, "free_sms = %d outside [0, %d)", free_sms, s->ctx->num_sms);
+  cudaSetDevice(s->ctx->device);
+  const cudaError_t e = gd::plan_serve(s->args, s->tile, s->grid_in_smem, s->ctx->num_sms - free_sms, &s->cfg);
+  if (e != cudaSuccess) return fail(GD_ECUDA, "server launch shape: %s", cudaGetErrorString(e));
+  g_err.clear();
+  return GD_OK;
 }
 
 gd_status gd_server_poll(gd_server* s, uint64_t seq, gd_result_batch* r, int blocking) {

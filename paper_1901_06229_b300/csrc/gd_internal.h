@@ -134,23 +134,29 @@ struct ServeArgs {
   unsigned long long* parked;           // [warps of the launch] ticket + 1 a warp held when its launch ended idle
   unsigned long long* idle_state;       // this launch's warps: started << 31 | idle or gone | SERVE_CLOSING
                                         // (zeroed before every launch)
+  int32_t* slot_nres;                   // [cap] restarts the slot's ligand searches (O: all of them)
+  uint16_t* slot_res;                   // [cap * O] which ones, when fewer than O
 };
 constexpr unsigned long long SERVE_CLOSING = 1ull << 62;
 constexpr unsigned long long SERVE_STARTED_ONE = 1ull << 31;
 
 // A ligand record in the server's mapped host memory (slot s at rec + s * rec_stride):
 // header, then xyz float4[amax] (preorder, w unused), perm uint8[amax], RotDesc[rmax]
-// (excl_off relative to the record's excluded pairs), excl uint16[emax].
+// (excl_off relative to the record's excluded pairs), excl uint16[emax], restarts
+// uint16[O] (the restarts to search, n_res of them; n_res 0: every restart in order).
 struct ServeRecHeader {
-  int32_t n, R, n_excl, pad;
+  int32_t n, R, n_excl, n_res;
 };
 __host__ __device__ inline long long serve_rec_perm_dev(int amax) { return 16 + 16LL * amax; }
 __host__ __device__ inline long long serve_rec_rots_dev(int amax) { return (16 + 17LL * amax + 15) / 16 * 16; }
 __host__ __device__ inline long long serve_rec_excl_dev(int amax, int rmax) {
   return serve_rec_rots_dev(amax) + 16LL * rmax;
 }
-__host__ __device__ inline long long serve_rec_bytes(int amax, int rmax, int emax) {
-  return (serve_rec_excl_dev(amax, rmax) + 2LL * emax + 127) / 128 * 128;
+__host__ __device__ inline long long serve_rec_res_dev(int amax, int rmax, int emax) {
+  return serve_rec_excl_dev(amax, rmax) + 2LL * emax;
+}
+__host__ __device__ inline long long serve_rec_bytes(int amax, int rmax, int emax, int O) {
+  return (serve_rec_res_dev(amax, rmax, emax) + 2LL * O + 127) / 128 * 128;
 }
 
 // Margin of the reach filter (A).  FP32 rounding moves a rotated atom by ~1e-5 A at

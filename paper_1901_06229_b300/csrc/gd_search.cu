@@ -927,7 +927,8 @@ __device__ void finalize(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(FULL, fsum, off);
-  const unsigned long long nres = a.item_cnt ? (unsigned long long)a.item_cnt[li] : (unsigned long long)O;
+  const unsigned long long nres = SRV ? (unsigned long long)__ldcg(sv->slot_nres + li)
+                                       : (a.item_cnt ? (unsigned long long)a.item_cnt[li] : (unsigned long long)O);
   if (lane == 0) {
     a.best_score[li] = sb;
     a.best_orient[li] = ob;
@@ -1069,7 +1070,8 @@ __device__ void complete(const SearchArgs& a, const uint8_t* sg, const WarpMem& 
   int prev = 0;
   if (lane == 0) prev = atomicAdd(a.done + li, done);
   prev = __shfl_sync(FULL, prev, 0);
-  if (prev + done == (a.item_cnt ? a.item_cnt[li] : a.O)) {
+  const int target = SRV ? __ldcg(sv->slot_nres + li) : (a.item_cnt ? a.item_cnt[li] : a.O);
+  if (prev + done == target) {
     __threadfence();
     finalize<G, SRV>(a, sg, w, li, lane, sv);
   }
@@ -1314,6 +1316,15 @@ __device__ void serve_stage(const SearchArgs& a, const ServeArgs& s, int slot, u
   // the host validated these against the slot sizes; clamped again so that no record can
   // make this warp write outside its slot
   const int n = min(max(h.x, 1), amax), R = min(max(h.y, 0), rmax), ne = min(max(h.z, 0), s.emax);
+  // the restarts to search: a list of n_res of them (validated on the host), else all;
+  // a listed ligand's other restarts are marked unsearched for the reduction over them
+  const int nres = h.w > 0 && h.w < a.O ? h.w : a.O;
+  if (nres < a.O) {
+    const unsigned short* res = reinterpret_cast<const unsigned short*>(rec + serve_rec_res_dev(amax, rmax, s.emax));
+    for (int i = lane; i < nres; i += 32) s.slot_res[(size_t)slot * a.O + i] = (uint16_t)min((int)__ldcv(res + i), a.O - 1);
+    for (int o = lane; o < a.O; o += 32) a.pose_score[(size_t)slot * a.O + o] = NOT_SEARCHED;
+  }
+  if (lane == 0) s.slot_nres[slot] = nres;
   const float4* x0 = reinterpret_cast<const float4*>(rec + 16);
   // centroid and centred coordinates with the pose-setup kernel's arithmetic and order
   float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -1442,12 +1453,19 @@ __global__ void __launch_bounds__(B == BUILD_LEAN ? 256 : 512, B == BUILD_LEAN ?
       }
       break;
     }
+    // item c covers positions [o0, o1) of the ligand's restarts (its list, or all in order);
+    // items past a shorter list have nothing to search
+    const int nres = __ldcg(sv.slot_nres + slot);
+    const int o0 = c * sv.chunk, o1 = o0 + sv.chunk < nres ? o0 + sv.chunk : nres;
+    if (o0 >= o1) continue;
     if (seq != cur_seq) {
       cur_seq = seq;
       e0 = load_ligand<false, true>(a, w, slot, lane);
     }
-    const int o0 = c * sv.chunk, o1 = o0 + sv.chunk < a.O ? o0 + sv.chunk : a.O;
-    for (int o = o0; o < o1; ++o) search_pose<S, G, PRUNE, false, true>(a, sg, w, slot, o, e0, lane);
+    for (int q = o0; q < o1; ++q) {
+      const int o = nres < a.O ? (int)__ldcg(sv.slot_res + (size_t)slot * a.O + q) : q;
+      search_pose<S, G, PRUNE, false, true>(a, sg, w, slot, o, e0, lane);
+    }
     // completed right away: a ligand's result must not wait for this warp's next item
     complete<G, true>(a, sg, w, slot, o1 - o0, lane, &sv);
   }

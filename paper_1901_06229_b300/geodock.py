@@ -31,7 +31,7 @@ EXPORTS = ["gd_create", "gd_destroy", "gd_last_error", "gd_load_pocket", "gd_fre
            "gd_check_batch", "gd_tile_count", "gd_tile_info", "gd_autotune", "gd_dock_batch_noalloc",
            "gd_prepare_batch", "gd_prepare_batch_sel", "gd_measure_peaks", "gd_job_info",
            "gd_server_create", "gd_server_submit", "gd_server_poll", "gd_server_collect", "gd_server_stats",
-           "gd_server_test_hold", "gd_server_destroy"]
+           "gd_server_test_hold", "gd_server_destroy", "gd_server_submit_restarts", "gd_server_reserve_sms"]
 
 
 class GeoDockError(RuntimeError):
@@ -95,6 +95,8 @@ def load():
     L.gd_server_collect.argtypes = [vp, vp, vp, vp, C.c_int, P(C.c_int)]
     L.gd_server_stats.argtypes = [vp] + [P(C.c_uint64)] * 6
     L.gd_server_test_hold.argtypes = [vp, C.c_int64]
+    L.gd_server_submit_restarts.argtypes = [vp, P(LigandBatchC), vp, C.c_int32, vp, vp, C.c_int32, P(C.c_uint64)]
+    L.gd_server_reserve_sms.argtypes = [vp, C.c_int]
     L.gd_server_destroy.argtypes = [vp]
     L.gd_check_batch.argtypes = [P(LigandBatchC), P(SearchParamsC)]
     L.gd_prepare_batch.argtypes = [vp, vp, P(LigandBatchC), P(SearchParamsC), vp, P(vp)]
@@ -413,7 +415,7 @@ class Server:
     The pocket must stay loaded while the server exists."""
 
     def __init__(self, ctx, pocket, params, capacity=4096, max_atoms=256, max_rotamers=64, max_excluded=0,
-                 idle_ms=200, tile=0):
+                 idle_ms=200, tile=0, free_sms=0):
         self.ctx, self.params = ctx, params
         self.h = None
         h = C.c_void_p()
@@ -423,24 +425,33 @@ class Server:
         self.h = h
         ctx._servers.add(self)
         pocket._servers.add(self)
+        if free_sms:  # gd_server_reserve_sms: SMs left to other kernels (before any submission)
+            ctx._check(load().gd_server_reserve_sms(h, int(free_sms)))
         self.capacity = capacity
         self._sizes = {}  # seq -> (atoms, rotamers) of ligands not yet returned in full
 
-    def submit(self, batch, sel=None) -> int:
+    def submit(self, batch, sel=None, restarts=None, n_restarts=None) -> int:
         """Submit ligands sel of batch (all when None); returns the first sequence number
-        (GeoDockError GD_EBUSY when there are not enough free slots)."""
+        (GeoDockError GD_EBUSY when there are not enough free slots).  With restarts (a
+        [n, stride] array of restart ids) and n_restarts ([n]), ligand i searches only
+        restarts[i, :n_restarts[i]] (gd_server_submit_restarts)."""
         arrs = _BatchArrays(batch)
         first = C.c_uint64()
-        if sel is None:
-            n = batch.n_ligands
-            self.ctx._check(load().gd_server_submit(self.h, C.byref(arrs.c), None, n, C.byref(first)))
-            idx = range(n)
-        else:
+        n = batch.n_ligands if sel is None else len(sel)
+        selp = None
+        if sel is not None:
             sel = np.ascontiguousarray(sel, np.int32)
-            n = len(sel)
-            self.ctx._check(load().gd_server_submit(self.h, C.byref(arrs.c), C.c_void_p(_addr(sel)), n,
-                                                    C.byref(first)))
-            idx = sel
+            selp = C.c_void_p(_addr(sel))
+        if restarts is None:
+            self.ctx._check(load().gd_server_submit(self.h, C.byref(arrs.c), selp, n, C.byref(first)))
+        else:
+            res = np.ascontiguousarray(restarts, np.uint16)
+            cnt = np.ascontiguousarray(n_restarts, np.int32)
+            assert res.ndim == 2 and res.shape[0] == n and cnt.shape == (n,)
+            self.ctx._check(load().gd_server_submit_restarts(self.h, C.byref(arrs.c), selp, n,
+                                                             C.c_void_p(_addr(res)), C.c_void_p(_addr(cnt)),
+                                                             int(res.shape[1]), C.byref(first)))
+        idx = range(n) if sel is None else sel
         na, nr = np.diff(batch.atom_off), np.diff(batch.rot_off)
         for k, i in enumerate(idx):
             self._sizes[first.value + k] = (int(na[i]), int(nr[i]))

@@ -148,6 +148,64 @@ def test_ligands_published_while_idle_warps_park_their_tickets(ctx):
     pk.free()
 
 
+def test_restart_lists_match_the_proposed_search(ctx):
+    """Ligands submitted with restart lists (gd_server_submit_restarts) search only those
+    restarts: every result is bit for bit what gd_job_launch_proposed gives when its
+    selection picks the same restarts -- predictions made so that the top 16 are a
+    ligand's list of 16, or so that the top-16 spread sends it to its best 128, its list
+    of 128 -- alone and in the mix, with SMs left out of the launch."""
+    import torch
+    L, O = 64, 256
+    w = synth.workload_stream(L, seed_offset=74)
+    pk = ctx.load_pocket(w.pocket)
+    rng = np.random.default_rng(5)
+    lists = np.zeros((L, 128), np.uint16)
+    counts = np.where(rng.random(L) < 0.25, 128, 16).astype(np.int32)
+    pred = np.zeros((L, O), np.float32)
+    for i in range(L):
+        k = int(counts[i])
+        chosen = rng.choice(O, size=k, replace=False)
+        lists[i, :k] = chosen
+        # decreasing in list order: a spread of 0.015 over a list of 16 (no fallback at
+        # margin 0.5), of 1.05 over the first 16 of a list of 128 (fallback to its 128)
+        pred[i, chosen] = (1.0 - 0.001 * np.arange(k)) if k == 16 else (10.0 - 0.07 * np.arange(k))
+    job = ctx.prepare_batch(pk, w.batch, w.params)
+    y = torch.tensor(pred.reshape(-1), device="cuda")
+    job.launch_proposed(y, 16, 0.5, 1, torch.cuda.current_stream(), k_fallback=128)
+    job.download(torch.cuda.current_stream())
+    ref = job.fetch()
+    cnt, _ = job.selection()
+    np.testing.assert_array_equal(cnt, counts)
+    job.free()
+    srv = gdk.Server(ctx, pk, w.params, capacity=128, max_atoms=256, max_rotamers=48, free_sms=16)
+    with pytest.raises(gdk.GeoDockError) as e:  # a restart listed twice
+        bad = lists[:1].copy()
+        bad[0, 1] = bad[0, 0]
+        srv.submit(w.batch, [0], restarts=bad, n_restarts=counts[:1])
+    assert e.value.status == gdk.GD_EINVAL
+    q = srv.submit(w.batch, [0], restarts=lists[:1], n_restarts=counts[:1])
+    seqs, got = {q: 0}, {q: srv.poll(q)}  # ligand 0 alone first
+    for wave in (np.arange(1, 33), np.arange(33, L)):  # then the rest in two overlapping waves
+        first = srv.submit(w.batch, wave, restarts=lists[wave], n_restarts=counts[wave])
+        for k, i in enumerate(wave):
+            seqs[first + k] = int(i)
+    got.update({qq: srv.poll(qq) for qq in seqs if qq != q})
+    with pytest.raises(gdk.GeoDockError) as e:  # SMs can only be reserved before the first launch
+        ctx._check(gdk.load().gd_server_reserve_sms(srv.h, 8))
+    assert e.value.status == gdk.GD_EBUSY
+    print(srv.stats())
+    srv.close()
+    ao, ro = np.asarray(w.batch.atom_off), np.asarray(w.batch.rot_off)
+    for qq, i in seqs.items():
+        view = dict(best_score=ref["best_score"][i:i + 1], best_orient=ref["best_orient"][i:i + 1],
+                    best_angle=ref["best_angle"][ro[i]:ro[i + 1]], best_xyz=ref["best_xyz"][ao[i]:ao[i + 1]],
+                    evals=ref["evals"][i:i + 1], pair_tests=ref["pair_tests"][i:i + 1],
+                    atom_moves=ref["atom_moves"][i:i + 1], reach_tests=ref["reach_tests"][i:i + 1],
+                    best_rigid=ref["best_rigid"][i:i + 1])
+        _same(got[qq], view, f"ligand {i} ({counts[i]} restarts)")
+    pk.free()
+
+
 def test_a_held_slot_times_out_and_the_context_stays_usable(ctx):
     w = synth.workload_stream(8, seed_offset=72)
     pk = ctx.load_pocket(w.pocket)
