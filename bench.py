@@ -61,6 +61,10 @@ VAL_RECALL_TARGET = 0.993
 # the serving sub-record of the default line: runs x seconds of Poisson arrivals at --rate
 SERVE_SUB_REPEATS = 3
 SERVE_SUB_SECONDS = 2.0
+# SMs the learned device-queue screen leaves to its proposer's kernels: with 16 their
+# stages ran 10-20x slower beside a busy search launch than alone, with 40 as fast as
+# alone, and at 100k ligands/s the pruned search needs a few percent of the GPU
+SERVE_LEARNED_FREE_SMS = 40
 # FP32 operations the kernel executes (the "executed" roofline figure)
 EXEC_OPS_PER_PAIR = 3        # 2 FFMA (|x_a - x_b|^2 + (cos-1) P + sin Q) + FMNMX
 EXEC_OPS_PER_ATOM_MOVE = 6   # turn about the bond axis (6 FFMA; coordinates are grid units)
@@ -666,13 +670,72 @@ def serve_record(args, world, rank, local, repeats, seconds):
         "server": st, "runs": runs, "clocks": clk.summary()}
 
 
+def run_serve_learned(args, world, rank, local):
+    rec = serve_learned_record(args, world, rank, local, args.stream_repeats, args.stream_seconds)
+    if rec is not None:
+        print(json.dumps(rec))
+
+
+def serve_learned_record(args, world, rank, local, repeats, seconds):
+    """The learned screen on the device queue: Poisson arrivals proposed in batches
+    (features, network, top-16 with the spread fallback to the best 128) on SMs the
+    server leaves free, each ligand then joining the running search launch with its
+    restart list; ligands/s and per-ligand latency over `repeats` runs of at least
+    `seconds` of arrivals, median and range."""
+    import torch
+    from paper_1901_06229_b300 import geodock as gdk, proposer, serve
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    n = args.ligands or 100000
+    w = synth.workload_stream(n, seed_offset=53 + 10 * rank)
+    ctx = gdk.Context(dev, mem_budget_bytes=8 << 30)
+    pk = ctx.load_pocket(w.pocket)
+    net, margin, info = proposer.fit(ctx, pk, target=VAL_RECALL_TARGET, k_fallback=K_FALLBACK)
+    R = np.diff(w.batch.rot_off)
+    free_sms = SERVE_LEARNED_FREE_SMS
+    scr = serve.QueueScreen(ctx, pk, w.params, net, k=16, margin=margin, k_fallback=K_FALLBACK,
+                            max_batch=args.max_batch, free_sms=free_sms, max_rotamers=int(R.max()),
+                            warm_library=w.batch)
+    warm = min(2048, n)
+    scr.run(synth.Workload("warm", w.pocket, w.batch.subset(np.arange(warm)), w.params), np.zeros(warm))
+    n_req = max(n, int(np.ceil(args.rate * seconds)))
+    runs = []
+    with ClockSampler(dev) as clk:
+        for rep in range(repeats):
+            arr = serve.poisson_arrivals(n_req, args.rate, seed=rank + 1000 * rep)
+            runs.append(scr.run(w, arr, ligand_of=np.arange(n_req) % n).summary())
+    st = scr.srv.stats()
+    scr.close()
+    pk.free()
+    ctx.close()
+    if rank != 0:
+        return None
+
+    def stat(key):
+        v = np.array([r[key] for r in runs])
+        return {"median": float(np.median(v)), "min": float(v.min()), "max": float(v.max())}
+    return {
+        "metric": "ligands/s and per-ligand latency (learned screen on the device queue, 1 B300)",
+        "value": stat("ligands_per_s")["median"], "unit": "ligands/s", "n_gpus": world, "steps": repeats,
+        "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 search / bf16 network", "data": "synthetic (seeded generators)",
+        "config": workload_config(w, "resident pocket; no flush (serving)") | {
+            "arrivals": f"Poisson, {args.rate:g} ligands/s", "requests_per_run": n_req, "runs": repeats,
+            "k": 16, "k_fallback": K_FALLBACK, "margin": margin, "free_sms": free_sms, "server_tile": 8,
+            "max_batch": args.max_batch, "proposer": info},
+        "ligands_per_s": stat("ligands_per_s"), "latency_ms": {"p50": stat("p50_ms"), "p99": stat("p99_ms")},
+        "restarts_per_ligand": stat("restarts_per_ligand"), "server": st, "runs": runs, "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "single", "learned", "learned24", "stream", "serve", "mlp"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "large", "single", "learned", "learned24", "stream", "serve", "serve_learned",
+                             "mlp"])
     ap.add_argument("--rate", type=float, default=100000.0, help="stream: Poisson arrival rate (ligands/s)")
     ap.add_argument("--max-batch", type=int, default=2048, help="stream: largest admitted batch")
     ap.add_argument("--stream-seconds", type=float, default=3.0, help="stream: least offered duration of a run")
@@ -698,6 +761,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, world, rank, local)
+        return
+    if args.workload == "serve_learned":
+        run_serve_learned(args, world, rank, local)
         return
     if args.workload == "mlp":
         run_mlp(args, world, rank, local)

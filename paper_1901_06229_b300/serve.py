@@ -182,3 +182,121 @@ def poisson_arrivals(n, rate, seed=0):
         t += -np.log(1.0 - rng.uniform()) / rate
         out[i] = t
     return out
+
+
+class QueueScreen:
+    """The learned screen on the device queue: arriving ligands are proposed in batches
+    (features -> proposer network -> top-k_fallback restarts by prediction, the k best
+    unless the spread pred(1st) - pred(k-th) exceeds the margin, then the k_fallback best:
+    the selection rule of the batched learned path) on SMs the server leaves free, and each
+    ligand then joins the running search launch with its restart list
+    (gd_server_submit_restarts); results come back per ligand as they finish.  The server
+    runs a wide tile (one block of 16 warps per SM, all of its registers), so the reserved
+    SMs stay free for the proposer's kernels.
+
+    A proposal batch is padded to one of a few sizes (powers of two from 64 up to
+    max_batch, the rows past the batch discarded), each prepared once before the server
+    starts (warm_library: a batch holding at least one ligand), so that the context's
+    memory caches and torch's allocator serve every later batch without allocating: an
+    allocation waits for the running search launch to end (it ends only after idle_ms
+    without work), which put 0.2 s into a batch's latency."""
+
+    def __init__(self, ctx, pocket, params, net, k=16, margin=1e30, k_fallback=128, max_batch=1024, free_sms=16,
+                 tile=8, capacity=8192, max_rotamers=64, idle_ms=200, warm_library=None):
+        import torch
+        self.ctx, self.pk, self.params, self.net = ctx, pocket, params, net
+        self.k, self.margin, self.kf = k, margin, min(k_fallback, params.n_orient)
+        self.max_batch = max_batch
+        self.srv = gdk.Server(ctx, pocket, params, capacity=capacity, max_atoms=256, max_rotamers=max_rotamers,
+                              idle_ms=idle_ms, tile=tile, free_sms=free_sms)
+        self.stream = torch.cuda.Stream()
+        rows = max_batch * params.n_orient
+        self.X = torch.empty((rows, 48), dtype=torch.bfloat16, device="cuda")
+        self.y = torch.empty(rows, device="cuda")
+        self.sizes = sorted({min(max_batch, 1 << b) for b in range(6, 16) if (1 << (b - 1)) < max_batch})
+        if warm_library is not None:
+            for n in self.sizes:
+                self.propose(warm_library, np.zeros(n, np.int64))
+
+    def _padded(self, n):
+        return next(s for s in self.sizes if s >= n)
+
+    def propose(self, batch, ids):
+        """Restart lists [n, k_fallback] (uint16) and their lengths [n] for ligands ids."""
+        import torch
+        O = self.params.n_orient
+        n = len(ids)
+        if n > self.max_batch:
+            parts = [self.propose(batch, ids[i:i + self.max_batch]) for i in range(0, n, self.max_batch)]
+            return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
+        m = self._padded(n)  # padded with copies of the first ligand
+        sel = np.concatenate([np.asarray(ids, np.int64), np.full(m - n, ids[0], np.int64)])
+        job = self.ctx.prepare_batch(self.pk, batch, self.params, stream=self.stream, sel=sel)
+        with torch.cuda.stream(self.stream):
+            X, y = self.X[:m * O], self.y[:m * O]
+            job.features(x_bf16=X, stream=self.stream)
+            self.net.predict(X, y)
+            val, idx = torch.topk(y.view(m, O), self.kf, dim=1)
+            fall = (val[:, 0] - val[:, self.k - 1]) > self.margin
+            cnt = torch.where(fall, self.kf, self.k).to(torch.int32)
+            lists, cnt = idx.to(torch.int32).cpu().numpy().astype(np.uint16), cnt.cpu().numpy()
+        job.free()
+        return lists[:n], cnt[:n]
+
+    def run(self, workload, arrival_times, clock=time.perf_counter, ligand_of=None):
+        """Serve one request per arrival time (as Screen.run)."""
+        N = len(arrival_times)
+        ligand_of = np.arange(N) if ligand_of is None else np.asarray(ligand_of, np.int64)
+        order = np.argsort(arrival_times, kind="stable")
+        res = ScreenResult(best_score=np.zeros(N, np.uint32), best_orient=np.zeros(N, np.int32),
+                           arrival=np.asarray(arrival_times, np.float64).copy(), done=np.zeros(N),
+                           restarts=np.zeros(N, np.int32))
+        pending = deque()
+        req_of = {}  # server sequence number -> request
+        nxt = finished = 0
+        t0 = clock()
+        while finished < N:
+            now = clock() - t0
+            while nxt < N and arrival_times[order[nxt]] <= now:
+                pending.append(order[nxt])
+                nxt += 1
+            progressed = False
+            if pending:
+                take = [pending.popleft() for _ in range(min(self.max_batch, len(pending)))]
+                ids = np.array(take, np.int64)
+                lists, cnt = self.propose(workload.batch, ligand_of[ids])
+                while True:
+                    try:
+                        first = self.srv.submit(workload.batch, ligand_of[ids], restarts=lists, n_restarts=cnt)
+                        break
+                    except gdk.GeoDockError as e:  # no free slot: return finished results first
+                        if e.status != gdk.GD_EBUSY:
+                            raise
+                        finished += self._collect(res, req_of, clock, t0)
+                for j, r in enumerate(take):
+                    req_of[first + j] = r
+                res.restarts[ids] = cnt
+                res.batches += 1
+                res.batch_sizes.append(len(ids))
+                progressed = True
+            got = self._collect(res, req_of, clock, t0)
+            finished += got
+            if not progressed and not got:
+                wait = 5e-5
+                if nxt < N and not req_of:
+                    wait = max(0.0, min(2e-4, arrival_times[order[nxt]] - (clock() - t0)))
+                time.sleep(wait)
+        return res
+
+    def _collect(self, res, req_of, clock, t0):
+        seqs, sc, ob = self.srv.collect(8192)
+        if not len(seqs):
+            return 0
+        t = clock() - t0
+        for q, a, b in zip(seqs.tolist(), sc.tolist(), ob.tolist()):
+            r = req_of.pop(q)
+            res.best_score[r], res.best_orient[r], res.done[r] = a, b, t
+        return len(seqs)
+
+    def close(self):
+        self.srv.close()

@@ -177,3 +177,32 @@ def test_concurrent_jobs_on_one_context(setup):
     for t in range(4):
         for key in ("best_score", "best_orient", "best_angle", "best_xyz"):
             np.testing.assert_array_equal(got[t][key], alone[t][key], err_msg=f"{key} of part {t}")
+
+
+def test_device_queue_screen_searches_the_proposed_restarts(setup):
+    """The learned screen on the device queue (QueueScreen: proposer on SMs the server
+    leaves free, each ligand joining the running launch with its restart list): every
+    result is the maximum over exactly the restarts its proposal chose (ties to the
+    smaller restart), against the exhaustive per-restart scores, with the fallback rule
+    giving k or k_fallback restarts."""
+    ctx, pk, w, net, margin = setup
+    L = 160
+    sub = synth.Workload("sub", w.pocket, w.batch.subset(np.arange(L)), w.params)
+    full = ctx.dock_batch(pk, sub.batch, sub.params, debug=True)
+    scores = full.fetch()["orient_score"].reshape(L, -1).astype(np.int64)
+    full.free()
+    scr = serve.QueueScreen(ctx, pk, w.params, net, k=16, margin=margin, k_fallback=128, max_batch=48,
+                            free_sms=16, max_rotamers=int(np.diff(w.batch.rot_off).max()))
+    arr = serve.poisson_arrivals(L, 20000.0, seed=4)
+    res = scr.run(sub, arr)
+    print(res.summary(), scr.srv.stats())
+    lists, cnt = scr.propose(sub.batch, np.arange(L))
+    scr.close()
+    np.testing.assert_array_equal(res.restarts, cnt)
+    assert set(np.unique(cnt)) <= {16, 128} and 0 < np.mean(cnt == 128) < 1
+    for i in range(L):
+        chosen = lists[i, :cnt[i]].astype(np.int64)
+        s = scores[i, chosen]
+        best = s.max()
+        assert res.best_score[i] == best, i
+        assert res.best_orient[i] == chosen[s == best].min(), i
