@@ -78,6 +78,10 @@ ALGORITHMIC_WORK = os.path.join(ROOT, "oracle", "algorithmic_work.json")
 # and by (workload, tile): reported only while the kernel is the one that was measured.
 SEARCH_KERNEL_SOURCES = ("paper_1901_06229_b300/csrc/gd_search.cu", "paper_1901_06229_b300/csrc/gd_internal.h")
 MEASURED_TRAFFIC = {
+    "d330ce6744aaba88": {("batched-4096lig-64grid", 14): 4557056 + 1178368,
+                         ("batched-4096lig-64grid", 15): 4860160 + 1211904,
+                         ("large-512lig-128grid", 16): 2730240 + 9728,
+                         ("large-512lig-128grid", 18): 3069696 + 9216},
     "0dd17a1cd3e68422": {("batched-4096lig-64grid", 14): 4561408 + 1121024,
                          ("batched-4096lig-64grid", 15): 4743424 + 1152512,
                          ("large-512lig-128grid", 16): 2742528 + 8960,
@@ -116,6 +120,10 @@ MEASURED_TRAFFIC = {
 # is issue-bound, so its instruction issue rate against the schedulers' peak (4 per SM
 # per clock) is the roofline that binds it.
 MEASURED_INSTRUCTIONS = {
+    "d330ce6744aaba88": {("batched-4096lig-64grid", 14): 8462969358,
+                         ("batched-4096lig-64grid", 15): 8463073248,
+                         ("large-512lig-128grid", 16): 15525958491,
+                         ("large-512lig-128grid", 18): 15526017451},
     "0dd17a1cd3e68422": {("batched-4096lig-64grid", 14): 8462969337,
                          ("batched-4096lig-64grid", 15): 8463073215,
                          ("large-512lig-128grid", 16): 15525958569,
