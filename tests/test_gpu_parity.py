@@ -137,7 +137,8 @@ def dense_exclusion_ligand(seed, min_sep, n_atoms=256, n_rot=128):
 
 @pytest.mark.parametrize("case", ["ragged_angles", "one_angle", "odd_euler", "reps2", "min_sep4",
                                   "bump25", "rigid_only", "two_atoms", "max_atoms", "rigid_sweep",
-                                  "rigid_sweep_span2", "max_exclusions", "max_angles"])
+                                  "rigid_sweep_span2", "max_exclusions", "max_angles", "many_restarts",
+                                  "max_reps"])
 def test_edge_cases(ctx, case):
     pocket = textured_pocket()
     rng = lambda s: synth.SplitMix64(synth.ligand_seed(4242, s))
@@ -170,6 +171,10 @@ def test_edge_cases(ctx, case):
         pocket, params = big, synth.SearchParams(1, 2, 1, 64)
     elif case == "max_angles":  # GD_MAX_ANGLES: a step sweeps its angles in 16 passes of 64
         params = synth.SearchParams(1, 2, 1, 1024)
+    elif case == "many_restarts":  # 1,000 restarts (10 x 10 x 10), ragged against the work chunks
+        params = synth.SearchParams(10, 10, 10, 16)
+    elif case == "max_reps":  # GD_MAX_REPS repetitions of the rotamer loop
+        params = synth.SearchParams(1, 2, 1, 24, repetitions=16)
     elif case == "max_exclusions":  # 128 rotamers, ~7.7k excluded pairs: ~205 KB of warp buffers
         lig, n_excl = dense_exclusion_ligand(60, 7)
         assert len(lig.rot_bond) == 128 and n_excl > 7000
