@@ -186,7 +186,7 @@ def poisson_arrivals(n, rate, seed=0):
 
 class QueueScreen:
     """The learned screen on the device queue: arriving ligands are proposed in batches
-    (features -> proposer network -> top-k_fallback restarts by prediction, the k best
+    (features -> proposer network -> restarts by prediction, ties to the smaller id, the k best
     unless the spread pred(1st) - pred(k-th) exceeds the margin, then the k_fallback best:
     the selection rule of the batched learned path) on SMs the server leaves free, and each
     ligand then joins the running search launch with its restart list
@@ -236,7 +236,9 @@ class QueueScreen:
             X, y = self.X[:m * O], self.y[:m * O]
             job.features(x_bf16=X, stream=self.stream)
             self.net.predict(X, y)
-            val, idx = torch.topk(y.view(m, O), self.kf, dim=1)
+            # larger prediction first, ties to the smaller restart (the device selection's order)
+            val, idx = torch.sort(y.view(m, O), dim=1, descending=True, stable=True)
+            val, idx = val[:, :self.kf], idx[:, :self.kf]
             fall = (val[:, 0] - val[:, self.k - 1]) > self.margin
             cnt = torch.where(fall, self.kf, self.k).to(torch.int32)
             lists, cnt = idx.to(torch.int32).cpu().numpy().astype(np.uint16), cnt.cpu().numpy()
