@@ -61,10 +61,10 @@ VAL_RECALL_TARGET = 0.993
 # the serving sub-record of the default line: runs x seconds of Poisson arrivals at --rate
 SERVE_SUB_REPEATS = 3
 SERVE_SUB_SECONDS = 2.0
-# SMs the learned device-queue screen leaves to its proposer's kernels: with 16 their
-# stages ran 10-20x slower beside a busy search launch than alone, with 40 as fast as
-# alone, and at 100k ligands/s the pruned search needs a few percent of the GPU
-SERVE_LEARNED_FREE_SMS = 40
+# SMs the learned device-queue screen leaves to its proposer's kernels: beside a busy
+# search launch on the rest, a small proposal took 33 ms with 40 left free and 0.9 ms
+# with 120, and at 100k ligands/s the pruned search needs a small part of the GPU
+SERVE_LEARNED_FREE_SMS = 100
 # FP32 operations the kernel executes (the "executed" roofline figure)
 EXEC_OPS_PER_PAIR = 3        # 2 FFMA (|x_a - x_b|^2 + (cos-1) P + sin Q) + FMNMX
 EXEC_OPS_PER_ATOM_MOVE = 6   # turn about the bond axis (6 FFMA; coordinates are grid units)

@@ -192,58 +192,80 @@ class QueueScreen:
     ligand then joins the running search launch with its restart list
     (gd_server_submit_restarts); results come back per ligand as they finish.  The server
     runs a wide tile (one block of 16 warps per SM, all of its registers), so the reserved
-    SMs stay free for the proposer's kernels.
+    SMs stay free for the proposer's kernels.  Up to max_inflight proposals run at once,
+    each on its own stream with its own buffers; a proposal's restart lists are copied to
+    pinned host memory and submitted once its event has completed, so the host loop never
+    waits for the device.
 
     A proposal batch is padded to one of a few sizes (powers of two from 64 up to
-    max_batch, the rows past the batch discarded), each prepared once before the server
-    starts (warm_library: a batch holding at least one ligand), so that the context's
-    memory caches and torch's allocator serve every later batch without allocating: an
-    allocation waits for the running search launch to end (it ends only after idle_ms
-    without work), which put 0.2 s into a batch's latency."""
+    max_batch, the rows past the batch discarded), each prepared once per stream before the
+    server starts (warm_library: a batch holding at least one ligand), so that the
+    context's memory caches and torch's allocator serve every later batch without
+    allocating: an allocation waits for the running search launch to end (it ends only
+    after idle_ms without work), which put 0.2 s into a batch's latency."""
 
     def __init__(self, ctx, pocket, params, net, k=16, margin=1e30, k_fallback=128, max_batch=1024, free_sms=16,
-                 tile=8, capacity=8192, max_rotamers=64, idle_ms=200, warm_library=None):
+                 tile=8, capacity=8192, max_rotamers=64, idle_ms=200, warm_library=None, max_inflight=3):
         import torch
         self.ctx, self.pk, self.params, self.net = ctx, pocket, params, net
         self.k, self.margin, self.kf = k, margin, min(k_fallback, params.n_orient)
         self.max_batch = max_batch
         self.srv = gdk.Server(ctx, pocket, params, capacity=capacity, max_atoms=256, max_rotamers=max_rotamers,
                               idle_ms=idle_ms, tile=tile, free_sms=free_sms)
-        self.stream = torch.cuda.Stream()
         rows = max_batch * params.n_orient
-        self.X = torch.empty((rows, 48), dtype=torch.bfloat16, device="cuda")
-        self.y = torch.empty(rows, device="cuda")
+        self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
+        self.X = [torch.empty((rows, 48), dtype=torch.bfloat16, device="cuda") for _ in range(max_inflight)]
+        self.y = [torch.empty(rows, device="cuda") for _ in range(max_inflight)]
+        self.h_lists = [torch.empty((max_batch, self.kf), dtype=torch.int32, pin_memory=True)
+                        for _ in range(max_inflight)]
+        self.h_cnt = [torch.empty(max_batch, dtype=torch.int32, pin_memory=True) for _ in range(max_inflight)]
         self.sizes = sorted({min(max_batch, 1 << b) for b in range(6, 16) if (1 << (b - 1)) < max_batch})
         if warm_library is not None:
-            for n in self.sizes:
-                self.propose(warm_library, np.zeros(n, np.int64))
+            for slot in range(max_inflight):
+                for n in self.sizes:
+                    job, ev = self._launch(warm_library, np.zeros(n, np.int64), slot)
+                    ev.synchronize()
+                    job.free()
 
     def _padded(self, n):
         return next(s for s in self.sizes if s >= n)
 
-    def propose(self, batch, ids):
-        """Restart lists [n, k_fallback] (uint16) and their lengths [n] for ligands ids."""
+    def _launch(self, batch, ids, slot):
+        """Queue the proposal of ligands ids on stream `slot`: (job, completion event)."""
         import torch
         O = self.params.n_orient
+        n = len(ids)
+        m = self._padded(n)  # padded with copies of the first ligand
+        sel = np.concatenate([np.asarray(ids, np.int64), np.full(m - n, ids[0], np.int64)])
+        st = self.streams[slot]
+        job = self.ctx.prepare_batch(self.pk, batch, self.params, stream=st, sel=sel)
+        with torch.cuda.stream(st):
+            X, y = self.X[slot][:m * O], self.y[slot][:m * O]
+            job.features(x_bf16=X, stream=st)
+            self.net.predict(X, y)
+            # larger prediction first, ties to the smaller restart (the device selection's order)
+            val, idx = torch.sort(y.view(m, O), dim=1, descending=True, stable=True)
+            fall = (val[:, 0] - val[:, self.k - 1]) > self.margin
+            self.h_lists[slot][:m].copy_(idx[:, :self.kf].to(torch.int32), non_blocking=True)
+            self.h_cnt[slot][:m].copy_(torch.where(fall, self.kf, self.k).to(torch.int32), non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return job, ev
+
+    def _lists(self, slot, n):
+        return self.h_lists[slot][:n].numpy().astype(np.uint16), self.h_cnt[slot][:n].numpy().copy()
+
+    def propose(self, batch, ids):
+        """Restart lists [n, k_fallback] (uint16) and their lengths [n] for ligands ids
+        (synchronously, on the first stream)."""
         n = len(ids)
         if n > self.max_batch:
             parts = [self.propose(batch, ids[i:i + self.max_batch]) for i in range(0, n, self.max_batch)]
             return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
-        m = self._padded(n)  # padded with copies of the first ligand
-        sel = np.concatenate([np.asarray(ids, np.int64), np.full(m - n, ids[0], np.int64)])
-        job = self.ctx.prepare_batch(self.pk, batch, self.params, stream=self.stream, sel=sel)
-        with torch.cuda.stream(self.stream):
-            X, y = self.X[:m * O], self.y[:m * O]
-            job.features(x_bf16=X, stream=self.stream)
-            self.net.predict(X, y)
-            # larger prediction first, ties to the smaller restart (the device selection's order)
-            val, idx = torch.sort(y.view(m, O), dim=1, descending=True, stable=True)
-            val, idx = val[:, :self.kf], idx[:, :self.kf]
-            fall = (val[:, 0] - val[:, self.k - 1]) > self.margin
-            cnt = torch.where(fall, self.kf, self.k).to(torch.int32)
-            lists, cnt = idx.to(torch.int32).cpu().numpy().astype(np.uint16), cnt.cpu().numpy()
+        job, ev = self._launch(batch, ids, 0)
+        ev.synchronize()
         job.free()
-        return lists[:n], cnt[:n]
+        return self._lists(0, n)
 
     def run(self, workload, arrival_times, clock=time.perf_counter, ligand_of=None):
         """Serve one request per arrival time (as Screen.run)."""
@@ -254,6 +276,9 @@ class QueueScreen:
                            arrival=np.asarray(arrival_times, np.float64).copy(), done=np.zeros(N),
                            restarts=np.zeros(N, np.int32))
         pending = deque()
+        inflight = []  # (slot, requests, job, event), oldest first
+        free = list(range(len(self.streams)))
+        ready = deque()  # (requests, restart lists, counts) proposed but not yet submitted
         req_of = {}  # server sequence number -> request
         nxt = finished = 0
         t0 = clock()
@@ -263,29 +288,39 @@ class QueueScreen:
                 pending.append(order[nxt])
                 nxt += 1
             progressed = False
-            if pending:
-                take = [pending.popleft() for _ in range(min(self.max_batch, len(pending)))]
-                ids = np.array(take, np.int64)
-                lists, cnt = self.propose(workload.batch, ligand_of[ids])
-                while True:
-                    try:
-                        first = self.srv.submit(workload.batch, ligand_of[ids], restarts=lists, n_restarts=cnt)
-                        break
-                    except gdk.GeoDockError as e:  # no free slot: return finished results first
-                        if e.status != gdk.GD_EBUSY:
-                            raise
-                        finished += self._collect(res, req_of, clock, t0)
-                for j, r in enumerate(take):
-                    req_of[first + j] = r
-                res.restarts[ids] = cnt
+            if pending and free:
+                take = np.array([pending.popleft() for _ in range(min(self.max_batch, len(pending)))], np.int64)
+                slot = free.pop()
+                job, ev = self._launch(workload.batch, ligand_of[take], slot)
+                inflight.append((slot, take, job, ev))
                 res.batches += 1
-                res.batch_sizes.append(len(ids))
+                res.batch_sizes.append(len(take))
+                progressed = True
+            while inflight and inflight[0][3].query():  # proposals complete in stream order per slot
+                slot, take, job, ev = inflight.pop(0)
+                lists, cnt = self._lists(slot, len(take))
+                job.free()
+                free.append(slot)
+                ready.append((take, lists, cnt))
+                progressed = True
+            while ready:
+                take, lists, cnt = ready[0]
+                try:
+                    first = self.srv.submit(workload.batch, ligand_of[take], restarts=lists, n_restarts=cnt)
+                except gdk.GeoDockError as e:  # no free slot: return finished results first
+                    if e.status != gdk.GD_EBUSY:
+                        raise
+                    break
+                ready.popleft()
+                for j, r in enumerate(take.tolist()):
+                    req_of[first + j] = r
+                res.restarts[take] = cnt
                 progressed = True
             got = self._collect(res, req_of, clock, t0)
             finished += got
             if not progressed and not got:
                 wait = 5e-5
-                if nxt < N and not req_of:
+                if nxt < N and not req_of and not inflight:
                     wait = max(0.0, min(2e-4, arrival_times[order[nxt]] - (clock() - t0)))
                 time.sleep(wait)
         return res
